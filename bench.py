@@ -1,0 +1,360 @@
+"""Benchmark: one step = one full compressed-sensing reconstruction of a 1.1 mm slice.
+
+Workload (paper-scale plain method): 200x200 image (1.1 mm, FOV 220 mm), 32 coils,
+single-shot spiral at R = 4 with 24 000 samples (1 us dwell), 3rd-order spherical-
+harmonic field (16 terms) plus B0 within +-150 Hz, Daubechies-4 wavelet with 4 levels,
+lambda = 1e-3 ||A^H y||_inf, 30 power iterations for L_f, 50 FISTA iterations.
+Synthetic, seeded inputs stand in for the paper's in-vivo data.
+
+Metric: A_exp + A_exp^H throughput in Gvoxel*sample*coil/s = (applications per step x
+nr x nt x nc) / step time; seconds per slice reconstruction is reported beside it.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "A_exp+A_exp^H Gvoxel*sample*coil/s; s per 1.1mm slice recon, TC vs FP32"
+UNIT = "Gvoxel*sample*coil/s"
+WORKLOAD = "slice_200: 200x200 1.1mm, 32 coils, 24000-sample R=4 spiral, 3rd-order SH + B0, db4 J=4, 50 FISTA + 30 power iterations"
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis:
+            ids = [v.strip() for v in vis.split(",") if v.strip()]
+            self.gpu = ids[gpu_index] if gpu_index < len(ids) else str(gpu_index)
+        else:
+            self.gpu = str(gpu_index)
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [s.strip() for s in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def fp32_alu_peak_tflops(sm_mhz: float) -> float:
+    """FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop per FMA x SM clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def launches_per_recon(levels: int, iters: int, n_power: int) -> int:
+    """Kernel launches issued by cs_recon (mirrors the host sequence in recon.cu)."""
+    prep = 4 + 1                      # coefficients, tiles, reference phases, coil maps; y transpose
+    power = 2 + 2 + n_power * 7 + 1   # A^H y; initial norm+scale; per iteration A^H A (5) + dot + scale; finalize
+    fista = iters * (5 + 2 * levels)  # coil weight, fwd, fwd reduce, adj, adj reduce; J fwd + J inv levels
+    return prep + power + fista
+
+
+def cpu_sample(p, y, seconds: float):
+    """Time the oracle (as it stands) on a bounded sample of the workload's operator
+    applications: forward rows and adjoint voxels in equal numbers of voxel*sample*coil."""
+    import oracle
+    nr, nt, nc = p["nx"] * p["ny"], p["nt"], p["nc"]
+    rng = np.random.default_rng(0)
+    done = 0.0
+    t0 = time.perf_counter()
+    rows = 0
+    while time.perf_counter() - t0 < seconds:
+        ts = rng.choice(nt, 16, replace=False)
+        oracle.forward_rows(p, p["x_gt"], ts)
+        rs = rng.choice(nr, int(round(16 * nr / nt)), replace=False)
+        oracle.adjoint_rows(p, y, rs)
+        done += 16 * nr * nc + len(rs) * nt * nc
+        rows += 16
+    dt = time.perf_counter() - t0
+    return done / dt / 1e9, dt, rows
+
+
+def run_reference(args):
+    rank, world, local = dist_info()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2211_07532_gb300 import synth
+    oracle.build()
+    p = synth.slice_200()
+    rng = np.random.default_rng(1)
+    y = synth.random_kspace(rng, p["nc"], p["nt"])
+    per_step = []
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, dt, rows = cpu_sample(p, y, args.ref_seconds)
+        if i >= args.warmup:
+            per_step.append(dt)
+            vals.append(v)
+    value = float(np.mean(vals))
+    cores = oracle.threads()
+    sample = (f"oracle forward rows (16 random samples x all 40000 voxels x 32 coils) and adjoint voxels "
+              f"(27 random voxels x all 24000 samples x 32 coils) repeated for {args.ref_seconds:.0f} s per step")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(per_step)),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "bounded oracle sample"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_info()
+    if world > 1:
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2211_07532_gb300 import build as _b
+    _b.build()
+    import paper_2211_07532_gb300 as ax
+    from paper_2211_07532_gb300 import synth
+
+    precision = {"fp32": ax.FP32, "bf16": ax.BF16_TC, "fp16x2": ax.FP16X2_TC}[args.form]
+    p = synth.slice_200(index=rank)           # each rank reconstructs its own slice (weak scaling)
+    nr, nt, nc = p["nx"] * p["ny"], p["nt"], p["nc"]
+    iters, levels, n_power = p["iters"], p["levels"], 30
+    prob = ax.Problem.from_arrays(p, device=dev)
+    x_gt = torch.as_tensor(p["x_gt"], device=dev)
+
+    # simulated data on the device through the library's own forward model (Sec. 2.2.2)
+    ws_op = ax.workspace(prob, precision)
+    ax.prepare(prob, ws_op, precision)
+    y0 = ax.a_exp_forward(prob, x_gt, ws_op, precision=precision)
+    sigma = float(torch.sqrt(torch.mean(y0.abs() ** 2))) / p["snr"]
+    y = (y0 + sigma * torch.as_tensor(p["noise"], device=dev)).contiguous()
+    lam = 1e-3 * float(ax.a_exp_adjoint(prob, y, ws_op, precision=precision).abs().max())
+    del ws_op
+
+    opts = ax.recon_opts(precision=precision, wavelet="db4", levels=levels, n_power=n_power)
+    ws = ax.recon_workspace(prob, opts)
+    x_out = torch.empty(nr, dtype=torch.complex64, device=dev)
+    L_out = torch.empty(1, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ax.cs_recon(prob, y, lam, iters, opts=opts, ws=ws, x_out=x_out, lipschitz_out=L_out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    applications = 2 * iters + 2 * n_power + 1
+    vsc_per_step = applications * nr * nt * nc
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()                     # L2 flushed between timed iterations (outside the events)
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * vsc_per_step * args.steps / (total_ms / 1e3) / 1e9
+    status = ax.read_status(ws)
+    nrmse = float(torch.linalg.vector_norm(x_out - x_gt) / torch.linalg.vector_norm(x_gt))
+
+    # end to end through the public API from pinned host memory: H2D of y, recon, D2H of x
+    y_host = y.cpu().pin_memory()
+    x_host = torch.empty(nr, dtype=torch.complex64).pin_memory()
+    y_dev = torch.empty_like(y)
+    e2e_ms = []
+    y_dev.copy_(y_host)
+    ax.cs_recon(prob, y_dev, lam, iters, opts=opts, ws=ws, x_out=x_out, lipschitz_out=L_out)  # capture, untimed
+    torch.cuda.synchronize()
+    for i in range(max(1, args.steps)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        y_dev.copy_(y_host, non_blocking=True)
+        ax.cs_recon(prob, y_dev, lam, iters, opts=opts, ws=ws, x_out=x_out, lipschitz_out=L_out)
+        x_host.copy_(x_out, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_total = float(sum(e2e_ms))
+    if world > 1:
+        t = torch.tensor([e2e_total], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = world * vsc_per_step * len(e2e_ms) / (e2e_total / 1e3) / 1e9
+
+    # dominant kernels timed on their own stream with CUDA events: one operator application
+    # (coil weighting + contraction + partial-sum reduction), forward and adjoint
+    ws_k = ax.workspace(prob, precision)
+    ax.prepare(prob, ws_k, precision)
+    kern = {}
+    for name, fn in (("a_exp_forward", lambda: ax.a_exp_forward(prob, x_gt, ws_k, y=y0, precision=precision)),
+                     ("a_exp_adjoint", lambda: ax.a_exp_adjoint(prob, y, ws_k, x=x_out, precision=precision))):
+        for _ in range(3):
+            fn()
+        reps = 10
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        kern[name] = float(np.mean(ts))
+    dom = max(kern, key=kern.get)
+    clocks = clk.summary()
+    nterms = p["nl"] + 1
+    flops_per_launch = nr * nt * (8.0 * nc + 2.0 * nterms + 4.0)   # contraction + phase FMAs + reduction
+    achieved = flops_per_launch / (kern[dom] / 1e3) / 1e12
+    sm_mhz_peak = measured_peaks().get("sm_max_mhz", 2070.0)
+    peak = fp32_alu_peak_tflops(sm_mhz_peak)
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        with open(tfile) as f:
+            traffic = json.load(f).get(f"{args.form}:{dom}")
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            v, dt, rows = cpu_sample(p, y.cpu().numpy(), args.cpu_seconds)
+            cpu = {"value": v, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                   "sample": f"{rows} forward sample rows + matching adjoint voxels of the same workload, "
+                             f"{dt:.1f} s of FP64 oracle work"}
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp16x2": "f16x2"}[args.form],
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "form": args.form, "nx": p["nx"], "nt": nt, "nc": nc,
+                       "terms": nterms, "fista_iters": iters, "power_iters": n_power,
+                       "applications_per_step": applications, "l2": "flushed between timed steps (512 MB write)",
+                       "parallelism": f"replicas x{world} (independent slices)"},
+            "s_per_slice": ms_per_step / 1e3,
+            "nrmse_vs_phantom": nrmse,
+            "device_status": status,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(y.numel() * 8),
+                    "d2h_bytes_per_step": int(nr * 8), "s_per_slice": e2e_total / len(e2e_ms) / 1e3},
+            "gpu_launches": launches_per_recon(levels, iters, n_power) * args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": dom,
+                         "kernel_ms": kern[dom],
+                         "peak_basis": f"FP32 FMA pipe 152 SM x 128 lanes x 2 flop at {sm_mhz_peak:.0f} MHz "
+                                       "(sm_max_mhz of MEASURED_PEAKS.json)"},
+            "kernels_ms": kern,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--form", choices=["fp32", "bf16", "fp16x2"], default="fp32")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * aexp.h -- C ABI of the GB300 (sm_103a) expanded-encoding reconstruction library.
+ *
+ * The library solves Eq. (1) of Varela-Mattatall, Dubovan et al., "High-resolution
+ * single-shot spiral diffusion-weighted imaging at 7T using expanded encoding with
+ * compressed sensing" (MRM Technical Note):
+ *
+ *     x^ = argmin_x  ||A_exp x - y||_2^2 + lambda ||W x||_1                      (Eq. 1)
+ *
+ * with the matrix-free expanded encoding operator (Sec. 1: static B0 offsets plus
+ * field dynamics expanded in spherical harmonics up to 2nd/3rd order; Sec. 2.1):
+ *
+ *     phi(t, r)   = sum_{l < nl} k_l(t) h_l(r) + omega(r) t
+ *     (A x)_c(t)  = sum_r exp(-i phi(t, r)) S_c(r) x(r)
+ *     (A^H y)(r)  = sum_c conj(S_c(r)) sum_t exp(+i phi(t, r)) y_c(t)
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - All array pointers are DEVICE pointers owned by the caller (allocate them with
+ *   cudaMalloc or a framework allocator).  The library never allocates device memory
+ *   on these paths; scratch comes from the caller's workspace `ws` of `ws_bytes`
+ *   bytes, sized by the matching *_workspace_size() call.  `ws` must be 256-byte
+ *   aligned (cudaMalloc memory is).
+ * - Complex arrays are complex64: interleaved (re, im) float pairs, 8-byte aligned.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Every
+ *   call is asynchronous on that stream; none synchronises the host unless stated.
+ * - Image voxel r = iy * nx + ix (row-major, x fastest).  k-space y[c * nt + t].
+ * - Return value: AEXP_OK (0) or a negative aexp_status.  On a negative return
+ *   nothing was launched.  Errors discovered on the device (a bounded wait that gave
+ *   up, a non-finite Lipschitz estimate) are written to a status word inside `ws`
+ *   and read with aexp_read_status().
+ * - Calls sharing one workspace must be ordered (same stream or explicit events);
+ *   concurrent calls need separate workspaces.
+ * - Limits: 1 <= nc <= 32, 1 <= nl + (omega != NULL) <= 20, nx, ny, nt >= 1.
+ */
+#ifndef AEXP_H
+#define AEXP_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define AEXP_API __attribute__((visibility("default")))
+#else
+#define AEXP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum aexp_status {
+    AEXP_OK = 0,
+    AEXP_ERR_INVALID_ARG = -1,     /* null pointer, size out of range, bad enum      */
+    AEXP_ERR_MISALIGNED = -2,      /* a pointer breaks its alignment rule           */
+    AEXP_ERR_UNSUPPORTED = -3,     /* valid but outside the limits listed above     */
+    AEXP_ERR_WORKSPACE = -4,       /* ws_bytes smaller than the size query returned */
+    AEXP_ERR_CUDA = -5,            /* a CUDA runtime call failed; see aexp_last_cuda_error() */
+    AEXP_ERR_DEVICE_TIMEOUT = -6,  /* a bounded device wait gave up (device status) */
+    AEXP_ERR_NONFINITE = -7,       /* NaN/Inf in a device scalar (device status)    */
+    AEXP_ERR_NOT_PREPARED = -8     /* workspace was not prepared for this problem   */
+} aexp_status;
+
+typedef enum aexp_precision {
+    AEXP_FP32 = 0,        /* FP32 CUDA cores: phase, sincos and contraction in FP32   */
+    AEXP_BF16_TC = 1,     /* encoding tile in BF16, tcgen05 tensor cores, FP32 accum  */
+    AEXP_FP16X2_TC = 2    /* encoding tile and coil images split hi+lo in FP16        */
+} aexp_precision;
+
+typedef enum aexp_wavelet {
+    AEXP_WAVELET_HAAR = 0, /* orthonormal Haar, 2 taps                          */
+    AEXP_WAVELET_DB4 = 1   /* orthonormal Daubechies, 4 vanishing moments, 8 taps */
+} aexp_wavelet;
+
+/* One 2-D slice problem.  Every pointer is a device pointer; the arrays must stay
+ * unchanged between aexp_prepare() and the operator calls that use the workspace. */
+typedef struct aexp_problem {
+    int nx, ny;           /* image size; nr = nx * ny                                    */
+    int nt;               /* k-space samples per coil                                    */
+    int nc;               /* receive coils                                               */
+    int nl;               /* spherical-harmonic field terms (Sec. 1: up to 3rd order = 16) */
+    const float *k;       /* [nl][nt] field coefficients k_l(t), rad / m^deg(l)          */
+    const float *h;       /* [nl][nr] basis values h_l(r), m^deg(l)                      */
+    const float *omega;   /* [nr] static off-resonance (B0 map), rad/s, or NULL          */
+    const float *t;       /* [nt] sample times, s (read only when omega != NULL)         */
+    const void *S;        /* [nc][nr] complex64 coil sensitivities S_c(r)                */
+} aexp_problem;
+
+/* ---------------------------------------------------------------------------
+ * Operator: A_exp and A_exp^H (Eq. 1; Sec. 2.1 writes the adjoint as A^T)
+ * --------------------------------------------------------------------------- */
+
+/* Bytes of device workspace that a_exp_forward / a_exp_adjoint need for `prob` at
+ * `precision`.  Host-only; reads no device memory.  Writes *bytes. */
+AEXP_API int aexp_workspace_size(const aexp_problem *prob, int precision, size_t *bytes);
+
+/* Derive the operator's internal layouts from prob into ws: field coefficients in
+ * turns as FP32 pairs, basis offsets per 8x8 voxel tile, the per-(tile, sample)
+ * reference phase table, coil maps in tile order.  Must precede the operator calls
+ * (stream-ordered) and be repeated whenever k, h, omega, t or S change. */
+AEXP_API int aexp_prepare(const aexp_problem *prob, int precision, void *ws, size_t ws_bytes, void *stream);
+
+/* y = A_exp x.  x: [nr] complex64 image; y: [nc][nt] complex64 (overwritten).
+ * ws must have been prepared for prob.  Returns AEXP_ERR_NOT_PREPARED when the
+ * host-side record of the last aexp_prepare on ws does not match prob. */
+AEXP_API int a_exp_forward(const aexp_problem *prob, int precision, const void *x, void *y,
+                  void *ws, size_t ws_bytes, void *stream);
+
+/* x = A_exp^H y.  y: [nc][nt] complex64; x: [nr] complex64 (overwritten). */
+AEXP_API int a_exp_adjoint(const aexp_problem *prob, int precision, const void *y, void *x,
+                  void *ws, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Compressed-sensing reconstruction: FISTA on Eq. (1) (Sec. 2.1, balanced FISTA;
+ * with an orthonormal W its prox step is exactly the one used here)
+ * --------------------------------------------------------------------------- */
+
+typedef struct aexp_recon_opts {
+    int precision;          /* aexp_precision of every A / A^H application              */
+    int wavelet;            /* aexp_wavelet                                              */
+    int levels;             /* wavelet levels J >= 1; the image is zero-padded to a
+                               multiple of 2^J per side, W is orthonormal on the padded grid */
+    int n_power;            /* power iterations for L_f = 2 lambda_max(A^H A); 0 with
+                               lipschitz <= 0 is invalid                                 */
+    double lipschitz;       /* > 0: use this L_f and skip the power iteration            */
+    const void *x0;         /* [nr] complex64 start image, or NULL for zero              */
+    const void *power_init; /* [nr] complex64 power-iteration start, or NULL for A^H y   */
+    int use_graph;          /* nonzero: capture the whole loop in one CUDA graph         */
+} aexp_recon_opts;
+
+/* Fill opts with defaults: FP32, Haar, 3 levels, 30 power iterations, estimate L_f,
+ * zero start, A^H y power start, graph capture on. */
+AEXP_API void aexp_recon_opts_default(aexp_recon_opts *opts);
+
+/* Bytes of workspace cs_recon needs (includes the operator workspace). */
+AEXP_API int aexp_recon_workspace_size(const aexp_problem *prob, const aexp_recon_opts *opts, size_t *bytes);
+
+/* x_out = FISTA iterate after `iters` iterations on Eq. (1):
+ *   F(x) = ||A x - y||^2 + lambda * sum over detail coefficients |(W pad x)_j|
+ * (low-pass weight 0, Supporting Information S1), gradient 2 A^H (A z - y), step 1/L_f,
+ * threshold lambda / L_f, momentum t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2 in FP64.
+ * y: [nc][nt] complex64; x_out: [nr] complex64.  lipschitz_out: optional DEVICE
+ * pointer to one double that receives the L_f used.  Prepares ws itself. */
+AEXP_API int cs_recon(const aexp_problem *prob, const void *y, float lambda, int iters,
+             const aexp_recon_opts *opts, void *x_out, double *lipschitz_out,
+             void *ws, size_t ws_bytes, void *stream);
+
+/* Estimate L_f = 2 lambda_max(A^H A) with n_power iterations from v0 ([nr] complex64,
+ * not modified).  Result to the DEVICE double *lipschitz_out.  ws as for cs_recon. */
+AEXP_API int aexp_power_lipschitz(const aexp_problem *prob, int precision, const void *v0, int n_power,
+                         double *lipschitz_out, void *ws, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Wavelet step on its own (Eq. 1 regulariser): out = crop(W^H soft(W pad(in), tau))
+ * --------------------------------------------------------------------------- */
+
+/* Bytes of workspace aexp_wavelet_prox needs. */
+AEXP_API int aexp_wavelet_workspace_size(int nx, int ny, int wavelet, int levels, size_t *bytes);
+
+/* Soft-threshold (w -> w max(0, 1 - tau/|w|)) of the detail coefficients only;
+ * in, out: [ny][nx] complex64 (may alias).  tau >= 0. */
+AEXP_API int aexp_wavelet_prox(int nx, int ny, int wavelet, int levels, float tau, const void *in,
+                      void *out, void *ws, size_t ws_bytes, void *stream);
+
+/* Forward transform only: coef = W pad(in), coef: [Npy][Npx] complex64 in Mallat
+ * layout, Npy = ceil(ny / 2^J) 2^J (same for x). */
+AEXP_API int aexp_wavelet_forward(int nx, int ny, int wavelet, int levels, const void *in, void *coef,
+                         void *ws, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Status
+ * --------------------------------------------------------------------------- */
+
+/* Synchronise `stream`, read and clear the device status word in ws (AEXP_OK when
+ * no device-side error was recorded since the last read). */
+AEXP_API int aexp_read_status(void *ws, void *stream, int *status);
+
+/* Short English description of a status code; never NULL. */
+AEXP_API const char *aexp_status_string(int status);
+
+/* The cudaError_t value of the last AEXP_ERR_CUDA on this host thread. */
+AEXP_API int aexp_last_cuda_error(void);
+
+/* Library version, e.g. 100 for 0.1.0. */
+AEXP_API int aexp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AEXP_H */

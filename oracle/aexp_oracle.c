@@ -42,14 +42,17 @@ void oracle_forward(int nt, int nr, int nc, int nl, const double *k, const doubl
 {
 #pragma omp parallel for schedule(dynamic, 16)
     for (int t = 0; t < nt; ++t) {
+        double complex acc[nc]; /* thread-local sums, stored once per sample */
         for (int c = 0; c < nc; ++c)
-            y[(size_t)c * nt + t] = 0.0;
+            acc[c] = 0.0;
         for (int r = 0; r < nr; ++r) {
             double phi = phase(nl, nt, nr, k, h, omega, tt, t, r);
             double complex e = cos(phi) - I * sin(phi);
             for (int c = 0; c < nc; ++c)
-                y[(size_t)c * nt + t] += e * S[(size_t)c * nr + r] * x[r];
+                acc[c] += e * S[(size_t)c * nr + r] * x[r];
         }
+        for (int c = 0; c < nc; ++c)
+            y[(size_t)c * nt + t] = acc[c];
     }
 }
 
@@ -80,14 +83,17 @@ void oracle_forward_rows(int nt, int nr, int nc, int nl, const double *k, const 
 #pragma omp parallel for schedule(dynamic, 1)
     for (int j = 0; j < ns; ++j) {
         int t = ts[j];
+        double complex acc[nc];
         for (int c = 0; c < nc; ++c)
-            y[(size_t)c * ns + j] = 0.0;
+            acc[c] = 0.0;
         for (int r = 0; r < nr; ++r) {
             double phi = phase(nl, nt, nr, k, h, omega, tt, t, r);
             double complex e = cos(phi) - I * sin(phi);
             for (int c = 0; c < nc; ++c)
-                y[(size_t)c * ns + j] += e * S[(size_t)c * nr + r] * x[r];
+                acc[c] += e * S[(size_t)c * nr + r] * x[r];
         }
+        for (int c = 0; c < nc; ++c)
+            y[(size_t)c * ns + j] = acc[c];
     }
 }
 
@@ -125,8 +131,9 @@ void oracle_forward_dk(int nt, int nr, int nc, int nl, const double *k, const do
 {
 #pragma omp parallel for schedule(dynamic, 16)
     for (int t = 0; t < nt; ++t) {
+        double complex acc[nl > 0 ? nl : 1];
         for (int l = 0; l < nl; ++l)
-            G[(size_t)l * nt + t] = 0.0;
+            acc[l] = 0.0;
         for (int r = 0; r < nr; ++r) {
             double phi = phase(nl, nt, nr, k, h, omega, tt, t, r);
             double complex e = cos(phi) - I * sin(phi);
@@ -135,8 +142,10 @@ void oracle_forward_dk(int nt, int nr, int nc, int nl, const double *k, const do
                 s += conj(g[(size_t)c * nt + t]) * S[(size_t)c * nr + r];
             double complex term = s * e * x[r] * (-I);
             for (int l = 0; l < nl; ++l)
-                G[(size_t)l * nt + t] += term * h[(size_t)l * nr + r];
+                acc[l] += term * h[(size_t)l * nr + r];
         }
+        for (int l = 0; l < nl; ++l)
+            G[(size_t)l * nt + t] = acc[l];
     }
 }
 
@@ -148,8 +157,9 @@ void oracle_adjoint_dk(int nt, int nr, int nc, int nl, const double *k, const do
 {
 #pragma omp parallel for schedule(dynamic, 16)
     for (int t = 0; t < nt; ++t) {
+        double complex acc[nl > 0 ? nl : 1];
         for (int l = 0; l < nl; ++l)
-            G[(size_t)l * nt + t] = 0.0;
+            acc[l] = 0.0;
         for (int r = 0; r < nr; ++r) {
             double phi = phase(nl, nt, nr, k, h, omega, tt, t, r);
             double complex ec = cos(phi) + I * sin(phi);
@@ -158,7 +168,9 @@ void oracle_adjoint_dk(int nt, int nr, int nc, int nl, const double *k, const do
                 s += conj(S[(size_t)c * nr + r]) * y[(size_t)c * nt + t];
             double complex term = conj(g[r]) * s * ec * I;
             for (int l = 0; l < nl; ++l)
-                G[(size_t)l * nt + t] += term * h[(size_t)l * nr + r];
+                acc[l] += term * h[(size_t)l * nr + r];
         }
+        for (int l = 0; l < nl; ++l)
+            G[(size_t)l * nt + t] = acc[l];
     }
 }

@@ -1,0 +1,293 @@
+"""GB300 (sm_103a) expanded-encoding compressed-sensing reconstruction (Eq. 1).
+
+Thin Python binding over the C ABI of ``libaexp.so`` (declared in include/aexp.h).
+Every numeric step runs in the library's CUDA kernels; this module only marshals
+arguments: PyTorch provides device memory and the current stream.  There is no CPU
+fallback: without the built library every entry point raises.
+
+Names follow the C ABI: ``a_exp_forward``, ``a_exp_adjoint``, ``cs_recon``,
+``power_lipschitz``, ``wavelet_prox``, ``wavelet_forward``.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libaexp.so")
+
+FP32, BF16_TC, FP16X2_TC = 0, 1, 2
+HAAR, DB4 = 0, 1
+WAVELETS = {"haar": HAAR, "db4": DB4}
+
+OK = 0
+STATUS = {0: "AEXP_OK", -1: "AEXP_ERR_INVALID_ARG", -2: "AEXP_ERR_MISALIGNED", -3: "AEXP_ERR_UNSUPPORTED",
+          -4: "AEXP_ERR_WORKSPACE", -5: "AEXP_ERR_CUDA", -6: "AEXP_ERR_DEVICE_TIMEOUT",
+          -7: "AEXP_ERR_NONFINITE", -8: "AEXP_ERR_NOT_PREPARED"}
+
+
+class AexpError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        msg = f"{what} failed: {STATUS.get(code, code)}"
+        if code == -5 and _lib is not None:
+            msg += f" (cudaError {_lib.aexp_last_cuda_error()})"
+        super().__init__(msg)
+
+
+class CProblem(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nt", ctypes.c_int), ("nc", ctypes.c_int),
+                ("nl", ctypes.c_int), ("k", ctypes.c_void_p), ("h", ctypes.c_void_p),
+                ("omega", ctypes.c_void_p), ("t", ctypes.c_void_p), ("S", ctypes.c_void_p)]
+
+
+class CReconOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("wavelet", ctypes.c_int), ("levels", ctypes.c_int),
+                ("n_power", ctypes.c_int), ("lipschitz", ctypes.c_double), ("x0", ctypes.c_void_p),
+                ("power_init", ctypes.c_void_p), ("use_graph", ctypes.c_int)]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every entry point in include/aexp.h
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_SZ = ctypes.c_size_t
+_PROB = ctypes.POINTER(CProblem)
+_OPTS = ctypes.POINTER(CReconOpts)
+SIGNATURES = [
+    ("aexp_workspace_size", _I, [_PROB, _I, ctypes.POINTER(_SZ)]),
+    ("aexp_prepare", _I, [_PROB, _I, _P, _SZ, _P]),
+    ("a_exp_forward", _I, [_PROB, _I, _P, _P, _P, _SZ, _P]),
+    ("a_exp_adjoint", _I, [_PROB, _I, _P, _P, _P, _SZ, _P]),
+    ("aexp_recon_opts_default", None, [_OPTS]),
+    ("aexp_recon_workspace_size", _I, [_PROB, _OPTS, ctypes.POINTER(_SZ)]),
+    ("cs_recon", _I, [_PROB, _P, ctypes.c_float, _I, _OPTS, _P, _P, _P, _SZ, _P]),
+    ("aexp_power_lipschitz", _I, [_PROB, _I, _P, _I, _P, _P, _SZ, _P]),
+    ("aexp_wavelet_workspace_size", _I, [_I, _I, _I, _I, ctypes.POINTER(_SZ)]),
+    ("aexp_wavelet_prox", _I, [_I, _I, _I, _I, ctypes.c_float, _P, _P, _P, _SZ, _P]),
+    ("aexp_wavelet_forward", _I, [_I, _I, _I, _I, _P, _P, _P, _SZ, _P]),
+    ("aexp_read_status", _I, [_P, _P, ctypes.POINTER(_I)]),
+    ("aexp_status_string", ctypes.c_char_p, [_I]),
+    ("aexp_last_cuda_error", _I, []),
+    ("aexp_version", _I, []),
+]
+
+
+def lib():
+    """Load libaexp.so (raises when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2211_07532_gb300.build.build()")
+        h = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            fn = getattr(h, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = h
+    return _lib
+
+
+def _check(code: int, what: str):
+    if code != OK:
+        raise AexpError(code, what)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Problem:
+    """Device arrays of one slice problem (see aexp_problem in include/aexp.h).
+
+    k: float32 [nl][nt]; h: float32 [nl][nr]; omega: float32 [nr] or None;
+    t: float32 [nt]; S: complex64 [nc][nr].  Tensors are kept alive by this object.
+    """
+
+    def __init__(self, nx, ny, k, h, S, omega=None, t=None):
+        torch = _torch()
+        self.nx, self.ny = int(nx), int(ny)
+        self.k = k.contiguous()
+        self.h = h.contiguous()
+        self.S = S.contiguous()
+        self.omega = None if omega is None else omega.contiguous()
+        self.t = None if t is None else t.contiguous()
+        assert self.k.dtype == torch.float32 and self.h.dtype == torch.float32
+        assert self.S.dtype == torch.complex64
+        self.nl, self.nt = self.k.shape
+        self.nc = self.S.shape[0]
+        self.nr = self.nx * self.ny
+        self._c = CProblem(self.nx, self.ny, self.nt, self.nc, self.nl, self.k.data_ptr(), self.h.data_ptr(),
+                           None if self.omega is None else self.omega.data_ptr(),
+                           None if self.t is None else self.t.data_ptr(), self.S.data_ptr())
+
+    @classmethod
+    def from_arrays(cls, d: dict, device="cuda", with_b0: bool = True):
+        """From a dict of numpy arrays (keys nx, ny, k, h, omega, t, S)."""
+        torch = _torch()
+        dev = torch.device(device)
+        om = d.get("omega")
+        use_b0 = with_b0 and om is not None
+        return cls(d["nx"], d["ny"], torch.as_tensor(d["k"], dtype=torch.float32, device=dev),
+                   torch.as_tensor(d["h"], dtype=torch.float32, device=dev),
+                   torch.as_tensor(d["S"], dtype=torch.complex64, device=dev),
+                   torch.as_tensor(om, dtype=torch.float32, device=dev) if use_b0 else None,
+                   torch.as_tensor(d["t"], dtype=torch.float32, device=dev) if use_b0 else None)
+
+    @property
+    def c(self):
+        return ctypes.byref(self._c)
+
+    @property
+    def device(self):
+        return self.S.device
+
+
+def workspace_size(prob: Problem, precision: int = FP32) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().aexp_workspace_size(prob.c, precision, ctypes.byref(n)), "aexp_workspace_size")
+    return n.value
+
+
+def _alloc(nbytes: int, device):
+    torch = _torch()
+    ws = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+    if ws.data_ptr() % 256:
+        raise RuntimeError("workspace is not 256-byte aligned")
+    return ws
+
+
+def workspace(prob: Problem, precision: int = FP32):
+    return _alloc(workspace_size(prob, precision), prob.device)
+
+
+def prepare(prob: Problem, ws, precision: int = FP32, stream=None):
+    _check(lib().aexp_prepare(prob.c, precision, _ptr(ws), ws.numel(), _stream(stream)), "aexp_prepare")
+
+
+def a_exp_forward(prob: Problem, x, ws, y=None, precision: int = FP32, stream=None):
+    """y = A_exp x  (x: complex64 [nr]; returns complex64 [nc][nt])."""
+    torch = _torch()
+    x = x.contiguous()
+    if y is None:
+        y = torch.empty((prob.nc, prob.nt), dtype=torch.complex64, device=x.device)
+    _check(lib().a_exp_forward(prob.c, precision, _ptr(x), _ptr(y), _ptr(ws), ws.numel(), _stream(stream)),
+           "a_exp_forward")
+    return y
+
+
+def a_exp_adjoint(prob: Problem, y, ws, x=None, precision: int = FP32, stream=None):
+    """x = A_exp^H y  (y: complex64 [nc][nt]; returns complex64 [nr])."""
+    torch = _torch()
+    y = y.contiguous()
+    if x is None:
+        x = torch.empty(prob.nr, dtype=torch.complex64, device=y.device)
+    _check(lib().a_exp_adjoint(prob.c, precision, _ptr(y), _ptr(x), _ptr(ws), ws.numel(), _stream(stream)),
+           "a_exp_adjoint")
+    return x
+
+
+def recon_opts(precision=FP32, wavelet="haar", levels=3, n_power=30, lipschitz=0.0, x0=None, power_init=None,
+               use_graph=True) -> CReconOpts:
+    o = CReconOpts()
+    lib().aexp_recon_opts_default(ctypes.byref(o))
+    o.precision = precision
+    o.wavelet = WAVELETS[wavelet] if isinstance(wavelet, str) else int(wavelet)
+    o.levels = levels
+    o.n_power = n_power
+    o.lipschitz = float(lipschitz)
+    o.x0 = None if x0 is None else x0.data_ptr()
+    o.power_init = None if power_init is None else power_init.data_ptr()
+    o.use_graph = 1 if use_graph else 0
+    return o
+
+
+def recon_workspace_size(prob: Problem, opts: CReconOpts) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().aexp_recon_workspace_size(prob.c, ctypes.byref(opts), ctypes.byref(n)),
+           "aexp_recon_workspace_size")
+    return n.value
+
+
+def recon_workspace(prob: Problem, opts: CReconOpts):
+    return _alloc(recon_workspace_size(prob, opts), prob.device)
+
+
+def cs_recon(prob: Problem, y, lam: float, iters: int, opts: CReconOpts | None = None, ws=None, x_out=None,
+             lipschitz_out=None, stream=None, **kw):
+    """FISTA on Eq. (1); returns (x complex64 [nr], L_f float64 device tensor [1])."""
+    torch = _torch()
+    opts = recon_opts(**kw) if opts is None else opts
+    y = y.contiguous()
+    if ws is None:
+        ws = recon_workspace(prob, opts)
+    if x_out is None:
+        x_out = torch.empty(prob.nr, dtype=torch.complex64, device=y.device)
+    if lipschitz_out is None:
+        lipschitz_out = torch.empty(1, dtype=torch.float64, device=y.device)
+    _check(lib().cs_recon(prob.c, _ptr(y), float(lam), int(iters), ctypes.byref(opts), _ptr(x_out),
+                          _ptr(lipschitz_out), _ptr(ws), ws.numel(), _stream(stream)), "cs_recon")
+    return x_out, lipschitz_out
+
+
+def power_lipschitz(prob: Problem, v0, n_power: int, ws=None, precision: int = FP32, stream=None):
+    """L_f = 2 lambda_max(A^H A) by n_power power iterations from v0 (device float64 [1])."""
+    torch = _torch()
+    if ws is None:
+        ws = recon_workspace(prob, recon_opts(precision=precision, levels=1))
+    out = torch.empty(1, dtype=torch.float64, device=v0.device)
+    _check(lib().aexp_power_lipschitz(prob.c, precision, _ptr(v0.contiguous()), int(n_power), _ptr(out),
+                                      _ptr(ws), ws.numel(), _stream(stream)), "aexp_power_lipschitz")
+    return out
+
+
+def wavelet_workspace(nx, ny, wavelet, levels, device):
+    n = ctypes.c_size_t()
+    w = WAVELETS[wavelet] if isinstance(wavelet, str) else int(wavelet)
+    _check(lib().aexp_wavelet_workspace_size(nx, ny, w, levels, ctypes.byref(n)), "aexp_wavelet_workspace_size")
+    return _alloc(n.value, device)
+
+
+def wavelet_prox(img, wavelet: str, levels: int, tau: float, ws=None, out=None, stream=None):
+    """crop(W^H soft_detail(W pad img, tau)) for a complex64 [ny][nx] image."""
+    torch = _torch()
+    img = img.contiguous()
+    ny, nx = img.shape
+    ws = wavelet_workspace(nx, ny, wavelet, levels, img.device) if ws is None else ws
+    out = torch.empty_like(img) if out is None else out
+    _check(lib().aexp_wavelet_prox(nx, ny, WAVELETS[wavelet], levels, float(tau), _ptr(img), _ptr(out), _ptr(ws),
+                                   ws.numel(), _stream(stream)), "aexp_wavelet_prox")
+    return out
+
+
+def wavelet_forward(img, wavelet: str, levels: int, ws=None, stream=None):
+    """W pad img, Mallat layout, complex64 [npy][npx]."""
+    torch = _torch()
+    img = img.contiguous()
+    ny, nx = img.shape
+    q = 1 << levels
+    npy, npx = -(-ny // q) * q, -(-nx // q) * q
+    ws = wavelet_workspace(nx, ny, wavelet, levels, img.device) if ws is None else ws
+    coef = torch.empty((npy, npx), dtype=torch.complex64, device=img.device)
+    _check(lib().aexp_wavelet_forward(nx, ny, WAVELETS[wavelet], levels, _ptr(img), _ptr(coef), _ptr(ws),
+                                      ws.numel(), _stream(stream)), "aexp_wavelet_forward")
+    return coef
+
+
+def read_status(ws, stream=None) -> int:
+    s = ctypes.c_int()
+    _check(lib().aexp_read_status(_ptr(ws), _stream(stream), ctypes.byref(s)), "aexp_read_status")
+    return s.value

@@ -1,0 +1,192 @@
+// Internal declarations shared by the translation units of libaexp.
+//
+// Data layout in device memory (one workspace per problem, caller-owned):
+//   - voxels are regrouped into 8x8 tiles ("tile order", p = tile*64 + (iy%8)*8 + ix%8);
+//     partial tiles at the right/bottom edge are padded with inert voxels;
+//   - field terms: the nl spherical-harmonic terms plus, when a B0 map is given,
+//     one more term with coefficient t and basis omega(r) (phi = ... + omega(r) t);
+//   - coefficients are kept in turns (k / 2pi) as an FP32 hi + lo pair;
+//   - each tile has a reference voxel r0; its phase per sample,
+//     f0(tile, t) = frac(sum_l k_l(t) h_l(r0) / 2pi), is tabulated accurately
+//     once per preparation, and the kernels add the FP32 local offset
+//     sum_l (k_l(t)/2pi) (h_l(r) - h_l(r0)), which stays small within a tile.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/aexp.h"
+
+namespace aexp {
+
+constexpr int kTileSide = 8;
+constexpr int kTileVox = 64;
+constexpr int kMaxTerms = 20;
+constexpr int kMaxCoils = 32;
+constexpr int kFwdThreads = 128;
+constexpr int kAdjThreads = 128;
+constexpr int kAdjStageT = 64;      // samples per adjoint smem stage
+constexpr int kTPad = 512;          // nt is padded to a multiple of this
+constexpr size_t kAlign = 256;
+
+// Header at the start of every workspace (device memory).
+struct WsHeader {
+    int status;          // first device-side error, 0 = none
+    int pad0;
+    double lipschitz;    // L_f in use
+    double mu;           // last Rayleigh quotient
+    double nrm2;         // last squared norm
+    double scratch[4];
+};
+
+struct OpLayout {
+    int nx, ny, nr, nt, nc, nl, has_b0;
+    int nterms;      // nl + has_b0
+    int LP;          // padded term count (template): 4, 8, 12 or 20
+    int CB;          // padded coil count (template): 4, 8, 16, 20 or 32
+    int ntx, nty, ntiles, nr_pad;
+    int ntp;         // nt padded to kTPad
+    int precision;
+    // forward split
+    int fwd_mt, fwd_tblocks, fwd_splits, fwd_tiles_per_split;
+    // adjoint split
+    int adj_vblocks, adj_splits, adj_t_per_split;
+    // byte offsets into the workspace
+    size_t off_hdr, off_khi_l, off_klo_l, off_khi_t, off_h0, off_dh, off_f0, off_S, off_b,
+        off_fpart, off_yt, off_apart;
+    size_t bytes;
+};
+
+struct WaveLayout {
+    int nx, ny, levels, wavelet, npx, npy;
+    size_t off_pyr;              // [npy][npx] complex
+    size_t off_approx[16];       // level j approximation (j = 1..levels-1)
+    size_t bytes;
+};
+
+struct RecLayout {
+    OpLayout op;
+    WaveLayout wv;               // offsets relative to off_wave
+    size_t off_wave, off_ymeas, off_xa, off_xb, off_z, off_v, off_w;
+    size_t bytes;
+};
+
+inline size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
+inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+// Host-side layout computation (layout.cu).
+int op_layout(const aexp_problem *p, int precision, OpLayout *L);
+int wave_layout(int nx, int ny, int wavelet, int levels, WaveLayout *W);
+int rec_layout(const aexp_problem *p, const aexp_recon_opts *o, RecLayout *R);
+
+// Launchers (all asynchronous on `st`; return cudaError_t of the launch).
+cudaError_t op_prepare(const aexp_problem *p, const OpLayout &L, char *ws, cudaStream_t st);
+// b = S * x into tile order; x in natural order [nr]
+cudaError_t op_coil_weight(const OpLayout &L, const float2 *x, char *ws, cudaStream_t st);
+// forward contraction on the prepared b -> partial sums
+cudaError_t op_forward_core(const OpLayout &L, char *ws, cudaStream_t st);
+// reduce forward partials: mode 0 -> y[c][t] public layout; mode 1 -> yt[t][CB] minus ymeas (residual)
+cudaError_t op_forward_reduce_public(const OpLayout &L, char *ws, float2 *y, cudaStream_t st);
+cudaError_t op_forward_reduce_residual(const OpLayout &L, char *ws, const float2 *ymeas_t, float2 *rt,
+                                       cudaStream_t st);
+// transpose public y[c][t] into yt[t][CB] (zero padded)
+cudaError_t op_transpose_y(const OpLayout &L, const float2 *y, float2 *yt, cudaStream_t st);
+// adjoint contraction of yt[t][CB] -> partials
+cudaError_t op_adjoint_core(const OpLayout &L, const float2 *yt, char *ws, cudaStream_t st);
+// reduce adjoint partials into natural order: out = sum (mode plain) or
+// out = z - (2/L_f) * sum (gradient step, L_f read from the workspace header)
+cudaError_t op_adjoint_reduce(const OpLayout &L, char *ws, float2 *out, cudaStream_t st);
+cudaError_t op_adjoint_reduce_step(const OpLayout &L, char *ws, const float2 *z, float2 *out,
+                                   cudaStream_t st);
+
+// Wavelet (wavelet.cu).  tau = lam / L_f with L_f from `lipschitz` (device), or
+// lam itself when lipschitz == nullptr.  threshold == 0 disables shrinkage.
+cudaError_t wave_forward(const WaveLayout &W, const float2 *img, char *wws, float lam,
+                         const double *lipschitz, int threshold, cudaStream_t st);
+// inverse into out (natural [ny][nx]); when momentum: x_new = result, z = x_new + beta (x_new - x_old)
+cudaError_t wave_inverse(const WaveLayout &W, char *wws, float2 *out, int momentum, double beta,
+                         const float2 *x_old, float2 *z_out, cudaStream_t st);
+
+// Reductions and small vector kernels (recon.cu).
+cudaError_t dot_norm_f64(const float2 *v, const float2 *w, int n, double *mu, double *nrm2, cudaStream_t st);
+cudaError_t scale_inv_sqrt(const float2 *w, float2 *v, int n, const double *nrm2, cudaStream_t st);
+
+// Solver pieces (recon.cu).
+cudaError_t normal_apply(const OpLayout &L, char *ws, const float2 *v, float2 *w, cudaStream_t st);
+cudaError_t power_iteration(const OpLayout &L, char *ws, const float2 *v0, float2 *v, float2 *w, int n_power,
+                            double *out, cudaStream_t st);
+cudaError_t set_lipschitz(const OpLayout &L, char *ws, double value, double *out, cudaStream_t st);
+cudaError_t recon_issue(const aexp_problem *p, const RecLayout &R, const aexp_recon_opts *o, const float2 *y,
+                        float lam, int iters, float2 *x_out, double *lip_out, char *ws, cudaStream_t st);
+
+// Error flag writers used by the kernels.
+__device__ __forceinline__ void set_status(int *status, int code) {
+    atomicCAS(status, 0, code);
+}
+
+// ---------------------------------------------------------------------------
+// PTX helpers: mbarrier + bulk (TMA) copies global -> shared.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after ~2^22 polls (each poll may suspend briefly), records
+// AEXP_ERR_DEVICE_TIMEOUT and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, int *status) {
+    for (int i = 0; i < (1 << 22); ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    set_status(status, AEXP_ERR_DEVICE_TIMEOUT);
+    return false;
+}
+
+// One bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// FP32 pair arithmetic (error-free transformations; Knuth two-sum, FMA two-product)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+}  // namespace aexp

@@ -1,0 +1,355 @@
+// The C ABI (include/aexp.h): argument validation, workspace sizing, the host-side
+// record of prepared workspaces, CUDA-graph capture of cs_recon, status strings.
+#include <string.h>
+
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "aexp_internal.cuh"
+
+using namespace aexp;
+
+namespace {
+
+thread_local int g_last_cuda_error = 0;
+
+int cuda_fail(cudaError_t e) {
+    g_last_cuda_error = (int)e;
+    return AEXP_ERR_CUDA;
+}
+
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+int check_problem(const aexp_problem *p) {
+    if (!p) return AEXP_ERR_INVALID_ARG;
+    if (p->nx < 1 || p->ny < 1 || p->nt < 1 || p->nc < 1 || p->nl < 0) return AEXP_ERR_INVALID_ARG;
+    if ((long long)p->nx * p->ny > (1LL << 28) || p->nt > (1 << 28)) return AEXP_ERR_UNSUPPORTED;
+    int nterms = p->nl + (p->omega != nullptr);
+    if (nterms < 1) return AEXP_ERR_INVALID_ARG;
+    if (nterms > kMaxTerms || p->nc > kMaxCoils) return AEXP_ERR_UNSUPPORTED;
+    if ((p->nl > 0 && (!p->k || !p->h)) || !p->S) return AEXP_ERR_INVALID_ARG;
+    if (p->omega && !p->t) return AEXP_ERR_INVALID_ARG;
+    if (!aligned(p->k, 4) || !aligned(p->h, 4) || !aligned(p->omega, 4) || !aligned(p->t, 4) ||
+        !aligned(p->S, 8))
+        return AEXP_ERR_MISALIGNED;
+    return AEXP_OK;
+}
+
+int check_precision(int precision) {
+    if (precision != AEXP_FP32 && precision != AEXP_BF16_TC && precision != AEXP_FP16X2_TC)
+        return AEXP_ERR_INVALID_ARG;
+    if (precision != AEXP_FP32) return AEXP_ERR_UNSUPPORTED;
+    return AEXP_OK;
+}
+
+int check_ws(const void *ws, size_t have, size_t need) {
+    if (!ws) return AEXP_ERR_INVALID_ARG;
+    if (!aligned(ws, kAlign)) return AEXP_ERR_MISALIGNED;
+    if (have < need) return AEXP_ERR_WORKSPACE;
+    return AEXP_OK;
+}
+
+// Host-side record of which problem a workspace was last prepared for.
+struct PrepRecord {
+    aexp_problem prob;
+    int precision;
+};
+std::mutex g_mu;
+std::unordered_map<const void *, PrepRecord> g_prepared;
+
+bool same_problem(const aexp_problem &a, const aexp_problem &b) { return memcmp(&a, &b, sizeof(a)) == 0; }
+
+void record_prepared(const void *ws, const aexp_problem *p, int precision) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_prepared[ws] = PrepRecord{*p, precision};
+}
+
+bool is_prepared(const void *ws, const aexp_problem *p, int precision) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_prepared.find(ws);
+    return it != g_prepared.end() && same_problem(it->second.prob, *p) && it->second.precision == precision;
+}
+
+// One captured cs_recon per workspace, relaunched while every argument is identical.
+struct GraphEntry {
+    std::vector<unsigned char> key;
+    cudaGraphExec_t exec = nullptr;
+};
+std::unordered_map<const void *, GraphEntry> g_graphs;
+
+template <class T>
+void put(std::vector<unsigned char> &v, const T &x) {
+    const unsigned char *b = reinterpret_cast<const unsigned char *>(&x);
+    v.insert(v.end(), b, b + sizeof(T));
+}
+
+int check_opts(const aexp_recon_opts *o) {
+    if (!o) return AEXP_ERR_INVALID_ARG;
+    int rc = check_precision(o->precision);
+    if (rc) return rc;
+    if (o->wavelet != AEXP_WAVELET_HAAR && o->wavelet != AEXP_WAVELET_DB4) return AEXP_ERR_INVALID_ARG;
+    if (o->levels < 1 || o->levels > 12) return AEXP_ERR_INVALID_ARG;
+    if (!(o->lipschitz > 0.0) && o->n_power < 1) return AEXP_ERR_INVALID_ARG;
+    if (!aligned(o->x0, 8) || !aligned(o->power_init, 8)) return AEXP_ERR_MISALIGNED;
+    return AEXP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int aexp_version(void) { return 100; }
+
+int aexp_last_cuda_error(void) { return g_last_cuda_error; }
+
+const char *aexp_status_string(int status) {
+    switch (status) {
+        case AEXP_OK: return "ok";
+        case AEXP_ERR_INVALID_ARG: return "invalid argument";
+        case AEXP_ERR_MISALIGNED: return "misaligned pointer";
+        case AEXP_ERR_UNSUPPORTED: return "unsupported size or option";
+        case AEXP_ERR_WORKSPACE: return "workspace too small";
+        case AEXP_ERR_CUDA: return "CUDA runtime error";
+        case AEXP_ERR_DEVICE_TIMEOUT: return "bounded device wait timed out";
+        case AEXP_ERR_NONFINITE: return "non-finite device scalar";
+        case AEXP_ERR_NOT_PREPARED: return "workspace not prepared for this problem";
+        default: return "unknown status";
+    }
+}
+
+int aexp_workspace_size(const aexp_problem *prob, int precision, size_t *bytes) {
+    int rc = check_problem(prob);
+    if (rc) return rc;
+    if ((rc = check_precision(precision))) return rc;
+    if (!bytes) return AEXP_ERR_INVALID_ARG;
+    OpLayout L;
+    op_layout(prob, precision, &L);
+    *bytes = L.bytes;
+    return AEXP_OK;
+}
+
+int aexp_prepare(const aexp_problem *prob, int precision, void *ws, size_t ws_bytes, void *stream) {
+    int rc = check_problem(prob);
+    if (rc) return rc;
+    if ((rc = check_precision(precision))) return rc;
+    OpLayout L;
+    op_layout(prob, precision, &L);
+    if ((rc = check_ws(ws, ws_bytes, L.bytes))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync((char *)ws + L.off_hdr, 0, sizeof(WsHeader), st);
+    if (e == cudaSuccess) e = op_prepare(prob, L, (char *)ws, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    record_prepared(ws, prob, precision);
+    return AEXP_OK;
+}
+
+int a_exp_forward(const aexp_problem *prob, int precision, const void *x, void *y, void *ws, size_t ws_bytes,
+                  void *stream) {
+    int rc = check_problem(prob);
+    if (rc) return rc;
+    if ((rc = check_precision(precision))) return rc;
+    if (!x || !y) return AEXP_ERR_INVALID_ARG;
+    if (!aligned(x, 8) || !aligned(y, 8)) return AEXP_ERR_MISALIGNED;
+    OpLayout L;
+    op_layout(prob, precision, &L);
+    if ((rc = check_ws(ws, ws_bytes, L.bytes))) return rc;
+    if (!is_prepared(ws, prob, precision)) return AEXP_ERR_NOT_PREPARED;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = (char *)ws;
+    cudaError_t e = op_coil_weight(L, (const float2 *)x, w, st);
+    if (e == cudaSuccess) e = op_forward_core(L, w, st);
+    if (e == cudaSuccess) e = op_forward_reduce_public(L, w, (float2 *)y, st);
+    return e == cudaSuccess ? AEXP_OK : cuda_fail(e);
+}
+
+int a_exp_adjoint(const aexp_problem *prob, int precision, const void *y, void *x, void *ws, size_t ws_bytes,
+                  void *stream) {
+    int rc = check_problem(prob);
+    if (rc) return rc;
+    if ((rc = check_precision(precision))) return rc;
+    if (!x || !y) return AEXP_ERR_INVALID_ARG;
+    if (!aligned(x, 8) || !aligned(y, 8)) return AEXP_ERR_MISALIGNED;
+    OpLayout L;
+    op_layout(prob, precision, &L);
+    if ((rc = check_ws(ws, ws_bytes, L.bytes))) return rc;
+    if (!is_prepared(ws, prob, precision)) return AEXP_ERR_NOT_PREPARED;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = (char *)ws;
+    float2 *yt = (float2 *)(w + L.off_yt);
+    cudaError_t e = op_transpose_y(L, (const float2 *)y, yt, st);
+    if (e == cudaSuccess) e = op_adjoint_core(L, yt, w, st);
+    if (e == cudaSuccess) e = op_adjoint_reduce(L, w, (float2 *)x, st);
+    return e == cudaSuccess ? AEXP_OK : cuda_fail(e);
+}
+
+void aexp_recon_opts_default(aexp_recon_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->precision = AEXP_FP32;
+    o->wavelet = AEXP_WAVELET_HAAR;
+    o->levels = 3;
+    o->n_power = 30;
+    o->lipschitz = 0.0;
+    o->x0 = nullptr;
+    o->power_init = nullptr;
+    o->use_graph = 1;
+}
+
+int aexp_recon_workspace_size(const aexp_problem *prob, const aexp_recon_opts *opts, size_t *bytes) {
+    int rc = check_problem(prob);
+    if (rc) return rc;
+    if ((rc = check_opts(opts))) return rc;
+    if (!bytes) return AEXP_ERR_INVALID_ARG;
+    RecLayout R;
+    rec_layout(prob, opts, &R);
+    *bytes = R.bytes;
+    return AEXP_OK;
+}
+
+int cs_recon(const aexp_problem *prob, const void *y, float lambda, int iters, const aexp_recon_opts *opts,
+             void *x_out, double *lipschitz_out, void *ws, size_t ws_bytes, void *stream) {
+    int rc = check_problem(prob);
+    if (rc) return rc;
+    if ((rc = check_opts(opts))) return rc;
+    if (!y || !x_out || iters < 0 || !(lambda >= 0.f)) return AEXP_ERR_INVALID_ARG;
+    if (!aligned(y, 8) || !aligned(x_out, 8) || !aligned(lipschitz_out, 8)) return AEXP_ERR_MISALIGNED;
+    RecLayout R;
+    rec_layout(prob, opts, &R);
+    if ((rc = check_ws(ws, ws_bytes, R.bytes))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = (char *)ws;
+
+    cudaError_t e = cudaMemsetAsync(w + R.op.off_hdr, 0, sizeof(WsHeader), st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (!opts->use_graph || st == nullptr) {
+        e = recon_issue(prob, R, opts, (const float2 *)y, lambda, iters, (float2 *)x_out,
+                        lipschitz_out, w, st);
+        if (e != cudaSuccess) return cuda_fail(e);
+        record_prepared(ws, prob, opts->precision);
+        return AEXP_OK;
+    }
+
+    std::vector<unsigned char> key;
+    put(key, *prob);
+    put(key, *opts);
+    put(key, y);
+    put(key, lambda);
+    put(key, iters);
+    put(key, x_out);
+    put(key, lipschitz_out);
+    put(key, ws_bytes);
+    std::lock_guard<std::mutex> lk(g_mu);
+    GraphEntry &ge = g_graphs[ws];
+    if (ge.exec == nullptr || ge.key != key) {
+        if (ge.exec) {
+            cudaGraphExecDestroy(ge.exec);
+            ge.exec = nullptr;
+        }
+        e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e);
+        cudaError_t ei = recon_issue(prob, R, opts, (const float2 *)y, lambda, iters, (float2 *)x_out,
+                                     lipschitz_out, w, st);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(st, &g);
+        if (ei != cudaSuccess || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(ei != cudaSuccess ? ei : e);
+        }
+        e = cudaGraphInstantiate(&ge.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            ge.exec = nullptr;
+            return cuda_fail(e);
+        }
+        ge.key = key;
+    }
+    e = cudaGraphLaunch(ge.exec, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    g_prepared[ws] = PrepRecord{*prob, opts->precision};
+    return AEXP_OK;
+}
+
+int aexp_power_lipschitz(const aexp_problem *prob, int precision, const void *v0, int n_power,
+                         double *lipschitz_out, void *ws, size_t ws_bytes, void *stream) {
+    int rc = check_problem(prob);
+    if (rc) return rc;
+    if ((rc = check_precision(precision))) return rc;
+    if (!v0 || !lipschitz_out || n_power < 1) return AEXP_ERR_INVALID_ARG;
+    if (!aligned(v0, 8) || !aligned(lipschitz_out, 8)) return AEXP_ERR_MISALIGNED;
+    aexp_recon_opts o;
+    aexp_recon_opts_default(&o);
+    o.precision = precision;
+    o.levels = 1;
+    RecLayout R;
+    rec_layout(prob, &o, &R);
+    if ((rc = check_ws(ws, ws_bytes, R.off_wave))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = (char *)ws;
+    cudaError_t e = cudaMemsetAsync(w + R.op.off_hdr, 0, sizeof(WsHeader), st);
+    if (e == cudaSuccess) e = op_prepare(prob, R.op, w, st);
+    if (e == cudaSuccess)
+        e = power_iteration(R.op, w, (const float2 *)v0, (float2 *)(w + R.off_v), (float2 *)(w + R.off_w), n_power,
+                            lipschitz_out, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    record_prepared(ws, prob, precision);
+    return AEXP_OK;
+}
+
+int aexp_wavelet_workspace_size(int nx, int ny, int wavelet, int levels, size_t *bytes) {
+    if (nx < 1 || ny < 1 || levels < 1 || levels > 12 || !bytes) return AEXP_ERR_INVALID_ARG;
+    if (wavelet != AEXP_WAVELET_HAAR && wavelet != AEXP_WAVELET_DB4) return AEXP_ERR_INVALID_ARG;
+    WaveLayout W;
+    wave_layout(nx, ny, wavelet, levels, &W);
+    *bytes = W.bytes;
+    return AEXP_OK;
+}
+
+int aexp_wavelet_prox(int nx, int ny, int wavelet, int levels, float tau, const void *in, void *out, void *ws,
+                      size_t ws_bytes, void *stream) {
+    size_t need;
+    int rc = aexp_wavelet_workspace_size(nx, ny, wavelet, levels, &need);
+    if (rc) return rc;
+    if (!in || !out || !(tau >= 0.f)) return AEXP_ERR_INVALID_ARG;
+    if (!aligned(in, 8) || !aligned(out, 8)) return AEXP_ERR_MISALIGNED;
+    if ((rc = check_ws(ws, ws_bytes, need))) return rc;
+    WaveLayout W;
+    wave_layout(nx, ny, wavelet, levels, &W);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = wave_forward(W, (const float2 *)in, (char *)ws, tau, nullptr, 1, st);
+    if (e == cudaSuccess) e = wave_inverse(W, (char *)ws, (float2 *)out, 0, 0.0, nullptr, nullptr, st);
+    return e == cudaSuccess ? AEXP_OK : cuda_fail(e);
+}
+
+int aexp_wavelet_forward(int nx, int ny, int wavelet, int levels, const void *in, void *coef, void *ws,
+                         size_t ws_bytes, void *stream) {
+    size_t need;
+    int rc = aexp_wavelet_workspace_size(nx, ny, wavelet, levels, &need);
+    if (rc) return rc;
+    if (!in || !coef) return AEXP_ERR_INVALID_ARG;
+    if (!aligned(in, 8) || !aligned(coef, 8)) return AEXP_ERR_MISALIGNED;
+    if ((rc = check_ws(ws, ws_bytes, need))) return rc;
+    WaveLayout W;
+    wave_layout(nx, ny, wavelet, levels, &W);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = wave_forward(W, (const float2 *)in, (char *)ws, 0.f, nullptr, 0, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(coef, (char *)ws + W.off_pyr, sizeof(float2) * (size_t)W.npx * W.npy,
+                            cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? AEXP_OK : cuda_fail(e);
+}
+
+int aexp_read_status(void *ws, void *stream, int *status) {
+    if (!ws || !status) return AEXP_ERR_INVALID_ARG;
+    if (!aligned(ws, kAlign)) return AEXP_ERR_MISALIGNED;
+    cudaStream_t st = (cudaStream_t)stream;
+    int s = 0;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemcpy(&s, ws, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(ws, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e);
+    *status = s;
+    return AEXP_OK;
+}
+
+}  // extern "C"

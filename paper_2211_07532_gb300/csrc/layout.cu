@@ -1,0 +1,131 @@
+// Host-side workspace layouts and launch-shape heuristics.
+#include <algorithm>
+
+#include "aexp_internal.cuh"
+
+namespace aexp {
+
+namespace {
+constexpr int kTargetBlocks = 152 * 4 * 4;  // SMs x resident blocks x waves
+
+int pad_terms(int n) { return n <= 4 ? 4 : n <= 8 ? 8 : n <= 12 ? 12 : 20; }
+int pad_coils(int n) { return n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : n <= 20 ? 20 : 32; }
+}  // namespace
+
+int fwd_mt_for(int CB) { return CB >= 32 ? 1 : CB >= 16 ? 2 : 4; }
+
+int op_layout(const aexp_problem *p, int precision, OpLayout *L) {
+    OpLayout o{};
+    o.nx = p->nx;
+    o.ny = p->ny;
+    o.nr = p->nx * p->ny;
+    o.nt = p->nt;
+    o.nc = p->nc;
+    o.nl = p->nl;
+    o.has_b0 = p->omega != nullptr;
+    o.nterms = o.nl + o.has_b0;
+    o.LP = pad_terms(o.nterms);
+    o.CB = pad_coils(o.nc);
+    o.precision = precision;
+    o.ntx = cdiv(o.nx, kTileSide);
+    o.nty = cdiv(o.ny, kTileSide);
+    o.ntiles = o.ntx * o.nty;
+    o.nr_pad = o.ntiles * kTileVox;
+    o.ntp = cdiv(o.nt, kTPad) * kTPad;
+
+    // forward: blocks own 128*mt samples and a contiguous run of tiles
+    o.fwd_mt = fwd_mt_for(o.CB);
+    o.fwd_tblocks = o.ntp / (kFwdThreads * o.fwd_mt);
+    {
+        int by_sum = cdiv(o.ntiles, 32);                       // <= 32 tiles (2048 voxels) per block
+        int by_occ = cdiv(kTargetBlocks, o.fwd_tblocks);
+        int s = std::max(by_sum, by_occ);
+        s = std::min(s, o.ntiles);
+        o.fwd_tiles_per_split = cdiv(o.ntiles, s);
+        o.fwd_splits = cdiv(o.ntiles, o.fwd_tiles_per_split);
+    }
+    // adjoint: blocks own 2 tiles (128 voxels) and a contiguous run of samples
+    o.adj_vblocks = cdiv(o.ntiles, 2);
+    {
+        int nstage = o.ntp / kAdjStageT;
+        int by_sum = cdiv(o.ntp, 2048);
+        int by_occ = cdiv(kTargetBlocks, o.adj_vblocks);
+        int s = std::min(std::max(by_sum, by_occ), nstage);
+        int stages_per = cdiv(nstage, s);
+        o.adj_t_per_split = stages_per * kAdjStageT;
+        o.adj_splits = cdiv(o.ntp, o.adj_t_per_split);
+    }
+
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off = align_up(off + bytes);
+        return at;
+    };
+    o.off_hdr = take(sizeof(WsHeader));
+    o.off_khi_l = take(sizeof(float) * o.LP * o.ntp);
+    o.off_klo_l = take(sizeof(float) * o.LP * o.ntp);
+    o.off_khi_t = take(sizeof(float) * o.LP * o.ntp);
+    o.off_h0 = take(sizeof(float) * o.LP * o.ntiles);
+    o.off_dh = take(sizeof(float) * o.LP * o.nr_pad);
+    o.off_f0 = take(sizeof(float) * (size_t)o.ntiles * o.ntp);
+    o.off_S = take(sizeof(float2) * (size_t)o.CB * o.nr_pad);
+    o.off_b = take(sizeof(float2) * (size_t)o.CB * o.nr_pad);
+    o.off_fpart = take(sizeof(float2) * (size_t)o.fwd_splits * o.ntp * o.CB);
+    o.off_yt = take(sizeof(float2) * (size_t)o.ntp * o.CB);
+    o.off_apart = take(sizeof(float2) * (size_t)o.adj_splits * o.nr_pad);
+    o.bytes = off;
+    *L = o;
+    return AEXP_OK;
+}
+
+int wave_layout(int nx, int ny, int wavelet, int levels, WaveLayout *W) {
+    WaveLayout w{};
+    w.nx = nx;
+    w.ny = ny;
+    w.levels = levels;
+    w.wavelet = wavelet;
+    int q = 1 << levels;
+    w.npx = cdiv(nx, q) * q;
+    w.npy = cdiv(ny, q) * q;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off = align_up(off + bytes);
+        return at;
+    };
+    w.off_pyr = take(sizeof(float2) * (size_t)w.npx * w.npy);
+    for (int j = 1; j < levels; ++j)
+        w.off_approx[j] = take(sizeof(float2) * (size_t)(w.npx >> j) * (w.npy >> j));
+    w.bytes = off;
+    *W = w;
+    return AEXP_OK;
+}
+
+int rec_layout(const aexp_problem *p, const aexp_recon_opts *opt, RecLayout *R) {
+    RecLayout r{};
+    int rc = op_layout(p, opt->precision, &r.op);
+    if (rc) return rc;
+    rc = wave_layout(p->nx, p->ny, opt->wavelet, opt->levels, &r.wv);
+    if (rc) return rc;
+    size_t off = r.op.bytes;
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off = align_up(off + bytes);
+        return at;
+    };
+    size_t nr = (size_t)r.op.nr;
+    // vectors first so that their offsets do not depend on the wavelet options
+    r.off_ymeas = take(sizeof(float2) * (size_t)r.op.ntp * r.op.CB);
+    r.off_xa = take(sizeof(float2) * nr);
+    r.off_xb = take(sizeof(float2) * nr);
+    r.off_z = take(sizeof(float2) * nr);
+    r.off_v = take(sizeof(float2) * nr);
+    r.off_w = take(sizeof(float2) * nr);
+    r.off_wave = take(r.wv.bytes);
+    r.bytes = off;
+    *R = r;
+    return AEXP_OK;
+}
+
+}  // namespace aexp

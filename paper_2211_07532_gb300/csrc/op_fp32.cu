@@ -1,0 +1,424 @@
+// A_exp and A_exp^H on FP32 CUDA cores (Eq. 1; Sec. 1 expanded model with B0 and
+// spherical-harmonic terms).
+//
+// Forward (y_c(t) = sum_r exp(-i phi) S_c(r) x(r)):  a block owns 128*MT samples
+// (MT per thread, coefficients k_l(t)/2pi held in registers) and a run of 8x8 voxel
+// tiles.  Per tile, one bulk (TMA) copy brings the tile's basis offsets dh[64][LP] and
+// coil-weighted image b[64][CB] into shared memory (double buffered, mbarrier
+// completion).  Every thread then walks the 64 voxels: LP FMAs of local phase on top
+// of the tabulated reference phase, reduction to [-1/2, 1/2] turns, one MUFU sincos,
+// and 4 FMAs per coil into register accumulators.  Partial sums per run of tiles are
+// reduced afterwards in a fixed order (deterministic).
+//
+// Adjoint (x(r) = sum_c conj S_c(r) sum_t exp(+i phi) y_c(t)):  a block owns two tiles
+// (one voxel per thread, basis offsets in registers) and a run of samples, staged by
+// bulk copies of k/2pi [TS][LP], y [TS][CB] and the two tiles' reference phases.
+// Per-coil sums stay in registers; the coil combination with conj(S_c) happens once
+// per voxel at the end of the run.
+#include "aexp_internal.cuh"
+
+namespace aexp {
+
+namespace {
+
+constexpr float kTwoPi = 6.283185307179586f;
+
+// Smallest of the per-voxel work: phase in turns -> (cos, sin) of 2 pi * frac.
+__device__ __forceinline__ void turns_sincos(float ph, float &s, float &c) {
+    ph = ph - rintf(ph);
+    __sincosf(ph * kTwoPi, &s, &c);
+}
+
+template <int CB, int LP, int MT>
+__global__ void __launch_bounds__(kFwdThreads, 2)
+    fwd_fp32_kernel(const float *__restrict__ khi_l, const float *__restrict__ f0, const float *__restrict__ dh,
+                    const float2 *__restrict__ b, float2 *__restrict__ part, int ntp, int ntiles,
+                    int tiles_per_split, int *status) {
+    constexpr unsigned DH_BYTES = kTileVox * LP * sizeof(float);
+    constexpr unsigned B_BYTES = kTileVox * CB * sizeof(float2);
+    constexpr unsigned STAGE = DH_BYTES + B_BYTES;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar[2];
+
+    const int tid = threadIdx.x;
+    const int split = blockIdx.y;
+    const int tile0 = split * tiles_per_split;
+    const int ntl = min(ntiles, tile0 + tiles_per_split) - tile0;
+    const int tbase = blockIdx.x * kFwdThreads * MT + tid;
+
+    float kh[MT][LP];
+#pragma unroll
+    for (int j = 0; j < MT; ++j)
+#pragma unroll
+        for (int l = 0; l < LP; ++l) kh[j][l] = khi_l[(size_t)l * ntp + tbase + j * kFwdThreads];
+
+    float are[MT][CB], aim[MT][CB];
+#pragma unroll
+    for (int j = 0; j < MT; ++j)
+#pragma unroll
+        for (int c = 0; c < CB; ++c) are[j][c] = aim[j][c] = 0.f;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int i) {
+        int buf = i & 1;
+        unsigned char *dst = smem + buf * STAGE;
+        size_t tile = (size_t)(tile0 + i);
+        mbar_arrive_expect_tx(&bar[buf], STAGE);
+        bulk_g2s(dst, dh + tile * kTileVox * LP, DH_BYTES, &bar[buf]);
+        bulk_g2s(dst + DH_BYTES, b + tile * kTileVox * CB, B_BYTES, &bar[buf]);
+    };
+    if (tid == 0) {
+        if (ntl > 0) issue(0);
+        if (ntl > 1) issue(1);
+    }
+
+    for (int i = 0; i < ntl; ++i) {
+        const int buf = i & 1;
+        bool ok = mbar_wait_bounded(&bar[buf], (i >> 1) & 1, status);
+        if (__syncthreads_or(!ok)) {
+            // a copy never completed: give in-flight copies a bounded chance to land, then leave
+            if (tid == 0)
+                for (int k = i; k < min(ntl, i + 2); ++k) mbar_wait_bounded(&bar[k & 1], (k >> 1) & 1, status);
+            __syncthreads();
+            return;
+        }
+        const float4 *sdh = reinterpret_cast<const float4 *>(smem + buf * STAGE);
+        const float4 *sb = reinterpret_cast<const float4 *>(smem + buf * STAGE + DH_BYTES);
+        float f[MT];
+#pragma unroll
+        for (int j = 0; j < MT; ++j) f[j] = f0[(size_t)(tile0 + i) * ntp + tbase + j * kFwdThreads];
+
+#pragma unroll 2
+        for (int v = 0; v < kTileVox; ++v) {
+            float d[LP];
+#pragma unroll
+            for (int q = 0; q < LP / 4; ++q) {
+                float4 w = sdh[v * (LP / 4) + q];
+                d[4 * q] = w.x;
+                d[4 * q + 1] = w.y;
+                d[4 * q + 2] = w.z;
+                d[4 * q + 3] = w.w;
+            }
+            float cr[MT], sr[MT];
+#pragma unroll
+            for (int j = 0; j < MT; ++j) {
+                // two interleaved chains halve the dependent-FMA latency
+                float p0 = f[j], p1 = 0.f;
+#pragma unroll
+                for (int l = 0; l < LP; l += 2) {
+                    p0 = fmaf(kh[j][l], d[l], p0);
+                    p1 = fmaf(kh[j][l + 1], d[l + 1], p1);
+                }
+                turns_sincos(p0 + p1, sr[j], cr[j]);
+            }
+            // E = cos - i sin;  acc += E * b
+#pragma unroll
+            for (int q = 0; q < CB / 2; ++q) {
+                float4 bb = sb[v * (CB / 2) + q];  // coils 2q, 2q+1
+#pragma unroll
+                for (int j = 0; j < MT; ++j) {
+                    are[j][2 * q] = fmaf(cr[j], bb.x, are[j][2 * q]);
+                    are[j][2 * q] = fmaf(sr[j], bb.y, are[j][2 * q]);
+                    aim[j][2 * q] = fmaf(cr[j], bb.y, aim[j][2 * q]);
+                    aim[j][2 * q] = fmaf(-sr[j], bb.x, aim[j][2 * q]);
+                    are[j][2 * q + 1] = fmaf(cr[j], bb.z, are[j][2 * q + 1]);
+                    are[j][2 * q + 1] = fmaf(sr[j], bb.w, are[j][2 * q + 1]);
+                    aim[j][2 * q + 1] = fmaf(cr[j], bb.w, aim[j][2 * q + 1]);
+                    aim[j][2 * q + 1] = fmaf(-sr[j], bb.z, aim[j][2 * q + 1]);
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && i + 2 < ntl) issue(i + 2);
+    }
+
+#pragma unroll
+    for (int j = 0; j < MT; ++j) {
+        float4 *dst = reinterpret_cast<float4 *>(part + ((size_t)split * ntp + tbase + j * kFwdThreads) * CB);
+#pragma unroll
+        for (int q = 0; q < CB / 2; ++q)
+            dst[q] = make_float4(are[j][2 * q], aim[j][2 * q], are[j][2 * q + 1], aim[j][2 * q + 1]);
+    }
+}
+
+template <int CB, int LP>
+__global__ void __launch_bounds__(kAdjThreads, 2)
+    adj_fp32_kernel(const float *__restrict__ khi_t, const float *__restrict__ f0, const float *__restrict__ dh,
+                    const float2 *__restrict__ Sp, const float2 *__restrict__ yt, float2 *__restrict__ part, int ntp,
+                    int ntiles, int t_per_split, int *status) {
+    constexpr int TS = kAdjStageT;
+    constexpr unsigned K_BYTES = TS * LP * sizeof(float);
+    constexpr unsigned Y_BYTES = TS * CB * sizeof(float2);
+    constexpr unsigned F_BYTES = TS * sizeof(float);
+    constexpr unsigned STAGE = K_BYTES + Y_BYTES + 2 * F_BYTES;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar[2];
+
+    const int tid = threadIdx.x;
+    const int split = blockIdx.y;
+    const int tileA = 2 * blockIdx.x;
+    const int tileB = tileA + 1 < ntiles ? tileA + 1 : tileA;  // odd count: duplicate, results discarded
+    const int p = blockIdx.x * kAdjThreads + tid;
+    const int my_tile = tileA + tid / kTileVox;
+    const bool valid = my_tile < ntiles;
+    const int t0 = split * t_per_split;
+    const int nst = (min(ntp, t0 + t_per_split) - t0) / TS;
+
+    float d[LP];
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(dh + (size_t)(valid ? p : 0) * LP);
+#pragma unroll
+        for (int q = 0; q < LP / 4; ++q) {
+            float4 w = src[q];
+            d[4 * q] = valid ? w.x : 0.f;
+            d[4 * q + 1] = valid ? w.y : 0.f;
+            d[4 * q + 2] = valid ? w.z : 0.f;
+            d[4 * q + 3] = valid ? w.w : 0.f;
+        }
+    }
+    float ure[CB], uim[CB];
+#pragma unroll
+    for (int c = 0; c < CB; ++c) ure[c] = uim[c] = 0.f;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int i) {
+        int buf = i & 1;
+        unsigned char *dst = smem + buf * STAGE;
+        size_t ts = (size_t)t0 + (size_t)i * TS;
+        mbar_arrive_expect_tx(&bar[buf], STAGE);
+        bulk_g2s(dst, khi_t + ts * LP, K_BYTES, &bar[buf]);
+        bulk_g2s(dst + K_BYTES, yt + ts * CB, Y_BYTES, &bar[buf]);
+        bulk_g2s(dst + K_BYTES + Y_BYTES, f0 + (size_t)tileA * ntp + ts, F_BYTES, &bar[buf]);
+        bulk_g2s(dst + K_BYTES + Y_BYTES + F_BYTES, f0 + (size_t)tileB * ntp + ts, F_BYTES, &bar[buf]);
+    };
+    if (tid == 0) {
+        if (nst > 0) issue(0);
+        if (nst > 1) issue(1);
+    }
+
+    const int half = tid / kTileVox;  // which of the two tiles (uniform per warp)
+    for (int i = 0; i < nst; ++i) {
+        const int buf = i & 1;
+        bool ok = mbar_wait_bounded(&bar[buf], (i >> 1) & 1, status);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0)
+                for (int k = i; k < min(nst, i + 2); ++k) mbar_wait_bounded(&bar[k & 1], (k >> 1) & 1, status);
+            __syncthreads();
+            return;
+        }
+        const float4 *sk = reinterpret_cast<const float4 *>(smem + buf * STAGE);
+        const float4 *sy = reinterpret_cast<const float4 *>(smem + buf * STAGE + K_BYTES);
+        const float *sf = reinterpret_cast<const float *>(smem + buf * STAGE + K_BYTES + Y_BYTES) + half * TS;
+
+#pragma unroll 2
+        for (int s = 0; s < TS; ++s) {
+            float p0 = sf[s], p1 = 0.f;
+#pragma unroll
+            for (int q = 0; q < LP / 4; ++q) {
+                float4 kk = sk[s * (LP / 4) + q];
+                p0 = fmaf(kk.x, d[4 * q], p0);
+                p1 = fmaf(kk.y, d[4 * q + 1], p1);
+                p0 = fmaf(kk.z, d[4 * q + 2], p0);
+                p1 = fmaf(kk.w, d[4 * q + 3], p1);
+            }
+            float sn, cs;
+            turns_sincos(p0 + p1, sn, cs);
+            // conj(E) = cos + i sin;  u += conj(E) * y
+#pragma unroll
+            for (int q = 0; q < CB / 2; ++q) {
+                float4 yy = sy[s * (CB / 2) + q];
+                ure[2 * q] = fmaf(cs, yy.x, ure[2 * q]);
+                ure[2 * q] = fmaf(-sn, yy.y, ure[2 * q]);
+                uim[2 * q] = fmaf(cs, yy.y, uim[2 * q]);
+                uim[2 * q] = fmaf(sn, yy.x, uim[2 * q]);
+                ure[2 * q + 1] = fmaf(cs, yy.z, ure[2 * q + 1]);
+                ure[2 * q + 1] = fmaf(-sn, yy.w, ure[2 * q + 1]);
+                uim[2 * q + 1] = fmaf(cs, yy.w, uim[2 * q + 1]);
+                uim[2 * q + 1] = fmaf(sn, yy.z, uim[2 * q + 1]);
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && i + 2 < nst) issue(i + 2);
+    }
+
+    if (valid) {
+        const float4 *s4 = reinterpret_cast<const float4 *>(Sp + (size_t)p * CB);
+        float xr = 0.f, xi = 0.f;
+#pragma unroll
+        for (int q = 0; q < CB / 2; ++q) {
+            float4 sv = s4[q];
+            // conj(S) * u
+            xr = fmaf(sv.x, ure[2 * q], xr);
+            xr = fmaf(sv.y, uim[2 * q], xr);
+            xi = fmaf(sv.x, uim[2 * q], xi);
+            xi = fmaf(-sv.y, ure[2 * q], xi);
+            xr = fmaf(sv.z, ure[2 * q + 1], xr);
+            xr = fmaf(sv.w, uim[2 * q + 1], xr);
+            xi = fmaf(sv.z, uim[2 * q + 1], xi);
+            xi = fmaf(-sv.w, ure[2 * q + 1], xi);
+        }
+        part[(size_t)split * (size_t)(ntiles * kTileVox) + p] = make_float2(xr, xi);
+    }
+}
+
+// ---- reductions of the partial sums (fixed order => deterministic) ----
+
+__global__ void fwd_reduce_public_kernel(const float2 *part, int splits, int ntp, int CB, int nt, int nc, float2 *y) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)nt * CB) return;
+    int t = (int)(i / CB), c = (int)(i % CB);
+    if (c >= nc) return;
+    float2 s = make_float2(0.f, 0.f);
+    for (int k = 0; k < splits; ++k) {
+        float2 v = part[((size_t)k * ntp + t) * CB + c];
+        s.x += v.x;
+        s.y += v.y;
+    }
+    y[(size_t)c * nt + t] = s;
+}
+
+__global__ void fwd_reduce_residual_kernel(const float2 *part, int splits, int ntp, int CB, int nt, int nc,
+                                           const float2 *ymeas, float2 *rt) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)ntp * CB) return;
+    int t = (int)(i / CB), c = (int)(i % CB);
+    float2 s = make_float2(0.f, 0.f);
+    if (t < nt && c < nc) {
+        for (int k = 0; k < splits; ++k) {
+            float2 v = part[((size_t)k * ntp + t) * CB + c];
+            s.x += v.x;
+            s.y += v.y;
+        }
+        if (ymeas) {
+            s.x -= ymeas[i].x;
+            s.y -= ymeas[i].y;
+        }
+    }
+    rt[i] = s;
+}
+
+__global__ void adj_reduce_kernel(const float2 *part, int splits, int nr_pad, int nx, int ny, int ntx,
+                                  const WsHeader *hdr, const float2 *z, float2 *out) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nx * ny) return;
+    int ix = r % nx, iy = r / nx;
+    int p = ((iy / kTileSide) * ntx + ix / kTileSide) * kTileVox + (iy % kTileSide) * kTileSide + ix % kTileSide;
+    float2 s = make_float2(0.f, 0.f);
+    for (int k = 0; k < splits; ++k) {
+        float2 v = part[(size_t)k * nr_pad + p];
+        s.x += v.x;
+        s.y += v.y;
+    }
+    if (z) {  // gradient step of Eq. (1): v = z - (1/L_f) * 2 A^H (A z - y)
+        float step = (float)(2.0 / hdr->lipschitz);
+        float2 zv = z[r];
+        s.x = zv.x - step * s.x;
+        s.y = zv.y - step * s.y;
+    }
+    out[r] = s;
+}
+
+// ---- dispatch over the compile-time coil / term paddings ----
+
+template <int CB, int LP>
+cudaError_t launch_fwd(const OpLayout &L, char *ws, cudaStream_t st) {
+    constexpr int MT = CB >= 32 ? 1 : CB >= 16 ? 2 : 4;
+    constexpr unsigned STAGE = kTileVox * LP * sizeof(float) + kTileVox * CB * sizeof(float2);
+    auto kern = fwd_fp32_kernel<CB, LP, MT>;
+    if (2 * STAGE > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * STAGE);
+        if (e != cudaSuccess) return e;
+    }
+    WsHeader *hdr = (WsHeader *)(ws + L.off_hdr);
+    kern<<<dim3(L.fwd_tblocks, L.fwd_splits), kFwdThreads, 2 * STAGE, st>>>(
+        (const float *)(ws + L.off_khi_l), (const float *)(ws + L.off_f0), (const float *)(ws + L.off_dh),
+        (const float2 *)(ws + L.off_b), (float2 *)(ws + L.off_fpart), L.ntp, L.ntiles, L.fwd_tiles_per_split,
+        &hdr->status);
+    return cudaGetLastError();
+}
+
+template <int CB, int LP>
+cudaError_t launch_adj(const OpLayout &L, const float2 *yt, char *ws, cudaStream_t st) {
+    constexpr unsigned STAGE = kAdjStageT * (LP * sizeof(float) + CB * sizeof(float2) + 2 * sizeof(float));
+    auto kern = adj_fp32_kernel<CB, LP>;
+    if (2 * STAGE > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * STAGE);
+        if (e != cudaSuccess) return e;
+    }
+    WsHeader *hdr = (WsHeader *)(ws + L.off_hdr);
+    kern<<<dim3(L.adj_vblocks, L.adj_splits), kAdjThreads, 2 * STAGE, st>>>(
+        (const float *)(ws + L.off_khi_t), (const float *)(ws + L.off_f0), (const float *)(ws + L.off_dh),
+        (const float2 *)(ws + L.off_S), yt, (float2 *)(ws + L.off_apart), L.ntp, L.ntiles, L.adj_t_per_split,
+        &hdr->status);
+    return cudaGetLastError();
+}
+
+#define AEXP_DISPATCH_LP(FN, CBV, ...)                   \
+    switch (L.LP) {                                      \
+        case 4: return FN<CBV, 4>(__VA_ARGS__);          \
+        case 8: return FN<CBV, 8>(__VA_ARGS__);          \
+        case 12: return FN<CBV, 12>(__VA_ARGS__);        \
+        default: return FN<CBV, 20>(__VA_ARGS__);        \
+    }
+
+#define AEXP_DISPATCH(FN, ...)                                   \
+    switch (L.CB) {                                              \
+        case 4: AEXP_DISPATCH_LP(FN, 4, __VA_ARGS__)             \
+        case 8: AEXP_DISPATCH_LP(FN, 8, __VA_ARGS__)             \
+        case 16: AEXP_DISPATCH_LP(FN, 16, __VA_ARGS__)           \
+        case 20: AEXP_DISPATCH_LP(FN, 20, __VA_ARGS__)           \
+        default: AEXP_DISPATCH_LP(FN, 32, __VA_ARGS__)           \
+    }
+
+}  // namespace
+
+cudaError_t op_forward_core(const OpLayout &L, char *ws, cudaStream_t st) {
+    AEXP_DISPATCH(launch_fwd, L, ws, st)
+}
+
+cudaError_t op_adjoint_core(const OpLayout &L, const float2 *yt, char *ws, cudaStream_t st) {
+    AEXP_DISPATCH(launch_adj, L, yt, ws, st)
+}
+
+cudaError_t op_forward_reduce_public(const OpLayout &L, char *ws, float2 *y, cudaStream_t st) {
+    size_t n = (size_t)L.nt * L.CB;
+    fwd_reduce_public_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        (const float2 *)(ws + L.off_fpart), L.fwd_splits, L.ntp, L.CB, L.nt, L.nc, y);
+    return cudaGetLastError();
+}
+
+cudaError_t op_forward_reduce_residual(const OpLayout &L, char *ws, const float2 *ymeas_t, float2 *rt,
+                                       cudaStream_t st) {
+    size_t n = (size_t)L.ntp * L.CB;
+    fwd_reduce_residual_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        (const float2 *)(ws + L.off_fpart), L.fwd_splits, L.ntp, L.CB, L.nt, L.nc, ymeas_t, rt);
+    return cudaGetLastError();
+}
+
+cudaError_t op_adjoint_reduce(const OpLayout &L, char *ws, float2 *out, cudaStream_t st) {
+    adj_reduce_kernel<<<cdiv(L.nr, 256), 256, 0, st>>>((const float2 *)(ws + L.off_apart), L.adj_splits, L.nr_pad,
+                                                      L.nx, L.ny, L.ntx, (const WsHeader *)(ws + L.off_hdr),
+                                                      nullptr, out);
+    return cudaGetLastError();
+}
+
+cudaError_t op_adjoint_reduce_step(const OpLayout &L, char *ws, const float2 *z, float2 *out, cudaStream_t st) {
+    adj_reduce_kernel<<<cdiv(L.nr, 256), 256, 0, st>>>((const float2 *)(ws + L.off_apart), L.adj_splits, L.nr_pad,
+                                                      L.nx, L.ny, L.ntx, (const WsHeader *)(ws + L.off_hdr), z,
+                                                      out);
+    return cudaGetLastError();
+}
+
+}  // namespace aexp

@@ -1,0 +1,128 @@
+"""Host-side checks of the C ABI: the library builds for sm_103a, loads, exports every
+entry point include/aexp.h declares, and rejects bad arguments before touching the GPU.
+No call here launches device work."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2211_07532_gb300 import build
+    build.build()
+    import paper_2211_07532_gb300 as ax
+    return ax.lib()
+
+
+def declared_names():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names += re.findall(r"^AEXP_API\s+(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", txt, re.M)
+    return names
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_names()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_binding_covers_every_declared_symbol():
+    import paper_2211_07532_gb300 as ax
+    bound = {s[0] for s in ax.SIGNATURES}
+    assert set(declared_names()) <= bound
+
+
+def test_internal_symbols_are_hidden():
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", os.path.join(ROOT, "paper_2211_07532_gb300", "libaexp.so")],
+                         capture_output=True, text=True).stdout
+    assert "_ZN4aexp" not in out
+
+
+def test_host_only_queries(L):
+    import paper_2211_07532_gb300 as ax
+    assert L.aexp_version() >= 100
+    assert L.aexp_status_string(0) == b"ok"
+    assert L.aexp_status_string(-8).startswith(b"workspace not prepared")
+    o = ax.CReconOpts()
+    L.aexp_recon_opts_default(ctypes.byref(o))
+    assert (o.precision, o.wavelet, o.levels, o.n_power, o.use_graph) == (0, 0, 3, 30, 1)
+    n = ctypes.c_size_t()
+    assert L.aexp_wavelet_workspace_size(200, 200, 1, 4, ctypes.byref(n)) == 0
+    assert n.value >= 208 * 208 * 8
+
+
+def _fake_problem(nx=64, ny=64, nt=2048, nc=8, nl=9, omega=True):
+    import paper_2211_07532_gb300 as ax
+    base = 1 << 20  # fake, aligned, never dereferenced by host-only calls
+    return ax.CProblem(nx, ny, nt, nc, nl, base, base + 4096, base if omega else None, base if omega else None, base)
+
+
+def test_workspace_size_is_host_arithmetic(L):
+    n = ctypes.c_size_t()
+    p = _fake_problem()
+    assert L.aexp_workspace_size(ctypes.byref(p), 0, ctypes.byref(n)) == 0
+    # 8 coils -> 8 padded, 9 terms + B0 -> 12 padded; the reference phase table is one float per tile and sample
+    assert n.value >= 64 * 2048 * 4
+    p2 = _fake_problem(nx=200, ny=200, nt=24000, nc=32, nl=16)
+    n2 = ctypes.c_size_t()
+    assert L.aexp_workspace_size(ctypes.byref(p2), 0, ctypes.byref(n2)) == 0
+    assert n2.value > n.value
+
+
+@pytest.mark.parametrize("field,value,code", [
+    ("nx", 0, -1), ("nt", -3, -1), ("nc", 0, -1), ("nc", 33, -3), ("nl", 20, -3),
+])
+def test_invalid_problems_are_rejected(L, field, value, code):
+    p = _fake_problem()
+    setattr(p, field, value)
+    n = ctypes.c_size_t()
+    assert L.aexp_workspace_size(ctypes.byref(p), 0, ctypes.byref(n)) == code
+
+
+def test_misaligned_and_null_pointers(L):
+    import paper_2211_07532_gb300 as ax
+    n = ctypes.c_size_t()
+    p = _fake_problem()
+    p.S = (1 << 20) + 4
+    assert L.aexp_workspace_size(ctypes.byref(p), 0, ctypes.byref(n)) == -2
+    p = _fake_problem()
+    p.S = None
+    assert L.aexp_workspace_size(ctypes.byref(p), 0, ctypes.byref(n)) == -1
+    p = _fake_problem()
+    # workspace checks happen before any launch
+    assert L.aexp_prepare(ctypes.byref(p), 0, ctypes.c_void_p((1 << 30) + 8), 1 << 30, None) == -2
+    assert L.aexp_prepare(ctypes.byref(p), 0, ctypes.c_void_p(1 << 30), 16, None) == -4
+    assert L.a_exp_forward(ctypes.byref(p), 0, None, ctypes.c_void_p(1 << 20), ctypes.c_void_p(1 << 30),
+                           1 << 40, None) == -1
+    # unprepared workspace
+    assert L.a_exp_forward(ctypes.byref(p), 0, ctypes.c_void_p(1 << 20), ctypes.c_void_p(1 << 20),
+                           ctypes.c_void_p(1 << 30), 1 << 40, None) == -8
+    # unsupported precision for now / bad enum
+    assert L.aexp_workspace_size(ctypes.byref(p), 7, ctypes.byref(n)) == -1
+    o = ax.CReconOpts()
+    L.aexp_recon_opts_default(ctypes.byref(o))
+    o.levels = 0
+    assert L.aexp_recon_workspace_size(ctypes.byref(p), ctypes.byref(o), ctypes.byref(n)) == -1
+    L.aexp_recon_opts_default(ctypes.byref(o))
+    o.n_power = 0
+    assert L.aexp_recon_workspace_size(ctypes.byref(p), ctypes.byref(o), ctypes.byref(n)) == -1
+    o.lipschitz = 3.0
+    assert L.aexp_recon_workspace_size(ctypes.byref(p), ctypes.byref(o), ctypes.byref(n)) == 0
+
+
+def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
+    import paper_2211_07532_gb300 as ax
+    monkeypatch.setattr(ax, "_lib", None)
+    monkeypatch.setattr(ax, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        ax.lib()
