@@ -182,6 +182,17 @@ def run_ours(args):
         dist.init_process_group("gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    side = torch.cuda.Stream(dev)      # a non-default stream, so cs_recon can capture its CUDA graph
+    with torch.cuda.stream(side):
+        _run_ours(args, rank, world, local, dev)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def _run_ours(args, rank, world, local, dev):
+    import torch
+    import torch.distributed as dist
 
     from paper_2211_07532_gb300 import build as _b
     _b.build()
@@ -334,9 +345,30 @@ def run_ours(args):
             "cpu_baseline": cpu,
         }
         print(json.dumps(out))
-    if world > 1:
-        dist.barrier()
-        dist.destroy_process_group()
+
+
+def run_op_only(args):
+    """Operator applications alone on the bench workload (a small, bounded profiling target)."""
+    import torch
+    from paper_2211_07532_gb300 import build as _b
+    _b.build()
+    import paper_2211_07532_gb300 as ax
+    from paper_2211_07532_gb300 import synth
+
+    precision = {"fp32": ax.FP32, "bf16": ax.BF16_TC, "fp16x2": ax.FP16X2_TC}[args.form]
+    p = synth.slice_200()
+    prob = ax.Problem.from_arrays(p)
+    ws = ax.workspace(prob, precision)
+    ax.prepare(prob, ws, precision)
+    x = torch.as_tensor(p["x_gt"], device="cuda")
+    y = torch.as_tensor(p["noise"], device="cuda")
+    for _ in range(args.reps):
+        yo = ax.a_exp_forward(prob, x, ws, precision=precision)
+        xo = ax.a_exp_adjoint(prob, y, ws, precision=precision)
+    torch.cuda.synchronize()
+    assert ax.read_status(ws) == 0
+    print(json.dumps({"mode": "op", "reps": args.reps, "y_norm": float(yo.abs().sum()),
+                      "x_norm": float(xo.abs().sum())}))
 
 
 def main():
@@ -349,8 +381,13 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=["recon", "op"], default="recon",
+                    help="op: only prepare + `--reps` forward/adjoint applications (profiling target)")
+    ap.add_argument("--reps", type=int, default=2)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.mode == "op":
+        run_op_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

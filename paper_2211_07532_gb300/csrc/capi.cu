@@ -28,6 +28,9 @@ int check_problem(const aexp_problem *p) {
     int nterms = p->nl + (p->omega != nullptr);
     if (nterms < 1) return AEXP_ERR_INVALID_ARG;
     if (nterms > kMaxTerms || p->nc > kMaxCoils) return AEXP_ERR_UNSUPPORTED;
+    // grid.y limits: one row of blocks per tile (reference phases) and per sample stage
+    if ((long long)cdiv(p->nx, kTileSide) * cdiv(p->ny, kTileSide) > 65535) return AEXP_ERR_UNSUPPORTED;
+    if ((long long)p->nt > 65535LL * kAdjStageT - kTPad) return AEXP_ERR_UNSUPPORTED;
     if ((p->nl > 0 && (!p->k || !p->h)) || !p->S) return AEXP_ERR_INVALID_ARG;
     if (p->omega && !p->t) return AEXP_ERR_INVALID_ARG;
     if (!aligned(p->k, 4) || !aligned(p->h, 4) || !aligned(p->omega, 4) || !aligned(p->t, 4) ||

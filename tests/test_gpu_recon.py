@@ -50,9 +50,11 @@ def test_tiny64_fista_matches_oracle(ax, tiny, use_graph):
     p, y, lam, Lf = tiny
     ref = recon.fista(p, y, lam, p["iters"], Lf, "haar", 3)
     prob = ax.Problem.from_arrays(p)
-    x, L = ax.cs_recon(prob, torch.as_tensor(y, device="cuda"), lam, p["iters"], wavelet="haar", levels=3,
-                       lipschitz=Lf, use_graph=use_graph)
-    xg = x.cpu().numpy()
+    side = torch.cuda.Stream()  # graph capture needs a non-default stream
+    with torch.cuda.stream(side):
+        x, L = ax.cs_recon(prob, torch.as_tensor(y, device="cuda"), lam, p["iters"], wavelet="haar", levels=3,
+                           lipschitz=Lf, use_graph=use_graph)
+        xg = x.cpu().numpy()
     e = rel(xg, ref)
     print(f"tiny64 fista rel {e:.2e}; nrmse vs phantom gpu {rel(xg, p['x_gt']):.4f} oracle {rel(ref, p['x_gt']):.4f}")
     assert e < TOL
@@ -65,11 +67,14 @@ def test_tiny64_graph_replay_is_identical(ax, tiny):
     yg = torch.as_tensor(y, device="cuda")
     opts = ax.recon_opts(wavelet="haar", levels=3, lipschitz=Lf)
     ws = ax.recon_workspace(prob, opts)
-    x1, _ = ax.cs_recon(prob, yg, lam, 5, opts=opts, ws=ws)
-    a = x1.clone()
-    x2, _ = ax.cs_recon(prob, yg, lam, 5, opts=opts, ws=ws, x_out=x1)
-    assert torch.equal(a, x2)
-    assert ax.read_status(ws) == 0
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        x1, _ = ax.cs_recon(prob, yg, lam, 5, opts=opts, ws=ws)      # captured
+        a = x1.clone()
+        x2, _ = ax.cs_recon(prob, yg, lam, 5, opts=opts, ws=ws, x_out=x1)  # replayed
+        torch.cuda.synchronize()
+        assert torch.equal(a, x2)
+        assert ax.read_status(ws) == 0
 
 
 def test_fista_with_start_image(ax, tiny):
