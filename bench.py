@@ -308,8 +308,13 @@ def _run_ours(args, rank, world, local, dev):
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
+        import hashlib
         with open(tfile) as f:
-            traffic = json.load(f).get(f"{args.form}:{dom}")
+            rec = json.load(f)
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            current = hashlib.sha256(f.read()).hexdigest()[:16]
+        if current == rec.get("sha256_16"):           # counters only valid for the profiled source
+            traffic = rec.get(f"{args.form}:{dom}")
 
     if rank == 0:
         cpu = None
