@@ -167,6 +167,32 @@ AEXP_API int aexp_wavelet_forward(int nx, int ny, int wavelet, int levels, const
                          void *ws, size_t ws_bytes, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Allocation-free wavelet step (no counterpart in the paper)
+ * --------------------------------------------------------------------------- */
+
+/* Same result as aexp_wavelet_prox, but without a caller workspace: the scratch (the
+ * wavelet pyramid and the intermediate approximation images) is a fixed 4 MiB device
+ * array inside the library, reserved on every GPU that loads the library until the
+ * process exits.  For callers that cannot allocate device memory at the point of the
+ * call -- code running while a CUDA stream is being captured (cudaMalloc is not allowed
+ * then), real-time reconstruction services that reserve all GPU memory at start-up and
+ * forbid later allocations, and plug-ins whose host framework owns the device allocator.
+ * The call itself allocates nothing (no cudaMalloc, cudaFree or allocating library call).
+ * - Size limit: the zero-padded image (each side rounded up to a multiple of 2^levels)
+ *   must have a pyramid of at most 4 MiB, about 4/3 * npy * npx * 8 bytes, i.e. up to
+ *   512 x 512; larger sizes return AEXP_ERR_UNSUPPORTED and launch nothing.
+ * - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *   with that device current, and caches it; make that first call before any stream
+ *   capture.
+ * - All calls share the one array and it keeps the last call's contents; each call writes
+ *   every scratch byte it reads, so nothing is cleared.  Calls that overlap on the GPU
+ *   (different streams, or different host threads on one device) race on the array:
+ *   order them, e.g. on one stream.
+ * in, out: [ny][nx] complex64 device arrays (may alias); tau >= 0. */
+AEXP_API int aexp_wavelet_prox_static(int nx, int ny, int wavelet, int levels, float tau, const void *in,
+                                      void *out, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Status
  * --------------------------------------------------------------------------- */
 

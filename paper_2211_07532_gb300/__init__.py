@@ -68,6 +68,7 @@ SIGNATURES = [
     ("aexp_wavelet_workspace_size", _I, [_I, _I, _I, _I, ctypes.POINTER(_SZ)]),
     ("aexp_wavelet_prox", _I, [_I, _I, _I, _I, ctypes.c_float, _P, _P, _P, _SZ, _P]),
     ("aexp_wavelet_forward", _I, [_I, _I, _I, _I, _P, _P, _P, _SZ, _P]),
+    ("aexp_wavelet_prox_static", _I, [_I, _I, _I, _I, ctypes.c_float, _P, _P, _P]),
     ("aexp_read_status", _I, [_P, _P, ctypes.POINTER(_I)]),
     ("aexp_status_string", ctypes.c_char_p, [_I]),
     ("aexp_last_cuda_error", _I, []),

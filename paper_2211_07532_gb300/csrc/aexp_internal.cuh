@@ -120,6 +120,9 @@ cudaError_t set_lipschitz(const OpLayout &L, char *ws, double value, double *out
 cudaError_t recon_issue(const aexp_problem *p, const RecLayout &R, const aexp_recon_opts *o, const float2 *y,
                         float lam, int iters, float2 *x_out, double *lip_out, char *ws, cudaStream_t st);
 
+// Record a CUDA error for aexp_last_cuda_error() (capi.cu).
+void aexp_set_last_cuda_error(int e);
+
 // Error flag writers used by the kernels.
 __device__ __forceinline__ void set_status(int *status, int code) {
     atomicCAS(status, 0, code);

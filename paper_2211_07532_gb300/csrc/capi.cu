@@ -100,6 +100,8 @@ int check_opts(const aexp_recon_opts *o) {
 
 }  // namespace
 
+void aexp::aexp_set_last_cuda_error(int e) { g_last_cuda_error = e; }
+
 extern "C" {
 
 int aexp_version(void) { return 100; }
