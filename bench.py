@@ -367,13 +367,27 @@ def run_op_only(args):
     ax.prepare(prob, ws, precision)
     x = torch.as_tensor(p["x_gt"], device="cuda")
     y = torch.as_tensor(p["noise"], device="cuda")
+    ms = {"a_exp_forward": [], "a_exp_adjoint": []}
     for _ in range(args.reps):
-        yo = ax.a_exp_forward(prob, x, ws, precision=precision)
-        xo = ax.a_exp_adjoint(prob, y, ws, precision=precision)
+        for name, fn in (("a_exp_forward", lambda: ax.a_exp_forward(prob, x, ws, precision=precision)),
+                         ("a_exp_adjoint", lambda: ax.a_exp_adjoint(prob, y, ws, precision=precision))):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            out = fn()
+            b.record()
+            b.synchronize()
+            ms[name].append(a.elapsed_time(b))
+            if name == "a_exp_forward":
+                yo = out
+            else:
+                xo = out
     torch.cuda.synchronize()
     assert ax.read_status(ws) == 0
-    print(json.dumps({"mode": "op", "reps": args.reps, "y_norm": float(yo.abs().sum()),
-                      "x_norm": float(xo.abs().sum())}))
+    vsc = p["nx"] * p["ny"] * p["nt"] * p["nc"]
+    best = {k: min(v) for k, v in ms.items()}
+    print(json.dumps({"mode": "op", "form": args.form, "reps": args.reps, "ms_min": best,
+                      "gvsc_per_s": {k: vsc / (v / 1e3) / 1e9 for k, v in best.items()},
+                      "y_norm": float(yo.abs().sum()), "x_norm": float(xo.abs().sum())}))
 
 
 def main():

@@ -44,17 +44,17 @@ struct OpLayout {
     int nx, ny, nr, nt, nc, nl, has_b0;
     int nterms;      // nl + has_b0
     int LP;          // padded term count (template): 4, 8, 12 or 20
-    int CB;          // padded coil count (template): 4, 8, 16, 20 or 32
+    int CB;          // padded coil count (template): 4, 8, 16, 20, 32 (FP32) or 8, 16, 32 (TC)
     int ntx, nty, ntiles, nr_pad;
     int ntp;         // nt padded to kTPad
     int precision;
     // forward split
     int fwd_mt, fwd_tblocks, fwd_splits, fwd_tiles_per_split;
     // adjoint split
-    int adj_vblocks, adj_splits, adj_t_per_split;
+    int adj_mr, adj_vblocks, adj_splits, adj_t_per_split;
     // byte offsets into the workspace
     size_t off_hdr, off_khi_l, off_klo_l, off_khi_t, off_h0, off_dh, off_f0, off_S, off_b,
-        off_fpart, off_yt, off_apart;
+        off_fpart, off_yt, off_apart, off_ypk;
     size_t bytes;
 };
 
@@ -71,6 +71,17 @@ struct RecLayout {
     size_t off_wave, off_ymeas, off_xa, off_xb, off_z, off_v, off_w;
     size_t bytes;
 };
+
+// Register blocking of the FP32 operator kernels: samples per thread in the forward,
+// voxels per thread in the adjoint (each staged value is reused this many times).
+#ifndef AEXP_FWD_MT32
+#define AEXP_FWD_MT32 2
+#endif
+#ifndef AEXP_ADJ_MR32
+#define AEXP_ADJ_MR32 2
+#endif
+constexpr int fwd_mt_for(int CB) { return CB >= 32 ? AEXP_FWD_MT32 : CB >= 16 ? 2 : 4; }
+constexpr int adj_mr_for(int CB) { return CB >= 32 ? AEXP_ADJ_MR32 : CB >= 16 ? 2 : CB >= 8 ? 2 : 4; }
 
 inline size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
 inline int cdiv(int a, int b) { return (a + b - 1) / b; }
@@ -99,6 +110,20 @@ cudaError_t op_adjoint_core(const OpLayout &L, const float2 *yt, char *ws, cudaS
 cudaError_t op_adjoint_reduce(const OpLayout &L, char *ws, float2 *out, cudaStream_t st);
 cudaError_t op_adjoint_reduce_step(const OpLayout &L, char *ws, const float2 *z, float2 *out,
                                    cudaStream_t st);
+
+// Tensor-core forms (op_tc.cu): the forward packs S*x itself; the adjoint packs yt.
+cudaError_t op_forward_tc(const OpLayout &L, const float2 *x, char *ws, cudaStream_t st);
+cudaError_t op_adjoint_tc(const OpLayout &L, const float2 *yt, char *ws, cudaStream_t st);
+cudaError_t op_forward_reduce_planar_public(const OpLayout &L, char *ws, float2 *y, cudaStream_t st);
+cudaError_t op_forward_reduce_planar_residual(const OpLayout &L, char *ws, const float2 *ymeas_t, float2 *rt,
+                                              cudaStream_t st);
+
+// Precision dispatch (op_dispatch.cu): one application = apply + reduce.
+cudaError_t op_apply_forward(const OpLayout &L, const float2 *x, char *ws, cudaStream_t st);
+cudaError_t op_reduce_forward_public(const OpLayout &L, char *ws, float2 *y, cudaStream_t st);
+cudaError_t op_reduce_forward_residual(const OpLayout &L, char *ws, const float2 *ymeas_t, float2 *rt,
+                                       cudaStream_t st);
+cudaError_t op_apply_adjoint(const OpLayout &L, const float2 *yt, char *ws, cudaStream_t st);
 
 // Wavelet (wavelet.cu).  tau = lam / L_f with L_f from `lipschitz` (device), or
 // lam itself when lipschitz == nullptr.  threshold == 0 disables shrinkage.

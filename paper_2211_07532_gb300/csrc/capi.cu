@@ -42,7 +42,7 @@ int check_problem(const aexp_problem *p) {
 int check_precision(int precision) {
     if (precision != AEXP_FP32 && precision != AEXP_BF16_TC && precision != AEXP_FP16X2_TC)
         return AEXP_ERR_INVALID_ARG;
-    if (precision != AEXP_FP32) return AEXP_ERR_UNSUPPORTED;
+    if (precision == AEXP_FP16X2_TC) return AEXP_ERR_UNSUPPORTED;
     return AEXP_OK;
 }
 
@@ -162,9 +162,8 @@ int a_exp_forward(const aexp_problem *prob, int precision, const void *x, void *
     if (!is_prepared(ws, prob, precision)) return AEXP_ERR_NOT_PREPARED;
     cudaStream_t st = (cudaStream_t)stream;
     char *w = (char *)ws;
-    cudaError_t e = op_coil_weight(L, (const float2 *)x, w, st);
-    if (e == cudaSuccess) e = op_forward_core(L, w, st);
-    if (e == cudaSuccess) e = op_forward_reduce_public(L, w, (float2 *)y, st);
+    cudaError_t e = op_apply_forward(L, (const float2 *)x, w, st);
+    if (e == cudaSuccess) e = op_reduce_forward_public(L, w, (float2 *)y, st);
     return e == cudaSuccess ? AEXP_OK : cuda_fail(e);
 }
 
@@ -183,7 +182,7 @@ int a_exp_adjoint(const aexp_problem *prob, int precision, const void *y, void *
     char *w = (char *)ws;
     float2 *yt = (float2 *)(w + L.off_yt);
     cudaError_t e = op_transpose_y(L, (const float2 *)y, yt, st);
-    if (e == cudaSuccess) e = op_adjoint_core(L, yt, w, st);
+    if (e == cudaSuccess) e = op_apply_adjoint(L, yt, w, st);
     if (e == cudaSuccess) e = op_adjoint_reduce(L, w, (float2 *)x, st);
     return e == cudaSuccess ? AEXP_OK : cuda_fail(e);
 }

@@ -10,9 +10,10 @@ constexpr int kTargetBlocks = 152 * 4 * 4;  // SMs x resident blocks x waves
 
 int pad_terms(int n) { return n <= 4 ? 4 : n <= 8 ? 8 : n <= 12 ? 12 : 20; }
 int pad_coils(int n) { return n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : n <= 20 ? 20 : 32; }
+// tensor-core forms: N = 2 * CB must be a multiple of 16 with a power-of-two half for TMEM loads
+int pad_coils_tc(int n) { return n <= 8 ? 8 : n <= 16 ? 16 : 32; }
+constexpr int kTcWaveBlocks = 152 * 8;  // one CTA per SM, ~8 waves
 }  // namespace
-
-int fwd_mt_for(int CB) { return CB >= 32 ? 1 : CB >= 16 ? 2 : 4; }
 
 int op_layout(const aexp_problem *p, int precision, OpLayout *L) {
     OpLayout o{};
@@ -25,7 +26,7 @@ int op_layout(const aexp_problem *p, int precision, OpLayout *L) {
     o.has_b0 = p->omega != nullptr;
     o.nterms = o.nl + o.has_b0;
     o.LP = pad_terms(o.nterms);
-    o.CB = pad_coils(o.nc);
+    o.CB = precision == AEXP_FP32 ? pad_coils(o.nc) : pad_coils_tc(o.nc);
     o.precision = precision;
     o.ntx = cdiv(o.nx, kTileSide);
     o.nty = cdiv(o.ny, kTileSide);
@@ -44,8 +45,9 @@ int op_layout(const aexp_problem *p, int precision, OpLayout *L) {
         o.fwd_tiles_per_split = cdiv(o.ntiles, s);
         o.fwd_splits = cdiv(o.ntiles, o.fwd_tiles_per_split);
     }
-    // adjoint: blocks own 2 tiles (128 voxels) and a contiguous run of samples
-    o.adj_vblocks = cdiv(o.ntiles, 2);
+    // adjoint: blocks own 2*mr tiles (128*mr voxels) and a contiguous run of samples
+    o.adj_mr = adj_mr_for(o.CB);
+    o.adj_vblocks = cdiv(o.ntiles, 2 * o.adj_mr);
     {
         int nstage = o.ntp / kAdjStageT;
         int by_sum = cdiv(o.ntp, 2048);
@@ -53,6 +55,21 @@ int op_layout(const aexp_problem *p, int precision, OpLayout *L) {
         int s = std::min(std::max(by_sum, by_occ), nstage);
         int stages_per = cdiv(nstage, s);
         o.adj_t_per_split = stages_per * kAdjStageT;
+        o.adj_splits = cdiv(o.ntp, o.adj_t_per_split);
+    }
+
+    if (precision != AEXP_FP32) {
+        // one CTA (128 samples or 2 tiles) per SM at a time; split the reduction dimension
+        // so the grid covers ~8 waves
+        const int tblocks = o.ntp / 128;
+        int s = std::min(std::max(cdiv(kTcWaveBlocks, tblocks), 1), o.ntiles);
+        o.fwd_tblocks = tblocks;
+        o.fwd_tiles_per_split = cdiv(o.ntiles, s);
+        o.fwd_splits = cdiv(o.ntiles, o.fwd_tiles_per_split);
+        o.adj_vblocks = cdiv(o.ntiles, 2);
+        const int nstage = o.ntp / kAdjStageT;
+        s = std::min(std::max(cdiv(kTcWaveBlocks, o.adj_vblocks), 1), nstage);
+        o.adj_t_per_split = cdiv(nstage, s) * kAdjStageT;
         o.adj_splits = cdiv(o.ntp, o.adj_t_per_split);
     }
 
@@ -74,6 +91,7 @@ int op_layout(const aexp_problem *p, int precision, OpLayout *L) {
     o.off_fpart = take(sizeof(float2) * (size_t)o.fwd_splits * o.ntp * o.CB);
     o.off_yt = take(sizeof(float2) * (size_t)o.ntp * o.CB);
     o.off_apart = take(sizeof(float2) * (size_t)o.adj_splits * o.nr_pad);
+    o.off_ypk = take(precision == AEXP_FP32 ? 0 : sizeof(float2) * (size_t)o.ntp * o.CB);
     o.bytes = off;
     *L = o;
     return AEXP_OK;

@@ -147,44 +147,48 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
     }
 }
 
-template <int CB, int LP>
+template <int CB, int LP, int MR>
 __global__ void __launch_bounds__(kAdjThreads, 2)
     adj_fp32_kernel(const float *__restrict__ khi_t, const float *__restrict__ f0, const float *__restrict__ dh,
                     const float2 *__restrict__ Sp, const float2 *__restrict__ yt, float2 *__restrict__ part, int ntp,
                     int ntiles, int t_per_split, int *status) {
     constexpr int TS = kAdjStageT;
+    constexpr int NT = 2 * MR;  // tiles per block
     constexpr unsigned K_BYTES = TS * LP * sizeof(float);
     constexpr unsigned Y_BYTES = TS * CB * sizeof(float2);
     constexpr unsigned F_BYTES = TS * sizeof(float);
-    constexpr unsigned STAGE = K_BYTES + Y_BYTES + 2 * F_BYTES;
+    constexpr unsigned STAGE = K_BYTES + Y_BYTES + NT * F_BYTES;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar[2];
 
     const int tid = threadIdx.x;
     const int split = blockIdx.y;
-    const int tileA = 2 * blockIdx.x;
-    const int tileB = tileA + 1 < ntiles ? tileA + 1 : tileA;  // odd count: duplicate, results discarded
-    const int p = blockIdx.x * kAdjThreads + tid;
-    const int my_tile = tileA + tid / kTileVox;
-    const bool valid = my_tile < ntiles;
+    const int tile_base = NT * blockIdx.x;
     const int t0 = split * t_per_split;
     const int nst = (min(ntp, t0 + t_per_split) - t0) / TS;
 
-    float d[LP];
-    {
-        const float4 *src = reinterpret_cast<const float4 *>(dh + (size_t)(valid ? p : 0) * LP);
+    float d[MR][LP];
+    bool valid[MR];
+    int pv[MR];
+#pragma unroll
+    for (int m = 0; m < MR; ++m) {
+        pv[m] = blockIdx.x * kAdjThreads * MR + m * kAdjThreads + tid;
+        valid[m] = pv[m] / kTileVox < ntiles;
+        const float4 *src = reinterpret_cast<const float4 *>(dh + (size_t)(valid[m] ? pv[m] : 0) * LP);
 #pragma unroll
         for (int q = 0; q < LP / 4; ++q) {
             float4 w = src[q];
-            d[4 * q] = valid ? w.x : 0.f;
-            d[4 * q + 1] = valid ? w.y : 0.f;
-            d[4 * q + 2] = valid ? w.z : 0.f;
-            d[4 * q + 3] = valid ? w.w : 0.f;
+            d[m][4 * q] = valid[m] ? w.x : 0.f;
+            d[m][4 * q + 1] = valid[m] ? w.y : 0.f;
+            d[m][4 * q + 2] = valid[m] ? w.z : 0.f;
+            d[m][4 * q + 3] = valid[m] ? w.w : 0.f;
         }
     }
-    float ure[CB], uim[CB];
+    float ure[MR][CB], uim[MR][CB];
 #pragma unroll
-    for (int c = 0; c < CB; ++c) ure[c] = uim[c] = 0.f;
+    for (int m = 0; m < MR; ++m)
+#pragma unroll
+        for (int c = 0; c < CB; ++c) ure[m][c] = uim[m][c] = 0.f;
 
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -200,15 +204,17 @@ __global__ void __launch_bounds__(kAdjThreads, 2)
         mbar_arrive_expect_tx(&bar[buf], STAGE);
         bulk_g2s(dst, khi_t + ts * LP, K_BYTES, &bar[buf]);
         bulk_g2s(dst + K_BYTES, yt + ts * CB, Y_BYTES, &bar[buf]);
-        bulk_g2s(dst + K_BYTES + Y_BYTES, f0 + (size_t)tileA * ntp + ts, F_BYTES, &bar[buf]);
-        bulk_g2s(dst + K_BYTES + Y_BYTES + F_BYTES, f0 + (size_t)tileB * ntp + ts, F_BYTES, &bar[buf]);
+        for (int q = 0; q < NT; ++q) {
+            // tiles past the end (last block) reuse a valid row; their results are discarded
+            int tile = min(tile_base + q, ntiles - 1);
+            bulk_g2s(dst + K_BYTES + Y_BYTES + q * F_BYTES, f0 + (size_t)tile * ntp + ts, F_BYTES, &bar[buf]);
+        }
     };
     if (tid == 0) {
         if (nst > 0) issue(0);
         if (nst > 1) issue(1);
     }
 
-    const int half = tid / kTileVox;  // which of the two tiles (uniform per warp)
     for (int i = 0; i < nst; ++i) {
         const int buf = i & 1;
         bool ok = mbar_wait_bounded(&bar[buf], (i >> 1) & 1, status);
@@ -220,56 +226,78 @@ __global__ void __launch_bounds__(kAdjThreads, 2)
         }
         const float4 *sk = reinterpret_cast<const float4 *>(smem + buf * STAGE);
         const float4 *sy = reinterpret_cast<const float4 *>(smem + buf * STAGE + K_BYTES);
-        const float *sf = reinterpret_cast<const float *>(smem + buf * STAGE + K_BYTES + Y_BYTES) + half * TS;
+        const float *sf = reinterpret_cast<const float *>(smem + buf * STAGE + K_BYTES + Y_BYTES);
 
+        // phase + sincos of sample s for each of this thread's voxels
+        auto encode = [&](int s, float *cs, float *sn) {
+#pragma unroll
+            for (int m = 0; m < MR; ++m) {
+                // the voxel's tile within the block is uniform per warp: 2m + tid/64
+                float p0 = sf[(2 * m + tid / kTileVox) * TS + s], p1 = 0.f;
+#pragma unroll
+                for (int q = 0; q < LP / 4; ++q) {
+                    float4 kk = sk[s * (LP / 4) + q];
+                    p0 = fmaf(kk.x, d[m][4 * q], p0);
+                    p1 = fmaf(kk.y, d[m][4 * q + 1], p1);
+                    p0 = fmaf(kk.z, d[m][4 * q + 2], p0);
+                    p1 = fmaf(kk.w, d[m][4 * q + 3], p1);
+                }
+                turns_sincos(p0 + p1, sn[m], cs[m]);
+            }
+        };
+        // software pipeline as in the forward kernel: sample s+1 is encoded before the
+        // contraction of sample s
+        float cnx[MR], snx[MR];
+        encode(0, cnx, snx);
 #pragma unroll 2
         for (int s = 0; s < TS; ++s) {
-            float p0 = sf[s], p1 = 0.f;
+            float cs[MR], sn[MR];
 #pragma unroll
-            for (int q = 0; q < LP / 4; ++q) {
-                float4 kk = sk[s * (LP / 4) + q];
-                p0 = fmaf(kk.x, d[4 * q], p0);
-                p1 = fmaf(kk.y, d[4 * q + 1], p1);
-                p0 = fmaf(kk.z, d[4 * q + 2], p0);
-                p1 = fmaf(kk.w, d[4 * q + 3], p1);
+            for (int m = 0; m < MR; ++m) {
+                cs[m] = cnx[m];
+                sn[m] = snx[m];
             }
-            float sn, cs;
-            turns_sincos(p0 + p1, sn, cs);
+            if (s + 1 < TS) encode(s + 1, cnx, snx);
             // conj(E) = cos + i sin;  u += conj(E) * y
 #pragma unroll
             for (int q = 0; q < CB / 2; ++q) {
                 float4 yy = sy[s * (CB / 2) + q];
-                ure[2 * q] = fmaf(cs, yy.x, ure[2 * q]);
-                ure[2 * q] = fmaf(-sn, yy.y, ure[2 * q]);
-                uim[2 * q] = fmaf(cs, yy.y, uim[2 * q]);
-                uim[2 * q] = fmaf(sn, yy.x, uim[2 * q]);
-                ure[2 * q + 1] = fmaf(cs, yy.z, ure[2 * q + 1]);
-                ure[2 * q + 1] = fmaf(-sn, yy.w, ure[2 * q + 1]);
-                uim[2 * q + 1] = fmaf(cs, yy.w, uim[2 * q + 1]);
-                uim[2 * q + 1] = fmaf(sn, yy.z, uim[2 * q + 1]);
+#pragma unroll
+                for (int m = 0; m < MR; ++m) {
+                    ure[m][2 * q] = fmaf(cs[m], yy.x, ure[m][2 * q]);
+                    ure[m][2 * q] = fmaf(-sn[m], yy.y, ure[m][2 * q]);
+                    uim[m][2 * q] = fmaf(cs[m], yy.y, uim[m][2 * q]);
+                    uim[m][2 * q] = fmaf(sn[m], yy.x, uim[m][2 * q]);
+                    ure[m][2 * q + 1] = fmaf(cs[m], yy.z, ure[m][2 * q + 1]);
+                    ure[m][2 * q + 1] = fmaf(-sn[m], yy.w, ure[m][2 * q + 1]);
+                    uim[m][2 * q + 1] = fmaf(cs[m], yy.w, uim[m][2 * q + 1]);
+                    uim[m][2 * q + 1] = fmaf(sn[m], yy.z, uim[m][2 * q + 1]);
+                }
             }
         }
         __syncthreads();
         if (tid == 0 && i + 2 < nst) issue(i + 2);
     }
 
-    if (valid) {
-        const float4 *s4 = reinterpret_cast<const float4 *>(Sp + (size_t)p * CB);
+#pragma unroll
+    for (int m = 0; m < MR; ++m) {
+        if (!valid[m]) continue;
+        const float4 *s4 = reinterpret_cast<const float4 *>(Sp + (size_t)pv[m] * CB);
         float xr = 0.f, xi = 0.f;
 #pragma unroll
         for (int q = 0; q < CB / 2; ++q) {
             float4 sv = s4[q];
             // conj(S) * u
-            xr = fmaf(sv.x, ure[2 * q], xr);
-            xr = fmaf(sv.y, uim[2 * q], xr);
-            xi = fmaf(sv.x, uim[2 * q], xi);
-            xi = fmaf(-sv.y, ure[2 * q], xi);
-            xr = fmaf(sv.z, ure[2 * q + 1], xr);
-            xr = fmaf(sv.w, uim[2 * q + 1], xr);
-            xi = fmaf(sv.z, uim[2 * q + 1], xi);
-            xi = fmaf(-sv.w, ure[2 * q + 1], xi);
+            xr = fmaf(sv.x, ure[m][2 * q], xr);
+            xr = fmaf(sv.y, uim[m][2 * q], xr);
+            xi = fmaf(sv.x, uim[m][2 * q], xi);
+            xi = fmaf(-sv.y, ure[m][2 * q], xi);
+            xr = fmaf(sv.z, ure[m][2 * q + 1], xr);
+            xr = fmaf(sv.w, uim[m][2 * q + 1], xr);
+            xi = fmaf(sv.z, uim[m][2 * q + 1], xi);
+            xi = fmaf(-sv.w, ure[m][2 * q + 1], xi);
         }
-        part[(size_t)split * (size_t)(ntiles * kTileVox) + p] = make_float2(xr, xi);
+        part[(size_t)split * (size_t)(ntiles * kTileVox) + pv[m]] = make_float2(xr, xi);
     }
 }
 
@@ -334,7 +362,7 @@ __global__ void adj_reduce_kernel(const float2 *part, int splits, int nr_pad, in
 
 template <int CB, int LP>
 cudaError_t launch_fwd(const OpLayout &L, char *ws, cudaStream_t st) {
-    constexpr int MT = CB >= 32 ? 1 : CB >= 16 ? 2 : 4;
+    constexpr int MT = fwd_mt_for(CB);
     constexpr unsigned STAGE = kTileVox * LP * sizeof(float) + kTileVox * CB * sizeof(float2);
     auto kern = fwd_fp32_kernel<CB, LP, MT>;
     if (2 * STAGE > 48 * 1024) {
@@ -351,8 +379,9 @@ cudaError_t launch_fwd(const OpLayout &L, char *ws, cudaStream_t st) {
 
 template <int CB, int LP>
 cudaError_t launch_adj(const OpLayout &L, const float2 *yt, char *ws, cudaStream_t st) {
-    constexpr unsigned STAGE = kAdjStageT * (LP * sizeof(float) + CB * sizeof(float2) + 2 * sizeof(float));
-    auto kern = adj_fp32_kernel<CB, LP>;
+    constexpr int MR = adj_mr_for(CB);
+    constexpr unsigned STAGE = kAdjStageT * (LP * sizeof(float) + CB * sizeof(float2) + 2 * MR * sizeof(float));
+    auto kern = adj_fp32_kernel<CB, LP, MR>;
     if (2 * STAGE > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * STAGE);
         if (e != cudaSuccess) return e;

@@ -1,0 +1,627 @@
+// A_exp and A_exp^H on the tcgen05 tensor cores (BF16 encoding tile, FP32 accumulation).
+//
+// The complex contraction is embedded in a real GEMM whose A operand is generated on
+// the fly and never leaves shared memory:
+//   forward   Y[t][n] = sum_k A[t][k] B[n][k],  A[t][2v] = cos phi, A[t][2v+1] = -sin phi,
+//             B[c][2v] = Re b_c(v), B[c][2v+1] = -Im b_c(v), B[C+c][2v] = Im b_c, B[C+c][2v+1] = Re b_c
+//             so that Y[t][c] = Re y_c(t) and Y[t][C+c] = Im y_c(t) (E = cos - i sin);
+//   adjoint   U[r][n] = sum_k A[r][k] B[n][k],  A[r][2s] = cos phi, A[r][2s+1] = sin phi,
+//             B[c][2s] = Re y_c, B[c][2s+1] = -Im y_c, B[C+c][2s] = Im y_c, B[C+c][2s+1] = Re y_c,
+//             so that U[r][c] + i U[r][C+c] = sum_t conj(E) y_c(t); the coil combination with
+//             conj(S_c(r)) runs in the epilogue.
+// M = 128 rows per CTA, N = 2C (16, 32 or 64), K = 128 per stage (64 voxels or 64 samples),
+// issued as 8 MMAs of K = 16.
+//
+// CTA = 8 generator warps + 1 MMA/producer warp.  Generators compute the FP32 phase
+// (tabulated reference phase + local offset, as in the CUDA-core kernels), reduce it to
+// [-1/2, 1/2] turns, take one MUFU sincos, round to BF16 and store 16-byte chunks straight
+// into the 128B-swizzled K-major layout.  Each generator thread owns 4 columns (one chunk)
+// x 8 rows, so every staged coefficient it loads serves 4 pairs.  The producer warp brings
+// the packed B tile (and the basis offsets or coefficient rows) with bulk TMA copies,
+// issues the MMAs from one thread, and tcgen05.commit frees each stage through an
+// mbarrier.  Every wait is bounded; on a timeout the CTA records
+// AEXP_ERR_DEVICE_TIMEOUT, drains its MMAs, frees TMEM and exits.
+#include <cuda_bf16.h>
+
+#include "aexp_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace aexp {
+
+namespace {
+
+constexpr int kTcGen = 256;              // generator threads
+constexpr int kTcThreads = kTcGen + 32;  // + MMA/producer warp
+constexpr int kRows = 128;               // M
+constexpr int kCols = 64;                // voxels (forward) or samples (adjoint) per stage
+constexpr int kA_BYTES = kRows * kCols * 2 * 2;  // 128 rows x 128 bf16 = 32 KB
+constexpr float kTwoPi = 6.283185307179586f;
+constexpr int kSpin = 1 << 22;
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// Bounded wait that also gives up as soon as another thread of the CTA has aborted.
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, unsigned parity, volatile int *abort_flag,
+                                              int *status) {
+    for (int i = 0; i < kSpin; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255) == 255 && *abort_flag) return false;
+    }
+    *abort_flag = 1;
+    set_status(status, AEXP_ERR_DEVICE_TIMEOUT);
+    return false;
+}
+
+__device__ __forceinline__ uint32_t align1024(uint32_t a) { return (a + 1023u) & ~1023u; }
+
+// ---------------------------------------------------------------------------
+// Forward
+// ---------------------------------------------------------------------------
+template <int CB, int LP>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    fwd_tc_kernel(const float *__restrict__ khi_t, const float *__restrict__ f0, const float *__restrict__ dh,
+                  const unsigned char *__restrict__ bpk, float *__restrict__ part, int ntp, int ntiles,
+                  int tiles_per_split, int *status) {
+    constexpr int N = 2 * CB;
+    constexpr unsigned B_BYTES = N * 256;  // N rows x 128 bf16
+    constexpr unsigned DH_BYTES = kTileVox * LP * 4;
+    constexpr unsigned TMEM_COLS = N <= 32 ? 32 : 64;
+    constexpr uint32_t IDESC = tc::idesc_f16(kRows, N, 1);
+
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ uint64_t bfull[2], afull[2], mdone[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int split = blockIdx.y;
+    const int tile0 = split * tiles_per_split;
+    const int ntl = max(0, min(ntiles, tile0 + tiles_per_split) - tile0);
+    const int tbase = blockIdx.x * kRows;
+
+    // carve 1024-aligned regions: A[2] | B[2] | DH[2]
+    const uint32_t sbase = align1024(smem_u32(smem_raw));
+    unsigned char *gbase = smem_raw + (sbase - smem_u32(smem_raw));
+    unsigned char *A[2] = {gbase, gbase + kA_BYTES};
+    unsigned char *B[2] = {gbase + 2 * kA_BYTES, gbase + 2 * kA_BYTES + B_BYTES};
+    float *DH[2] = {(float *)(gbase + 2 * kA_BYTES + 2 * B_BYTES),
+                    (float *)(gbase + 2 * kA_BYTES + 2 * B_BYTES + DH_BYTES)};
+
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&bfull[s], 1);
+            mbar_init(&afull[s], kTcGen);
+            mbar_init(&mdone[s], 1);
+        }
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 8) {
+        tc::tmem_alloc(&tmem_base, TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+
+    int issued = 0;  // MMA stages issued (producer thread)
+    if (warp == 8) {
+        if (tid == kTcGen) {
+            auto load = [&](int it) {
+                int s = it & 1;
+                size_t tile = (size_t)(tile0 + it);
+                mbar_arrive_expect_tx(&bfull[s], B_BYTES + DH_BYTES);
+                bulk_g2s(B[s], bpk + tile * B_BYTES, B_BYTES, &bfull[s]);
+                bulk_g2s(DH[s], dh + tile * kTileVox * LP, DH_BYTES, &bfull[s]);
+            };
+            if (ntl > 0) load(0);
+            if (ntl > 1) load(1);
+            for (int it = 0; it < ntl; ++it) {
+                const int s = it & 1;
+                const unsigned ph = (it >> 1) & 1;
+                if (!wait_or_abort(&afull[s], ph, &abort_flag, status)) break;
+                if (!wait_or_abort(&bfull[s], ph, &abort_flag, status)) break;
+                tc::fence_after_sync();
+                const uint32_t a0 = smem_u32(A[s]), b0 = smem_u32(B[s]);
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) {
+                    const uint32_t koff = (uint32_t)((kk >> 2) * (kRows * 128) + (kk & 3) * 32);
+                    const uint32_t kofb = (uint32_t)((kk >> 2) * (N * 128) + (kk & 3) * 32);
+                    tc::mma_f16(tmem, tc::sdesc_k128(a0 + koff), tc::sdesc_k128(b0 + kofb), IDESC,
+                                (it | kk) != 0);
+                }
+                tc::mma_commit(&mdone[s]);
+                issued = it + 1;
+                if (it + 2 < ntl) {
+                    if (!wait_or_abort(&mdone[s], ph, &abort_flag, status)) break;
+                    load(it + 2);
+                }
+            }
+            // drain: the last commit covers every MMA issued before it
+            if (issued > 0) {
+                const int last = issued - 1;
+                mbar_wait_bounded(&mdone[last & 1], (last >> 1) & 1, status);
+            }
+        }
+    } else {
+        // generator: warp w owns chunk columns w and w + 8 (voxels 4w..4w+3 and 32+4w..),
+        // lane g owns rows g, g+32, g+64, g+96 and keeps their coefficients in registers
+        const int jp = warp;
+        const int g = tid & 31;
+        float k[4][LP];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int q = 0; q < LP / 4; ++q) {
+                float4 w = reinterpret_cast<const float4 *>(khi_t + (size_t)(tbase + g + 32 * i) * LP)[q];
+                k[i][4 * q] = w.x;
+                k[i][4 * q + 1] = w.y;
+                k[i][4 * q + 2] = w.z;
+                k[i][4 * q + 3] = w.w;
+            }
+        for (int it = 0; it < ntl; ++it) {
+            const int s = it & 1;
+            const unsigned ph = (it >> 1) & 1;
+            if (!wait_or_abort(&bfull[s], ph, &abort_flag, status)) break;
+            if (it >= 2 && !wait_or_abort(&mdone[s], ((it - 2) >> 1) & 1, &abort_flag, status)) break;
+            const float *f0row = f0 + (size_t)(tile0 + it) * ntp + tbase + g;
+            float f[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) f[i] = f0row[32 * i];
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int j = jp + 8 * hh;  // chunk of 4 voxels; atom hh, swizzle column jp
+                uint32_t packed[4][4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    float d[LP];
+#pragma unroll
+                    for (int q = 0; q < LP / 4; ++q) {
+                        float4 w = reinterpret_cast<const float4 *>(DH[s])[(4 * j + u) * (LP / 4) + q];
+                        d[4 * q] = w.x;
+                        d[4 * q + 1] = w.y;
+                        d[4 * q + 2] = w.z;
+                        d[4 * q + 3] = w.w;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        float p0 = f[i], p1 = 0.f;
+#pragma unroll
+                        for (int l = 0; l < LP; l += 2) {
+                            p0 = fmaf(k[i][l], d[l], p0);
+                            p1 = fmaf(k[i][l + 1], d[l + 1], p1);
+                        }
+                        float ph_ = p0 + p1;
+                        ph_ = ph_ - rintf(ph_);
+                        float sn, cs;
+                        __sincosf(ph_ * kTwoPi, &sn, &cs);
+                        packed[i][u] = pack_bf16(cs, -sn);  // E = cos - i sin
+                    }
+                }
+                unsigned char *atom_base = A[s] + hh * (kRows * 128);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    *reinterpret_cast<uint4 *>(atom_base + tc::swz128(g + 32 * i, jp)) =
+                        make_uint4(packed[i][0], packed[i][1], packed[i][2], packed[i][3]);
+            }
+            tc::fence_proxy_async_smem();
+            tc::mbar_arrive(&afull[s]);
+        }
+        // epilogue: wait for the last stage's MMAs, then TMEM -> partial sums (planar re | im)
+        bool ok = !abort_flag;
+        if (ntl > 0 && ok) ok = wait_or_abort(&mdone[(ntl - 1) & 1], ((ntl - 1) >> 1) & 1, &abort_flag, status);
+        ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
+        tc::fence_after_sync();
+        const int lane_base = 32 * (warp & 3);
+        const int half = warp >> 2;
+        const int t = tbase + lane_base + (tid & 31);
+        float v[N / 2];
+        if (ntl > 0 && ok) {
+            tc::tmem_ld<N / 2>(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(half * (N / 2)), v);
+            tc::tmem_ld_wait();
+        } else {
+#pragma unroll
+            for (int c = 0; c < N / 2; ++c) v[c] = 0.f;
+        }
+        float4 *dst = reinterpret_cast<float4 *>(part + ((size_t)split * ntp + t) * N + half * (N / 2));
+#pragma unroll
+        for (int c = 0; c < N / 8; ++c) dst[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 8) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint
+// ---------------------------------------------------------------------------
+template <int CB, int LP>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    adj_tc_kernel(const float *__restrict__ khi_t, const float *__restrict__ f0, const float *__restrict__ dh,
+                  const float2 *__restrict__ Sp, const unsigned char *__restrict__ ypk, float2 *__restrict__ part,
+                  int ntp, int ntiles, int t_per_split, int *status) {
+    constexpr int N = 2 * CB;
+    constexpr int TS = kCols;  // samples per stage
+    constexpr unsigned B_BYTES = N * 256;
+    constexpr unsigned K_BYTES = TS * LP * 4;
+    constexpr unsigned F_BYTES = TS * 4;
+    constexpr unsigned TMEM_COLS = N <= 32 ? 32 : 64;
+    constexpr uint32_t IDESC = tc::idesc_f16(kRows, N, 1);
+
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ uint64_t bfull[2], afull[2], mdone[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int split = blockIdx.y;
+    const int tileA = 2 * blockIdx.x;
+    const int tileB = min(tileA + 1, ntiles - 1);  // odd tile count: duplicate row, discarded
+    const int t0 = split * t_per_split;
+    const int nst = max(0, (min(ntp, t0 + t_per_split) - t0) / TS);
+
+    // A[2] | B[2] | KS[2] (coefficient rows of the stage) | FS[2] (two tiles' reference phases)
+    const uint32_t sbase = align1024(smem_u32(smem_raw));
+    unsigned char *gbase = smem_raw + (sbase - smem_u32(smem_raw));
+    unsigned char *A[2] = {gbase, gbase + kA_BYTES};
+    unsigned char *B[2] = {gbase + 2 * kA_BYTES, gbase + 2 * kA_BYTES + B_BYTES};
+    unsigned char *stg = gbase + 2 * kA_BYTES + 2 * B_BYTES;
+    float *KS[2] = {(float *)stg, (float *)(stg + K_BYTES)};
+    float *FS[2] = {(float *)(stg + 2 * K_BYTES), (float *)(stg + 2 * K_BYTES + 2 * F_BYTES)};
+
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&bfull[s], 1);
+            mbar_init(&afull[s], kTcGen);
+            mbar_init(&mdone[s], 1);
+        }
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 8) {
+        tc::tmem_alloc(&tmem_base, TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+
+    int issued = 0;
+    if (warp == 8) {
+        if (tid == kTcGen) {
+            auto load = [&](int it) {
+                int s = it & 1;
+                size_t ts = (size_t)t0 + (size_t)it * TS;
+                mbar_arrive_expect_tx(&bfull[s], B_BYTES + K_BYTES + 2 * F_BYTES);
+                bulk_g2s(B[s], ypk + (ts / TS) * B_BYTES, B_BYTES, &bfull[s]);
+                bulk_g2s(KS[s], khi_t + ts * LP, K_BYTES, &bfull[s]);
+                bulk_g2s(FS[s], f0 + (size_t)tileA * ntp + ts, F_BYTES, &bfull[s]);
+                bulk_g2s(FS[s] + TS, f0 + (size_t)tileB * ntp + ts, F_BYTES, &bfull[s]);
+            };
+            if (nst > 0) load(0);
+            if (nst > 1) load(1);
+            for (int it = 0; it < nst; ++it) {
+                const int s = it & 1;
+                const unsigned ph = (it >> 1) & 1;
+                if (!wait_or_abort(&afull[s], ph, &abort_flag, status)) break;
+                if (!wait_or_abort(&bfull[s], ph, &abort_flag, status)) break;
+                tc::fence_after_sync();
+                const uint32_t a0 = smem_u32(A[s]), b0 = smem_u32(B[s]);
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) {
+                    const uint32_t koff = (uint32_t)((kk >> 2) * (kRows * 128) + (kk & 3) * 32);
+                    const uint32_t kofb = (uint32_t)((kk >> 2) * (N * 128) + (kk & 3) * 32);
+                    tc::mma_f16(tmem, tc::sdesc_k128(a0 + koff), tc::sdesc_k128(b0 + kofb), IDESC,
+                                (it | kk) != 0);
+                }
+                tc::mma_commit(&mdone[s]);
+                issued = it + 1;
+                if (it + 2 < nst) {
+                    if (!wait_or_abort(&mdone[s], ph, &abort_flag, status)) break;
+                    load(it + 2);
+                }
+            }
+            if (issued > 0) {
+                const int last = issued - 1;
+                mbar_wait_bounded(&mdone[last & 1], (last >> 1) & 1, status);
+            }
+        }
+    } else {
+        // generator: warp w owns sample chunks w and w + 8 of each stage, lane g owns voxel
+        // rows g, g+32 (first tile) and g+64, g+96 (second tile) with their basis offsets
+        const int jp = warp;
+        const int g = tid & 31;
+        float d[4][LP];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int p = blockIdx.x * kRows + g + 32 * i;
+            const bool valid = p < ntiles * kTileVox;
+#pragma unroll
+            for (int q = 0; q < LP / 4; ++q) {
+                float4 w = reinterpret_cast<const float4 *>(dh + (size_t)(valid ? p : 0) * LP)[q];
+                d[i][4 * q] = valid ? w.x : 0.f;
+                d[i][4 * q + 1] = valid ? w.y : 0.f;
+                d[i][4 * q + 2] = valid ? w.z : 0.f;
+                d[i][4 * q + 3] = valid ? w.w : 0.f;
+            }
+        }
+        for (int it = 0; it < nst; ++it) {
+            const int s = it & 1;
+            const unsigned ph = (it >> 1) & 1;
+            if (!wait_or_abort(&bfull[s], ph, &abort_flag, status)) break;
+            if (it >= 2 && !wait_or_abort(&mdone[s], ((it - 2) >> 1) & 1, &abort_flag, status)) break;
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int j = jp + 8 * hh;  // samples 4j..4j+3 of the stage
+                const float4 fa = reinterpret_cast<const float4 *>(FS[s])[j];
+                const float4 fb = reinterpret_cast<const float4 *>(FS[s] + TS)[j];
+                const float fA[4] = {fa.x, fa.y, fa.z, fa.w};
+                const float fB[4] = {fb.x, fb.y, fb.z, fb.w};
+                uint32_t packed[4][4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    float k[LP];
+#pragma unroll
+                    for (int q = 0; q < LP / 4; ++q) {
+                        float4 w = reinterpret_cast<const float4 *>(KS[s])[(4 * j + u) * (LP / 4) + q];
+                        k[4 * q] = w.x;
+                        k[4 * q + 1] = w.y;
+                        k[4 * q + 2] = w.z;
+                        k[4 * q + 3] = w.w;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        float p0 = i < 2 ? fA[u] : fB[u], p1 = 0.f;
+#pragma unroll
+                        for (int l = 0; l < LP; l += 2) {
+                            p0 = fmaf(k[l], d[i][l], p0);
+                            p1 = fmaf(k[l + 1], d[i][l + 1], p1);
+                        }
+                        float ph_ = p0 + p1;
+                        ph_ = ph_ - rintf(ph_);
+                        float sn, cs;
+                        __sincosf(ph_ * kTwoPi, &sn, &cs);
+                        packed[i][u] = pack_bf16(cs, sn);  // conj(E) = cos + i sin
+                    }
+                }
+                unsigned char *atom_base = A[s] + hh * (kRows * 128);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    *reinterpret_cast<uint4 *>(atom_base + tc::swz128(g + 32 * i, jp)) =
+                        make_uint4(packed[i][0], packed[i][1], packed[i][2], packed[i][3]);
+            }
+            tc::fence_proxy_async_smem();
+            tc::mbar_arrive(&afull[s]);
+        }
+        // epilogue (warps 0-3, one voxel row per thread): conj(S) . u over coils
+        bool ok = !abort_flag;
+        if (nst > 0 && ok) ok = wait_or_abort(&mdone[(nst - 1) & 1], ((nst - 1) >> 1) & 1, &abort_flag, status);
+        ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
+        tc::fence_after_sync();
+        if (warp < 4) {
+            const int m = 32 * warp + (tid & 31);
+            const int p = blockIdx.x * kRows + m;
+            float u[N];
+            if (nst > 0 && ok) {
+                tc::tmem_ld<N / 2>(tmem + ((uint32_t)(32 * warp) << 16), u);
+                tc::tmem_ld<N / 2>(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(N / 2), u + N / 2);
+                tc::tmem_ld_wait();
+            } else {
+#pragma unroll
+                for (int c = 0; c < N; ++c) u[c] = 0.f;
+            }
+            if (p < ntiles * kTileVox) {
+                const float4 *s4 = reinterpret_cast<const float4 *>(Sp + (size_t)p * CB);
+                float xr = 0.f, xi = 0.f;
+#pragma unroll
+                for (int q = 0; q < CB / 2; ++q) {
+                    float4 sv = s4[q];
+                    const float ur0 = u[2 * q], ui0 = u[CB + 2 * q], ur1 = u[2 * q + 1], ui1 = u[CB + 2 * q + 1];
+                    xr = fmaf(sv.x, ur0, xr);
+                    xr = fmaf(sv.y, ui0, xr);
+                    xi = fmaf(sv.x, ui0, xi);
+                    xi = fmaf(-sv.y, ur0, xi);
+                    xr = fmaf(sv.z, ur1, xr);
+                    xr = fmaf(sv.w, ui1, xr);
+                    xi = fmaf(sv.z, ui1, xi);
+                    xi = fmaf(-sv.w, ur1, xi);
+                }
+                part[(size_t)split * (size_t)(ntiles * kTileVox) + p] = make_float2(xr, xi);
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 8) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Packing of the B operands into the swizzled K-major smem image (one tile/stage each)
+// ---------------------------------------------------------------------------
+
+// Forward: coil-weighted image b_c(v) = S_c(v) x(v) of every 8x8 tile, rows n < C carry
+// (Re b, -Im b), rows C + c carry (Im b, Re b) at K positions (2v, 2v+1).
+template <int CB>
+__global__ void pack_b_fwd_kernel(const float2 *__restrict__ Sp, const float2 *__restrict__ x, int nx, int ny,
+                                  int ntx, int ntiles, unsigned char *__restrict__ bpk) {
+    constexpr int N = 2 * CB;
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // (tile, n, chunk)
+    if (i >= (size_t)ntiles * N * 16) return;
+    int jj = (int)(i % 16);
+    int n = (int)((i / 16) % N);
+    int tile = (int)(i / (16 * N));
+    int c = n < CB ? n : n - CB;
+    uint32_t w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        int v = 4 * jj + u;
+        int ix = (tile % ntx) * kTileSide + v % kTileSide, iy = (tile / ntx) * kTileSide + v / kTileSide;
+        float br = 0.f, bi = 0.f;
+        if (ix < nx && iy < ny) {
+            float2 s = Sp[((size_t)tile * kTileVox + v) * CB + c];
+            float2 xv = x[(size_t)iy * nx + ix];
+            br = s.x * xv.x - s.y * xv.y;
+            bi = s.x * xv.y + s.y * xv.x;
+        }
+        w[u] = n < CB ? pack_bf16(br, -bi) : pack_bf16(bi, br);
+    }
+    unsigned char *dst = bpk + (size_t)tile * (N * 256) + (jj >> 3) * (N * 128) + tc::swz128(n, jj & 7);
+    *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Adjoint: k-space yt[t][c] per stage of 64 samples; rows n < C carry (Re y, -Im y),
+// rows C + c carry (Im y, Re y) at K positions (2s, 2s+1).
+template <int CB>
+__global__ void pack_y_adj_kernel(const float2 *__restrict__ yt, int nstages, unsigned char *__restrict__ ypk) {
+    constexpr int N = 2 * CB;
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // (stage, n, chunk)
+    if (i >= (size_t)nstages * N * 16) return;
+    int jj = (int)(i % 16);
+    int n = (int)((i / 16) % N);
+    int st = (int)(i / (16 * N));
+    int c = n < CB ? n : n - CB;
+    uint32_t w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        size_t t = (size_t)st * kCols + 4 * jj + u;
+        float2 y = yt[t * CB + c];
+        w[u] = n < CB ? pack_bf16(y.x, -y.y) : pack_bf16(y.y, y.x);
+    }
+    unsigned char *dst = ypk + (size_t)st * (N * 256) + (jj >> 3) * (N * 128) + tc::swz128(n, jj & 7);
+    *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Reductions of the planar forward partials [split][t][re(0..C) | im(0..C)].
+__global__ void fwd_reduce_planar_public_kernel(const float *part, int splits, int ntp, int CB, int nt, int nc,
+                                                float2 *y) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)nt * CB) return;
+    int t = (int)(i / CB), c = (int)(i % CB);
+    if (c >= nc) return;
+    float re = 0.f, im = 0.f;
+    for (int k = 0; k < splits; ++k) {
+        const float *row = part + ((size_t)k * ntp + t) * 2 * CB;
+        re += row[c];
+        im += row[CB + c];
+    }
+    y[(size_t)c * nt + t] = make_float2(re, im);
+}
+
+__global__ void fwd_reduce_planar_residual_kernel(const float *part, int splits, int ntp, int CB, int nt, int nc,
+                                                  const float2 *ymeas, float2 *rt) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)ntp * CB) return;
+    int t = (int)(i / CB), c = (int)(i % CB);
+    float2 s = make_float2(0.f, 0.f);
+    if (t < nt && c < nc) {
+        for (int k = 0; k < splits; ++k) {
+            const float *row = part + ((size_t)k * ntp + t) * 2 * CB;
+            s.x += row[c];
+            s.y += row[CB + c];
+        }
+        if (ymeas) {
+            s.x -= ymeas[i].x;
+            s.y -= ymeas[i].y;
+        }
+    }
+    rt[i] = s;
+}
+
+// ---- launch helpers ----
+template <int CB, int LP>
+size_t fwd_tc_smem() {
+    return 1024 + 2 * kA_BYTES + 2 * (2 * CB * 256) + 2 * (kTileVox * LP * 4);
+}
+template <int CB, int LP>
+size_t adj_tc_smem() {
+    return 1024 + 2 * kA_BYTES + 2 * (2 * CB * 256) + 2 * (kCols * LP * 4) + 4 * (kCols * 4);
+}
+
+template <int CB, int LP>
+cudaError_t launch_fwd_tc(const OpLayout &L, const float2 *x, char *ws, cudaStream_t st) {
+    const size_t n = (size_t)L.ntiles * 2 * CB * 16;
+    pack_b_fwd_kernel<CB><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        (const float2 *)(ws + L.off_S), x, L.nx, L.ny, L.ntx, L.ntiles, (unsigned char *)(ws + L.off_b));
+    auto kern = fwd_tc_kernel<CB, LP>;
+    const size_t smem = fwd_tc_smem<CB, LP>();
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    WsHeader *hdr = (WsHeader *)(ws + L.off_hdr);
+    kern<<<dim3(L.ntp / kRows, L.fwd_splits), kTcThreads, smem, st>>>(
+        (const float *)(ws + L.off_khi_t), (const float *)(ws + L.off_f0), (const float *)(ws + L.off_dh),
+        (const unsigned char *)(ws + L.off_b), (float *)(ws + L.off_fpart), L.ntp, L.ntiles, L.fwd_tiles_per_split,
+        &hdr->status);
+    return cudaGetLastError();
+}
+
+template <int CB, int LP>
+cudaError_t launch_adj_tc(const OpLayout &L, const float2 *yt, char *ws, cudaStream_t st) {
+    const int nstages = L.ntp / kCols;
+    const size_t n = (size_t)nstages * 2 * CB * 16;
+    pack_y_adj_kernel<CB><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(yt, nstages,
+                                                                       (unsigned char *)(ws + L.off_ypk));
+    auto kern = adj_tc_kernel<CB, LP>;
+    const size_t smem = adj_tc_smem<CB, LP>();
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    WsHeader *hdr = (WsHeader *)(ws + L.off_hdr);
+    kern<<<dim3(L.adj_vblocks, L.adj_splits), kTcThreads, smem, st>>>(
+        (const float *)(ws + L.off_khi_t), (const float *)(ws + L.off_f0), (const float *)(ws + L.off_dh),
+        (const float2 *)(ws + L.off_S), (const unsigned char *)(ws + L.off_ypk), (float2 *)(ws + L.off_apart),
+        L.ntp, L.ntiles, L.adj_t_per_split, &hdr->status);
+    return cudaGetLastError();
+}
+
+#define AEXP_TC_LP(FN, CBV, ...)                         \
+    switch (L.LP) {                                      \
+        case 4: return FN<CBV, 4>(__VA_ARGS__);          \
+        case 8: return FN<CBV, 8>(__VA_ARGS__);          \
+        case 12: return FN<CBV, 12>(__VA_ARGS__);        \
+        default: return FN<CBV, 20>(__VA_ARGS__);        \
+    }
+#define AEXP_TC_DISPATCH(FN, ...)                                \
+    switch (L.CB) {                                              \
+        case 8: AEXP_TC_LP(FN, 8, __VA_ARGS__)                   \
+        case 16: AEXP_TC_LP(FN, 16, __VA_ARGS__)                 \
+        default: AEXP_TC_LP(FN, 32, __VA_ARGS__)                 \
+    }
+
+}  // namespace
+
+cudaError_t op_forward_tc(const OpLayout &L, const float2 *x, char *ws, cudaStream_t st) {
+    AEXP_TC_DISPATCH(launch_fwd_tc, L, x, ws, st)
+}
+
+cudaError_t op_adjoint_tc(const OpLayout &L, const float2 *yt, char *ws, cudaStream_t st) {
+    AEXP_TC_DISPATCH(launch_adj_tc, L, yt, ws, st)
+}
+
+cudaError_t op_forward_reduce_planar_public(const OpLayout &L, char *ws, float2 *y, cudaStream_t st) {
+    size_t n = (size_t)L.nt * L.CB;
+    fwd_reduce_planar_public_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        (const float *)(ws + L.off_fpart), L.fwd_splits, L.ntp, L.CB, L.nt, L.nc, y);
+    return cudaGetLastError();
+}
+
+cudaError_t op_forward_reduce_planar_residual(const OpLayout &L, char *ws, const float2 *ymeas_t, float2 *rt,
+                                              cudaStream_t st) {
+    size_t n = (size_t)L.ntp * L.CB;
+    fwd_reduce_planar_residual_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        (const float *)(ws + L.off_fpart), L.fwd_splits, L.ntp, L.CB, L.nt, L.nc, ymeas_t, rt);
+    return cudaGetLastError();
+}
+
+}  // namespace aexp

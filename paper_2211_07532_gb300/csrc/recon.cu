@@ -96,10 +96,9 @@ cudaError_t scale_inv_sqrt(const float2 *w, float2 *v, int n, const double *nrm2
 // w = A^H A v (v in natural order); uses the operator workspace only.
 cudaError_t normal_apply(const OpLayout &L, char *ws, const float2 *v, float2 *w, cudaStream_t st) {
     float2 *rt = (float2 *)(ws + L.off_yt);
-    CK(op_coil_weight(L, v, ws, st));
-    CK(op_forward_core(L, ws, st));
-    CK(op_forward_reduce_residual(L, ws, nullptr, rt, st));
-    CK(op_adjoint_core(L, rt, ws, st));
+    CK(op_apply_forward(L, v, ws, st));
+    CK(op_reduce_forward_residual(L, ws, nullptr, rt, st));
+    CK(op_apply_adjoint(L, rt, ws, st));
     CK(op_adjoint_reduce(L, ws, w, st));
     return cudaSuccess;
 }
@@ -148,7 +147,7 @@ cudaError_t recon_issue(const aexp_problem *p, const RecLayout &R, const aexp_re
     } else {
         const float2 *v0 = (const float2 *)o->power_init;
         if (!v0) {  // A^H y, the zero-filled reconstruction
-            CK(op_adjoint_core(L, ymeas, ws, st));
+            CK(op_apply_adjoint(L, ymeas, ws, st));
             CK(op_adjoint_reduce(L, ws, w, st));
             v0 = w;
         }
@@ -165,10 +164,9 @@ cudaError_t recon_issue(const aexp_problem *p, const RecLayout &R, const aexp_re
     double t = 1.0;
     for (int k = 0; k < iters; ++k) {
         // v = z - (2/L_f) A^H (A z - y)
-        CK(op_coil_weight(L, z, ws, st));
-        CK(op_forward_core(L, ws, st));
-        CK(op_forward_reduce_residual(L, ws, ymeas, rt, st));
-        CK(op_adjoint_core(L, rt, ws, st));
+        CK(op_apply_forward(L, z, ws, st));
+        CK(op_reduce_forward_residual(L, ws, ymeas, rt, st));
+        CK(op_apply_adjoint(L, rt, ws, st));
         CK(op_adjoint_reduce_step(L, ws, z, v, st));
         // x_k = crop W^H soft(W pad v, lam / L_f);  z_{k+1} = x_k + beta_k (x_k - x_{k-1})
         double t_next = (1.0 + sqrt(1.0 + 4.0 * t * t)) / 2.0;
