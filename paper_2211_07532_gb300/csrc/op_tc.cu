@@ -12,11 +12,11 @@
 // M = 128 rows per CTA, N = 2C (16, 32 or 64), K = 128 per stage (64 voxels or 64 samples),
 // issued as 8 MMAs of K = 16.
 //
-// CTA = 8 generator warps + 1 MMA/producer warp.  Generators compute the FP32 phase
+// CTA = 16 generator warps + 1 MMA/producer warp.  Generators compute the FP32 phase
 // (tabulated reference phase + local offset, as in the CUDA-core kernels), reduce it to
 // [-1/2, 1/2] turns, take one MUFU sincos, round to BF16 and store 16-byte chunks straight
-// into the 128B-swizzled K-major layout.  Each generator thread owns 4 columns (one chunk)
-// x 8 rows, so every staged coefficient it loads serves 4 pairs.  The producer warp brings
+// into the 128B-swizzled K-major layout.  Each generator thread owns 2 rows x 8 columns
+// (two 16-byte chunks), so every staged coefficient it loads serves 2 pairs.  The producer warp brings
 // the packed B tile (and the basis offsets or coefficient rows) with bulk TMA copies,
 // issues the MMAs from one thread, and tcgen05.commit frees each stage through an
 // mbarrier.  Every wait is bounded; on a timeout the CTA records
@@ -30,13 +30,14 @@ namespace aexp {
 
 namespace {
 
-constexpr int kTcGen = 256;              // generator threads
+constexpr int kTcGen = 512;              // generator threads (16 warps)
 constexpr int kTcThreads = kTcGen + 32;  // + MMA/producer warp
 constexpr int kRows = 128;               // M
 constexpr int kCols = 64;                // voxels (forward) or samples (adjoint) per stage
 constexpr int kA_BYTES = kRows * kCols * 2 * 2;  // 128 rows x 128 bf16 = 32 KB
 constexpr float kTwoPi = 6.283185307179586f;
 constexpr int kSpin = 1 << 22;
+constexpr int kNB = 4;  // staged B tiles (loaded kNB - 1 tiles ahead of the generators)
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -68,11 +69,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     constexpr int N = 2 * CB;
     constexpr unsigned B_BYTES = N * 256;  // N rows x 128 bf16
     constexpr unsigned DH_BYTES = kTileVox * LP * 4;
+    constexpr unsigned F_BYTES = kRows * 4;
+    // one staged tile (B | dh | f0 rows): S_DATA bytes arrive per stage; the stride
+    // S_BYTES keeps every B tile 1024-byte aligned
+    constexpr unsigned S_DATA = B_BYTES + DH_BYTES + F_BYTES;
+    constexpr unsigned S_BYTES = (S_DATA + 1023u) & ~1023u;
     constexpr unsigned TMEM_COLS = N <= 32 ? 32 : 64;
     constexpr uint32_t IDESC = tc::idesc_f16(kRows, N, 1);
 
     extern __shared__ unsigned char smem_raw[];
-    __shared__ uint64_t bfull[2], afull[2], mdone[2];
+    __shared__ uint64_t bfull[kNB], bfree[kNB], afull[2], afree[2];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
 
@@ -83,24 +89,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int ntl = max(0, min(ntiles, tile0 + tiles_per_split) - tile0);
     const int tbase = blockIdx.x * kRows;
 
-    // carve 1024-aligned regions: A[2] | B[2] | DH[2]
+    // 1024-aligned regions: A[2] | staged tiles[kNB] (each B | dh | f0)
     const uint32_t sbase = align1024(smem_u32(smem_raw));
     unsigned char *gbase = smem_raw + (sbase - smem_u32(smem_raw));
     unsigned char *A[2] = {gbase, gbase + kA_BYTES};
-    unsigned char *B[2] = {gbase + 2 * kA_BYTES, gbase + 2 * kA_BYTES + B_BYTES};
-    float *DH[2] = {(float *)(gbase + 2 * kA_BYTES + 2 * B_BYTES),
-                    (float *)(gbase + 2 * kA_BYTES + 2 * B_BYTES + DH_BYTES)};
+    unsigned char *stage0 = gbase + 2 * kA_BYTES;
 
     if (tid == 0) {
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < kNB; ++s) {
             mbar_init(&bfull[s], 1);
+            mbar_init(&bfree[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
             mbar_init(&afull[s], kTcGen);
-            mbar_init(&mdone[s], 1);
+            mbar_init(&afree[s], 1);
         }
         abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == 8) {
+    if (warp == kTcGen / 32) {
         tc::tmem_alloc(&tmem_base, TMEM_COLS);
         tc::tmem_relinquish();
     }
@@ -109,25 +116,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc::fence_after_sync();
     const uint32_t tmem = tmem_base;
 
-    int issued = 0;  // MMA stages issued (producer thread)
-    if (warp == 8) {
+    if (warp == kTcGen / 32) {
         if (tid == kTcGen) {
             auto load = [&](int it) {
-                int s = it & 1;
+                const int sb = it % kNB;
+                unsigned char *dst = stage0 + sb * S_BYTES;
                 size_t tile = (size_t)(tile0 + it);
-                mbar_arrive_expect_tx(&bfull[s], B_BYTES + DH_BYTES);
-                bulk_g2s(B[s], bpk + tile * B_BYTES, B_BYTES, &bfull[s]);
-                bulk_g2s(DH[s], dh + tile * kTileVox * LP, DH_BYTES, &bfull[s]);
+                mbar_arrive_expect_tx(&bfull[sb], S_DATA);
+                bulk_g2s(dst, bpk + tile * B_BYTES, B_BYTES, &bfull[sb]);
+                bulk_g2s(dst + B_BYTES, dh + tile * kTileVox * LP, DH_BYTES, &bfull[sb]);
+                bulk_g2s(dst + B_BYTES + DH_BYTES, f0 + tile * ntp + tbase, F_BYTES, &bfull[sb]);
             };
-            if (ntl > 0) load(0);
-            if (ntl > 1) load(1);
+            for (int j = 0; j < min(kNB, ntl); ++j) load(j);
+            int issued = 0;
             for (int it = 0; it < ntl; ++it) {
-                const int s = it & 1;
-                const unsigned ph = (it >> 1) & 1;
-                if (!wait_or_abort(&afull[s], ph, &abort_flag, status)) break;
-                if (!wait_or_abort(&bfull[s], ph, &abort_flag, status)) break;
+                const int sa = it & 1, sb = it % kNB;
+                if (!wait_or_abort(&afull[sa], (it >> 1) & 1, &abort_flag, status)) break;
+                if (!wait_or_abort(&bfull[sb], (it / kNB) & 1, &abort_flag, status)) break;
                 tc::fence_after_sync();
-                const uint32_t a0 = smem_u32(A[s]), b0 = smem_u32(B[s]);
+                const uint32_t a0 = smem_u32(A[sa]), b0 = smem_u32(stage0 + sb * S_BYTES);
 #pragma unroll
                 for (int kk = 0; kk < 8; ++kk) {
                     const uint32_t koff = (uint32_t)((kk >> 2) * (kRows * 128) + (kk & 3) * 32);
@@ -135,61 +142,65 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     tc::mma_f16(tmem, tc::sdesc_k128(a0 + koff), tc::sdesc_k128(b0 + kofb), IDESC,
                                 (it | kk) != 0);
                 }
-                tc::mma_commit(&mdone[s]);
+                tc::mma_commit(&afree[sa]);
+                tc::mma_commit(&bfree[sb]);
                 issued = it + 1;
-                if (it + 2 < ntl) {
-                    if (!wait_or_abort(&mdone[s], ph, &abort_flag, status)) break;
-                    load(it + 2);
+                if (it + kNB < ntl) {
+                    if (!wait_or_abort(&bfree[sb], (it / kNB) & 1, &abort_flag, status)) break;
+                    load(it + kNB);
                 }
             }
             // drain: the last commit covers every MMA issued before it
             if (issued > 0) {
                 const int last = issued - 1;
-                mbar_wait_bounded(&mdone[last & 1], (last >> 1) & 1, status);
+                mbar_wait_bounded(&afree[last & 1], (last >> 1) & 1, status);
             }
         }
     } else {
-        // generator: warp w owns chunk columns w and w + 8 (voxels 4w..4w+3 and 32+4w..),
-        // lane g owns rows g, g+32, g+64, g+96 and keeps their coefficients in registers
-        const int jp = warp;
+        // generator: warp w owns chunk columns (w & 7) and (w & 7) + 8 (voxels 4jp..4jp+3 and
+        // 32+4jp..), lane g owns rows r0 = 64 (w >> 3) + g and r0 + 32 and keeps their
+        // coefficients in registers
+        const int jp = warp & 7;
         const int g = tid & 31;
-        float k[4][LP];
+        const int r0 = 64 * (warp >> 3) + g;
+        float k[2][LP];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 2; ++i)
 #pragma unroll
             for (int q = 0; q < LP / 4; ++q) {
-                float4 w = reinterpret_cast<const float4 *>(khi_t + (size_t)(tbase + g + 32 * i) * LP)[q];
+                float4 w = reinterpret_cast<const float4 *>(khi_t + (size_t)(tbase + r0 + 32 * i) * LP)[q];
                 k[i][4 * q] = w.x;
                 k[i][4 * q + 1] = w.y;
                 k[i][4 * q + 2] = w.z;
                 k[i][4 * q + 3] = w.w;
             }
         for (int it = 0; it < ntl; ++it) {
-            const int s = it & 1;
-            const unsigned ph = (it >> 1) & 1;
-            if (!wait_or_abort(&bfull[s], ph, &abort_flag, status)) break;
-            if (it >= 2 && !wait_or_abort(&mdone[s], ((it - 2) >> 1) & 1, &abort_flag, status)) break;
-            const float *f0row = f0 + (size_t)(tile0 + it) * ntp + tbase + g;
-            float f[4];
+            const int sa = it & 1, sb = it % kNB;
+            if (!wait_or_abort(&bfull[sb], (it / kNB) & 1, &abort_flag, status)) break;
+            if (it >= 2 && !wait_or_abort(&afree[sa], ((it - 2) >> 1) & 1, &abort_flag, status)) break;
+            const unsigned char *stg = stage0 + sb * S_BYTES;
+            const float4 *DH = reinterpret_cast<const float4 *>(stg + B_BYTES);
+            const float *F0 = reinterpret_cast<const float *>(stg + B_BYTES + DH_BYTES);
+            float f[2];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) f[i] = f0row[32 * i];
+            for (int i = 0; i < 2; ++i) f[i] = F0[r0 + 32 * i];
 #pragma unroll
             for (int hh = 0; hh < 2; ++hh) {
                 const int j = jp + 8 * hh;  // chunk of 4 voxels; atom hh, swizzle column jp
-                uint32_t packed[4][4];
+                uint32_t packed[2][4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     float d[LP];
 #pragma unroll
                     for (int q = 0; q < LP / 4; ++q) {
-                        float4 w = reinterpret_cast<const float4 *>(DH[s])[(4 * j + u) * (LP / 4) + q];
+                        float4 w = DH[(4 * j + u) * (LP / 4) + q];
                         d[4 * q] = w.x;
                         d[4 * q + 1] = w.y;
                         d[4 * q + 2] = w.z;
                         d[4 * q + 3] = w.w;
                     }
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
+                    for (int i = 0; i < 2; ++i) {
                         float p0 = f[i], p1 = 0.f;
 #pragma unroll
                         for (int l = 0; l < LP; l += 2) {
@@ -203,38 +214,42 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         packed[i][u] = pack_bf16(cs, -sn);  // E = cos - i sin
                     }
                 }
-                unsigned char *atom_base = A[s] + hh * (kRows * 128);
+                unsigned char *atom_base = A[sa] + hh * (kRows * 128);
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    *reinterpret_cast<uint4 *>(atom_base + tc::swz128(g + 32 * i, jp)) =
+                for (int i = 0; i < 2; ++i)
+                    *reinterpret_cast<uint4 *>(atom_base + tc::swz128(r0 + 32 * i, jp)) =
                         make_uint4(packed[i][0], packed[i][1], packed[i][2], packed[i][3]);
             }
             tc::fence_proxy_async_smem();
-            tc::mbar_arrive(&afull[s]);
+            tc::mbar_arrive(&afull[sa]);
         }
-        // epilogue: wait for the last stage's MMAs, then TMEM -> partial sums (planar re | im)
+        // epilogue (warps 0-7): wait for the last tile's MMAs, then TMEM -> partial sums
+        // (planar re | im)
         bool ok = !abort_flag;
-        if (ntl > 0 && ok) ok = wait_or_abort(&mdone[(ntl - 1) & 1], ((ntl - 1) >> 1) & 1, &abort_flag, status);
+        if (ntl > 0 && ok) ok = wait_or_abort(&afree[(ntl - 1) & 1], ((ntl - 1) >> 1) & 1, &abort_flag, status);
         ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
         tc::fence_after_sync();
-        const int lane_base = 32 * (warp & 3);
-        const int half = warp >> 2;
-        const int t = tbase + lane_base + (tid & 31);
-        float v[N / 2];
-        if (ntl > 0 && ok) {
-            tc::tmem_ld<N / 2>(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(half * (N / 2)), v);
-            tc::tmem_ld_wait();
-        } else {
+        if (warp < 8) {
+            const int lane_base = 32 * (warp & 3);
+            const int half = warp >> 2;
+            const int t = tbase + lane_base + (tid & 31);
+            float v[N / 2];
+            if (ntl > 0 && ok) {
+                tc::tmem_ld<N / 2>(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(half * (N / 2)), v);
+                tc::tmem_ld_wait();
+            } else {
 #pragma unroll
-            for (int c = 0; c < N / 2; ++c) v[c] = 0.f;
+                for (int c = 0; c < N / 2; ++c) v[c] = 0.f;
+            }
+            float4 *dst = reinterpret_cast<float4 *>(part + ((size_t)split * ntp + t) * N + half * (N / 2));
+#pragma unroll
+            for (int c = 0; c < N / 8; ++c)
+                dst[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
         }
-        float4 *dst = reinterpret_cast<float4 *>(part + ((size_t)split * ntp + t) * N + half * (N / 2));
-#pragma unroll
-        for (int c = 0; c < N / 8; ++c) dst[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 8) {
+    if (warp == kTcGen / 32) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem, TMEM_COLS);
     }
@@ -253,11 +268,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     constexpr unsigned B_BYTES = N * 256;
     constexpr unsigned K_BYTES = TS * LP * 4;
     constexpr unsigned F_BYTES = TS * 4;
+    // B | k rows | f0 (2 tiles): S_DATA bytes arrive per stage; the stride S_BYTES keeps
+    // every B tile 1024-byte aligned
+    constexpr unsigned S_DATA = B_BYTES + K_BYTES + 2 * F_BYTES;
+    constexpr unsigned S_BYTES = (S_DATA + 1023u) & ~1023u;
     constexpr unsigned TMEM_COLS = N <= 32 ? 32 : 64;
     constexpr uint32_t IDESC = tc::idesc_f16(kRows, N, 1);
 
     extern __shared__ unsigned char smem_raw[];
-    __shared__ uint64_t bfull[2], afull[2], mdone[2];
+    __shared__ uint64_t bfull[kNB], bfree[kNB], afull[2], afree[2];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
 
@@ -269,25 +288,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int t0 = split * t_per_split;
     const int nst = max(0, (min(ntp, t0 + t_per_split) - t0) / TS);
 
-    // A[2] | B[2] | KS[2] (coefficient rows of the stage) | FS[2] (two tiles' reference phases)
     const uint32_t sbase = align1024(smem_u32(smem_raw));
     unsigned char *gbase = smem_raw + (sbase - smem_u32(smem_raw));
     unsigned char *A[2] = {gbase, gbase + kA_BYTES};
-    unsigned char *B[2] = {gbase + 2 * kA_BYTES, gbase + 2 * kA_BYTES + B_BYTES};
-    unsigned char *stg = gbase + 2 * kA_BYTES + 2 * B_BYTES;
-    float *KS[2] = {(float *)stg, (float *)(stg + K_BYTES)};
-    float *FS[2] = {(float *)(stg + 2 * K_BYTES), (float *)(stg + 2 * K_BYTES + 2 * F_BYTES)};
+    unsigned char *stage0 = gbase + 2 * kA_BYTES;
 
     if (tid == 0) {
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < kNB; ++s) {
             mbar_init(&bfull[s], 1);
+            mbar_init(&bfree[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
             mbar_init(&afull[s], kTcGen);
-            mbar_init(&mdone[s], 1);
+            mbar_init(&afree[s], 1);
         }
         abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == 8) {
+    if (warp == kTcGen / 32) {
         tc::tmem_alloc(&tmem_base, TMEM_COLS);
         tc::tmem_relinquish();
     }
@@ -296,27 +314,26 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc::fence_after_sync();
     const uint32_t tmem = tmem_base;
 
-    int issued = 0;
-    if (warp == 8) {
+    if (warp == kTcGen / 32) {
         if (tid == kTcGen) {
             auto load = [&](int it) {
-                int s = it & 1;
+                const int sb = it % kNB;
+                unsigned char *dst = stage0 + sb * S_BYTES;
                 size_t ts = (size_t)t0 + (size_t)it * TS;
-                mbar_arrive_expect_tx(&bfull[s], B_BYTES + K_BYTES + 2 * F_BYTES);
-                bulk_g2s(B[s], ypk + (ts / TS) * B_BYTES, B_BYTES, &bfull[s]);
-                bulk_g2s(KS[s], khi_t + ts * LP, K_BYTES, &bfull[s]);
-                bulk_g2s(FS[s], f0 + (size_t)tileA * ntp + ts, F_BYTES, &bfull[s]);
-                bulk_g2s(FS[s] + TS, f0 + (size_t)tileB * ntp + ts, F_BYTES, &bfull[s]);
+                mbar_arrive_expect_tx(&bfull[sb], S_DATA);
+                bulk_g2s(dst, ypk + (ts / TS) * B_BYTES, B_BYTES, &bfull[sb]);
+                bulk_g2s(dst + B_BYTES, khi_t + ts * LP, K_BYTES, &bfull[sb]);
+                bulk_g2s(dst + B_BYTES + K_BYTES, f0 + (size_t)tileA * ntp + ts, F_BYTES, &bfull[sb]);
+                bulk_g2s(dst + B_BYTES + K_BYTES + F_BYTES, f0 + (size_t)tileB * ntp + ts, F_BYTES, &bfull[sb]);
             };
-            if (nst > 0) load(0);
-            if (nst > 1) load(1);
+            for (int j = 0; j < min(kNB, nst); ++j) load(j);
+            int issued = 0;
             for (int it = 0; it < nst; ++it) {
-                const int s = it & 1;
-                const unsigned ph = (it >> 1) & 1;
-                if (!wait_or_abort(&afull[s], ph, &abort_flag, status)) break;
-                if (!wait_or_abort(&bfull[s], ph, &abort_flag, status)) break;
+                const int sa = it & 1, sb = it % kNB;
+                if (!wait_or_abort(&afull[sa], (it >> 1) & 1, &abort_flag, status)) break;
+                if (!wait_or_abort(&bfull[sb], (it / kNB) & 1, &abort_flag, status)) break;
                 tc::fence_after_sync();
-                const uint32_t a0 = smem_u32(A[s]), b0 = smem_u32(B[s]);
+                const uint32_t a0 = smem_u32(A[sa]), b0 = smem_u32(stage0 + sb * S_BYTES);
 #pragma unroll
                 for (int kk = 0; kk < 8; ++kk) {
                     const uint32_t koff = (uint32_t)((kk >> 2) * (kRows * 128) + (kk & 3) * 32);
@@ -324,27 +341,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     tc::mma_f16(tmem, tc::sdesc_k128(a0 + koff), tc::sdesc_k128(b0 + kofb), IDESC,
                                 (it | kk) != 0);
                 }
-                tc::mma_commit(&mdone[s]);
+                tc::mma_commit(&afree[sa]);
+                tc::mma_commit(&bfree[sb]);
                 issued = it + 1;
-                if (it + 2 < nst) {
-                    if (!wait_or_abort(&mdone[s], ph, &abort_flag, status)) break;
-                    load(it + 2);
+                if (it + kNB < nst) {
+                    if (!wait_or_abort(&bfree[sb], (it / kNB) & 1, &abort_flag, status)) break;
+                    load(it + kNB);
                 }
             }
             if (issued > 0) {
                 const int last = issued - 1;
-                mbar_wait_bounded(&mdone[last & 1], (last >> 1) & 1, status);
+                mbar_wait_bounded(&afree[last & 1], (last >> 1) & 1, status);
             }
         }
     } else {
-        // generator: warp w owns sample chunks w and w + 8 of each stage, lane g owns voxel
-        // rows g, g+32 (first tile) and g+64, g+96 (second tile) with their basis offsets
-        const int jp = warp;
+        // generator: warp w owns sample chunks (w & 7) and (w & 7) + 8 of each stage; lane g
+        // owns voxel rows r0 = 64 (w >> 3) + g and r0 + 32 (both in tile w >> 3 of the block)
+        // with their basis offsets in registers
+        const int jp = warp & 7;
         const int g = tid & 31;
-        float d[4][LP];
+        const int th = warp >> 3;  // which of the block's two tiles
+        const int r0 = 64 * th + g;
+        float d[2][LP];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int p = blockIdx.x * kRows + g + 32 * i;
+        for (int i = 0; i < 2; ++i) {
+            const int p = blockIdx.x * kRows + r0 + 32 * i;
             const bool valid = p < ntiles * kTileVox;
 #pragma unroll
             for (int q = 0; q < LP / 4; ++q) {
@@ -356,32 +377,32 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
         }
         for (int it = 0; it < nst; ++it) {
-            const int s = it & 1;
-            const unsigned ph = (it >> 1) & 1;
-            if (!wait_or_abort(&bfull[s], ph, &abort_flag, status)) break;
-            if (it >= 2 && !wait_or_abort(&mdone[s], ((it - 2) >> 1) & 1, &abort_flag, status)) break;
+            const int sa = it & 1, sb = it % kNB;
+            if (!wait_or_abort(&bfull[sb], (it / kNB) & 1, &abort_flag, status)) break;
+            if (it >= 2 && !wait_or_abort(&afree[sa], ((it - 2) >> 1) & 1, &abort_flag, status)) break;
+            const unsigned char *stg = stage0 + sb * S_BYTES;
+            const float4 *KS = reinterpret_cast<const float4 *>(stg + B_BYTES);
+            const float4 *FS = reinterpret_cast<const float4 *>(stg + B_BYTES + K_BYTES);
 #pragma unroll
             for (int hh = 0; hh < 2; ++hh) {
                 const int j = jp + 8 * hh;  // samples 4j..4j+3 of the stage
-                const float4 fa = reinterpret_cast<const float4 *>(FS[s])[j];
-                const float4 fb = reinterpret_cast<const float4 *>(FS[s] + TS)[j];
+                const float4 fa = FS[th * (TS / 4) + j];
                 const float fA[4] = {fa.x, fa.y, fa.z, fa.w};
-                const float fB[4] = {fb.x, fb.y, fb.z, fb.w};
-                uint32_t packed[4][4];
+                uint32_t packed[2][4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     float k[LP];
 #pragma unroll
                     for (int q = 0; q < LP / 4; ++q) {
-                        float4 w = reinterpret_cast<const float4 *>(KS[s])[(4 * j + u) * (LP / 4) + q];
+                        float4 w = KS[(4 * j + u) * (LP / 4) + q];
                         k[4 * q] = w.x;
                         k[4 * q + 1] = w.y;
                         k[4 * q + 2] = w.z;
                         k[4 * q + 3] = w.w;
                     }
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        float p0 = i < 2 ? fA[u] : fB[u], p1 = 0.f;
+                    for (int i = 0; i < 2; ++i) {
+                        float p0 = fA[u], p1 = 0.f;
 #pragma unroll
                         for (int l = 0; l < LP; l += 2) {
                             p0 = fmaf(k[l], d[i][l], p0);
@@ -394,18 +415,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         packed[i][u] = pack_bf16(cs, sn);  // conj(E) = cos + i sin
                     }
                 }
-                unsigned char *atom_base = A[s] + hh * (kRows * 128);
+                unsigned char *atom_base = A[sa] + hh * (kRows * 128);
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    *reinterpret_cast<uint4 *>(atom_base + tc::swz128(g + 32 * i, jp)) =
+                for (int i = 0; i < 2; ++i)
+                    *reinterpret_cast<uint4 *>(atom_base + tc::swz128(r0 + 32 * i, jp)) =
                         make_uint4(packed[i][0], packed[i][1], packed[i][2], packed[i][3]);
             }
             tc::fence_proxy_async_smem();
-            tc::mbar_arrive(&afull[s]);
+            tc::mbar_arrive(&afull[sa]);
         }
         // epilogue (warps 0-3, one voxel row per thread): conj(S) . u over coils
         bool ok = !abort_flag;
-        if (nst > 0 && ok) ok = wait_or_abort(&mdone[(nst - 1) & 1], ((nst - 1) >> 1) & 1, &abort_flag, status);
+        if (nst > 0 && ok) ok = wait_or_abort(&afree[(nst - 1) & 1], ((nst - 1) >> 1) & 1, &abort_flag, status);
         ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
         tc::fence_after_sync();
         if (warp < 4) {
@@ -442,7 +463,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 8) {
+    if (warp == kTcGen / 32) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem, TMEM_COLS);
     }
@@ -541,13 +562,14 @@ __global__ void fwd_reduce_planar_residual_kernel(const float *part, int splits,
 }
 
 // ---- launch helpers ----
+constexpr size_t round1k(size_t v) { return (v + 1023) & ~size_t(1023); }
 template <int CB, int LP>
 size_t fwd_tc_smem() {
-    return 1024 + 2 * kA_BYTES + 2 * (2 * CB * 256) + 2 * (kTileVox * LP * 4);
+    return 1024 + 2 * kA_BYTES + kNB * round1k(2 * CB * 256 + kTileVox * LP * 4 + kRows * 4);
 }
 template <int CB, int LP>
 size_t adj_tc_smem() {
-    return 1024 + 2 * kA_BYTES + 2 * (2 * CB * 256) + 2 * (kCols * LP * 4) + 4 * (kCols * 4);
+    return 1024 + 2 * kA_BYTES + kNB * round1k(2 * CB * 256 + kCols * LP * 4 + 2 * kCols * 4);
 }
 
 template <int CB, int LP>
