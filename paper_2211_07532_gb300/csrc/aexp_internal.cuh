@@ -37,7 +37,33 @@ struct WsHeader {
     double lipschitz;    // L_f in use
     double mu;           // last Rayleigh quotient
     double nrm2;         // last squared norm
-    double scratch[4];
+    int counter[2];      // work-item counters of the persistent kernels (forward, adjoint)
+    int item_off[4];     // single problem: {0, forward items} and {0, adjoint items}
+    double scratch[2];
+};
+
+// Per-problem descriptor read by the persistent tensor-core kernels and by the batched
+// solver kernels (device memory; one entry per problem).
+struct ProbDesc {
+    int nx, ny, nr, nt, nc, ntp, ntiles, ntx, nr_pad, CB, LP;
+    int fwd_splits, fwd_tps, adj_splits, adj_tps, adj_vblocks;
+    // operator workspace
+    const float *khi_t, *f0, *dh;
+    const float2 *Sp;
+    unsigned char *bpk, *ypk;
+    float *fpart;
+    float2 *apart, *rt;
+    WsHeader *hdr;
+    // solver vectors: 0 xa, 1 xb, 2 z, 3 v, 4 w, 5 ymeas (sample-major)
+    float2 *vec[6];
+    char *wws;
+    int npx, npy, levels, pad1;
+    size_t off_pyr, off_approx[12];
+    float lam;
+    int pad2;
+    const float2 *y_in;
+    float2 *x_out;
+    double *lip_out;
 };
 
 struct OpLayout {
@@ -54,7 +80,8 @@ struct OpLayout {
     int adj_mr, adj_vblocks, adj_splits, adj_t_per_split;
     // byte offsets into the workspace
     size_t off_hdr, off_khi_l, off_klo_l, off_khi_t, off_h0, off_dh, off_f0, off_S, off_b,
-        off_fpart, off_yt, off_apart, off_ypk;
+        off_fpart, off_yt, off_apart, off_ypk, off_desc;
+    int fwd_items, adj_items;  // persistent tensor-core work items
     size_t bytes;
 };
 
@@ -111,9 +138,23 @@ cudaError_t op_adjoint_reduce(const OpLayout &L, char *ws, float2 *out, cudaStre
 cudaError_t op_adjoint_reduce_step(const OpLayout &L, char *ws, const float2 *z, float2 *out,
                                    cudaStream_t st);
 
+// Descriptor of one problem's operator workspace (solver fields left empty).
+ProbDesc make_op_desc(const OpLayout &L, char *ws);
+cudaError_t write_desc(const ProbDesc &d, ProbDesc *dst, cudaStream_t st);
+int num_sms();
+
 // Tensor-core forms (op_tc.cu): the forward packs S*x itself; the adjoint packs yt.
 cudaError_t op_forward_tc(const OpLayout &L, const float2 *x, char *ws, cudaStream_t st);
 cudaError_t op_adjoint_tc(const OpLayout &L, const float2 *yt, char *ws, cudaStream_t st);
+// Batched tensor-core applications over nprob descriptors (uniform CB and LP): pack the
+// image vec[src] (forward) or rt (adjoint), then one persistent launch over all work items.
+// item_off: device prefix offsets [nprob + 1]; counter: device int reset by these calls.
+cudaError_t batch_forward_tc(int CB, int LP, const ProbDesc *pd, int nprob, int max_pack_blocks, int src,
+                             const int *item_off, int total_items, int *counter, cudaStream_t st);
+cudaError_t batch_adjoint_tc(int CB, int LP, const ProbDesc *pd, int nprob, int max_pack_blocks,
+                             const int *item_off, int total_items, int *counter, cudaStream_t st);
+int fwd_pack_blocks(int ntiles, int CB);
+int adj_pack_blocks(int ntp, int CB);
 cudaError_t op_forward_reduce_planar_public(const OpLayout &L, char *ws, float2 *y, cudaStream_t st);
 cudaError_t op_forward_reduce_planar_residual(const OpLayout &L, char *ws, const float2 *ymeas_t, float2 *rt,
                                               cudaStream_t st);

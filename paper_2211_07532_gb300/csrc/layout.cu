@@ -92,6 +92,9 @@ int op_layout(const aexp_problem *p, int precision, OpLayout *L) {
     o.off_yt = take(sizeof(float2) * (size_t)o.ntp * o.CB);
     o.off_apart = take(sizeof(float2) * (size_t)o.adj_splits * o.nr_pad);
     o.off_ypk = take(precision == AEXP_FP32 ? 0 : sizeof(float2) * (size_t)o.ntp * o.CB);
+    o.off_desc = take(sizeof(ProbDesc));
+    o.fwd_items = o.fwd_tblocks * o.fwd_splits;
+    o.adj_items = o.adj_vblocks * o.adj_splits;
     o.bytes = off;
     *L = o;
     return AEXP_OK;
@@ -144,6 +147,52 @@ int rec_layout(const aexp_problem *p, const aexp_recon_opts *opt, RecLayout *R) 
     r.bytes = off;
     *R = r;
     return AEXP_OK;
+}
+
+}  // namespace aexp
+
+namespace aexp {
+
+ProbDesc make_op_desc(const OpLayout &L, char *ws) {
+    ProbDesc d{};
+    d.nx = L.nx;
+    d.ny = L.ny;
+    d.nr = L.nr;
+    d.nt = L.nt;
+    d.nc = L.nc;
+    d.ntp = L.ntp;
+    d.ntiles = L.ntiles;
+    d.ntx = L.ntx;
+    d.nr_pad = L.nr_pad;
+    d.CB = L.CB;
+    d.LP = L.LP;
+    d.fwd_splits = L.fwd_splits;
+    d.fwd_tps = L.fwd_tiles_per_split;
+    d.adj_splits = L.adj_splits;
+    d.adj_tps = L.adj_t_per_split;
+    d.adj_vblocks = L.adj_vblocks;
+    d.khi_t = (const float *)(ws + L.off_khi_t);
+    d.f0 = (const float *)(ws + L.off_f0);
+    d.dh = (const float *)(ws + L.off_dh);
+    d.Sp = (const float2 *)(ws + L.off_S);
+    d.bpk = (unsigned char *)(ws + L.off_b);
+    d.ypk = (unsigned char *)(ws + L.off_ypk);
+    d.fpart = (float *)(ws + L.off_fpart);
+    d.apart = (float2 *)(ws + L.off_apart);
+    d.rt = (float2 *)(ws + L.off_yt);
+    d.hdr = (WsHeader *)(ws + L.off_hdr);
+    return d;
+}
+
+int num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            n = 152;
+    }
+    return n;
 }
 
 }  // namespace aexp

@@ -125,6 +125,13 @@ __global__ void coil_weight_kernel(const float2 *Sp, const float2 *x, int nx, in
     b[i] = out;
 }
 
+__global__ void set_items_kernel(WsHeader *hdr, int fwd_items, int adj_items) {
+    hdr->item_off[0] = 0;
+    hdr->item_off[1] = fwd_items;
+    hdr->item_off[2] = 0;
+    hdr->item_off[3] = adj_items;
+}
+
 __global__ void transpose_y_kernel(const float2 *y, int nt, int nc, int ntp, int CB, float2 *yt) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (size_t)ntp * CB) return;
@@ -151,6 +158,12 @@ cudaError_t op_prepare(const aexp_problem *p, const OpLayout &L, char *ws, cudaS
     size_t n = (size_t)L.nr_pad * L.CB;
     prep_coil_kernel<<<(unsigned)((n + T - 1) / T), T, 0, st>>>((const float2 *)p->S, L.nc, L.nx, L.ny, L.ntx,
                                                                L.nr_pad, L.CB, Sp);
+    if (L.precision != AEXP_FP32) {
+        // descriptor and work items of the persistent tensor-core kernels
+        cudaError_t e = write_desc(make_op_desc(L, ws), (ProbDesc *)(ws + L.off_desc), st);
+        if (e != cudaSuccess) return e;
+        set_items_kernel<<<1, 1, 0, st>>>((WsHeader *)(ws + L.off_hdr), L.fwd_items, L.adj_items);
+    }
     return cudaGetLastError();
 }
 
