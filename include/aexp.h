@@ -150,6 +150,30 @@ AEXP_API int aexp_power_lipschitz(const aexp_problem *prob, int precision, const
                          double *lipschitz_out, void *ws, size_t ws_bytes, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Ragged batches: many independent slice problems (several resolutions, diffusion volumes
+ * with their own field coefficients, slices) reconstructed together.  Sec. 2.2.1 acquires
+ * 15 protocols x (1 b=0 + 6 directions) x 10 slices, each reconstructed as its own 2-D
+ * problem (Sec. 2.1); here every operator application of the whole batch is one persistent
+ * tensor-core launch and the complete solve is one CUDA graph.
+ * --------------------------------------------------------------------------- */
+
+/* Bytes of workspace cs_recon_batched needs.  probs: HOST array of nprob problems
+ * (1 <= nprob <= 4095) whose padded coil and term counts agree (e.g. all 32 coils with
+ * 3rd-order terms plus B0); opts->precision must be a tensor-core form. */
+AEXP_API int aexp_batch_workspace_size(const aexp_problem *probs, int nprob, const aexp_recon_opts *opts,
+                                       size_t *bytes);
+
+/* cs_recon for every problem of the batch, same wavelet, levels, iteration count and
+ * power-iteration count; per-problem lambda.  y, x_out: HOST arrays of nprob device
+ * pointers ([nc][nt] and [nr] complex64 per problem); lambda: HOST array of nprob floats;
+ * lipschitz_out: optional DEVICE array of nprob doubles.  opts->x0 and opts->power_init
+ * must be NULL (zero start, A^H y power start).  The first device-side error of any
+ * problem is reported by aexp_read_status(ws). */
+AEXP_API int cs_recon_batched(const aexp_problem *probs, int nprob, const void *const *y, const float *lambda,
+                              int iters, const aexp_recon_opts *opts, void *const *x_out, double *lipschitz_out,
+                              void *ws, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Wavelet step on its own (Eq. 1 regulariser): out = crop(W^H soft(W pad(in), tau))
  * --------------------------------------------------------------------------- */
 

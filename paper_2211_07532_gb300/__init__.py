@@ -65,6 +65,9 @@ SIGNATURES = [
     ("aexp_recon_workspace_size", _I, [_PROB, _OPTS, ctypes.POINTER(_SZ)]),
     ("cs_recon", _I, [_PROB, _P, ctypes.c_float, _I, _OPTS, _P, _P, _P, _SZ, _P]),
     ("aexp_power_lipschitz", _I, [_PROB, _I, _P, _I, _P, _P, _SZ, _P]),
+    ("aexp_batch_workspace_size", _I, [_PROB, _I, _OPTS, ctypes.POINTER(_SZ)]),
+    ("cs_recon_batched", _I, [_PROB, _I, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_float), _I, _OPTS,
+                              ctypes.POINTER(_P), _P, _P, _SZ, _P]),
     ("aexp_wavelet_workspace_size", _I, [_I, _I, _I, _I, ctypes.POINTER(_SZ)]),
     ("aexp_wavelet_prox", _I, [_I, _I, _I, _I, ctypes.c_float, _P, _P, _P, _SZ, _P]),
     ("aexp_wavelet_forward", _I, [_I, _I, _I, _I, _P, _P, _P, _SZ, _P]),
@@ -242,6 +245,43 @@ def cs_recon(prob: Problem, y, lam: float, iters: int, opts: CReconOpts | None =
     _check(lib().cs_recon(prob.c, _ptr(y), float(lam), int(iters), ctypes.byref(opts), _ptr(x_out),
                           _ptr(lipschitz_out), _ptr(ws), ws.numel(), _stream(stream)), "cs_recon")
     return x_out, lipschitz_out
+
+
+def _prob_array(probs):
+    arr = (CProblem * len(probs))()
+    for i, pr in enumerate(probs):
+        arr[i] = pr._c
+    return arr
+
+
+def batch_workspace_size(probs, opts: CReconOpts) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().aexp_batch_workspace_size(_prob_array(probs), len(probs), ctypes.byref(opts), ctypes.byref(n)),
+           "aexp_batch_workspace_size")
+    return n.value
+
+
+def cs_recon_batched(probs, ys, lams, iters: int, opts: CReconOpts | None = None, ws=None, x_outs=None,
+                     lipschitz_out=None, stream=None, **kw):
+    """FISTA on Eq. (1) for a ragged batch of problems in one graph; returns (list of x, L_f [n])."""
+    torch = _torch()
+    opts = recon_opts(**kw) if opts is None else opts
+    n = len(probs)
+    probs_c = _prob_array(probs)
+    ys = [y.contiguous() for y in ys]
+    dev = ys[0].device
+    if ws is None:
+        ws = _alloc(batch_workspace_size(probs, opts), dev)
+    if x_outs is None:
+        x_outs = [torch.empty(pr.nr, dtype=torch.complex64, device=dev) for pr in probs]
+    if lipschitz_out is None:
+        lipschitz_out = torch.empty(n, dtype=torch.float64, device=dev)
+    yp = (ctypes.c_void_p * n)(*[y.data_ptr() for y in ys])
+    xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in x_outs])
+    lp = (ctypes.c_float * n)(*[float(v) for v in lams])
+    _check(lib().cs_recon_batched(probs_c, n, yp, lp, int(iters), ctypes.byref(opts), xp, _ptr(lipschitz_out),
+                                  _ptr(ws), ws.numel(), _stream(stream)), "cs_recon_batched")
+    return x_outs, lipschitz_out
 
 
 def power_lipschitz(prob: Problem, v0, n_power: int, ws=None, precision: int = FP32, stream=None):

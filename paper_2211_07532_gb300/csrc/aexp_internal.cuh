@@ -114,9 +114,11 @@ inline size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a
 inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 
 // Host-side layout computation (layout.cu).
-int op_layout(const aexp_problem *p, int precision, OpLayout *L);
+// tc_target_items: work items the tensor-core splits aim for (a batch passes a share of the
+// SM-count target so that large batches use whole-problem items and few partial sums).
+int op_layout(const aexp_problem *p, int precision, OpLayout *L, int tc_target_items = 152 * 8);
 int wave_layout(int nx, int ny, int wavelet, int levels, WaveLayout *W);
-int rec_layout(const aexp_problem *p, const aexp_recon_opts *o, RecLayout *R);
+int rec_layout(const aexp_problem *p, const aexp_recon_opts *o, RecLayout *R, int tc_target_items = 152 * 8);
 
 // Launchers (all asynchronous on `st`; return cudaError_t of the launch).
 cudaError_t op_prepare(const aexp_problem *p, const OpLayout &L, char *ws, cudaStream_t st);
@@ -151,7 +153,7 @@ cudaError_t op_adjoint_tc(const OpLayout &L, const float2 *yt, char *ws, cudaStr
 // item_off: device prefix offsets [nprob + 1]; counter: device int reset by these calls.
 cudaError_t batch_forward_tc(int CB, int LP, const ProbDesc *pd, int nprob, int max_pack_blocks, int src,
                              const int *item_off, int total_items, int *counter, cudaStream_t st);
-cudaError_t batch_adjoint_tc(int CB, int LP, const ProbDesc *pd, int nprob, int max_pack_blocks,
+cudaError_t batch_adjoint_tc(int CB, int LP, const ProbDesc *pd, int nprob, int max_pack_blocks, int src,
                              const int *item_off, int total_items, int *counter, cudaStream_t st);
 int fwd_pack_blocks(int ntiles, int CB);
 int adj_pack_blocks(int ntp, int CB);
@@ -173,6 +175,13 @@ cudaError_t wave_forward(const WaveLayout &W, const float2 *img, char *wws, floa
 // inverse into out (natural [ny][nx]); when momentum: x_new = result, z = x_new + beta (x_new - x_old)
 cudaError_t wave_inverse(const WaveLayout &W, char *wws, float2 *out, int momentum, double beta,
                          const float2 *x_old, float2 *z_out, cudaStream_t st);
+
+// Batched wavelet levels over a descriptor table (uniform wavelet and levels; grid sized
+// for the largest padded image max_npy x max_npx).  Roles index ProbDesc::vec.
+cudaError_t batch_wave_forward(int wavelet, const ProbDesc *pd, int nprob, int levels, int max_npx, int max_npy,
+                               int img_role, int threshold, cudaStream_t st);
+cudaError_t batch_wave_inverse(int wavelet, const ProbDesc *pd, int nprob, int levels, int max_npx, int max_npy,
+                               int out_role, int momentum, double beta, int xold_role, int z_role, cudaStream_t st);
 
 // Reductions and small vector kernels (recon.cu).
 cudaError_t dot_norm_f64(const float2 *v, const float2 *w, int n, double *mu, double *nrm2, cudaStream_t st);

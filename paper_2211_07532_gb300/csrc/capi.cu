@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "aexp_internal.cuh"
+#include "batch_internal.h"
 
 using namespace aexp;
 
@@ -272,6 +273,84 @@ int cs_recon(const aexp_problem *prob, const void *y, float lambda, int iters, c
     if (e != cudaSuccess) return cuda_fail(e);
     g_prepared[ws] = PrepRecord{*prob, opts->precision};
     return AEXP_OK;
+}
+
+int aexp_batch_workspace_size(const aexp_problem *probs, int nprob, const aexp_recon_opts *opts, size_t *bytes) {
+    if (!probs || nprob < 1 || nprob > kMaxBatchProblems || !bytes) return AEXP_ERR_INVALID_ARG;
+    int rc = check_opts(opts);
+    if (rc) return rc;
+    if (opts->precision == AEXP_FP32) return AEXP_ERR_UNSUPPORTED;
+    for (int q = 0; q < nprob; ++q)
+        if ((rc = check_problem(&probs[q]))) return rc;
+    BatchLayout B;
+    if ((rc = batch_layout(probs, nprob, opts, &B))) return rc;
+    *bytes = B.bytes;
+    return AEXP_OK;
+}
+
+int cs_recon_batched(const aexp_problem *probs, int nprob, const void *const *y, const float *lambda, int iters,
+                     const aexp_recon_opts *opts, void *const *x_out, double *lipschitz_out, void *ws,
+                     size_t ws_bytes, void *stream) {
+    if (!probs || nprob < 1 || nprob > kMaxBatchProblems || !y || !lambda || !x_out || iters < 0)
+        return AEXP_ERR_INVALID_ARG;
+    int rc = check_opts(opts);
+    if (rc) return rc;
+    if (opts->precision == AEXP_FP32) return AEXP_ERR_UNSUPPORTED;
+    if (opts->x0 || opts->power_init) return AEXP_ERR_UNSUPPORTED;
+    if (!aligned(lipschitz_out, 8)) return AEXP_ERR_MISALIGNED;
+    for (int q = 0; q < nprob; ++q) {
+        if ((rc = check_problem(&probs[q]))) return rc;
+        if (!y[q] || !x_out[q] || !(lambda[q] >= 0.f)) return AEXP_ERR_INVALID_ARG;
+        if (!aligned(y[q], 8) || !aligned(x_out[q], 8)) return AEXP_ERR_MISALIGNED;
+    }
+    BatchLayout B;
+    if ((rc = batch_layout(probs, nprob, opts, &B))) return rc;
+    if ((rc = check_ws(ws, ws_bytes, B.bytes))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = (char *)ws;
+    cudaError_t e = cudaMemsetAsync(w + B.off_hdr, 0, sizeof(WsHeader), st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (!opts->use_graph || st == nullptr) {
+        e = batch_recon_issue(probs, B, opts, y, lambda, iters, x_out, lipschitz_out, w, st);
+        return e == cudaSuccess ? AEXP_OK : cuda_fail(e);
+    }
+    std::vector<unsigned char> key;
+    for (int q = 0; q < nprob; ++q) {
+        put(key, probs[q]);
+        put(key, y[q]);
+        put(key, lambda[q]);
+        put(key, x_out[q]);
+    }
+    put(key, *opts);
+    put(key, iters);
+    put(key, lipschitz_out);
+    put(key, ws_bytes);
+    std::lock_guard<std::mutex> lk(g_mu);
+    GraphEntry &ge = g_graphs[ws];
+    if (ge.exec == nullptr || ge.key != key) {
+        if (ge.exec) {
+            cudaGraphExecDestroy(ge.exec);
+            ge.exec = nullptr;
+        }
+        e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e);
+        cudaError_t ei = batch_recon_issue(probs, B, opts, y, lambda, iters, x_out, lipschitz_out, w, st);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(st, &g);
+        if (ei != cudaSuccess || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(ei != cudaSuccess ? ei : e);
+        }
+        e = cudaGraphInstantiate(&ge.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            ge.exec = nullptr;
+            return cuda_fail(e);
+        }
+        ge.key = key;
+    }
+    e = cudaGraphLaunch(ge.exec, st);
+    return e == cudaSuccess ? AEXP_OK : cuda_fail(e);
 }
 
 int aexp_power_lipschitz(const aexp_problem *prob, int precision, const void *v0, int n_power,

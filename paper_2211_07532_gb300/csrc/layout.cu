@@ -12,10 +12,9 @@ int pad_terms(int n) { return n <= 4 ? 4 : n <= 8 ? 8 : n <= 12 ? 12 : 20; }
 int pad_coils(int n) { return n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : n <= 20 ? 20 : 32; }
 // tensor-core forms: N = 2 * CB must be a multiple of 16 with a power-of-two half for TMEM loads
 int pad_coils_tc(int n) { return n <= 8 ? 8 : n <= 16 ? 16 : 32; }
-constexpr int kTcWaveBlocks = 152 * 8;  // one CTA per SM, ~8 waves
 }  // namespace
 
-int op_layout(const aexp_problem *p, int precision, OpLayout *L) {
+int op_layout(const aexp_problem *p, int precision, OpLayout *L, int tc_target_items) {
     OpLayout o{};
     o.nx = p->nx;
     o.ny = p->ny;
@@ -62,13 +61,13 @@ int op_layout(const aexp_problem *p, int precision, OpLayout *L) {
         // one CTA (128 samples or 2 tiles) per SM at a time; split the reduction dimension
         // so the grid covers ~8 waves
         const int tblocks = o.ntp / 128;
-        int s = std::min(std::max(cdiv(kTcWaveBlocks, tblocks), 1), o.ntiles);
+        int s = std::min(std::max(cdiv(tc_target_items, tblocks), 1), o.ntiles);
         o.fwd_tblocks = tblocks;
         o.fwd_tiles_per_split = cdiv(o.ntiles, s);
         o.fwd_splits = cdiv(o.ntiles, o.fwd_tiles_per_split);
         o.adj_vblocks = cdiv(o.ntiles, 2);
         const int nstage = o.ntp / kAdjStageT;
-        s = std::min(std::max(cdiv(kTcWaveBlocks, o.adj_vblocks), 1), nstage);
+        s = std::min(std::max(cdiv(tc_target_items, o.adj_vblocks), 1), nstage);
         o.adj_t_per_split = cdiv(nstage, s) * kAdjStageT;
         o.adj_splits = cdiv(o.ntp, o.adj_t_per_split);
     }
@@ -123,9 +122,9 @@ int wave_layout(int nx, int ny, int wavelet, int levels, WaveLayout *W) {
     return AEXP_OK;
 }
 
-int rec_layout(const aexp_problem *p, const aexp_recon_opts *opt, RecLayout *R) {
+int rec_layout(const aexp_problem *p, const aexp_recon_opts *opt, RecLayout *R, int tc_target_items) {
     RecLayout r{};
-    int rc = op_layout(p, opt->precision, &r.op);
+    int rc = op_layout(p, opt->precision, &r.op, tc_target_items);
     if (rc) return rc;
     rc = wave_layout(p->nx, p->ny, opt->wavelet, opt->levels, &r.wv);
     if (rc) return rc;

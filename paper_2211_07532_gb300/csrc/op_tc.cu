@@ -534,16 +534,17 @@ __global__ void pack_b_fwd_kernel(const ProbDesc *__restrict__ pd, const float2 
     *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// Adjoint: k-space yt[t][c] (or the descriptor's rt) per stage of 64 samples; rows n < C
+// Adjoint: k-space yt[t][c] (or the descriptor's vec[src], or rt when src < 0) per stage of
+// 64 samples; rows n < C
 // carry (Re y, -Im y), rows C + c carry (Im y, Re y) at K positions (2s, 2s+1).
 template <int CB>
-__global__ void pack_y_adj_kernel(const ProbDesc *__restrict__ pd, const float2 *__restrict__ yt) {
+__global__ void pack_y_adj_kernel(const ProbDesc *__restrict__ pd, const float2 *__restrict__ yt, int src) {
     constexpr int N = 2 * CB;
     const ProbDesc &P = pd[blockIdx.y];
     const int nstages = P.ntp / kCols;
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // (stage, n, chunk)
     if (i >= (size_t)nstages * N * 16) return;
-    const float2 *y = yt ? yt : P.rt;
+    const float2 *y = yt ? yt : (src >= 0 ? P.vec[src] : P.rt);
     const int jj = (int)(i % 16);
     const int n = (int)((i / 16) % N);
     const int st = (int)(i / (16 * N));
@@ -622,9 +623,9 @@ cudaError_t launch_fwd_tc(const ProbDesc *pd, int nprob, int max_pack_blocks, co
 }
 
 template <int CB, int LP>
-cudaError_t launch_adj_tc(const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *yt,
+cudaError_t launch_adj_tc(const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *yt, int src,
                           const int *item_off, int total_items, int *counter, cudaStream_t st) {
-    pack_y_adj_kernel<CB><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, yt);
+    pack_y_adj_kernel<CB><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, yt, src);
     auto kern = adj_tc_kernel<CB, LP>;
     const size_t smem = adj_tc_smem<CB, LP>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -672,7 +673,7 @@ cudaError_t op_adjoint_tc(const OpLayout &L, const float2 *yt, char *ws, cudaStr
     const int CBv = L.CB, LPv = L.LP;
     WsHeader *hdr = (WsHeader *)(ws + L.off_hdr);
     const ProbDesc *pd = (const ProbDesc *)(ws + L.off_desc);
-    AEXP_TC_DISPATCH(launch_adj_tc, pd, 1, adj_pack_blocks(L.ntp, L.CB), yt, &hdr->item_off[2], L.adj_items,
+    AEXP_TC_DISPATCH(launch_adj_tc, pd, 1, adj_pack_blocks(L.ntp, L.CB), yt, -1, &hdr->item_off[2], L.adj_items,
                      &hdr->counter[1], st)
 }
 
@@ -682,10 +683,10 @@ cudaError_t batch_forward_tc(int CB, int LP, const ProbDesc *pd, int nprob, int 
     AEXP_TC_DISPATCH(launch_fwd_tc, pd, nprob, max_pack_blocks, nullptr, src, item_off, total_items, counter, st)
 }
 
-cudaError_t batch_adjoint_tc(int CB, int LP, const ProbDesc *pd, int nprob, int max_pack_blocks,
+cudaError_t batch_adjoint_tc(int CB, int LP, const ProbDesc *pd, int nprob, int max_pack_blocks, int src,
                              const int *item_off, int total_items, int *counter, cudaStream_t st) {
     const int CBv = CB, LPv = LP;
-    AEXP_TC_DISPATCH(launch_adj_tc, pd, nprob, max_pack_blocks, nullptr, item_off, total_items, counter, st)
+    AEXP_TC_DISPATCH(launch_adj_tc, pd, nprob, max_pack_blocks, nullptr, src, item_off, total_items, counter, st)
 }
 
 cudaError_t op_forward_reduce_planar_public(const OpLayout &L, char *ws, float2 *y, cudaStream_t st) {

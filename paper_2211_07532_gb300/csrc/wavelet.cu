@@ -52,17 +52,19 @@ __device__ __forceinline__ float thresh_tau(float lam, const double *lipschitz) 
 constexpr int OB = 16;   // forward: output coefficients per subband per block side
 constexpr int OBI = 32;  // inverse: output samples per block side
 
+// One level of analysis for output block (bx, by): reads the n_y x n_x input (zero outside
+// valid_y x valid_x), writes LL to `ll` and the three detail bands into the quadrants of the
+// n_y x n_x block of `pyr`, shrinking details by tau when `threshold`.
 template <int TAPS>
-__global__ void __launch_bounds__(256)
-    dwt_fwd_level(const float2 *__restrict__ in, int in_stride, int valid_y, int valid_x, int n_y, int n_x,
-                  float2 *__restrict__ ll, int ll_stride, float2 *__restrict__ pyr, int pyr_stride, float lam,
-                  const double *lipschitz, int threshold) {
+__device__ __forceinline__ void dwt_fwd_level_body(const float2 *__restrict__ in, int in_stride, int valid_y,
+                                                   int valid_x, int n_y, int n_x, float2 *__restrict__ ll,
+                                                   int ll_stride, float2 *__restrict__ pyr, int pyr_stride,
+                                                   float tau, int threshold, int bx, int by) {
     constexpr int IN = 2 * OB + TAPS - 2;
     __shared__ float2 s_in[IN][IN];
     __shared__ float2 s_row[IN][2 * OB];
     const int my = n_y / 2, mx = n_x / 2;
-    const int oy0 = blockIdx.y * OB, ox0 = blockIdx.x * OB;
-    const float tau = threshold ? thresh_tau(lam, lipschitz) : 0.f;
+    const int oy0 = by * OB, ox0 = bx * OB;
 
     for (int idx = threadIdx.x; idx < IN * IN; idx += blockDim.x) {
         int i = idx / IN, j = idx % IN;
@@ -114,15 +116,29 @@ __global__ void __launch_bounds__(256)
 
 template <int TAPS>
 __global__ void __launch_bounds__(256)
-    dwt_inv_level(const float2 *__restrict__ ll, int ll_stride, const float2 *__restrict__ pyr, int pyr_stride,
-                  int n_y, int n_x, float2 *__restrict__ out, int out_stride, int valid_y, int valid_x,
-                  int momentum, float beta, const float2 *__restrict__ x_old, float2 *__restrict__ z_out) {
+    dwt_fwd_level(const float2 *__restrict__ in, int in_stride, int valid_y, int valid_x, int n_y, int n_x,
+                  float2 *__restrict__ ll, int ll_stride, float2 *__restrict__ pyr, int pyr_stride, float lam,
+                  const double *lipschitz, int threshold) {
+    const float tau = threshold ? thresh_tau(lam, lipschitz) : 0.f;
+    dwt_fwd_level_body<TAPS>(in, in_stride, valid_y, valid_x, n_y, n_x, ll, ll_stride, pyr, pyr_stride, tau,
+                             threshold, blockIdx.x, blockIdx.y);
+}
+
+// One level of synthesis for output block (bx, by) of the n_y x n_x result; writes inside
+// valid_y x valid_x only; with `momentum` also z = x + beta (x - x_old) (same layout as out).
+template <int TAPS>
+__device__ __forceinline__ void dwt_inv_level_body(const float2 *__restrict__ ll, int ll_stride,
+                                                   const float2 *__restrict__ pyr, int pyr_stride, int n_y, int n_x,
+                                                   float2 *__restrict__ out, int out_stride, int valid_y,
+                                                   int valid_x, int momentum, float beta,
+                                                   const float2 *__restrict__ x_old, float2 *__restrict__ z_out,
+                                                   int bx, int by) {
     constexpr int HALO = TAPS / 2 - 1;
     constexpr int SB = OBI / 2 + HALO;
     __shared__ float2 s_sb[4][SB][SB];     // LL, (lo-y,hi-x), (hi-y,lo-x), HH
     __shared__ float2 s_col[OBI][2 * SB];  // after y-synthesis: [row][lo-x j | hi-x j]
     const int my = n_y / 2, mx = n_x / 2;
-    const int qy0 = blockIdx.y * OBI, qx0 = blockIdx.x * OBI;
+    const int qy0 = by * OBI, qx0 = bx * OBI;
     const int jy0 = qy0 / 2 - HALO, jx0 = qx0 / 2 - HALO;
 
     for (int idx = threadIdx.x; idx < 4 * SB * SB; idx += blockDim.x) {
@@ -144,7 +160,7 @@ __global__ void __launch_bounds__(256)
         int q = qy0 + a;
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int m = (TAPS > 1 ? 0 : 0); m < TAPS; ++m) {
+        for (int m = 0; m < TAPS; ++m) {
             if (((q - m) & 1) != 0) continue;
             int i = ((q - m) >> 1) - jy0;
             float2 lo = s_sb[xband == 0 ? 0 : 1][i][j];
@@ -178,6 +194,73 @@ __global__ void __launch_bounds__(256)
         }
         out[o] = acc;
     }
+}
+
+template <int TAPS>
+__global__ void __launch_bounds__(256)
+    dwt_inv_level(const float2 *__restrict__ ll, int ll_stride, const float2 *__restrict__ pyr, int pyr_stride,
+                  int n_y, int n_x, float2 *__restrict__ out, int out_stride, int valid_y, int valid_x,
+                  int momentum, float beta, const float2 *__restrict__ x_old, float2 *__restrict__ z_out) {
+    dwt_inv_level_body<TAPS>(ll, ll_stride, pyr, pyr_stride, n_y, n_x, out, out_stride, valid_y, valid_x, momentum,
+                             beta, x_old, z_out, blockIdx.x, blockIdx.y);
+}
+
+// ---- batched levels: grid.z = problem; blocks beyond a problem's level extent return ----
+template <int TAPS>
+__global__ void __launch_bounds__(256)
+    batch_dwt_fwd_level(const ProbDesc *__restrict__ pd, int j, int img_role, int threshold) {
+    const ProbDesc &P = pd[blockIdx.z];
+    const int n_y = P.npy >> (j - 1), n_x = P.npx >> (j - 1);
+    if ((int)blockIdx.x * OB >= n_x / 2 || (int)blockIdx.y * OB >= n_y / 2) return;
+    const float2 *in;
+    int in_stride, vy, vx;
+    if (j == 1) {
+        in = P.vec[img_role];
+        in_stride = P.nx;
+        vy = P.ny;
+        vx = P.nx;
+    } else {
+        in = (const float2 *)(P.wws + P.off_approx[j - 1]);
+        in_stride = n_x;
+        vy = n_y;
+        vx = n_x;
+    }
+    float2 *pyr = (float2 *)(P.wws + P.off_pyr);
+    float2 *llp = j == P.levels ? pyr : (float2 *)(P.wws + P.off_approx[j]);
+    const int ll_stride = j == P.levels ? P.npx : n_x / 2;
+    const float tau = threshold ? thresh_tau(P.lam, &P.hdr->lipschitz) : 0.f;
+    dwt_fwd_level_body<TAPS>(in, in_stride, vy, vx, n_y, n_x, llp, ll_stride, pyr, P.npx, tau, threshold, blockIdx.x,
+                             blockIdx.y);
+}
+
+template <int TAPS>
+__global__ void __launch_bounds__(256)
+    batch_dwt_inv_level(const ProbDesc *__restrict__ pd, int j, int out_role, int momentum, float beta,
+                        int xold_role, int z_role) {
+    const ProbDesc &P = pd[blockIdx.z];
+    const int n_y = P.npy >> (j - 1), n_x = P.npx >> (j - 1);
+    if ((int)blockIdx.x * OBI >= n_x || (int)blockIdx.y * OBI >= n_y) return;
+    const float2 *pyr = (const float2 *)(P.wws + P.off_pyr);
+    const float2 *llp = j == P.levels ? pyr : (const float2 *)(P.wws + P.off_approx[j]);
+    const int ll_stride = j == P.levels ? P.npx : n_x / 2;
+    float2 *o;
+    int o_stride, vy, vx, mom;
+    if (j == 1) {
+        o = P.vec[out_role];
+        o_stride = P.nx;
+        vy = P.ny;
+        vx = P.nx;
+        mom = momentum;
+    } else {
+        o = (float2 *)(P.wws + P.off_approx[j - 1]);
+        o_stride = n_x;
+        vy = n_y;
+        vx = n_x;
+        mom = 0;
+    }
+    dwt_inv_level_body<TAPS>(llp, ll_stride, pyr, P.npx, n_y, n_x, o, o_stride, vy, vx, mom, beta,
+                             mom ? P.vec[xold_role] : nullptr, mom ? P.vec[z_role] : nullptr, blockIdx.x,
+                             blockIdx.y);
 }
 
 template <int TAPS>
@@ -252,7 +335,45 @@ cudaError_t run_inverse(const WaveLayout &W, char *wws, float2 *out, int momentu
     return cudaGetLastError();
 }
 
+template <int TAPS>
+cudaError_t run_batch_forward(const ProbDesc *pd, int nprob, int levels, int max_npx, int max_npy, int img_role,
+                              int threshold, cudaStream_t st) {
+    for (int j = 1; j <= levels; ++j) {
+        int n_y = max_npy >> (j - 1), n_x = max_npx >> (j - 1);
+        dim3 grid(cdiv(n_x / 2, OB), cdiv(n_y / 2, OB), nprob);
+        batch_dwt_fwd_level<TAPS><<<grid, 256, 0, st>>>(pd, j, img_role, threshold);
+    }
+    return cudaGetLastError();
+}
+
+template <int TAPS>
+cudaError_t run_batch_inverse(const ProbDesc *pd, int nprob, int levels, int max_npx, int max_npy, int out_role,
+                              int momentum, double beta, int xold_role, int z_role, cudaStream_t st) {
+    for (int j = levels; j >= 1; --j) {
+        int n_y = max_npy >> (j - 1), n_x = max_npx >> (j - 1);
+        dim3 grid(cdiv(n_x, OBI), cdiv(n_y, OBI), nprob);
+        batch_dwt_inv_level<TAPS><<<grid, 256, 0, st>>>(pd, j, out_role, momentum, (float)beta, xold_role, z_role);
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t batch_wave_forward(int wavelet, const ProbDesc *pd, int nprob, int levels, int max_npx, int max_npy,
+                               int img_role, int threshold, cudaStream_t st) {
+    return wavelet == AEXP_WAVELET_HAAR
+               ? run_batch_forward<2>(pd, nprob, levels, max_npx, max_npy, img_role, threshold, st)
+               : run_batch_forward<8>(pd, nprob, levels, max_npx, max_npy, img_role, threshold, st);
+}
+
+cudaError_t batch_wave_inverse(int wavelet, const ProbDesc *pd, int nprob, int levels, int max_npx, int max_npy,
+                               int out_role, int momentum, double beta, int xold_role, int z_role, cudaStream_t st) {
+    return wavelet == AEXP_WAVELET_HAAR
+               ? run_batch_inverse<2>(pd, nprob, levels, max_npx, max_npy, out_role, momentum, beta, xold_role,
+                                      z_role, st)
+               : run_batch_inverse<8>(pd, nprob, levels, max_npx, max_npy, out_role, momentum, beta, xold_role,
+                                      z_role, st);
+}
 
 cudaError_t wave_forward(const WaveLayout &W, const float2 *img, char *wws, float lam, const double *lipschitz,
                          int threshold, cudaStream_t st) {

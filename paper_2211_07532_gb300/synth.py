@@ -98,14 +98,11 @@ def spiral_k(nt: int, kmax: float, turns: float, density_power: float) -> np.nda
 
 
 def exp_smooth(sig: np.ndarray, dt: float, tau: float) -> np.ndarray:
-    """Causal convolution with the unit-area kernel e^{-t/tau}/tau (sample recursion)."""
+    """Causal convolution with the unit-area kernel e^{-t/tau}/tau, as the first-order
+    recursion s[n] = a s[n-1] + (1 - a) x[n], a = exp(-dt/tau)."""
+    from scipy.signal import lfilter
     a = math.exp(-dt / tau)
-    out = np.empty_like(sig)
-    acc = 0.0
-    for n, v in enumerate(sig):
-        acc = a * acc + (1.0 - a) * v
-        out[n] = acc
-    return out
+    return lfilter([1.0 - a], [1.0, -a], np.asarray(sig, np.float64))
 
 
 def ellipse_phantom(rng, X, Y, fov: float, n_ellipses: int = 10) -> np.ndarray:
