@@ -109,3 +109,78 @@ def nrmse(x, x_ref) -> float:
 def default_lambda(prob, y, rel: float = 1e-3) -> float:
     """lam = rel * ||A^H y||_inf (the workload's fixed-lambda rule)."""
     return rel * float(np.max(np.abs(adjoint(prob, y))))
+
+
+def soft_vjp(w, gbar, tau):
+    """VJP of the complex soft-threshold S(w) = w max(0, 1 - tau/|w|) at w for cotangent gbar.
+
+    For |w| > tau the real Jacobian is (1 - tau/r) I + (tau/r^3) [a b]^T [a b] (w = a + ib,
+    r = |w|), symmetric, so wbar = (1 - tau/r) gbar + (tau/r^3) w Re(conj(w) gbar); dS/dtau =
+    -w/r gives taubar = -Re(conj(gbar) w)/r.  For |w| <= tau both are zero.
+    Returns (wbar, taubar summed over all entries)."""
+    w = np.asarray(w, np.complex128)
+    g = np.asarray(gbar, np.complex128)
+    r = np.abs(w)
+    act = r > tau
+    rs = np.where(act, r, 1.0)
+    wbar = np.where(act, (1.0 - tau / rs) * g + (tau / rs ** 3) * w * np.real(np.conj(w) * g), 0.0)
+    taubar = float(np.sum(np.where(act, -np.real(np.conj(g) * w) / rs, 0.0)))
+    return wbar, taubar
+
+
+def fista_unrolled_grad(prob, y, lam, lipschitz, iters, name, levels, x0, xbar_K):
+    """Reverse-mode gradient through `iters` FISTA steps (x_0 -> x_iters), FP64.
+
+    Cotangent convention: for a real loss, gbar = dLoss/dRe + i dLoss/dIm.  Given the
+    cotangent xbar_K of x_iters, returns (x0bar complex [nr], lambar float, kbar [nl][nt])
+    with L_f held fixed.  Recursion (z_{k+1} = (1+b_k) x_k - b_k x_{k-1}, x_k = P(v_k),
+    v_k = z_k - (2/L) A^H (A z_k - y)):
+        xbar_k = (1+b_k) zbar_{k+1} - b_{k+1} zbar_{k+2}  (+ xbar_K at k = iters)
+        vbar_k = crop W^H S'^T W pad xbar_k,   lambar += taubar / L
+        zbar_k = vbar_k - (2/L) A^H A vbar_k
+        kbar  += -(2/L) Re[ d/dk <A vbar_k, A z_k> + d/dk <vbar_k, A^H r_k> ]   (r_k = A z_k - y)
+        x0bar  = zbar_1 - b_1 zbar_2
+    """
+    from . import adjoint_dk, forward_dk
+    ny, nx = prob["ny"], prob["nx"]
+    nr = nx * ny
+    y = np.asarray(y, np.complex128)
+    L = float(lipschitz)
+    tau = lam / L
+    shp = wv.padded_shape(ny, nx, levels)
+    mask = wv.detail_mask(shp, levels)
+    # forward pass with checkpoints z_k, x_k and the momentum weights b_k
+    x = [np.asarray(x0, np.complex128).reshape(nr)]
+    z = [None, x[0].copy()]
+    b = [0.0] * (iters + 3)
+    t = 1.0
+    for k in range(1, iters + 1):
+        v = z[k] - 2.0 * adjoint(prob, forward(prob, z[k]) - y) / L
+        x.append(wv.prox(v, ny, nx, name, levels, tau))
+        t_next = (1.0 + math.sqrt(1.0 + 4.0 * t * t)) / 2.0
+        b[k] = (t - 1.0) / t_next
+        t = t_next
+        z.append(x[k] + b[k] * (x[k] - x[k - 1]))
+    # backward pass
+    zbar = [None] * (iters + 3)
+    zbar[iters + 1] = np.zeros(nr, np.complex128)
+    zbar[iters + 2] = np.zeros(nr, np.complex128)
+    kbar = np.zeros(np.shape(prob["k"]))
+    lambar = 0.0
+    for k in range(iters, 0, -1):
+        xbar = (1.0 + b[k]) * zbar[k + 1] - b[k + 1] * zbar[k + 2]
+        if k == iters:
+            xbar = xbar + np.asarray(xbar_K, np.complex128).reshape(nr)
+        r = forward(prob, z[k]) - y
+        v = z[k] - 2.0 * adjoint(prob, r) / L
+        w = wv.dwt2(wv.pad(v.reshape(ny, nx), shp), name, levels)
+        gw = wv.dwt2(wv.pad(xbar.reshape(ny, nx), shp), name, levels)
+        wbar_d, taubar = soft_vjp(w[mask], gw[mask], tau)
+        gw[mask] = wbar_d
+        lambar += taubar / L
+        vbar = wv.idwt2(gw, name, levels)[:ny, :nx].reshape(nr)
+        u = forward(prob, vbar)
+        zbar[k] = vbar - 2.0 * adjoint(prob, u) / L
+        kbar += -(2.0 / L) * np.real(forward_dk(prob, z[k], u) + adjoint_dk(prob, r, vbar))
+    x0bar = zbar[1] - b[1] * zbar[2]
+    return x0bar, lambar, kbar
