@@ -174,6 +174,36 @@ AEXP_API int cs_recon_batched(const aexp_problem *probs, int nprob, const void *
                               void *ws, size_t ws_bytes, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Differentiation through unrolled FISTA.  Sec. 5 names unrolled CS as future work; these
+ * two calls give one FISTA step of Eq. (1) with its state, and the step's vector-Jacobian
+ * product, so that a caller can unroll K steps with per-step checkpoints (z_k) and
+ * back-propagate to the start image, lambda and every k_l(t) (L_f held fixed).
+ * Cotangents follow the real-loss convention dLoss/dRe + i dLoss/dIm.
+ * --------------------------------------------------------------------------- */
+
+/* Bytes of workspace for aexp_fista_step / aexp_fista_step_vjp (includes the operator
+ * workspace, which must have been prepared with aexp_prepare for prob and opts->precision). */
+AEXP_API int aexp_unroll_workspace_size(const aexp_problem *prob, const aexp_recon_opts *opts, size_t *bytes);
+
+/* One step: v = z - (2/L) A^H (A z - y), x_out = crop W^H soft(W pad v, lambda/L),
+ * z_out = x_out + beta (x_out - x_prev).  y: [nc][nt]; z, x_prev, x_out, z_out: [nr]
+ * complex64 (x_out and z_out must not alias the inputs).  Uses opts->wavelet and levels. */
+AEXP_API int aexp_fista_step(const aexp_problem *prob, const aexp_recon_opts *opts, const void *y, float lambda,
+                             double lipschitz, const void *z, const void *x_prev, double beta, void *x_out,
+                             void *z_out, void *ws, size_t ws_bytes, void *stream);
+
+/* VJP of step k given its checkpoint z = z_k, b_k = beta, b_{k+1} = beta_next and the
+ * cotangents zbar_next = zbar_{k+1}, zbar_next2 = zbar_{k+2} (NULL = 0) and xbar_in (extra
+ * cotangent of x_k, NULL = 0):  xbar_k = (1+b_k) zbar_{k+1} - b_{k+1} zbar_{k+2} + xbar_in,
+ * zbar_out = zbar_k = (I - (2/L) A^H A) crop W^H S'^T W pad xbar_k.  Accumulates (+=)
+ * kbar [nl][nt] (float, device, may be NULL) and *lambar (double, device, may be NULL).
+ * The start image's cotangent is zbar_1 (b_1 = 0). */
+AEXP_API int aexp_fista_step_vjp(const aexp_problem *prob, const aexp_recon_opts *opts, const void *y, float lambda,
+                                 double lipschitz, const void *z, double beta, double beta_next, const void *xbar_in,
+                                 const void *zbar_next, const void *zbar_next2, void *zbar_out, float *kbar,
+                                 double *lambar, void *ws, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Wavelet step on its own (Eq. 1 regulariser): out = crop(W^H soft(W pad(in), tau))
  * --------------------------------------------------------------------------- */
 

@@ -68,6 +68,11 @@ SIGNATURES = [
     ("aexp_batch_workspace_size", _I, [_PROB, _I, _OPTS, ctypes.POINTER(_SZ)]),
     ("cs_recon_batched", _I, [_PROB, _I, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_float), _I, _OPTS,
                               ctypes.POINTER(_P), _P, _P, _SZ, _P]),
+    ("aexp_unroll_workspace_size", _I, [_PROB, _OPTS, ctypes.POINTER(_SZ)]),
+    ("aexp_fista_step", _I, [_PROB, _OPTS, _P, ctypes.c_float, ctypes.c_double, _P, _P, ctypes.c_double, _P, _P, _P,
+                             _SZ, _P]),
+    ("aexp_fista_step_vjp", _I, [_PROB, _OPTS, _P, ctypes.c_float, ctypes.c_double, _P, ctypes.c_double,
+                                 ctypes.c_double, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     ("aexp_wavelet_workspace_size", _I, [_I, _I, _I, _I, ctypes.POINTER(_SZ)]),
     ("aexp_wavelet_prox", _I, [_I, _I, _I, _I, ctypes.c_float, _P, _P, _P, _SZ, _P]),
     ("aexp_wavelet_forward", _I, [_I, _I, _I, _I, _P, _P, _P, _SZ, _P]),

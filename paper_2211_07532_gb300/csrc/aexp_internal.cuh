@@ -80,7 +80,7 @@ struct OpLayout {
     int adj_mr, adj_vblocks, adj_splits, adj_t_per_split;
     // byte offsets into the workspace
     size_t off_hdr, off_khi_l, off_klo_l, off_khi_t, off_h0, off_dh, off_f0, off_S, off_b,
-        off_fpart, off_yt, off_apart, off_ypk, off_desc;
+        off_fpart, off_yt, off_apart, off_ypk, off_desc, off_hp;
     int fwd_items, adj_items;  // persistent tensor-core work items
     size_t bytes;
 };
@@ -94,8 +94,11 @@ struct WaveLayout {
 
 struct RecLayout {
     OpLayout op;
-    WaveLayout wv;               // offsets relative to off_wave
+    WaveLayout wv;               // offsets relative to off_wave (and off_wave2)
     size_t off_wave, off_ymeas, off_xa, off_xb, off_z, off_v, off_w;
+    // differentiation buffers (with_grad only)
+    size_t off_rk, off_xbar, off_vbar, off_wave2, off_zq, off_gq, off_gpart;
+    int grad_splits, grad_tiles_per_split;
     size_t bytes;
 };
 
@@ -118,7 +121,8 @@ inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 // SM-count target so that large batches use whole-problem items and few partial sums).
 int op_layout(const aexp_problem *p, int precision, OpLayout *L, int tc_target_items = 152 * 8);
 int wave_layout(int nx, int ny, int wavelet, int levels, WaveLayout *W);
-int rec_layout(const aexp_problem *p, const aexp_recon_opts *o, RecLayout *R, int tc_target_items = 152 * 8);
+int rec_layout(const aexp_problem *p, const aexp_recon_opts *o, RecLayout *R, int tc_target_items = 152 * 8,
+               int with_grad = 0);
 
 // Launchers (all asynchronous on `st`; return cudaError_t of the launch).
 cudaError_t op_prepare(const aexp_problem *p, const OpLayout &L, char *ws, cudaStream_t st);
@@ -197,6 +201,14 @@ cudaError_t recon_issue(const aexp_problem *p, const RecLayout &R, const aexp_re
 
 // Record a CUDA error for aexp_last_cuda_error() (capi.cu).
 void aexp_set_last_cuda_error(int e);
+
+// Differentiation through unrolled FISTA (grad.cu).
+cudaError_t unroll_step(const RecLayout &R, const float2 *y, float lam, double lipschitz, const float2 *z,
+                        const float2 *x_prev, double beta, float2 *x_out, float2 *z_out, char *ws, cudaStream_t st);
+cudaError_t unroll_step_vjp(const RecLayout &R, const float2 *y, float lam, double lipschitz, const float2 *z,
+                            double beta, double beta_next, const float2 *xbar_in, const float2 *zbar_next,
+                            const float2 *zbar_next2, float2 *zbar_out, float *kbar, double *lambar, char *ws,
+                            cudaStream_t st);
 
 // Error flag writers used by the kernels.
 __device__ __forceinline__ void set_status(int *status, int code) {

@@ -379,6 +379,60 @@ int aexp_power_lipschitz(const aexp_problem *prob, int precision, const void *v0
     return AEXP_OK;
 }
 
+int aexp_unroll_workspace_size(const aexp_problem *prob, const aexp_recon_opts *opts, size_t *bytes) {
+    int rc = check_problem(prob);
+    if (rc) return rc;
+    if ((rc = check_opts(opts))) return rc;
+    if (!bytes) return AEXP_ERR_INVALID_ARG;
+    RecLayout R;
+    rec_layout(prob, opts, &R, 152 * 8, 1);
+    *bytes = R.bytes;
+    return AEXP_OK;
+}
+
+static int unroll_common(const aexp_problem *prob, const aexp_recon_opts *opts, const void *y, double lipschitz,
+                         void *ws, size_t ws_bytes, RecLayout *R) {
+    int rc = check_problem(prob);
+    if (rc) return rc;
+    if ((rc = check_opts(opts))) return rc;
+    if (!y || !(lipschitz > 0.0)) return AEXP_ERR_INVALID_ARG;
+    if (!aligned(y, 8)) return AEXP_ERR_MISALIGNED;
+    rec_layout(prob, opts, R, 152 * 8, 1);
+    if ((rc = check_ws(ws, ws_bytes, R->bytes))) return rc;
+    if (!is_prepared(ws, prob, opts->precision)) return AEXP_ERR_NOT_PREPARED;
+    return AEXP_OK;
+}
+
+int aexp_fista_step(const aexp_problem *prob, const aexp_recon_opts *opts, const void *y, float lambda,
+                    double lipschitz, const void *z, const void *x_prev, double beta, void *x_out, void *z_out,
+                    void *ws, size_t ws_bytes, void *stream) {
+    RecLayout R;
+    int rc = unroll_common(prob, opts, y, lipschitz, ws, ws_bytes, &R);
+    if (rc) return rc;
+    if (!z || !x_prev || !x_out || !z_out || !(lambda >= 0.f)) return AEXP_ERR_INVALID_ARG;
+    if (!aligned(z, 8) || !aligned(x_prev, 8) || !aligned(x_out, 8) || !aligned(z_out, 8)) return AEXP_ERR_MISALIGNED;
+    cudaError_t e = unroll_step(R, (const float2 *)y, lambda, lipschitz, (const float2 *)z, (const float2 *)x_prev,
+                                beta, (float2 *)x_out, (float2 *)z_out, (char *)ws, (cudaStream_t)stream);
+    return e == cudaSuccess ? AEXP_OK : cuda_fail(e);
+}
+
+int aexp_fista_step_vjp(const aexp_problem *prob, const aexp_recon_opts *opts, const void *y, float lambda,
+                        double lipschitz, const void *z, double beta, double beta_next, const void *xbar_in,
+                        const void *zbar_next, const void *zbar_next2, void *zbar_out, float *kbar, double *lambar,
+                        void *ws, size_t ws_bytes, void *stream) {
+    RecLayout R;
+    int rc = unroll_common(prob, opts, y, lipschitz, ws, ws_bytes, &R);
+    if (rc) return rc;
+    if (!z || !zbar_out || !(lambda >= 0.f)) return AEXP_ERR_INVALID_ARG;
+    if (!aligned(z, 8) || !aligned(xbar_in, 8) || !aligned(zbar_next, 8) || !aligned(zbar_next2, 8) ||
+        !aligned(zbar_out, 8) || !aligned(kbar, 4) || !aligned(lambar, 8))
+        return AEXP_ERR_MISALIGNED;
+    cudaError_t e = unroll_step_vjp(R, (const float2 *)y, lambda, lipschitz, (const float2 *)z, beta, beta_next,
+                                    (const float2 *)xbar_in, (const float2 *)zbar_next, (const float2 *)zbar_next2,
+                                    (float2 *)zbar_out, kbar, lambar, (char *)ws, (cudaStream_t)stream);
+    return e == cudaSuccess ? AEXP_OK : cuda_fail(e);
+}
+
 int aexp_wavelet_workspace_size(int nx, int ny, int wavelet, int levels, size_t *bytes) {
     if (nx < 1 || ny < 1 || levels < 1 || levels > 12 || !bytes) return AEXP_ERR_INVALID_ARG;
     if (wavelet != AEXP_WAVELET_HAAR && wavelet != AEXP_WAVELET_DB4) return AEXP_ERR_INVALID_ARG;

@@ -92,6 +92,7 @@ int op_layout(const aexp_problem *p, int precision, OpLayout *L, int tc_target_i
     o.off_apart = take(sizeof(float2) * (size_t)o.adj_splits * o.nr_pad);
     o.off_ypk = take(precision == AEXP_FP32 ? 0 : sizeof(float2) * (size_t)o.ntp * o.CB);
     o.off_desc = take(sizeof(ProbDesc));
+    o.off_hp = take(sizeof(float) * (size_t)o.LP * o.nr_pad);
     o.fwd_items = o.fwd_tblocks * o.fwd_splits;
     o.adj_items = o.adj_vblocks * o.adj_splits;
     o.bytes = off;
@@ -122,7 +123,8 @@ int wave_layout(int nx, int ny, int wavelet, int levels, WaveLayout *W) {
     return AEXP_OK;
 }
 
-int rec_layout(const aexp_problem *p, const aexp_recon_opts *opt, RecLayout *R, int tc_target_items) {
+int rec_layout(const aexp_problem *p, const aexp_recon_opts *opt, RecLayout *R, int tc_target_items,
+               int with_grad) {
     RecLayout r{};
     int rc = op_layout(p, opt->precision, &r.op, tc_target_items);
     if (rc) return rc;
@@ -143,6 +145,21 @@ int rec_layout(const aexp_problem *p, const aexp_recon_opts *opt, RecLayout *R, 
     r.off_v = take(sizeof(float2) * nr);
     r.off_w = take(sizeof(float2) * nr);
     r.off_wave = take(r.wv.bytes);
+    if (with_grad) {
+        const OpLayout &L = r.op;
+        const int tblocks = L.ntp / 128;
+        int s = std::max(cdiv(L.ntiles, 32), cdiv(152 * 8, tblocks));
+        s = std::min(s, L.ntiles);
+        r.grad_tiles_per_split = cdiv(L.ntiles, s);
+        r.grad_splits = cdiv(L.ntiles, r.grad_tiles_per_split);
+        r.off_rk = take(sizeof(float2) * (size_t)L.ntp * L.CB);
+        r.off_xbar = take(sizeof(float2) * nr);
+        r.off_vbar = take(sizeof(float2) * nr);
+        r.off_wave2 = take(r.wv.bytes);
+        r.off_zq = take(sizeof(float2) * (size_t)L.nr_pad);
+        r.off_gq = take(sizeof(float2) * (size_t)L.nr_pad);
+        r.off_gpart = take(sizeof(float) * (size_t)r.grad_splits * L.LP * L.ntp);
+    }
     r.bytes = off;
     *R = r;
     return AEXP_OK;

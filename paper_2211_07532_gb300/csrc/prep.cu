@@ -48,10 +48,11 @@ __global__ void prep_coef_kernel(const float *k, const float *tt, int nl, int ha
     khi_t[(size_t)t * LP + l] = hi;
 }
 
-// Reference voxel of each tile (centre, clipped into the image) and the FP32 basis
-// offsets dh[p][l] = h_l(r) - h_l(r0), zero for padded voxels.  One thread per (p, l).
+// Reference voxel of each tile (centre, clipped into the image), the FP32 basis offsets
+// dh[p][l] = h_l(r) - h_l(r0) and the basis values hp[p][l] = h_l(r) in tile order, zero for
+// padded voxels.  One thread per (p, l).
 __global__ void prep_tile_kernel(const float *h, const float *om, int nl, int has_b0, int nx, int ny, int ntx,
-                                 int ntiles, int LP, float *h0, float *dh) {
+                                 int ntiles, int LP, float *h0, float *dh, float *hp) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     int l = blockIdx.y;
     if (p >= ntiles * kTileVox) return;
@@ -62,9 +63,13 @@ __global__ void prep_tile_kernel(const float *h, const float *om, int nl, int ha
     int ry = min(ty * kTileSide + kTileSide / 2, ny - 1);
     int nr = nx * ny;
     float ref = term_basis(h, om, nl, has_b0, nr, l, ry * nx + rx);
-    float d = 0.f;
-    if (ix < nx && iy < ny) d = __fsub_rn(term_basis(h, om, nl, has_b0, nr, l, iy * nx + ix), ref);
+    float d = 0.f, hv = 0.f;
+    if (ix < nx && iy < ny) {
+        hv = term_basis(h, om, nl, has_b0, nr, l, iy * nx + ix);
+        d = __fsub_rn(hv, ref);
+    }
     dh[(size_t)p * LP + l] = d;
+    hp[(size_t)p * LP + l] = hv;  // basis values in tile order (gradient with respect to k)
     if (v == 0) h0[(size_t)tile * LP + l] = ref;
 }
 
@@ -153,7 +158,8 @@ cudaError_t op_prepare(const aexp_problem *p, const OpLayout &L, char *ws, cudaS
     prep_coef_kernel<<<dim3(cdiv(L.ntp, T), L.LP), T, 0, st>>>(p->k, p->t, L.nl, L.has_b0, L.nt, L.ntp, L.LP,
                                                               khi_l, klo_l, khi_t);
     prep_tile_kernel<<<dim3(cdiv(L.nr_pad, T), L.LP), T, 0, st>>>(p->h, p->omega, L.nl, L.has_b0, L.nx, L.ny,
-                                                                 L.ntx, L.ntiles, L.LP, h0, dh);
+                                                                 L.ntx, L.ntiles, L.LP, h0, dh,
+                                                                 (float *)(ws + L.off_hp));
     prep_f0_kernel<<<dim3(cdiv(L.ntp, T), L.ntiles), T, 0, st>>>(khi_l, klo_l, h0, L.nterms, L.ntp, L.LP, f0);
     size_t n = (size_t)L.nr_pad * L.CB;
     prep_coil_kernel<<<(unsigned)((n + T - 1) / T), T, 0, st>>>((const float2 *)p->S, L.nc, L.nx, L.ny, L.ntx,
