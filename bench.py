@@ -190,6 +190,31 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _kernel_ms(ax, torch, prob, x, y, precision, flush, stream, reps=10):
+    """One operator application each way (packing/coil weighting + contraction + partial-sum
+    reduction), CUDA events on the launching stream."""
+    ws_k = ax.workspace(prob, precision)
+    ax.prepare(prob, ws_k, precision)
+    yo = torch.empty_like(y)
+    xo = torch.empty_like(x)
+    kern = {}
+    for name, fn in (("a_exp_forward", lambda: ax.a_exp_forward(prob, x, ws_k, y=yo, precision=precision)),
+                     ("a_exp_adjoint", lambda: ax.a_exp_adjoint(prob, y, ws_k, x=xo, precision=precision))):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        kern[name] = float(np.mean(ts))
+    return kern
+
+
 def _run_ours(args, rank, world, local, dev):
     import torch
     import torch.distributed as dist
@@ -199,47 +224,47 @@ def _run_ours(args, rank, world, local, dev):
     import paper_2211_07532_gb300 as ax
     from paper_2211_07532_gb300 import synth
 
-    precision = {"fp32": ax.FP32, "bf16": ax.BF16_TC, "fp16x2": ax.FP16X2_TC}[args.form]
+    forms = {"fp32": ax.FP32, "bf16": ax.BF16_TC}
+    precision = forms[args.form]
     p = synth.slice_200(index=rank)           # each rank reconstructs its own slice (weak scaling)
     nr, nt, nc = p["nx"] * p["ny"], p["nt"], p["nc"]
     iters, levels, n_power = p["iters"], p["levels"], 30
     prob = ax.Problem.from_arrays(p, device=dev)
     x_gt = torch.as_tensor(p["x_gt"], device=dev)
 
-    # simulated data on the device through the library's own forward model (Sec. 2.2.2)
-    ws_op = ax.workspace(prob, precision)
-    ax.prepare(prob, ws_op, precision)
-    y0 = ax.a_exp_forward(prob, x_gt, ws_op, precision=precision)
+    # simulated data on the device through the library's own FP32 forward model (Sec. 2.2.2)
+    ws_op = ax.workspace(prob, ax.FP32)
+    ax.prepare(prob, ws_op, ax.FP32)
+    y0 = ax.a_exp_forward(prob, x_gt, ws_op)
     sigma = float(torch.sqrt(torch.mean(y0.abs() ** 2))) / p["snr"]
     y = (y0 + sigma * torch.as_tensor(p["noise"], device=dev)).contiguous()
-    lam = 1e-3 * float(ax.a_exp_adjoint(prob, y, ws_op, precision=precision).abs().max())
+    lam = 1e-3 * float(ax.a_exp_adjoint(prob, y, ws_op).abs().max())
     del ws_op
 
-    opts = ax.recon_opts(precision=precision, wavelet="db4", levels=levels, n_power=n_power)
-    ws = ax.recon_workspace(prob, opts)
-    x_out = torch.empty(nr, dtype=torch.complex64, device=dev)
-    L_out = torch.empty(1, dtype=torch.float64, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
+    applications = 2 * iters + 2 * n_power + 1
+    vsc_per_step = applications * nr * nt * nc
+    x_out = torch.empty(nr, dtype=torch.complex64, device=dev)
+    L_out = torch.empty(1, dtype=torch.float64, device=dev)
 
-    def step():
-        ax.cs_recon(prob, y, lam, iters, opts=opts, ws=ws, x_out=x_out, lipschitz_out=L_out)
+    def recon_ws(prec):
+        o = ax.recon_opts(precision=prec, wavelet="db4", levels=levels, n_power=n_power)
+        return o, ax.recon_workspace(prob, o)
 
+    opts, ws = recon_ws(precision)
     for _ in range(args.warmup):
-        step()
+        ax.cs_recon(prob, y, lam, iters, opts=opts, ws=ws, x_out=x_out, lipschitz_out=L_out)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-
-    applications = 2 * iters + 2 * n_power + 1
-    vsc_per_step = applications * nr * nt * nc
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         for i in range(args.steps):
             flush.zero_()                     # L2 flushed between timed iterations (outside the events)
             ev[i][0].record(stream)
-            step()
+            ax.cs_recon(prob, y, lam, iters, opts=opts, ws=ws, x_out=x_out, lipschitz_out=L_out)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -257,10 +282,10 @@ def _run_ours(args, rank, world, local, dev):
     y_host = y.cpu().pin_memory()
     x_host = torch.empty(nr, dtype=torch.complex64).pin_memory()
     y_dev = torch.empty_like(y)
-    e2e_ms = []
     y_dev.copy_(y_host)
     ax.cs_recon(prob, y_dev, lam, iters, opts=opts, ws=ws, x_out=x_out, lipschitz_out=L_out)  # capture, untimed
     torch.cuda.synchronize()
+    e2e_ms = []
     for i in range(max(1, args.steps)):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -278,26 +303,7 @@ def _run_ours(args, rank, world, local, dev):
         e2e_total = float(t.item())
     e2e_value = world * vsc_per_step * len(e2e_ms) / (e2e_total / 1e3) / 1e9
 
-    # dominant kernels timed on their own stream with CUDA events: one operator application
-    # (coil weighting + contraction + partial-sum reduction), forward and adjoint
-    ws_k = ax.workspace(prob, precision)
-    ax.prepare(prob, ws_k, precision)
-    kern = {}
-    for name, fn in (("a_exp_forward", lambda: ax.a_exp_forward(prob, x_gt, ws_k, y=y0, precision=precision)),
-                     ("a_exp_adjoint", lambda: ax.a_exp_adjoint(prob, y, ws_k, x=x_out, precision=precision))):
-        for _ in range(3):
-            fn()
-        reps = 10
-        ts = []
-        for _ in range(reps):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            fn()
-            b.record(stream)
-            b.synchronize()
-            ts.append(a.elapsed_time(b))
-        kern[name] = float(np.mean(ts))
+    kern = _kernel_ms(ax, torch, prob, x_gt, y, precision, flush, stream)
     dom = max(kern, key=kern.get)
     clocks = clk.summary()
     nterms = p["nl"] + 1
@@ -316,6 +322,38 @@ def _run_ours(args, rank, world, local, dev):
         if current == rec.get("sha256_16"):           # counters only valid for the profiled source
             traffic = rec.get(f"{args.form}:{dom}")
 
+    # the other form of the same workload, same timing rules (the metric compares TC and FP32)
+    other = "bf16" if args.form == "fp32" else "fp32"
+    o_opts, o_ws = recon_ws(forms[other])
+    o_ms = []
+    for _ in range(args.warmup):
+        ax.cs_recon(prob, y, lam, iters, opts=o_opts, ws=o_ws, x_out=x_out, lipschitz_out=L_out)
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ax.cs_recon(prob, y, lam, iters, opts=o_opts, ws=o_ws, x_out=x_out, lipschitz_out=L_out)
+        b.record(stream)
+        b.synchronize()
+        o_ms.append(a.elapsed_time(b))
+    o_nrmse = float(torch.linalg.vector_norm(x_out - x_gt) / torch.linalg.vector_norm(x_gt))
+    o_kern = _kernel_ms(ax, torch, prob, x_gt, y, forms[other], flush, stream)
+    o_step = float(np.mean(o_ms))
+    bf16_peak = measured_peaks().get("bf16_tflops", 1977.2)
+    contraction_flops = nr * nt * 8.0 * nc
+    comparison = {"form": other, "s_per_slice": o_step / 1e3,
+                  "value": world * vsc_per_step / (o_step / 1e3) / 1e9, "unit": UNIT,
+                  "nrmse_vs_phantom": o_nrmse, "device_status": ax.read_status(o_ws), "kernels_ms": o_kern,
+                  "speedup_vs_primary": ms_per_step / o_step}
+    if other == "bf16":
+        o_dom = max(o_kern, key=o_kern.get)
+        comparison["tensor_contraction"] = {
+            "achieved": contraction_flops / (o_kern[o_dom] / 1e3) / 1e12, "unit": "TFLOP/s",
+            "peak": bf16_peak, "frac": contraction_flops / (o_kern[o_dom] / 1e3) / 1e12 / bf16_peak,
+            "note": "tensor pipe carries the 8C flops per (sample, voxel); the bound is the CUDA-core "
+                    "generation of the BF16 encoding tile (phase + sincos)"}
+
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -328,7 +366,7 @@ def _run_ours(args, rank, world, local, dev):
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp16x2": "f16x2"}[args.form],
+            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16"}[args.form],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "form": args.form, "nx": p["nx"], "nt": nt, "nc": nc,
                        "terms": nterms, "fista_iters": iters, "power_iters": n_power,
@@ -339,17 +377,144 @@ def _run_ours(args, rank, world, local, dev):
             "device_status": status,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(y.numel() * 8),
                     "d2h_bytes_per_step": int(nr * 8), "s_per_slice": e2e_total / len(e2e_ms) / 1e3},
-            "gpu_launches": launches_per_recon(levels, iters, n_power) * args.steps,
+            "gpu_launches": launches_per_recon(levels, iters, n_power) * args.steps if args.form == "fp32" else None,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": dom,
                          "kernel_ms": kern[dom],
                          "peak_basis": f"FP32 FMA pipe 152 SM x 128 lanes x 2 flop at {sm_mhz_peak:.0f} MHz "
                                        "(sm_max_mhz of MEASURED_PEAKS.json)"},
             "kernels_ms": kern,
+            "comparison": comparison,
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
         print(json.dumps(out))
+
+
+def run_ragged(args):
+    """372 ragged problems (148/170/200 px x 31 diffusion volumes x 4 slices, 32 coils, 3rd-order
+    field + B0, each volume with its own coefficients), BF16 tensor cores, one persistent launch
+    per operator application, whole 30-power + 50-FISTA solve captured in one CUDA graph."""
+    import torch
+    from paper_2211_07532_gb300 import build as _b
+    _b.build()
+    import paper_2211_07532_gb300 as ax
+    from paper_2211_07532_gb300 import synth
+
+    dev = torch.device("cuda")
+    side = torch.cuda.Stream()
+    nvol, nsl = args.volumes, 4
+    t0 = time.time()
+    probs, ys, lams, gts, vsc = [], [], [], [], 0
+    with torch.cuda.stream(side):
+        ws_sim = None
+        for res in range(3):
+            for sl in range(nsl):
+                for vol in range(nvol):
+                    p = synth.ragged_problem(res, vol, sl)
+                    pr = ax.Problem.from_arrays(p, device=dev)
+                    need = ax.workspace_size(pr)
+                    if ws_sim is None or ws_sim.numel() < need:
+                        ws_sim = torch.empty(need, dtype=torch.uint8, device=dev)
+                    ax.prepare(pr, ws_sim)
+                    xg = torch.as_tensor(p["x_gt"], device=dev)
+                    y0 = ax.a_exp_forward(pr, xg, ws_sim)
+                    sigma = float(torch.sqrt(torch.mean(y0.abs() ** 2))) / p["snr"]
+                    y = (y0 + sigma * torch.as_tensor(p["noise"], device=dev)).contiguous()
+                    lams.append(1e-3 * float(ax.a_exp_adjoint(pr, y, ws_sim).abs().max()))
+                    probs.append(pr)
+                    ys.append(y)
+                    gts.append(xg)
+                    vsc += pr.nr * pr.nt * pr.nc
+        del ws_sim
+        gen_s = time.time() - t0
+        iters, n_power, levels = 50, 30, 4
+        opts = ax.recon_opts(precision=ax.BF16_TC, wavelet="db4", levels=levels, n_power=n_power)
+        ws = torch.empty(ax.batch_workspace_size(probs, opts), dtype=torch.uint8, device=dev)
+        xs = [torch.empty(pr.nr, dtype=torch.complex64, device=dev) for pr in probs]
+        L = torch.empty(len(probs), dtype=torch.float64, device=dev)
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        for _ in range(max(1, args.warmup)):
+            ax.cs_recon_batched(probs, ys, lams, iters, opts=opts, ws=ws, x_outs=xs, lipschitz_out=L)
+        torch.cuda.synchronize()
+        ms = []
+        with ClockSampler(0) as clk:
+            for _ in range(args.steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                ax.cs_recon_batched(probs, ys, lams, iters, opts=opts, ws=ws, x_outs=xs, lipschitz_out=L)
+                b.record()
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+        status = ax.read_status(ws)
+        nrmse = [float(torch.linalg.vector_norm(x - g) / torch.linalg.vector_norm(g)) for x, g in zip(xs, gts)]
+    step = float(np.mean(ms))
+    applications = 2 * iters + 2 * n_power + 1
+    print(json.dumps({
+        "metric": METRIC, "workload": "ragged", "value": applications * vsc / (step / 1e3) / 1e9, "unit": UNIT,
+        "n_gpus": 1, "steps": args.steps, "warmup": max(1, args.warmup), "ms_per_step": step,
+        "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"ragged batch: 3 resolutions (148/170/200) x {nvol} volumes x {nsl} slices = "
+                               f"{len(probs)} problems, 32 coils, 3rd-order SH + B0, db4 J=4, 50 FISTA + 30 power",
+                   "problems": len(probs), "vsc_per_application": vsc, "applications_per_step": applications,
+                   "workspace_gb": ws.numel() / 1e9, "generation_s": gen_s},
+        "s_per_slice": step / 1e3 / len(probs), "nrmse_vs_phantom_median": float(np.median(nrmse)),
+        "device_status": status, "clocks": clk.summary()}))
+
+
+def run_diff(args):
+    """Unrolled-FISTA gradients: 170x170, 16 coils, 12k samples, 2nd order + B0, 10 iterations,
+    batch of 8 slices; forward unroll and backward (x0, lambda, k) timed with CUDA events."""
+    import torch
+    from paper_2211_07532_gb300 import build as _b
+    _b.build()
+    import paper_2211_07532_gb300 as ax
+    from paper_2211_07532_gb300 import synth
+    from paper_2211_07532_gb300.autograd import unrolled_fista
+
+    iters, B = 10, 8
+    slices = []
+    for i in range(B):
+        p = synth.diff_170(index=i)
+        prob = ax.Problem.from_arrays(p)
+        ws = ax.workspace(prob)
+        ax.prepare(prob, ws)
+        xg = torch.as_tensor(p["x_gt"], device="cuda")
+        y0 = ax.a_exp_forward(prob, xg, ws)
+        y = (y0 + float(torch.sqrt(torch.mean(y0.abs() ** 2))) / p["snr"]
+             * torch.as_tensor(p["noise"], device="cuda")).contiguous()
+        _, L = ax.cs_recon(prob, y, 0.0, 0, n_power=30)
+        lam = 1e-3 * float(ax.a_exp_adjoint(prob, y, ws).abs().max())
+        slices.append((p, y, xg, float(L.cpu()[0]), lam))
+
+    def run():
+        x0s = [torch.zeros(170 * 170, dtype=torch.complex64, device="cuda").requires_grad_(True) for _ in slices]
+        lam_s = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+        ks = [torch.as_tensor(s[0]["k"], device="cuda").requires_grad_(True) for s in slices]
+        a, m, b = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record()
+        loss = 0.0
+        for (p, y, xg, L, lam), x0, k in zip(slices, x0s, ks):
+            xK = unrolled_fista(p, y, x0, lam_s * lam, k, iters, L, wavelet="db4", levels=4)
+            loss = loss + torch.mean(torch.abs(xK - xg) ** 2)
+        m.record()
+        (loss / B).backward()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(m), m.elapsed_time(b)
+
+    for _ in range(max(1, args.warmup)):
+        run()
+    f, bw = zip(*[run() for _ in range(args.steps)])
+    vsc = 170 * 170 * 12000 * 16
+    print(json.dumps({
+        "workload": "diff", "metric": "unrolled FISTA forward + backward time", "unit": "ms", "dtype": "f32",
+        "config": {"workload": "170x170, 16 coils, 12k samples, 2nd-order SH + B0, 10 unrolled FISTA, batch of 8",
+                   "applications_forward": B * iters * 2, "applications_backward": B * iters * 4 + B * iters * 2},
+        "forward_ms": float(np.mean(f)), "backward_ms": float(np.mean(bw)),
+        "backward_over_forward": float(np.mean(bw) / np.mean(f)),
+        "forward_gvsc_per_s": B * iters * 2 * vsc / (np.mean(f) / 1e3) / 1e9}))
 
 
 def run_op_only(args):
@@ -360,7 +525,7 @@ def run_op_only(args):
     import paper_2211_07532_gb300 as ax
     from paper_2211_07532_gb300 import synth
 
-    precision = {"fp32": ax.FP32, "bf16": ax.BF16_TC, "fp16x2": ax.FP16X2_TC}[args.form]
+    precision = {"fp32": ax.FP32, "bf16": ax.BF16_TC}[args.form]
     p = synth.slice_200()
     prob = ax.Problem.from_arrays(p)
     ws = ax.workspace(prob, precision)
@@ -396,16 +561,24 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--form", choices=["fp32", "bf16", "fp16x2"], default="fp32")
+    ap.add_argument("--form", choices=["fp32", "bf16"], default="fp32")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", choices=["recon", "op"], default="recon",
                     help="op: only prepare + `--reps` forward/adjoint applications (profiling target)")
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--workload", choices=["slice", "ragged", "diff"], default="slice",
+                    help="slice: the 200x200 paper-scale slice (default); ragged: the 372-problem batch; "
+                         "diff: unrolled-FISTA gradients")
+    ap.add_argument("--volumes", type=int, default=31, help="diffusion volumes per slice (ragged workload)")
     args = ap.parse_args()
     if args.mode == "op":
         run_op_only(args)
+    elif args.workload == "ragged" and args.impl == "ours":
+        run_ragged(args)
+    elif args.workload == "diff" and args.impl == "ours":
+        run_diff(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
