@@ -115,11 +115,15 @@ def fp32_alu_peak_tflops(sm_mhz: float) -> float:
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def launches_per_recon(levels: int, iters: int, n_power: int) -> int:
+def launches_per_recon(levels: int, iters: int, n_power: int, form: str = "fp32") -> int:
     """Kernel launches issued by cs_recon (mirrors the host sequence in recon.cu)."""
-    prep = 4 + 1                      # coefficients, tiles, reference phases, coil maps; y transpose
-    power = 2 + 2 + n_power * 7 + 1   # A^H y; initial norm+scale; per iteration A^H A (5) + dot + scale; finalize
-    fista = iters * (5 + 2 * levels)  # coil weight, fwd, fwd reduce, adj, adj reduce; J fwd + J inv levels
+    # one application: FP32 forward = coil weight + contraction + reduce, adjoint = contraction
+    # + reduce; tensor-core forms pack + persistent contraction + reduce each way, the FP16
+    # hi+lo form two more (max reset + max reduction) per packing
+    fwd, adj = {"fp32": (3, 2), "bf16": (3, 3), "fp16x2": (5, 5)}[form]
+    prep = 4 + 1 + (0 if form == "fp32" else 2)  # coef, tiles, phases, coils; y transpose; descriptor + items
+    power = adj + 2 + n_power * (fwd + adj + 2) + 1  # A^H y; norm + scale; per iteration A^H A + dot + scale; finalize
+    fista = iters * (fwd + adj + 2 * levels)          # A^H (A z - y) + J analysis + J synthesis levels
     return prep + power + fista
 
 
@@ -224,7 +228,7 @@ def _run_ours(args, rank, world, local, dev):
     import paper_2211_07532_gb300 as ax
     from paper_2211_07532_gb300 import synth
 
-    forms = {"fp32": ax.FP32, "bf16": ax.BF16_TC}
+    forms = {"fp32": ax.FP32, "bf16": ax.BF16_TC, "fp16x2": ax.FP16X2_TC}
     precision = forms[args.form]
     p = synth.slice_200(index=rank)           # each rank reconstructs its own slice (weak scaling)
     nr, nt, nc = p["nx"] * p["ny"], p["nt"], p["nc"]
@@ -322,37 +326,41 @@ def _run_ours(args, rank, world, local, dev):
         if current == rec.get("sha256_16"):           # counters only valid for the profiled source
             traffic = rec.get(f"{args.form}:{dom}")
 
-    # the other form of the same workload, same timing rules (the metric compares TC and FP32)
-    other = "bf16" if args.form == "fp32" else "fp32"
-    o_opts, o_ws = recon_ws(forms[other])
-    o_ms = []
-    for _ in range(args.warmup):
-        ax.cs_recon(prob, y, lam, iters, opts=o_opts, ws=o_ws, x_out=x_out, lipschitz_out=L_out)
-    torch.cuda.synchronize()
-    for i in range(args.steps):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        ax.cs_recon(prob, y, lam, iters, opts=o_opts, ws=o_ws, x_out=x_out, lipschitz_out=L_out)
-        b.record(stream)
-        b.synchronize()
-        o_ms.append(a.elapsed_time(b))
-    o_nrmse = float(torch.linalg.vector_norm(x_out - x_gt) / torch.linalg.vector_norm(x_gt))
-    o_kern = _kernel_ms(ax, torch, prob, x_gt, y, forms[other], flush, stream)
-    o_step = float(np.mean(o_ms))
+    # the other forms of the same workload, same timing rules (the metric compares TC and FP32)
     bf16_peak = measured_peaks().get("bf16_tflops", 1977.2)
     contraction_flops = nr * nt * 8.0 * nc
-    comparison = {"form": other, "s_per_slice": o_step / 1e3,
-                  "value": world * vsc_per_step / (o_step / 1e3) / 1e9, "unit": UNIT,
-                  "nrmse_vs_phantom": o_nrmse, "device_status": ax.read_status(o_ws), "kernels_ms": o_kern,
-                  "speedup_vs_primary": ms_per_step / o_step}
-    if other == "bf16":
-        o_dom = max(o_kern, key=o_kern.get)
-        comparison["tensor_contraction"] = {
-            "achieved": contraction_flops / (o_kern[o_dom] / 1e3) / 1e12, "unit": "TFLOP/s",
-            "peak": bf16_peak, "frac": contraction_flops / (o_kern[o_dom] / 1e3) / 1e12 / bf16_peak,
-            "note": "tensor pipe carries the 8C flops per (sample, voxel); the bound is the CUDA-core "
-                    "generation of the BF16 encoding tile (phase + sincos)"}
+    comparison = {}
+    for other in [f for f in forms if f != args.form]:
+        o_opts, o_ws = recon_ws(forms[other])
+        o_ms = []
+        for _ in range(args.warmup):
+            ax.cs_recon(prob, y, lam, iters, opts=o_opts, ws=o_ws, x_out=x_out, lipschitz_out=L_out)
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ax.cs_recon(prob, y, lam, iters, opts=o_opts, ws=o_ws, x_out=x_out, lipschitz_out=L_out)
+            b.record(stream)
+            b.synchronize()
+            o_ms.append(a.elapsed_time(b))
+        o_nrmse = float(torch.linalg.vector_norm(x_out - x_gt) / torch.linalg.vector_norm(x_gt))
+        o_kern = _kernel_ms(ax, torch, prob, x_gt, y, forms[other], flush, stream)
+        o_step = float(np.mean(o_ms))
+        c = {"s_per_slice": o_step / 1e3, "value": world * vsc_per_step / (o_step / 1e3) / 1e9, "unit": UNIT,
+             "nrmse_vs_phantom": o_nrmse, "device_status": ax.read_status(o_ws), "kernels_ms": o_kern,
+             "speedup_vs_primary": ms_per_step / o_step}
+        if other != "fp32":
+            o_dom = max(o_kern, key=o_kern.get)
+            passes = 3 if other == "fp16x2" else 1    # hi.hi + hi.lo + lo.hi MMA passes
+            ach = contraction_flops / (o_kern[o_dom] / 1e3) / 1e12
+            c["tensor_contraction"] = {
+                "achieved": ach, "unit": "TFLOP/s", "peak": bf16_peak, "frac": ach / bf16_peak,
+                "mma_passes": passes, "tensor_pipe_frac": passes * ach / bf16_peak,
+                "note": "algorithmic 8C flops per (sample, voxel) per application; the tensor pipe runs "
+                        "mma_passes x that; the bound is the CUDA-core generation of the encoding tile"}
+        comparison[other] = c
+        del o_ws
 
     if rank == 0:
         cpu = None
@@ -366,7 +374,7 @@ def _run_ours(args, rank, world, local, dev):
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16"}[args.form],
+            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp16x2": "f16x2"}[args.form],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "form": args.form, "nx": p["nx"], "nt": nt, "nc": nc,
                        "terms": nterms, "fista_iters": iters, "power_iters": n_power,
@@ -377,7 +385,7 @@ def _run_ours(args, rank, world, local, dev):
             "device_status": status,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(y.numel() * 8),
                     "d2h_bytes_per_step": int(nr * 8), "s_per_slice": e2e_total / len(e2e_ms) / 1e3},
-            "gpu_launches": launches_per_recon(levels, iters, n_power) * args.steps if args.form == "fp32" else None,
+            "gpu_launches": launches_per_recon(levels, iters, n_power, args.form) * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": dom,
                          "kernel_ms": kern[dom],
@@ -429,7 +437,9 @@ def run_ragged(args):
         del ws_sim
         gen_s = time.time() - t0
         iters, n_power, levels = 50, 30, 4
-        opts = ax.recon_opts(precision=ax.BF16_TC, wavelet="db4", levels=levels, n_power=n_power)
+        tc_form = args.form if args.form != "fp32" else "bf16"   # the batched path runs on the tensor cores
+        opts = ax.recon_opts(precision={"bf16": ax.BF16_TC, "fp16x2": ax.FP16X2_TC}[tc_form], wavelet="db4",
+                             levels=levels, n_power=n_power)
         ws = torch.empty(ax.batch_workspace_size(probs, opts), dtype=torch.uint8, device=dev)
         xs = [torch.empty(pr.nr, dtype=torch.complex64, device=dev) for pr in probs]
         L = torch.empty(len(probs), dtype=torch.float64, device=dev)
@@ -454,7 +464,7 @@ def run_ragged(args):
     print(json.dumps({
         "metric": METRIC, "workload": "ragged", "value": applications * vsc / (step / 1e3) / 1e9, "unit": UNIT,
         "n_gpus": 1, "steps": args.steps, "warmup": max(1, args.warmup), "ms_per_step": step,
-        "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+        "higher_is_better": True, "dtype": {"bf16": "bf16", "fp16x2": "f16x2"}[tc_form], "data": "synthetic",
         "config": {"workload": f"ragged batch: 3 resolutions (148/170/200) x {nvol} volumes x {nsl} slices = "
                                f"{len(probs)} problems, 32 coils, 3rd-order SH + B0, db4 J=4, 50 FISTA + 30 power",
                    "problems": len(probs), "vsc_per_application": vsc, "applications_per_step": applications,
@@ -525,7 +535,7 @@ def run_op_only(args):
     import paper_2211_07532_gb300 as ax
     from paper_2211_07532_gb300 import synth
 
-    precision = {"fp32": ax.FP32, "bf16": ax.BF16_TC}[args.form]
+    precision = {"fp32": ax.FP32, "bf16": ax.BF16_TC, "fp16x2": ax.FP16X2_TC}[args.form]
     p = synth.slice_200()
     prob = ax.Problem.from_arrays(p)
     ws = ax.workspace(prob, precision)
@@ -561,7 +571,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--form", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--form", choices=["fp32", "bf16", "fp16x2"], default="fp32")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -40,6 +40,10 @@ struct WsHeader {
     int counter[2];      // work-item counters of the persistent kernels (forward, adjoint)
     int item_off[4];     // single problem: {0, forward items} and {0, adjoint items}
     double scratch[2];
+    // FP16 hi+lo form: bit patterns of max |Re|, |Im| over the packed operand of the
+    // current application (forward S x, adjoint y); they fix the power-of-two scales
+    unsigned amax[2];
+    int pad1[2];
 };
 
 // Per-problem descriptor read by the persistent tensor-core kernels and by the batched
@@ -155,10 +159,11 @@ cudaError_t op_adjoint_tc(const OpLayout &L, const float2 *yt, char *ws, cudaStr
 // Batched tensor-core applications over nprob descriptors (uniform CB and LP): pack the
 // image vec[src] (forward) or rt (adjoint), then one persistent launch over all work items.
 // item_off: device prefix offsets [nprob + 1]; counter: device int reset by these calls.
-cudaError_t batch_forward_tc(int CB, int LP, const ProbDesc *pd, int nprob, int max_pack_blocks, int src,
-                             const int *item_off, int total_items, int *counter, cudaStream_t st);
-cudaError_t batch_adjoint_tc(int CB, int LP, const ProbDesc *pd, int nprob, int max_pack_blocks, int src,
-                             const int *item_off, int total_items, int *counter, cudaStream_t st);
+// precision: AEXP_BF16_TC or AEXP_FP16X2_TC.
+cudaError_t batch_forward_tc(int precision, int CB, int LP, const ProbDesc *pd, int nprob, int max_pack_blocks,
+                             int src, const int *item_off, int total_items, int *counter, cudaStream_t st);
+cudaError_t batch_adjoint_tc(int precision, int CB, int LP, const ProbDesc *pd, int nprob, int max_pack_blocks,
+                             int src, const int *item_off, int total_items, int *counter, cudaStream_t st);
 int fwd_pack_blocks(int ntiles, int CB);
 int adj_pack_blocks(int ntp, int CB);
 cudaError_t op_forward_reduce_planar_public(const OpLayout &L, char *ws, float2 *y, cudaStream_t st);

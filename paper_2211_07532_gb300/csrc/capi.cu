@@ -43,7 +43,6 @@ int check_problem(const aexp_problem *p) {
 int check_precision(int precision) {
     if (precision != AEXP_FP32 && precision != AEXP_BF16_TC && precision != AEXP_FP16X2_TC)
         return AEXP_ERR_INVALID_ARG;
-    if (precision == AEXP_FP16X2_TC) return AEXP_ERR_UNSUPPORTED;
     return AEXP_OK;
 }
 

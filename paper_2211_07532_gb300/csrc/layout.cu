@@ -86,11 +86,13 @@ int op_layout(const aexp_problem *p, int precision, OpLayout *L, int tc_target_i
     o.off_dh = take(sizeof(float) * o.LP * o.nr_pad);
     o.off_f0 = take(sizeof(float) * (size_t)o.ntiles * o.ntp);
     o.off_S = take(sizeof(float2) * (size_t)o.CB * o.nr_pad);
-    o.off_b = take(sizeof(float2) * (size_t)o.CB * o.nr_pad);
+    // FP32: b = S x in tile order; tensor-core forms: the packed B operand (FP16 hi+lo: two images)
+    const size_t npk = precision == AEXP_FP16X2_TC ? 2 : 1;
+    o.off_b = take(npk * sizeof(float2) * (size_t)o.CB * o.nr_pad);
     o.off_fpart = take(sizeof(float2) * (size_t)o.fwd_splits * o.ntp * o.CB);
     o.off_yt = take(sizeof(float2) * (size_t)o.ntp * o.CB);
     o.off_apart = take(sizeof(float2) * (size_t)o.adj_splits * o.nr_pad);
-    o.off_ypk = take(precision == AEXP_FP32 ? 0 : sizeof(float2) * (size_t)o.ntp * o.CB);
+    o.off_ypk = take(precision == AEXP_FP32 ? 0 : npk * sizeof(float2) * (size_t)o.ntp * o.CB);
     o.off_desc = take(sizeof(ProbDesc));
     o.off_hp = take(sizeof(float) * (size_t)o.LP * o.nr_pad);
     o.fwd_items = o.fwd_tblocks * o.fwd_splits;

@@ -1,4 +1,5 @@
-// A_exp and A_exp^H on the tcgen05 tensor cores (BF16 encoding tile, FP32 accumulation).
+// A_exp and A_exp^H on the tcgen05 tensor cores: BF16 encoding tile, or the FP16 hi+lo
+// split of both operands; FP32 accumulation in TMEM.
 //
 // The complex contraction is embedded in a real GEMM whose A operand is generated on
 // the fly and never leaves shared memory:
@@ -23,10 +24,27 @@
 // [-1/2, 1/2] turns, take one MUFU sincos, round to BF16 and store 16-byte chunks straight
 // into the 128B-swizzled K-major layout; each thread owns 2 rows x 8 columns.  The producer
 // warp brings the packed B tile (plus basis offsets or coefficient rows and reference
-// phases) with bulk TMA copies up to kNB - 1 tiles ahead, issues the MMAs from one thread,
+// phases) with bulk TMA copies up to NB - 1 tiles ahead, issues the MMAs from one thread,
 // and two tcgen05.commit per tile release the A and B stages.  Every wait is bounded; on a
 // timeout the CTA records AEXP_ERR_DEVICE_TIMEOUT, drains its MMAs, frees TMEM and exits.
+//
+// FP16 hi+lo form (HL): every operand value v is split into v_hi = fp16(v) and
+// v_lo' = fp16(2^11 (v - v_hi)), so v = v_hi + 2^-11 v_lo' to about 2^-22 relative.  Per
+// stage three MMA passes run: A_hi B_hi into accumulator D1 and A_hi B_lo' + A_lo' B_hi into
+// D2 (the lo x lo product, ~2^-22, is dropped); the epilogue forms D1 + 2^-11 D2.  |E| <= 1
+// needs no scaling; the B operand (S x, or y) is scaled by a power of two 2^e chosen from
+// its largest component so that it lies below 2^14 (FP16 tops out at 65504), and the
+// epilogue multiplies by 2^-e.  The largest component is found by a reduction kernel before
+// the packing (an atomic max on the float bit pattern in the problem's header).  Stages
+// carry twice the operand bytes, so two B stages are kept instead of four.
+// The tensor core's FP32 accumulation loses about 2^-24 of the running sum per MMA, which
+// over a long item (hundreds of MMAs) would dominate the hi+lo error; so the accumulator is
+// promoted every kPromote stages: two accumulator sets alternate by chunk of stages, the
+// epilogue warps add a finished set into FP32 partial sums (forward: the item's rows of
+// the partial-sum buffer; adjoint: the coil-combined value in registers) and release the
+// set through an mbarrier that the MMA thread waits on before reusing it.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 
@@ -45,11 +63,45 @@ constexpr int kCols = 64;                // voxels (forward) or samples (adjoint
 constexpr int kA_BYTES = kRows * kCols * 2 * 2;  // 128 rows x 128 bf16 = 32 KB
 constexpr float kTwoPi = 6.283185307179586f;
 constexpr int kSpin = 1 << 22;
-constexpr int kNB = 4;  // staged B tiles
+constexpr int kNBMax = 4;  // staged B tiles (BF16: 4, FP16 hi+lo: 2)
+constexpr float kLoScale = 2048.f;           // 2^11: scale of the low parts
+constexpr float kLoInv = 1.f / 2048.f;
+constexpr int kPromote = 8;                  // FP16 hi+lo: stages per accumulator chunk
+
+// Per-form constants: stages of B, bytes of one generated A stage, operand images per tile.
+template <bool HL>
+struct TcForm {
+    static constexpr int NB = HL ? 2 : 4;
+    static constexpr int NPK = HL ? 2 : 1;
+    static constexpr unsigned A_STAGE = NPK * kA_BYTES;
+};
+
+// TMEM columns of one accumulator (N = 2C columns rounded up to a power of two >= 32).
+constexpr uint32_t tmem_acc_cols(int N) { return N <= 32 ? 32u : 64u; }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// (a, b) -> FP16 pairs hi = (fp16 a, fp16 b) and lo = fp16(2^11 (a - hi.a)), fp16(2^11 (b - hi.b)).
+// The differences are exact in FP32 (hi is the rounding of the same value).
+__device__ __forceinline__ void split_f16(float a, float b, uint32_t &hi, uint32_t &lo) {
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn((a - hf.x) * kLoScale, (b - hf.y) * kLoScale);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+
+// Power-of-two scale 2^e (or 2^-e when `inverse`) that maps a largest component with bit
+// pattern `bits` into [2^13, 2^14); zero (or subnormal) maxima give the largest scale, a
+// non-finite one a small scale (the non-finite values then propagate).
+__device__ __forceinline__ float hl_scale(unsigned bits, bool inverse) {
+    const int ex = (int)((bits >> 23) & 0xffu);
+    int se = 140 - max(ex, 1);  // 13 - (ex - 127)
+    se = max(-126, min(126, se));
+    return __int_as_float((127 + (inverse ? -se : se)) << 23);
 }
 
 // Bounded wait that also gives up as soon as another thread of the CTA has aborted.
@@ -78,21 +130,22 @@ __device__ __forceinline__ int find_problem(const int *item_off, int nprob, int 
 
 // Shared state of a persistent tensor-core CTA.
 struct TcShared {
-    uint64_t bfull[kNB], bfree[kNB], afull[2], afree[2];
+    uint64_t bfull[kNBMax], bfree[kNBMax], afull[2], afree[2], accfree[2];
     uint32_t tmem_base;
     int abort_flag;
     int item[2], stop[2];
 };
 
-__device__ __forceinline__ void tc_setup(TcShared &sh, int tid, int warp, uint32_t ncols) {
+__device__ __forceinline__ void tc_setup(TcShared &sh, int tid, int warp, uint32_t ncols, unsigned acc_count) {
     if (tid == 0) {
-        for (int s = 0; s < kNB; ++s) {
+        for (int s = 0; s < kNBMax; ++s) {
             mbar_init(&sh.bfull[s], 1);
             mbar_init(&sh.bfree[s], 1);
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(&sh.afull[s], kTcGen);
             mbar_init(&sh.afree[s], 1);
+            mbar_init(&sh.accfree[s], acc_count);
         }
         sh.abort_flag = 0;
         fence_mbar_init();
@@ -133,11 +186,12 @@ __device__ __forceinline__ void tc_teardown(TcShared &sh, int warp, uint32_t nco
     }
 }
 
-// Issue the 8 MMAs of one stage and commit both stage barriers.
-template <int N>
+// Issue the MMAs of one stage (8 of K = 16; FP16 hi+lo: 24, the cross products into the
+// second accumulator) and commit both stage barriers.
+template <int N, bool HL>
 __device__ __forceinline__ void tc_mma_stage(TcShared &sh, uint32_t tmem, const unsigned char *A,
                                              const unsigned char *B, bool first, int sa, int sb) {
-    constexpr uint32_t IDESC = tc::idesc_f16(kRows, N, 1);
+    constexpr uint32_t IDESC = tc::idesc_f16(kRows, N, HL ? 0 : 1);
     const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
 #pragma unroll
     for (int kk = 0; kk < 8; ++kk) {
@@ -145,25 +199,134 @@ __device__ __forceinline__ void tc_mma_stage(TcShared &sh, uint32_t tmem, const 
         const uint32_t kofb = (uint32_t)((kk >> 2) * (N * 128) + (kk & 3) * 32);
         tc::mma_f16(tmem, tc::sdesc_k128(a0 + koff), tc::sdesc_k128(b0 + kofb), IDESC, !(first && kk == 0));
     }
+    if constexpr (HL) {
+        const uint32_t t2 = tmem + tmem_acc_cols(N);
+        const uint32_t a1 = a0 + kA_BYTES, b1 = b0 + N * 256;
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            const uint32_t koff = (uint32_t)((kk >> 2) * (kRows * 128) + (kk & 3) * 32);
+            const uint32_t kofb = (uint32_t)((kk >> 2) * (N * 128) + (kk & 3) * 32);
+            tc::mma_f16(t2, tc::sdesc_k128(a0 + koff), tc::sdesc_k128(b1 + kofb), IDESC, !(first && kk == 0));
+        }
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            const uint32_t koff = (uint32_t)((kk >> 2) * (kRows * 128) + (kk & 3) * 32);
+            const uint32_t kofb = (uint32_t)((kk >> 2) * (N * 128) + (kk & 3) * 32);
+            tc::mma_f16(t2, tc::sdesc_k128(a1 + koff), tc::sdesc_k128(b0 + kofb), IDESC, 1u);
+        }
+    }
     tc::mma_commit(&sh.afree[sa]);
     tc::mma_commit(&sh.bfree[sb]);
+}
+
+// Store the 2 x 4 generated pairs of one 16-byte chunk column of both row slots: BF16, or
+// FP16 hi into the first A image and lo' into the second.
+template <bool HL>
+__device__ __forceinline__ void store_a_chunk(unsigned char *A, int hh, int r0, int jp, const float (&re)[2][4],
+                                              const float (&im)[2][4]) {
+    unsigned char *atom_base = A + hh * (kRows * 128);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        uint32_t w[4], wl[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if constexpr (HL) split_f16(re[i][u], im[i][u], w[u], wl[u]);
+            else w[u] = pack_bf16(re[i][u], im[i][u]);
+        }
+        const uint32_t o = tc::swz128(r0 + 32 * i, jp);
+        *reinterpret_cast<uint4 *>(atom_base + o) = make_uint4(w[0], w[1], w[2], w[3]);
+        if constexpr (HL) *reinterpret_cast<uint4 *>(atom_base + kA_BYTES + o) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+    }
+}
+
+// FP16 hi+lo promotion, forward: (D1 + 2^-11 D2) 2^-e of one accumulator set for this warp's
+// 32 rows x N/2 columns (TMEM address `ta`), stored to or added into the partial sums `dst`.
+template <int N>
+__device__ __forceinline__ void fwd_promote(uint32_t ta, float inv, float4 *dst, bool add) {
+    constexpr int CH = 8;
+#pragma unroll 1
+    for (int c0 = 0; c0 < N / 2; c0 += CH) {
+        float v[CH], w[CH];
+        tc::tmem_ld<CH>(ta + (uint32_t)c0, v);
+        tc::tmem_ld<CH>(ta + tmem_acc_cols(N) + (uint32_t)c0, w);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int c = 0; c < CH / 4; ++c) {
+            float4 o = make_float4(fmaf(w[4 * c], kLoInv, v[4 * c]) * inv, fmaf(w[4 * c + 1], kLoInv, v[4 * c + 1]) * inv,
+                                   fmaf(w[4 * c + 2], kLoInv, v[4 * c + 2]) * inv,
+                                   fmaf(w[4 * c + 3], kLoInv, v[4 * c + 3]) * inv);
+            if (add) {
+                const float4 q = dst[c0 / 4 + c];
+                o.x += q.x;
+                o.y += q.y;
+                o.z += q.z;
+                o.w += q.w;
+            }
+            dst[c0 / 4 + c] = o;
+        }
+    }
+}
+
+// FP16 hi+lo promotion, adjoint: xr + i xi += sum_c conj(S_c) (D1 + 2^-11 D2)_c over the
+// coils of one accumulator set for this thread's voxel row (scale 2^-e applied by the caller).
+template <int CB>
+__device__ __forceinline__ void adj_promote(uint32_t ta, const float4 *s4, float &xr, float &xi) {
+    constexpr uint32_t TM = tmem_acc_cols(2 * CB);
+#pragma unroll 1
+    for (int c0 = 0; c0 < CB; c0 += 8) {
+        float ur[8], ui[8], wr[8], wi[8];
+        tc::tmem_ld<8>(ta + (uint32_t)c0, ur);
+        tc::tmem_ld<8>(ta + (uint32_t)(CB + c0), ui);
+        tc::tmem_ld<8>(ta + TM + (uint32_t)c0, wr);
+        tc::tmem_ld<8>(ta + TM + (uint32_t)(CB + c0), wi);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+            const float4 sv = s4[c0 / 2 + q4];
+            const float ar = fmaf(wr[2 * q4], kLoInv, ur[2 * q4]), ai = fmaf(wi[2 * q4], kLoInv, ui[2 * q4]);
+            const float br = fmaf(wr[2 * q4 + 1], kLoInv, ur[2 * q4 + 1]);
+            const float bi = fmaf(wi[2 * q4 + 1], kLoInv, ui[2 * q4 + 1]);
+            xr = fmaf(sv.x, ar, xr);
+            xr = fmaf(sv.y, ai, xr);
+            xi = fmaf(sv.x, ai, xi);
+            xi = fmaf(-sv.y, ar, xi);
+            xr = fmaf(sv.z, br, xr);
+            xr = fmaf(sv.w, bi, xr);
+            xi = fmaf(sv.z, bi, xi);
+            xi = fmaf(-sv.w, br, xi);
+        }
+    }
+}
+
+// MMA-thread bookkeeping of the accumulator-set barriers: every chunk but the last of an
+// item is promoted once and arrives once on accfree[chunk & 1]; `base` counts the completed
+// phases of both barriers over the items already done.
+__device__ __forceinline__ void acc_advance(int (&base)[2], int nch) {
+    if (nch > 0) {
+        base[0] += nch / 2;
+        base[1] += (nch - 1) / 2;
+    }
 }
 
 // ---------------------------------------------------------------------------
 // Forward: item = (problem, block of 128 samples, run of voxel tiles)
 // ---------------------------------------------------------------------------
-template <int CB, int LP>
+template <int CB, int LP, bool HL>
 __global__ void __launch_bounds__(kTcThreads, 1)
     fwd_tc_kernel(const ProbDesc *__restrict__ pd, const int *__restrict__ item_off, int nprob, int *counter) {
     constexpr int N = 2 * CB;
-    constexpr unsigned B_BYTES = N * 256;  // N rows x 128 bf16
+    constexpr int NB = TcForm<HL>::NB;
+    constexpr unsigned B_BYTES = N * 256;  // N rows x 128 16-bit values
+    constexpr unsigned B_ALL = TcForm<HL>::NPK * B_BYTES;
     constexpr unsigned DH_BYTES = kTileVox * LP * 4;
     constexpr unsigned F_BYTES = kRows * 4;
-    // one staged tile (B | dh | f0 rows): S_DATA bytes arrive per stage; the stride S_BYTES
-    // keeps every B tile 1024-byte aligned
-    constexpr unsigned S_DATA = B_BYTES + DH_BYTES + F_BYTES;
+    // one staged tile (B [hi | lo'] | dh | f0 rows): S_DATA bytes arrive per stage; the
+    // stride S_BYTES keeps every B tile 1024-byte aligned
+    constexpr unsigned S_DATA = B_ALL + DH_BYTES + F_BYTES;
     constexpr unsigned S_BYTES = (S_DATA + 1023u) & ~1023u;
-    constexpr unsigned TMEM_COLS = N <= 32 ? 32 : 64;
+    // FP16 hi+lo: two accumulator sets of (D1 | D2), alternating by chunk of kPromote stages
+    constexpr uint32_t SET_COLS = 2 * tmem_acc_cols(N);
+    constexpr unsigned TMEM_COLS = HL ? 2 * SET_COLS : tmem_acc_cols(N);
 
     extern __shared__ unsigned char smem_raw[];
     __shared__ TcShared sh;
@@ -171,14 +334,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int warp = tid >> 5;
     const uint32_t sbase = align1024(smem_u32(smem_raw));
     unsigned char *gbase = smem_raw + (sbase - smem_u32(smem_raw));
-    unsigned char *A[2] = {gbase, gbase + kA_BYTES};
-    unsigned char *stage0 = gbase + 2 * kA_BYTES;
+    unsigned char *A[2] = {gbase, gbase + TcForm<HL>::A_STAGE};
+    unsigned char *stage0 = gbase + 2 * TcForm<HL>::A_STAGE;
     const int total = item_off[nprob];
 
-    tc_setup(sh, tid, warp, TMEM_COLS);
+    tc_setup(sh, tid, warp, TMEM_COLS, 256);  // accumulator sets are released by warps 0-7
     const uint32_t tmem = sh.tmem_base;
     int gs = 0;            // stages (tiles) this CTA has processed
     int last_issued = -1;  // producer: last stage whose MMAs were committed
+    int acc_base[2] = {0, 0};
 
     int item;
     for (int iter = 0; tc_next_item(sh, tid, iter, counter, total, item); ++iter) {
@@ -195,27 +359,37 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (warp == kProdWarp) {
             if (tid == kTcGen) {
                 auto load = [&](int it) {
-                    const int sb = (gs + it) % kNB;
+                    const int sb = (gs + it) % NB;
                     unsigned char *dst = stage0 + sb * S_BYTES;
                     const size_t tile = (size_t)(tile0 + it);
                     mbar_arrive_expect_tx(&sh.bfull[sb], S_DATA);
-                    bulk_g2s(dst, P.bpk + tile * B_BYTES, B_BYTES, &sh.bfull[sb]);
-                    bulk_g2s(dst + B_BYTES, P.dh + tile * kTileVox * LP, DH_BYTES, &sh.bfull[sb]);
-                    bulk_g2s(dst + B_BYTES + DH_BYTES, P.f0 + tile * ntp + tbase, F_BYTES, &sh.bfull[sb]);
+                    bulk_g2s(dst, P.bpk + tile * B_ALL, B_ALL, &sh.bfull[sb]);
+                    bulk_g2s(dst + B_ALL, P.dh + tile * kTileVox * LP, DH_BYTES, &sh.bfull[sb]);
+                    bulk_g2s(dst + B_ALL + DH_BYTES, P.f0 + tile * ntp + tbase, F_BYTES, &sh.bfull[sb]);
                 };
-                for (int j = 0; j < min(kNB, ntl); ++j) load(j);
+                for (int j = 0; j < min(NB, ntl); ++j) load(j);
                 for (int it = 0; it < ntl; ++it) {
-                    const int g = gs + it, sa = g & 1, sb = g % kNB;
+                    const int g = gs + it, sa = g & 1, sb = g % NB;
+                    const int m = it / kPromote;
+                    if (HL && it % kPromote == 0 && m >= 2 &&
+                        !wait_or_abort(&sh.accfree[m & 1], (acc_base[m & 1] + ((m - 2) >> 1)) & 1, &sh.abort_flag,
+                                       status))
+                        break;  // set m & 1 still holds chunk m - 2
                     if (!wait_or_abort(&sh.afull[sa], (g >> 1) & 1, &sh.abort_flag, status)) break;
-                    if (!wait_or_abort(&sh.bfull[sb], (g / kNB) & 1, &sh.abort_flag, status)) break;
+                    if (!wait_or_abort(&sh.bfull[sb], (g / NB) & 1, &sh.abort_flag, status)) break;
                     tc::fence_after_sync();
-                    tc_mma_stage<N>(sh, tmem, A[sa], stage0 + sb * S_BYTES, it == 0, sa, sb);
+                    if constexpr (HL)
+                        tc_mma_stage<N, HL>(sh, tmem + (uint32_t)(m & 1) * SET_COLS, A[sa], stage0 + sb * S_BYTES,
+                                            it % kPromote == 0, sa, sb);
+                    else
+                        tc_mma_stage<N, HL>(sh, tmem, A[sa], stage0 + sb * S_BYTES, it == 0, sa, sb);
                     last_issued = g;
-                    if (it + kNB < ntl) {
-                        if (!wait_or_abort(&sh.bfree[sb], (g / kNB) & 1, &sh.abort_flag, status)) break;
-                        load(it + kNB);
+                    if (it + NB < ntl) {
+                        if (!wait_or_abort(&sh.bfree[sb], (g / NB) & 1, &sh.abort_flag, status)) break;
+                        load(it + NB);
                     }
                 }
+                if constexpr (HL) acc_advance(acc_base, (ntl + kPromote - 1) / kPromote);
             }
         } else {
             // generator: warp w owns chunk columns (w & 7) and (w & 7) + 8, lane g owns rows
@@ -233,20 +407,45 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     k[i][4 * q4 + 2] = w.z;
                     k[i][4 * q4 + 3] = w.w;
                 }
+            // epilogue rows and columns (warps 0-7): 32 samples x N/2 columns per warp, computed
+            // where used so that they hold no registers during the generation
+            auto epi_dst = [&]() {
+                return reinterpret_cast<float4 *>(P.fpart +
+                                                  ((size_t)split * ntp + tbase + 32 * (warp & 3) + (tid & 31)) * N +
+                                                  ((warp >> 2) & 1) * (N / 2));
+            };
+            auto epi_tmem = [&]() {
+                return tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(((warp >> 2) & 1) * (N / 2));
+            };
+            int next_promo = 0;  // FP16 hi+lo: next accumulator chunk to promote
             for (int it = 0; it < ntl; ++it) {
-                const int g = gs + it, sa = g & 1, sb = g % kNB;
-                if (!wait_or_abort(&sh.bfull[sb], (g / kNB) & 1, &sh.abort_flag, status)) break;
-                if (g >= 2 && !wait_or_abort(&sh.afree[sa], ((g - 2) >> 1) & 1, &sh.abort_flag, status)) break;
+                const int g = gs + it, sa = g & 1, sb = g % NB;
+                bool w_ok = wait_or_abort(&sh.bfull[sb], (g / NB) & 1, &sh.abort_flag, status);
+                if (w_ok && g >= 2) w_ok = wait_or_abort(&sh.afree[sa], ((g - 2) >> 1) & 1, &sh.abort_flag, status);
+                if (!__all_sync(0xffffffffu, w_ok)) break;  // warp-uniform exit
+                if constexpr (HL) {
+                    // stages <= it - 2 are complete: promote a finished chunk and release its set
+                    if (next_promo < (it - 1) / kPromote) {
+                        if (warp < 8) {
+                            tc::fence_after_sync();
+                            fwd_promote<N>(epi_tmem() + (uint32_t)(next_promo & 1) * SET_COLS,
+                                           hl_scale(P.hdr->amax[0], true), epi_dst(), next_promo > 0);
+                            tc::fence_before_sync();
+                            tc::mbar_arrive(&sh.accfree[next_promo & 1]);
+                        }
+                        ++next_promo;
+                    }
+                }
                 const unsigned char *stg = stage0 + sb * S_BYTES;
-                const float4 *DH = reinterpret_cast<const float4 *>(stg + B_BYTES);
-                const float *F0 = reinterpret_cast<const float *>(stg + B_BYTES + DH_BYTES);
+                const float4 *DH = reinterpret_cast<const float4 *>(stg + B_ALL);
+                const float *F0 = reinterpret_cast<const float *>(stg + B_ALL + DH_BYTES);
                 float f[2];
 #pragma unroll
                 for (int i = 0; i < 2; ++i) f[i] = F0[r0 + 32 * i];
 #pragma unroll
                 for (int hh = 0; hh < 2; ++hh) {
                     const int j = jp + 8 * hh;  // chunk of 4 voxels; atom hh, swizzle column jp
-                    uint32_t packed[2][4];
+                    float er[2][4], ei[2][4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         float d[LP];
@@ -270,14 +469,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                             ph = ph - rintf(ph);
                             float sn, cs;
                             __sincosf(ph * kTwoPi, &sn, &cs);
-                            packed[i][u] = pack_bf16(cs, -sn);  // E = cos - i sin
+                            er[i][u] = cs;  // E = cos - i sin
+                            ei[i][u] = -sn;
                         }
                     }
-                    unsigned char *atom_base = A[sa] + hh * (kRows * 128);
-#pragma unroll
-                    for (int i = 0; i < 2; ++i)
-                        *reinterpret_cast<uint4 *>(atom_base + tc::swz128(r0 + 32 * i, jp)) =
-                            make_uint4(packed[i][0], packed[i][1], packed[i][2], packed[i][3]);
+                    store_a_chunk<HL>(A[sa], hh, r0, jp, er, ei);
                 }
                 tc::fence_proxy_async_smem();
                 tc::mbar_arrive(&sh.afull[sa]);
@@ -289,22 +485,35 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
             tc::fence_after_sync();
             if (warp < 8) {
-                const int lane_base = 32 * (warp & 3);
-                const int half = warp >> 2;
-                const int t = tbase + lane_base + (tid & 31);
-                float v[N / 2];
-                if (ntl > 0 && ok) {
-                    tc::tmem_ld<N / 2>(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(half * (N / 2)), v);
-                    tc::tmem_ld_wait();
+                float4 *dst = epi_dst();
+                const uint32_t ta0 = epi_tmem();
+                if constexpr (!HL) {
+                    float v[N / 2];
+                    if (ntl > 0 && ok) {
+                        tc::tmem_ld<N / 2>(ta0, v);
+                        tc::tmem_ld_wait();
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < N / 2; ++c) v[c] = 0.f;
+                    }
+#pragma unroll
+                    for (int c = 0; c < N / 8; ++c)
+                        dst[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+                } else if (ntl > 0 && ok) {
+                    // the remaining (at most two) chunks; all but the item's last release their set
+                    const int nch = (ntl + kPromote - 1) / kPromote;
+                    const float inv = hl_scale(P.hdr->amax[0], true);
+                    for (int m = next_promo; m < nch; ++m) {
+                        fwd_promote<N>(ta0 + (uint32_t)(m & 1) * SET_COLS, inv, dst, m > 0);
+                        if (m < nch - 1) {
+                            tc::fence_before_sync();
+                            tc::mbar_arrive(&sh.accfree[m & 1]);
+                        }
+                    }
                 } else {
 #pragma unroll
-                    for (int c = 0; c < N / 2; ++c) v[c] = 0.f;
+                    for (int c = 0; c < N / 8; ++c) dst[c] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
-                float4 *dst =
-                    reinterpret_cast<float4 *>(P.fpart + ((size_t)split * ntp + t) * N + half * (N / 2));
-#pragma unroll
-                for (int c = 0; c < N / 8; ++c)
-                    dst[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
             }
         }
         gs += ntl;
@@ -315,19 +524,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // ---------------------------------------------------------------------------
 // Adjoint: item = (problem, two voxel tiles, run of 64-sample stages)
 // ---------------------------------------------------------------------------
-template <int CB, int LP>
+template <int CB, int LP, bool HL>
 __global__ void __launch_bounds__(kTcThreads, 1)
     adj_tc_kernel(const ProbDesc *__restrict__ pd, const int *__restrict__ item_off, int nprob, int *counter) {
     constexpr int N = 2 * CB;
     constexpr int TS = kCols;  // samples per stage
+    constexpr int NB = TcForm<HL>::NB;
     constexpr unsigned B_BYTES = N * 256;
+    constexpr unsigned B_ALL = TcForm<HL>::NPK * B_BYTES;
     constexpr unsigned K_BYTES = TS * LP * 4;
     constexpr unsigned F_BYTES = TS * 4;
-    // B | k rows | f0 (2 tiles): S_DATA bytes arrive per stage; the stride S_BYTES keeps
-    // every B tile 1024-byte aligned
-    constexpr unsigned S_DATA = B_BYTES + K_BYTES + 2 * F_BYTES;
+    // B [hi | lo'] | k rows | f0 (2 tiles): S_DATA bytes arrive per stage; the stride
+    // S_BYTES keeps every B tile 1024-byte aligned
+    constexpr unsigned S_DATA = B_ALL + K_BYTES + 2 * F_BYTES;
     constexpr unsigned S_BYTES = (S_DATA + 1023u) & ~1023u;
-    constexpr unsigned TMEM_COLS = N <= 32 ? 32 : 64;
+    // FP16 hi+lo: two accumulator sets of (D1 | D2), alternating by chunk of kPromote stages
+    constexpr uint32_t SET_COLS = 2 * tmem_acc_cols(N);
+    constexpr unsigned TMEM_COLS = HL ? 2 * SET_COLS : tmem_acc_cols(N);
 
     extern __shared__ unsigned char smem_raw[];
     __shared__ TcShared sh;
@@ -335,14 +548,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int warp = tid >> 5;
     const uint32_t sbase = align1024(smem_u32(smem_raw));
     unsigned char *gbase = smem_raw + (sbase - smem_u32(smem_raw));
-    unsigned char *A[2] = {gbase, gbase + kA_BYTES};
-    unsigned char *stage0 = gbase + 2 * kA_BYTES;
+    unsigned char *A[2] = {gbase, gbase + TcForm<HL>::A_STAGE};
+    unsigned char *stage0 = gbase + 2 * TcForm<HL>::A_STAGE;
     const int total = item_off[nprob];
 
-    tc_setup(sh, tid, warp, TMEM_COLS);
+    tc_setup(sh, tid, warp, TMEM_COLS, 128);  // accumulator sets are released by warps 0-3
     const uint32_t tmem = sh.tmem_base;
     int gs = 0;
     int last_issued = -1;
+    int acc_base[2] = {0, 0};
 
     int item;
     for (int iter = 0; tc_next_item(sh, tid, iter, counter, total, item); ++iter) {
@@ -360,29 +574,39 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (warp == kProdWarp) {
             if (tid == kTcGen) {
                 auto load = [&](int it) {
-                    const int sb = (gs + it) % kNB;
+                    const int sb = (gs + it) % NB;
                     unsigned char *dst = stage0 + sb * S_BYTES;
                     const size_t ts = (size_t)t0 + (size_t)it * TS;
                     mbar_arrive_expect_tx(&sh.bfull[sb], S_DATA);
-                    bulk_g2s(dst, P.ypk + (ts / TS) * B_BYTES, B_BYTES, &sh.bfull[sb]);
-                    bulk_g2s(dst + B_BYTES, P.khi_t + ts * LP, K_BYTES, &sh.bfull[sb]);
-                    bulk_g2s(dst + B_BYTES + K_BYTES, P.f0 + (size_t)tileA * ntp + ts, F_BYTES, &sh.bfull[sb]);
-                    bulk_g2s(dst + B_BYTES + K_BYTES + F_BYTES, P.f0 + (size_t)tileB * ntp + ts, F_BYTES,
+                    bulk_g2s(dst, P.ypk + (ts / TS) * B_ALL, B_ALL, &sh.bfull[sb]);
+                    bulk_g2s(dst + B_ALL, P.khi_t + ts * LP, K_BYTES, &sh.bfull[sb]);
+                    bulk_g2s(dst + B_ALL + K_BYTES, P.f0 + (size_t)tileA * ntp + ts, F_BYTES, &sh.bfull[sb]);
+                    bulk_g2s(dst + B_ALL + K_BYTES + F_BYTES, P.f0 + (size_t)tileB * ntp + ts, F_BYTES,
                              &sh.bfull[sb]);
                 };
-                for (int j = 0; j < min(kNB, nst); ++j) load(j);
+                for (int j = 0; j < min(NB, nst); ++j) load(j);
                 for (int it = 0; it < nst; ++it) {
-                    const int g = gs + it, sa = g & 1, sb = g % kNB;
+                    const int g = gs + it, sa = g & 1, sb = g % NB;
+                    const int m = it / kPromote;
+                    if (HL && it % kPromote == 0 && m >= 2 &&
+                        !wait_or_abort(&sh.accfree[m & 1], (acc_base[m & 1] + ((m - 2) >> 1)) & 1, &sh.abort_flag,
+                                       status))
+                        break;  // set m & 1 still holds chunk m - 2
                     if (!wait_or_abort(&sh.afull[sa], (g >> 1) & 1, &sh.abort_flag, status)) break;
-                    if (!wait_or_abort(&sh.bfull[sb], (g / kNB) & 1, &sh.abort_flag, status)) break;
+                    if (!wait_or_abort(&sh.bfull[sb], (g / NB) & 1, &sh.abort_flag, status)) break;
                     tc::fence_after_sync();
-                    tc_mma_stage<N>(sh, tmem, A[sa], stage0 + sb * S_BYTES, it == 0, sa, sb);
+                    if constexpr (HL)
+                        tc_mma_stage<N, HL>(sh, tmem + (uint32_t)(m & 1) * SET_COLS, A[sa], stage0 + sb * S_BYTES,
+                                            it % kPromote == 0, sa, sb);
+                    else
+                        tc_mma_stage<N, HL>(sh, tmem, A[sa], stage0 + sb * S_BYTES, it == 0, sa, sb);
                     last_issued = g;
-                    if (it + kNB < nst) {
-                        if (!wait_or_abort(&sh.bfree[sb], (g / kNB) & 1, &sh.abort_flag, status)) break;
-                        load(it + kNB);
+                    if (it + NB < nst) {
+                        if (!wait_or_abort(&sh.bfree[sb], (g / NB) & 1, &sh.abort_flag, status)) break;
+                        load(it + NB);
                     }
                 }
+                if constexpr (HL) acc_advance(acc_base, (nst + kPromote - 1) / kPromote);
             }
         } else {
             // generator: warp w owns sample chunks (w & 7) and (w & 7) + 8 of each stage; lane g
@@ -405,19 +629,42 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     d[i][4 * q4 + 3] = valid ? w.w : 0.f;
                 }
             }
+            // epilogue row (warps 0-3): voxel p = vb * 128 + 32 warp + lane; addressing computed
+            // where used so that it holds no registers during the generation
+            auto epi_row = [&]() { return vb * kRows + 32 * (warp & 3) + (tid & 31); };
+            auto epi_s4 = [&]() {
+                const int pr = epi_row();
+                return reinterpret_cast<const float4 *>(P.Sp + (size_t)(pr < ntiles * kTileVox ? pr : 0) * CB);
+            };
+            auto epi_tmem = [&]() { return tmem + ((uint32_t)(32 * (warp & 3)) << 16); };
+            float xr = 0.f, xi = 0.f;  // FP16 hi+lo: promoted, coil-combined partial sum
+            int next_promo = 0;
             for (int it = 0; it < nst; ++it) {
-                const int g = gs + it, sa = g & 1, sb = g % kNB;
-                if (!wait_or_abort(&sh.bfull[sb], (g / kNB) & 1, &sh.abort_flag, status)) break;
-                if (g >= 2 && !wait_or_abort(&sh.afree[sa], ((g - 2) >> 1) & 1, &sh.abort_flag, status)) break;
+                const int g = gs + it, sa = g & 1, sb = g % NB;
+                bool w_ok = wait_or_abort(&sh.bfull[sb], (g / NB) & 1, &sh.abort_flag, status);
+                if (w_ok && g >= 2) w_ok = wait_or_abort(&sh.afree[sa], ((g - 2) >> 1) & 1, &sh.abort_flag, status);
+                if (!__all_sync(0xffffffffu, w_ok)) break;  // warp-uniform exit
+                if constexpr (HL) {
+                    // stages <= it - 2 are complete: promote a finished chunk and release its set
+                    if (next_promo < (it - 1) / kPromote) {
+                        if (warp < 4) {
+                            tc::fence_after_sync();
+                            adj_promote<CB>(epi_tmem() + (uint32_t)(next_promo & 1) * SET_COLS, epi_s4(), xr, xi);
+                            tc::fence_before_sync();
+                            tc::mbar_arrive(&sh.accfree[next_promo & 1]);
+                        }
+                        ++next_promo;
+                    }
+                }
                 const unsigned char *stg = stage0 + sb * S_BYTES;
-                const float4 *KS = reinterpret_cast<const float4 *>(stg + B_BYTES);
-                const float4 *FS = reinterpret_cast<const float4 *>(stg + B_BYTES + K_BYTES);
+                const float4 *KS = reinterpret_cast<const float4 *>(stg + B_ALL);
+                const float4 *FS = reinterpret_cast<const float4 *>(stg + B_ALL + K_BYTES);
 #pragma unroll
                 for (int hh = 0; hh < 2; ++hh) {
                     const int j = jp + 8 * hh;  // samples 4j..4j+3 of the stage
                     const float4 fa = FS[th * (TS / 4) + j];
                     const float fA[4] = {fa.x, fa.y, fa.z, fa.w};
-                    uint32_t packed[2][4];
+                    float er[2][4], ei[2][4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         float kk[LP];
@@ -441,55 +688,72 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                             ph = ph - rintf(ph);
                             float sn, cs;
                             __sincosf(ph * kTwoPi, &sn, &cs);
-                            packed[i][u] = pack_bf16(cs, sn);  // conj(E) = cos + i sin
+                            er[i][u] = cs;  // conj(E) = cos + i sin
+                            ei[i][u] = sn;
                         }
                     }
-                    unsigned char *atom_base = A[sa] + hh * (kRows * 128);
-#pragma unroll
-                    for (int i = 0; i < 2; ++i)
-                        *reinterpret_cast<uint4 *>(atom_base + tc::swz128(r0 + 32 * i, jp)) =
-                            make_uint4(packed[i][0], packed[i][1], packed[i][2], packed[i][3]);
+                    store_a_chunk<HL>(A[sa], hh, r0, jp, er, ei);
                 }
                 tc::fence_proxy_async_smem();
                 tc::mbar_arrive(&sh.afull[sa]);
             }
-            // epilogue (warps 0-3, one voxel row per thread): conj(S) . u over coils
+            // epilogue (warps 0-3, one voxel row per thread): conj(S) . u over coils, read
+            // from TMEM in chunks of 8 coils (FP16 hi+lo: u = (D1 + 2^-11 D2) 2^-e)
             bool ok = !sh.abort_flag;
             const int gl = gs + nst - 1;
             if (nst > 0 && ok) ok = wait_or_abort(&sh.afree[gl & 1], (gl >> 1) & 1, &sh.abort_flag, status);
             ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
             tc::fence_after_sync();
             if (warp < 4) {
-                const int m = 32 * warp + (tid & 31);
-                const int p = vb * kRows + m;
-                float u[N];
-                if (nst > 0 && ok) {
-                    tc::tmem_ld<N / 2>(tmem + ((uint32_t)(32 * warp) << 16), u);
-                    tc::tmem_ld<N / 2>(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(N / 2), u + N / 2);
-                    tc::tmem_ld_wait();
-                } else {
-#pragma unroll
-                    for (int c = 0; c < N; ++c) u[c] = 0.f;
-                }
-                if (p < ntiles * kTileVox) {
-                    const float4 *s4 = reinterpret_cast<const float4 *>(P.Sp + (size_t)p * CB);
-                    float xr = 0.f, xi = 0.f;
-#pragma unroll
-                    for (int q4 = 0; q4 < CB / 2; ++q4) {
-                        float4 sv = s4[q4];
-                        const float ur0 = u[2 * q4], ui0 = u[CB + 2 * q4];
-                        const float ur1 = u[2 * q4 + 1], ui1 = u[CB + 2 * q4 + 1];
-                        xr = fmaf(sv.x, ur0, xr);
-                        xr = fmaf(sv.y, ui0, xr);
-                        xi = fmaf(sv.x, ui0, xi);
-                        xi = fmaf(-sv.y, ur0, xi);
-                        xr = fmaf(sv.z, ur1, xr);
-                        xr = fmaf(sv.w, ui1, xr);
-                        xi = fmaf(sv.z, ui1, xi);
-                        xi = fmaf(-sv.w, ur1, xi);
+                const bool have = nst > 0 && ok;
+                const int p_row = epi_row();
+                const bool inside = p_row < ntiles * kTileVox;
+                const uint32_t ta0 = epi_tmem();
+                const float4 *s4 = epi_s4();
+                if constexpr (HL) {
+                    if (have) {
+                        // the remaining (at most two) chunks; all but the item's last release their set
+                        const int nch = (nst + kPromote - 1) / kPromote;
+                        for (int m = next_promo; m < nch; ++m) {
+                            adj_promote<CB>(ta0 + (uint32_t)(m & 1) * SET_COLS, s4, xr, xi);
+                            if (m < nch - 1) {
+                                tc::fence_before_sync();
+                                tc::mbar_arrive(&sh.accfree[m & 1]);
+                            }
+                        }
+                        const float inv = hl_scale(P.hdr->amax[1], true);
+                        xr *= inv;
+                        xi *= inv;
+                    } else {
+                        xr = xi = 0.f;
                     }
-                    P.apart[(size_t)split * (size_t)(ntiles * kTileVox) + p] = make_float2(xr, xi);
+                } else {
+#pragma unroll 1
+                    for (int c0 = 0; c0 < CB; c0 += 8) {
+                        float ur[8], ui[8];
+                        if (have) {
+                            tc::tmem_ld<8>(ta0 + (uint32_t)c0, ur);
+                            tc::tmem_ld<8>(ta0 + (uint32_t)(CB + c0), ui);
+                            tc::tmem_ld_wait();
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) ur[c] = ui[c] = 0.f;
+                        }
+#pragma unroll
+                        for (int q4 = 0; q4 < 4; ++q4) {
+                            const float4 sv = s4[c0 / 2 + q4];
+                            xr = fmaf(sv.x, ur[2 * q4], xr);
+                            xr = fmaf(sv.y, ui[2 * q4], xr);
+                            xi = fmaf(sv.x, ui[2 * q4], xi);
+                            xi = fmaf(-sv.y, ur[2 * q4], xi);
+                            xr = fmaf(sv.z, ur[2 * q4 + 1], xr);
+                            xr = fmaf(sv.w, ui[2 * q4 + 1], xr);
+                            xi = fmaf(sv.z, ui[2 * q4 + 1], xi);
+                            xi = fmaf(-sv.w, ur[2 * q4 + 1], xi);
+                        }
+                    }
                 }
+                if (inside) P.apart[(size_t)split * (size_t)(ntiles * kTileVox) + p_row] = make_float2(xr, xi);
             }
         }
         gs += nst;
@@ -502,21 +766,39 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // problems (grid.y = problem; blocks beyond a problem's extent return at once)
 // ---------------------------------------------------------------------------
 
+// Four (first, second) pairs -> one 16-byte chunk of the B image(s) at `dst` (FP16 hi+lo:
+// hi at dst, lo' one image of `img_bytes` further).
+template <bool HL>
+__device__ __forceinline__ void store_b_chunk(unsigned char *dst, unsigned img_bytes, const float (&a)[4],
+                                              const float (&b)[4]) {
+    uint32_t w[4], wl[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        if constexpr (HL) split_f16(a[u], b[u], w[u], wl[u]);
+        else w[u] = pack_bf16(a[u], b[u]);
+    }
+    *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+    if constexpr (HL) *reinterpret_cast<uint4 *>(dst + img_bytes) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+}
+
 // Forward: coil-weighted image b_c(v) = S_c(v) x(v) of every 8x8 tile, rows n < C carry
 // (Re b, -Im b), rows C + c carry (Im b, Re b) at K positions (2v, 2v+1).  The image is
-// `x` when given (single problem) or the descriptor's vec[src].
-template <int CB>
+// `x` when given (single problem) or the descriptor's vec[src].  FP16 hi+lo: b is scaled by
+// the power of two fixed by the problem's amax[0].
+template <int CB, bool HL>
 __global__ void pack_b_fwd_kernel(const ProbDesc *__restrict__ pd, const float2 *__restrict__ x, int src) {
     constexpr int N = 2 * CB;
+    constexpr int NPK = HL ? 2 : 1;
     const ProbDesc &P = pd[blockIdx.y];
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // (tile, n, chunk)
     if (i >= (size_t)P.ntiles * N * 16) return;
     const float2 *img = x ? x : P.vec[src];
+    const float sc = HL ? hl_scale(P.hdr->amax[0], false) : 1.f;
     const int jj = (int)(i % 16);
     const int n = (int)((i / 16) % N);
     const int tile = (int)(i / (16 * N));
     const int c = n < CB ? n : n - CB;
-    uint32_t w[4];
+    float a[4], b[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int v = 4 * jj + u;
@@ -525,39 +807,94 @@ __global__ void pack_b_fwd_kernel(const ProbDesc *__restrict__ pd, const float2 
         if (ix < P.nx && iy < P.ny) {
             float2 s = P.Sp[((size_t)tile * kTileVox + v) * CB + c];
             float2 xv = img[(size_t)iy * P.nx + ix];
-            br = s.x * xv.x - s.y * xv.y;
-            bi = s.x * xv.y + s.y * xv.x;
+            br = (s.x * xv.x - s.y * xv.y) * sc;
+            bi = (s.x * xv.y + s.y * xv.x) * sc;
         }
-        w[u] = n < CB ? pack_bf16(br, -bi) : pack_bf16(bi, br);
+        a[u] = n < CB ? br : bi;
+        b[u] = n < CB ? -bi : br;
     }
-    unsigned char *dst = P.bpk + (size_t)tile * (N * 256) + (jj >> 3) * (N * 128) + tc::swz128(n, jj & 7);
-    *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+    unsigned char *dst =
+        P.bpk + (size_t)tile * (NPK * N * 256) + (jj >> 3) * (N * 128) + tc::swz128(n, jj & 7);
+    store_b_chunk<HL>(dst, N * 256, a, b);
 }
 
 // Adjoint: k-space yt[t][c] (or the descriptor's vec[src], or rt when src < 0) per stage of
-// 64 samples; rows n < C
-// carry (Re y, -Im y), rows C + c carry (Im y, Re y) at K positions (2s, 2s+1).
-template <int CB>
+// 64 samples; rows n < C carry (Re y, -Im y), rows C + c carry (Im y, Re y) at K positions
+// (2s, 2s+1).  FP16 hi+lo: y is scaled by the power of two fixed by amax[1].
+template <int CB, bool HL>
 __global__ void pack_y_adj_kernel(const ProbDesc *__restrict__ pd, const float2 *__restrict__ yt, int src) {
     constexpr int N = 2 * CB;
+    constexpr int NPK = HL ? 2 : 1;
     const ProbDesc &P = pd[blockIdx.y];
     const int nstages = P.ntp / kCols;
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // (stage, n, chunk)
     if (i >= (size_t)nstages * N * 16) return;
     const float2 *y = yt ? yt : (src >= 0 ? P.vec[src] : P.rt);
+    const float sc = HL ? hl_scale(P.hdr->amax[1], false) : 1.f;
     const int jj = (int)(i % 16);
     const int n = (int)((i / 16) % N);
     const int st = (int)(i / (16 * N));
     const int c = n < CB ? n : n - CB;
-    uint32_t w[4];
+    float a[4], b[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const size_t t = (size_t)st * kCols + 4 * jj + u;
         float2 v = y[t * CB + c];
-        w[u] = n < CB ? pack_bf16(v.x, -v.y) : pack_bf16(v.y, v.x);
+        v.x *= sc;
+        v.y *= sc;
+        a[u] = n < CB ? v.x : v.y;
+        b[u] = n < CB ? -v.y : v.x;
     }
-    unsigned char *dst = P.ypk + (size_t)st * (N * 256) + (jj >> 3) * (N * 128) + tc::swz128(n, jj & 7);
-    *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+    unsigned char *dst = P.ypk + (size_t)st * (NPK * N * 256) + (jj >> 3) * (N * 128) + tc::swz128(n, jj & 7);
+    store_b_chunk<HL>(dst, N * 256, a, b);
+}
+
+// ---- FP16 hi+lo: largest component of the operand to be packed (atomic max on the bit
+// pattern of a non-negative float, which orders like the value) ----
+__global__ void amax_reset_kernel(const ProbDesc *__restrict__ pd, int nprob, int which) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nprob) pd[q].hdr->amax[which] = 0u;
+}
+
+__device__ __forceinline__ void amax_commit(float m, unsigned *slot) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(slot, __float_as_uint(m));
+}
+
+// max |Re|, |Im| of b_c(v) = S_c(v) x(v); thread = (voxel in tile order, pair of coils)
+template <int CB>
+__global__ void amax_b_kernel(const ProbDesc *__restrict__ pd, const float2 *__restrict__ x, int src) {
+    const ProbDesc &P = pd[blockIdx.y];
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float m = 0.f;
+    if (i < (size_t)P.ntiles * kTileVox * (CB / 2)) {
+        const float2 *img = x ? x : P.vec[src];
+        const int p = (int)(i / (CB / 2));
+        const int tile = p / kTileVox, v = p % kTileVox;
+        const int ix = (tile % P.ntx) * kTileSide + v % kTileSide, iy = (tile / P.ntx) * kTileSide + v / kTileSide;
+        if (ix < P.nx && iy < P.ny) {
+            const float4 s = reinterpret_cast<const float4 *>(P.Sp)[i];
+            const float2 xv = img[(size_t)iy * P.nx + ix];
+            m = fmaxf(fmaxf(fabsf(s.x * xv.x - s.y * xv.y), fabsf(s.x * xv.y + s.y * xv.x)),
+                      fmaxf(fabsf(s.z * xv.x - s.w * xv.y), fabsf(s.z * xv.y + s.w * xv.x)));
+        }
+    }
+    amax_commit(m, &P.hdr->amax[0]);
+}
+
+// max |Re|, |Im| of the sample-major k-space yt[t][CB] (or vec[src], or rt when src < 0)
+template <int CB>
+__global__ void amax_y_kernel(const ProbDesc *__restrict__ pd, const float2 *__restrict__ yt, int src) {
+    const ProbDesc &P = pd[blockIdx.y];
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float m = 0.f;
+    if (i < (size_t)P.ntp * (CB / 2)) {
+        const float2 *y = yt ? yt : (src >= 0 ? P.vec[src] : P.rt);
+        const float4 v = reinterpret_cast<const float4 *>(y)[i];
+        m = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
+    }
+    amax_commit(m, &P.hdr->amax[1]);
 }
 
 // Reductions of the planar forward partials [split][t][re(0..C) | im(0..C)].
@@ -600,21 +937,29 @@ __global__ void write_desc_kernel(ProbDesc d, ProbDesc *dst) { *dst = d; }
 
 // ---- launch helpers ----
 constexpr size_t round1k(size_t v) { return (v + 1023) & ~size_t(1023); }
-template <int CB, int LP>
+template <int CB, int LP, bool HL>
 size_t fwd_tc_smem() {
-    return 1024 + 2 * kA_BYTES + kNB * round1k(2 * CB * 256 + kTileVox * LP * 4 + kRows * 4);
+    using F = TcForm<HL>;
+    return 1024 + 2 * F::A_STAGE + F::NB * round1k(F::NPK * 2 * CB * 256 + kTileVox * LP * 4 + kRows * 4);
 }
-template <int CB, int LP>
+template <int CB, int LP, bool HL>
 size_t adj_tc_smem() {
-    return 1024 + 2 * kA_BYTES + kNB * round1k(2 * CB * 256 + kCols * LP * 4 + 2 * kCols * 4);
+    using F = TcForm<HL>;
+    return 1024 + 2 * F::A_STAGE + F::NB * round1k(F::NPK * 2 * CB * 256 + kCols * LP * 4 + 2 * kCols * 4);
 }
 
-template <int CB, int LP>
+// The max-reduction grids equal the packing grids: both cover ntiles * 64 * CB / 2 (forward)
+// and ntp * CB / 2 (adjoint) threads.
+template <int CB, int LP, bool HL>
 cudaError_t launch_fwd_tc(const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *x, int src,
                           const int *item_off, int total_items, int *counter, cudaStream_t st) {
-    pack_b_fwd_kernel<CB><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, x, src);
-    auto kern = fwd_tc_kernel<CB, LP>;
-    const size_t smem = fwd_tc_smem<CB, LP>();
+    if constexpr (HL) {
+        amax_reset_kernel<<<cdiv(nprob, 256), 256, 0, st>>>(pd, nprob, 0);
+        amax_b_kernel<CB><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, x, src);
+    }
+    pack_b_fwd_kernel<CB, HL><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, x, src);
+    auto kern = fwd_tc_kernel<CB, LP, HL>;
+    const size_t smem = fwd_tc_smem<CB, LP, HL>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
@@ -622,12 +967,16 @@ cudaError_t launch_fwd_tc(const ProbDesc *pd, int nprob, int max_pack_blocks, co
     return cudaGetLastError();
 }
 
-template <int CB, int LP>
+template <int CB, int LP, bool HL>
 cudaError_t launch_adj_tc(const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *yt, int src,
                           const int *item_off, int total_items, int *counter, cudaStream_t st) {
-    pack_y_adj_kernel<CB><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, yt, src);
-    auto kern = adj_tc_kernel<CB, LP>;
-    const size_t smem = adj_tc_smem<CB, LP>();
+    if constexpr (HL) {
+        amax_reset_kernel<<<cdiv(nprob, 256), 256, 0, st>>>(pd, nprob, 1);
+        amax_y_kernel<CB><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, yt, src);
+    }
+    pack_y_adj_kernel<CB, HL><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, yt, src);
+    auto kern = adj_tc_kernel<CB, LP, HL>;
+    const size_t smem = adj_tc_smem<CB, LP, HL>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
@@ -635,12 +984,14 @@ cudaError_t launch_adj_tc(const ProbDesc *pd, int nprob, int max_pack_blocks, co
     return cudaGetLastError();
 }
 
+#define AEXP_TC_HL(FN, CBV, LPV, ...)                               \
+    return HLv ? FN<CBV, LPV, true>(__VA_ARGS__) : FN<CBV, LPV, false>(__VA_ARGS__);
 #define AEXP_TC_LP(FN, CBV, ...)                         \
     switch (LPv) {                                       \
-        case 4: return FN<CBV, 4>(__VA_ARGS__);          \
-        case 8: return FN<CBV, 8>(__VA_ARGS__);          \
-        case 12: return FN<CBV, 12>(__VA_ARGS__);        \
-        default: return FN<CBV, 20>(__VA_ARGS__);        \
+        case 4: AEXP_TC_HL(FN, CBV, 4, __VA_ARGS__)      \
+        case 8: AEXP_TC_HL(FN, CBV, 8, __VA_ARGS__)      \
+        case 12: AEXP_TC_HL(FN, CBV, 12, __VA_ARGS__)    \
+        default: AEXP_TC_HL(FN, CBV, 20, __VA_ARGS__)    \
     }
 #define AEXP_TC_DISPATCH(FN, ...)                                \
     switch (CBv) {                                               \
@@ -663,6 +1014,7 @@ cudaError_t write_desc(const ProbDesc &d, ProbDesc *dst, cudaStream_t st) {
 // (written by op_prepare for the tensor-core precisions).
 cudaError_t op_forward_tc(const OpLayout &L, const float2 *x, char *ws, cudaStream_t st) {
     const int CBv = L.CB, LPv = L.LP;
+    const bool HLv = L.precision == AEXP_FP16X2_TC;
     WsHeader *hdr = (WsHeader *)(ws + L.off_hdr);
     const ProbDesc *pd = (const ProbDesc *)(ws + L.off_desc);
     AEXP_TC_DISPATCH(launch_fwd_tc, pd, 1, fwd_pack_blocks(L.ntiles, L.CB), x, 0, &hdr->item_off[0], L.fwd_items,
@@ -671,21 +1023,24 @@ cudaError_t op_forward_tc(const OpLayout &L, const float2 *x, char *ws, cudaStre
 
 cudaError_t op_adjoint_tc(const OpLayout &L, const float2 *yt, char *ws, cudaStream_t st) {
     const int CBv = L.CB, LPv = L.LP;
+    const bool HLv = L.precision == AEXP_FP16X2_TC;
     WsHeader *hdr = (WsHeader *)(ws + L.off_hdr);
     const ProbDesc *pd = (const ProbDesc *)(ws + L.off_desc);
     AEXP_TC_DISPATCH(launch_adj_tc, pd, 1, adj_pack_blocks(L.ntp, L.CB), yt, -1, &hdr->item_off[2], L.adj_items,
                      &hdr->counter[1], st)
 }
 
-cudaError_t batch_forward_tc(int CB, int LP, const ProbDesc *pd, int nprob, int max_pack_blocks, int src,
-                             const int *item_off, int total_items, int *counter, cudaStream_t st) {
+cudaError_t batch_forward_tc(int precision, int CB, int LP, const ProbDesc *pd, int nprob, int max_pack_blocks,
+                             int src, const int *item_off, int total_items, int *counter, cudaStream_t st) {
     const int CBv = CB, LPv = LP;
+    const bool HLv = precision == AEXP_FP16X2_TC;
     AEXP_TC_DISPATCH(launch_fwd_tc, pd, nprob, max_pack_blocks, nullptr, src, item_off, total_items, counter, st)
 }
 
-cudaError_t batch_adjoint_tc(int CB, int LP, const ProbDesc *pd, int nprob, int max_pack_blocks, int src,
-                             const int *item_off, int total_items, int *counter, cudaStream_t st) {
+cudaError_t batch_adjoint_tc(int precision, int CB, int LP, const ProbDesc *pd, int nprob, int max_pack_blocks,
+                             int src, const int *item_off, int total_items, int *counter, cudaStream_t st) {
     const int CBv = CB, LPv = LP;
+    const bool HLv = precision == AEXP_FP16X2_TC;
     AEXP_TC_DISPATCH(launch_adj_tc, pd, nprob, max_pack_blocks, nullptr, src, item_off, total_items, counter, st)
 }
 
