@@ -253,8 +253,11 @@ def _run_ours(args, rank, world, local, dev):
     L_out = torch.empty(1, dtype=torch.float64, device=dev)
 
     def recon_ws(prec):
+        # autotuned work-item granularity (untimed); the tuner's workspace then serves the solve
         o = ax.recon_opts(precision=prec, wavelet="db4", levels=levels, n_power=n_power)
-        return o, ax.recon_workspace(prob, o)
+        w = torch.empty(ax.lib_autotune_workspace_size(prob, o), dtype=torch.uint8, device=dev)
+        o.items_per_sm, _ = ax.autotune(prob, o, ws=w)
+        return o, w
 
     opts, ws = recon_ws(precision)
     for _ in range(args.warmup):
@@ -349,7 +352,7 @@ def _run_ours(args, rank, world, local, dev):
         o_step = float(np.mean(o_ms))
         c = {"s_per_slice": o_step / 1e3, "value": world * vsc_per_step / (o_step / 1e3) / 1e9, "unit": UNIT,
              "nrmse_vs_phantom": o_nrmse, "device_status": ax.read_status(o_ws), "kernels_ms": o_kern,
-             "speedup_vs_primary": ms_per_step / o_step}
+             "speedup_vs_primary": ms_per_step / o_step, "items_per_sm": o_opts.items_per_sm}
         if other != "fp32":
             o_dom = max(o_kern, key=o_kern.get)
             passes = 3 if other == "fp16x2" else 1    # hi.hi + hi.lo + lo.hi MMA passes
@@ -379,6 +382,7 @@ def _run_ours(args, rank, world, local, dev):
             "config": {"workload": WORKLOAD, "form": args.form, "nx": p["nx"], "nt": nt, "nc": nc,
                        "terms": nterms, "fista_iters": iters, "power_iters": n_power,
                        "applications_per_step": applications, "l2": "flushed between timed steps (512 MB write)",
+                       "items_per_sm": opts.items_per_sm,
                        "parallelism": f"replicas x{world} (independent slices)"},
             "s_per_slice": ms_per_step / 1e3,
             "nrmse_vs_phantom": nrmse,
@@ -440,7 +444,13 @@ def run_ragged(args):
         tc_form = args.form if args.form != "fp32" else "bf16"   # the batched path runs on the tensor cores
         opts = ax.recon_opts(precision={"bf16": ax.BF16_TC, "fp16x2": ax.FP16X2_TC}[tc_form], wavelet="db4",
                              levels=levels, n_power=n_power)
-        ws = torch.empty(ax.batch_workspace_size(probs, opts), dtype=torch.uint8, device=dev)
+        # one workspace serves the autotuner (every candidate layout) and the solve
+        tune_bytes = ax.lib_autotune_workspace_size(probs, opts)
+        ws = torch.empty(tune_bytes, dtype=torch.uint8, device=dev)
+        t0 = time.time()
+        best_ips, best_ms = ax.autotune(probs, opts, ws=ws)
+        tune_s = time.time() - t0
+        opts.items_per_sm = best_ips
         xs = [torch.empty(pr.nr, dtype=torch.complex64, device=dev) for pr in probs]
         L = torch.empty(len(probs), dtype=torch.float64, device=dev)
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -468,7 +478,8 @@ def run_ragged(args):
         "config": {"workload": f"ragged batch: 3 resolutions (148/170/200) x {nvol} volumes x {nsl} slices = "
                                f"{len(probs)} problems, 32 coils, 3rd-order SH + B0, db4 J=4, 50 FISTA + 30 power",
                    "problems": len(probs), "vsc_per_application": vsc, "applications_per_step": applications,
-                   "workspace_gb": ws.numel() / 1e9, "generation_s": gen_s},
+                   "workspace_gb": ws.numel() / 1e9, "generation_s": gen_s,
+                   "autotune": {"items_per_sm": best_ips, "ms_per_AhA": best_ms, "seconds": tune_s}},
         "s_per_slice": step / 1e3 / len(probs), "nrmse_vs_phantom_median": float(np.median(nrmse)),
         "device_status": status, "clocks": clk.summary()}))
 

@@ -65,6 +65,16 @@ typedef enum aexp_precision {
     AEXP_BF16_TC = 1,     /* encoding tile in BF16, tcgen05 tensor cores, FP32 accum  */
     AEXP_FP16X2_TC = 2    /* encoding tile and coil images split hi+lo in FP16        */
 } aexp_precision;
+/* Accuracy (relative L2 error of A x and A^H y against an FP64 evaluation of the operator
+ * of Eq. 1, Sec. 2.1):
+ *   AEXP_FP32       ~2e-7 .. 1.2e-6;
+ *   AEXP_BF16_TC    ~2e-3 for white inputs (each factor rounded to 8 significant bits),
+ *                   ~1e-4 .. 3e-4 for smooth images;
+ *   AEXP_FP16X2_TC  ~5e-7 .. 3e-6: each operand value is v_hi + 2^-11 v_lo' in FP16,
+ *                   products hi*hi + hi*lo + lo*hi on the tensor cores, accumulators
+ *                   promoted to FP32 every 8 stages; the coil-weighted image (forward)
+ *                   and the k-space data (adjoint) are scaled by a power of two chosen
+ *                   from their largest component, so any finite FP32 input is accepted. */
 
 typedef enum aexp_wavelet {
     AEXP_WAVELET_HAAR = 0, /* orthonormal Haar, 2 taps                          */
@@ -125,10 +135,15 @@ typedef struct aexp_recon_opts {
     const void *x0;         /* [nr] complex64 start image, or NULL for zero              */
     const void *power_init; /* [nr] complex64 power-iteration start, or NULL for A^H y   */
     int use_graph;          /* nonzero: capture the whole loop in one CUDA graph         */
+    int items_per_sm;       /* work-item granularity of the operator launches: the sample
+                               (forward) and voxel (adjoint) reductions are split until a
+                               launch holds about 152 x items_per_sm blocks or persistent
+                               work items (shared among the problems of a batch); 0 = the
+                               default (FP32 16, tensor cores 8); aexp_autotune picks one */
 } aexp_recon_opts;
 
 /* Fill opts with defaults: FP32, Haar, 3 levels, 30 power iterations, estimate L_f,
- * zero start, A^H y power start, graph capture on. */
+ * zero start, A^H y power start, graph capture on, default work-item granularity. */
 AEXP_API void aexp_recon_opts_default(aexp_recon_opts *opts);
 
 /* Bytes of workspace cs_recon needs (includes the operator workspace). */
@@ -148,6 +163,24 @@ AEXP_API int cs_recon(const aexp_problem *prob, const void *y, float lambda, int
  * not modified).  Result to the DEVICE double *lipschitz_out.  ws as for cs_recon. */
 AEXP_API int aexp_power_lipschitz(const aexp_problem *prob, int precision, const void *v0, int n_power,
                          double *lipschitz_out, void *ws, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Autotuning of the work-item granularity (no counterpart in the paper; it serves the
+ * ragged many-problem workload of Sec. 2.2.1's protocol grid).  For each candidate
+ * items_per_sm in {2, 4, 8, 16, 32} the call lays out the workspace, prepares the
+ * problem(s) and times (CUDA events, best of 3 after one warm-up) one A^H A
+ * application: of `probs[0]` alone when nprob == 1 (the cs_recon layout, any precision),
+ * of the whole batch when nprob > 1 (the cs_recon_batched layout, tensor-core
+ * precisions only).  The fastest candidate goes to *best_items_per_sm, its time in ms
+ * to *best_ms (optional).  ws: device memory of aexp_autotune_workspace_size bytes, whose
+ * contents are overwritten (a preparation of ws for the operator calls is void afterwards).
+ * The call synchronizes `stream` and returns AEXP_ERR_INVALID_ARG while it is being captured;
+ * a device-side error status met while timing is returned as it is.
+ * --------------------------------------------------------------------------- */
+AEXP_API int aexp_autotune_workspace_size(const aexp_problem *probs, int nprob, const aexp_recon_opts *opts,
+                                          size_t *bytes);
+AEXP_API int aexp_autotune(const aexp_problem *probs, int nprob, const aexp_recon_opts *opts, void *ws,
+                           size_t ws_bytes, void *stream, int *best_items_per_sm, float *best_ms);
 
 /* ---------------------------------------------------------------------------
  * Ragged batches: many independent slice problems (several resolutions, diffusion volumes

@@ -45,7 +45,7 @@ class CProblem(ctypes.Structure):
 class CReconOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("wavelet", ctypes.c_int), ("levels", ctypes.c_int),
                 ("n_power", ctypes.c_int), ("lipschitz", ctypes.c_double), ("x0", ctypes.c_void_p),
-                ("power_init", ctypes.c_void_p), ("use_graph", ctypes.c_int)]
+                ("power_init", ctypes.c_void_p), ("use_graph", ctypes.c_int), ("items_per_sm", ctypes.c_int)]
 
 
 _lib = None
@@ -77,6 +77,8 @@ SIGNATURES = [
     ("aexp_wavelet_prox", _I, [_I, _I, _I, _I, ctypes.c_float, _P, _P, _P, _SZ, _P]),
     ("aexp_wavelet_forward", _I, [_I, _I, _I, _I, _P, _P, _P, _SZ, _P]),
     ("aexp_wavelet_prox_static", _I, [_I, _I, _I, _I, ctypes.c_float, _P, _P, _P]),
+    ("aexp_autotune_workspace_size", _I, [_PROB, _I, _OPTS, ctypes.POINTER(_SZ)]),
+    ("aexp_autotune", _I, [_PROB, _I, _OPTS, _P, _SZ, _P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]),
     ("aexp_read_status", _I, [_P, _P, ctypes.POINTER(_I)]),
     ("aexp_status_string", ctypes.c_char_p, [_I]),
     ("aexp_last_cuda_error", _I, []),
@@ -210,7 +212,7 @@ def a_exp_adjoint(prob: Problem, y, ws, x=None, precision: int = FP32, stream=No
 
 
 def recon_opts(precision=FP32, wavelet="haar", levels=3, n_power=30, lipschitz=0.0, x0=None, power_init=None,
-               use_graph=True) -> CReconOpts:
+               use_graph=True, items_per_sm=0) -> CReconOpts:
     o = CReconOpts()
     lib().aexp_recon_opts_default(ctypes.byref(o))
     o.precision = precision
@@ -221,6 +223,7 @@ def recon_opts(precision=FP32, wavelet="haar", levels=3, n_power=30, lipschitz=0
     o.x0 = None if x0 is None else x0.data_ptr()
     o.power_init = None if power_init is None else power_init.data_ptr()
     o.use_graph = 1 if use_graph else 0
+    o.items_per_sm = int(items_per_sm)
     return o
 
 
@@ -287,6 +290,31 @@ def cs_recon_batched(probs, ys, lams, iters: int, opts: CReconOpts | None = None
     _check(lib().cs_recon_batched(probs_c, n, yp, lp, int(iters), ctypes.byref(opts), xp, _ptr(lipschitz_out),
                                   _ptr(ws), ws.numel(), _stream(stream)), "cs_recon_batched")
     return x_outs, lipschitz_out
+
+
+def lib_autotune_workspace_size(probs, opts: CReconOpts) -> int:
+    """Bytes of workspace aexp_autotune needs for `probs` (covers every candidate layout)."""
+    probs = list(probs) if isinstance(probs, (list, tuple)) else [probs]
+    need = ctypes.c_size_t()
+    _check(lib().aexp_autotune_workspace_size(_prob_array(probs), len(probs), ctypes.byref(opts), ctypes.byref(need)),
+           "aexp_autotune_workspace_size")
+    return need.value
+
+
+def autotune(probs, opts: CReconOpts, ws=None, stream=None):
+    """Time the candidate work-item granularities for `probs` (one problem: cs_recon's layout;
+    several: cs_recon_batched's) and return (best items_per_sm, ms per A^H A application).
+    Synchronizes the stream; `opts` is not modified."""
+    probs = list(probs) if isinstance(probs, (list, tuple)) else [probs]
+    n = len(probs)
+    probs_c = _prob_array(probs)
+    if ws is None:
+        ws = _alloc(lib_autotune_workspace_size(probs, opts), probs[0].device)
+    best = ctypes.c_int()
+    ms = ctypes.c_float()
+    _check(lib().aexp_autotune(probs_c, n, ctypes.byref(opts), _ptr(ws), ws.numel(), _stream(stream),
+                               ctypes.byref(best), ctypes.byref(ms)), "aexp_autotune")
+    return best.value, ms.value
 
 
 def power_lipschitz(prob: Problem, v0, n_power: int, ws=None, precision: int = FP32, stream=None):

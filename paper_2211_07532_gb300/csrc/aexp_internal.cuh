@@ -121,11 +121,19 @@ inline size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a
 inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 
 // Host-side layout computation (layout.cu).
-// tc_target_items: work items the tensor-core splits aim for (a batch passes a share of the
-// SM-count target so that large batches use whole-problem items and few partial sums).
-int op_layout(const aexp_problem *p, int precision, OpLayout *L, int tc_target_items = 152 * 8);
+// target_items: blocks (FP32) or persistent work items (tensor cores) one launch aims for
+// when the reduction dimensions are split; <= 0 selects the default, 152 SMs x
+// default_items_per_sm(precision).  A batch passes its share of the target so that large
+// batches use whole-problem items and few partial sums.
+constexpr int kLayoutSMs = 152;
+inline int default_items_per_sm(int precision) { return precision == AEXP_FP32 ? 16 : 8; }
+inline int items_target(int precision, int items_per_sm) {
+    return kLayoutSMs * (items_per_sm > 0 ? items_per_sm : default_items_per_sm(precision));
+}
+int op_layout(const aexp_problem *p, int precision, OpLayout *L, int target_items = -1);
 int wave_layout(int nx, int ny, int wavelet, int levels, WaveLayout *W);
-int rec_layout(const aexp_problem *p, const aexp_recon_opts *o, RecLayout *R, int tc_target_items = 152 * 8,
+// target_items < 0: taken from o->items_per_sm
+int rec_layout(const aexp_problem *p, const aexp_recon_opts *o, RecLayout *R, int target_items = -1,
                int with_grad = 0);
 
 // Launchers (all asynchronous on `st`; return cudaError_t of the launch).
@@ -206,6 +214,8 @@ cudaError_t recon_issue(const aexp_problem *p, const RecLayout &R, const aexp_re
 
 // Record a CUDA error for aexp_last_cuda_error() (capi.cu).
 void aexp_set_last_cuda_error(int e);
+// Drop the host-side record of what `ws` was prepared for (its contents were overwritten).
+void forget_prepared(const void *ws);
 
 // Differentiation through unrolled FISTA (grad.cu).
 cudaError_t unroll_step(const RecLayout &R, const float2 *y, float lam, double lipschitz, const float2 *z,

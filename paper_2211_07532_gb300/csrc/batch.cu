@@ -190,7 +190,7 @@ int batch_layout(const aexp_problem *probs, int nprob, const aexp_recon_opts *op
     BatchLayout b{};
     b.nprob = nprob;
     // whole-problem items once the batch alone fills the GPU several times over
-    const int target = std::max(1, (152 * 8) / nprob);
+    const int target = std::max(1, items_target(opts->precision, opts->items_per_sm) / nprob);
     b.R.resize(nprob);
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -230,12 +230,10 @@ int batch_layout(const aexp_problem *probs, int nprob, const aexp_recon_opts *op
     return AEXP_OK;
 }
 
-cudaError_t batch_recon_issue(const aexp_problem *probs, const BatchLayout &B, const aexp_recon_opts *o,
-                              const void *const *y, const float *lambda, int iters, void *const *x_out,
-                              double *lip_out, char *ws, cudaStream_t st) {
+cudaError_t batch_setup(const aexp_problem *probs, const BatchLayout &B, const void *const *y, const float *lambda,
+                        void *const *x_out, double *lip_out, char *ws, cudaStream_t st) {
     const int n = B.nprob;
     ProbDesc *pd = (ProbDesc *)(ws + B.off_desc);
-    WsHeader *bh = (WsHeader *)(ws + B.off_hdr);
     int *ifwd = (int *)(ws + B.off_items_fwd);
     int *iadj = (int *)(ws + B.off_items_adj);
     const int T = 256;
@@ -258,9 +256,9 @@ cudaError_t batch_recon_issue(const aexp_problem *probs, const BatchLayout &B, c
         d.levels = R.wv.levels;
         d.off_pyr = R.wv.off_pyr;
         for (int j = 0; j < 12; ++j) d.off_approx[j] = R.wv.off_approx[j];
-        d.lam = lambda[q];
-        d.y_in = (const float2 *)y[q];
-        d.x_out = (float2 *)x_out[q];
+        d.lam = lambda ? lambda[q] : 0.f;
+        d.y_in = y ? (const float2 *)y[q] : nullptr;
+        d.x_out = x_out ? (float2 *)x_out[q] : nullptr;
         d.lip_out = lip_out ? lip_out + q : nullptr;
         CK(write_desc(d, pd + q, st));
     }
@@ -273,6 +271,41 @@ cudaError_t batch_recon_issue(const aexp_problem *probs, const BatchLayout &B, c
         set_offsets_kernel<<<1, 256, 0, st>>>(iadj, a);
     }
     batch_reset_kernel<<<cdiv(n, T), T, 0, st>>>(pd, n);
+    return cudaGetLastError();
+}
+
+// One A^H A application of every problem of a set-up batch on a zero image (the
+// autotuner's timing unit: the work does not depend on the values).
+cudaError_t batch_normal_once(const BatchLayout &B, const aexp_recon_opts *o, char *ws, cudaStream_t st) {
+    const int n = B.nprob;
+    ProbDesc *pd = (ProbDesc *)(ws + B.off_desc);
+    WsHeader *bh = (WsHeader *)(ws + B.off_hdr);
+    const int *ifwd = (const int *)(ws + B.off_items_fwd);
+    const int *iadj = (const int *)(ws + B.off_items_adj);
+    const int T = 256;
+    const dim3 g_nr(cdiv(B.max_nr, T), n), g_ntp(cdiv(B.max_ntpcb, T), n);
+    enum { Z = 2, W = 4 };
+    batch_zero_kernel<<<g_nr, T, 0, st>>>(pd, Z);
+    CK(batch_forward_tc(o->precision, B.CB, B.LP, pd, n, B.max_fwd_pack, Z, ifwd, B.items_fwd[n], &bh->counter[0],
+                        st));
+    batch_fwd_reduce_kernel<<<g_ntp, T, 0, st>>>(pd, 0);
+    CK(batch_adjoint_tc(o->precision, B.CB, B.LP, pd, n, B.max_adj_pack, -1, iadj, B.items_adj[n], &bh->counter[1],
+                        st));
+    batch_adj_reduce_kernel<<<g_nr, T, 0, st>>>(pd, -1, W);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_recon_issue(const aexp_problem *probs, const BatchLayout &B, const aexp_recon_opts *o,
+                              const void *const *y, const float *lambda, int iters, void *const *x_out,
+                              double *lip_out, char *ws, cudaStream_t st) {
+    const int n = B.nprob;
+    ProbDesc *pd = (ProbDesc *)(ws + B.off_desc);
+    WsHeader *bh = (WsHeader *)(ws + B.off_hdr);
+    int *ifwd = (int *)(ws + B.off_items_fwd);
+    int *iadj = (int *)(ws + B.off_items_adj);
+    const int T = 256;
+
+    CK(batch_setup(probs, B, y, lambda, x_out, lip_out, ws, st));
     batch_transpose_y_kernel<<<dim3(cdiv(B.max_ntpcb, T), n), T, 0, st>>>(pd);
     CK(cudaGetLastError());
 

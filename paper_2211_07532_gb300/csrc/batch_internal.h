@@ -22,6 +22,11 @@ struct BatchLayout {
 };
 
 int batch_layout(const aexp_problem *probs, int nprob, const aexp_recon_opts *opts, BatchLayout *B);
+// Per-problem preparation, descriptors, item offsets and header reset (y, lambda, x_out
+// and lip_out may be null when only operator applications follow).
+cudaError_t batch_setup(const aexp_problem *probs, const BatchLayout &B, const void *const *y, const float *lambda,
+                        void *const *x_out, double *lip_out, char *ws, cudaStream_t st);
+cudaError_t batch_normal_once(const BatchLayout &B, const aexp_recon_opts *o, char *ws, cudaStream_t st);
 cudaError_t batch_recon_issue(const aexp_problem *probs, const BatchLayout &B, const aexp_recon_opts *o,
                               const void *const *y, const float *lambda, int iters, void *const *x_out,
                               double *lip_out, char *ws, cudaStream_t st);

@@ -57,21 +57,28 @@ int check_ws(const void *ws, size_t have, size_t need) {
 struct PrepRecord {
     aexp_problem prob;
     int precision;
+    int items_per_sm;  // layout granularity the workspace was prepared with (0 = default)
 };
 std::mutex g_mu;
 std::unordered_map<const void *, PrepRecord> g_prepared;
 
 bool same_problem(const aexp_problem &a, const aexp_problem &b) { return memcmp(&a, &b, sizeof(a)) == 0; }
 
-void record_prepared(const void *ws, const aexp_problem *p, int precision) {
-    std::lock_guard<std::mutex> lk(g_mu);
-    g_prepared[ws] = PrepRecord{*p, precision};
+// the granularity a layout actually uses (0 stands for the precision's default)
+int effective_items(int precision, int items_per_sm) {
+    return items_per_sm > 0 ? items_per_sm : default_items_per_sm(precision);
 }
 
-bool is_prepared(const void *ws, const aexp_problem *p, int precision) {
+void record_prepared(const void *ws, const aexp_problem *p, int precision, int items_per_sm = 0) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_prepared[ws] = PrepRecord{*p, precision, effective_items(precision, items_per_sm)};
+}
+
+bool is_prepared(const void *ws, const aexp_problem *p, int precision, int items_per_sm = 0) {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_prepared.find(ws);
-    return it != g_prepared.end() && same_problem(it->second.prob, *p) && it->second.precision == precision;
+    return it != g_prepared.end() && same_problem(it->second.prob, *p) && it->second.precision == precision &&
+           it->second.items_per_sm == effective_items(precision, items_per_sm);
 }
 
 // One captured cs_recon per workspace, relaunched while every argument is identical.
@@ -94,6 +101,7 @@ int check_opts(const aexp_recon_opts *o) {
     if (o->wavelet != AEXP_WAVELET_HAAR && o->wavelet != AEXP_WAVELET_DB4) return AEXP_ERR_INVALID_ARG;
     if (o->levels < 1 || o->levels > 12) return AEXP_ERR_INVALID_ARG;
     if (!(o->lipschitz > 0.0) && o->n_power < 1) return AEXP_ERR_INVALID_ARG;
+    if (o->items_per_sm < 0 || o->items_per_sm > 256) return AEXP_ERR_INVALID_ARG;
     if (!aligned(o->x0, 8) || !aligned(o->power_init, 8)) return AEXP_ERR_MISALIGNED;
     return AEXP_OK;
 }
@@ -101,6 +109,11 @@ int check_opts(const aexp_recon_opts *o) {
 }  // namespace
 
 void aexp::aexp_set_last_cuda_error(int e) { g_last_cuda_error = e; }
+
+void aexp::forget_prepared(const void *ws) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_prepared.erase(ws);
+}
 
 extern "C" {
 
@@ -198,6 +211,7 @@ void aexp_recon_opts_default(aexp_recon_opts *o) {
     o->x0 = nullptr;
     o->power_init = nullptr;
     o->use_graph = 1;
+    o->items_per_sm = 0;
 }
 
 int aexp_recon_workspace_size(const aexp_problem *prob, const aexp_recon_opts *opts, size_t *bytes) {
@@ -230,7 +244,7 @@ int cs_recon(const aexp_problem *prob, const void *y, float lambda, int iters, c
         e = recon_issue(prob, R, opts, (const float2 *)y, lambda, iters, (float2 *)x_out,
                         lipschitz_out, w, st);
         if (e != cudaSuccess) return cuda_fail(e);
-        record_prepared(ws, prob, opts->precision);
+        record_prepared(ws, prob, opts->precision, opts->items_per_sm);
         return AEXP_OK;
     }
 
@@ -270,7 +284,7 @@ int cs_recon(const aexp_problem *prob, const void *y, float lambda, int iters, c
     }
     e = cudaGraphLaunch(ge.exec, st);
     if (e != cudaSuccess) return cuda_fail(e);
-    g_prepared[ws] = PrepRecord{*prob, opts->precision};
+    g_prepared[ws] = PrepRecord{*prob, opts->precision, effective_items(opts->precision, opts->items_per_sm)};
     return AEXP_OK;
 }
 
@@ -384,7 +398,7 @@ int aexp_unroll_workspace_size(const aexp_problem *prob, const aexp_recon_opts *
     if ((rc = check_opts(opts))) return rc;
     if (!bytes) return AEXP_ERR_INVALID_ARG;
     RecLayout R;
-    rec_layout(prob, opts, &R, 152 * 8, 1);
+    rec_layout(prob, opts, &R, -1, 1);
     *bytes = R.bytes;
     return AEXP_OK;
 }
@@ -396,9 +410,9 @@ static int unroll_common(const aexp_problem *prob, const aexp_recon_opts *opts, 
     if ((rc = check_opts(opts))) return rc;
     if (!y || !(lipschitz > 0.0)) return AEXP_ERR_INVALID_ARG;
     if (!aligned(y, 8)) return AEXP_ERR_MISALIGNED;
-    rec_layout(prob, opts, R, 152 * 8, 1);
+    rec_layout(prob, opts, R, -1, 1);
     if ((rc = check_ws(ws, ws_bytes, R->bytes))) return rc;
-    if (!is_prepared(ws, prob, opts->precision)) return AEXP_ERR_NOT_PREPARED;
+    if (!is_prepared(ws, prob, opts->precision, opts->items_per_sm)) return AEXP_ERR_NOT_PREPARED;
     return AEXP_OK;
 }
 

@@ -6,15 +6,14 @@
 namespace aexp {
 
 namespace {
-constexpr int kTargetBlocks = 152 * 4 * 4;  // SMs x resident blocks x waves
-
 int pad_terms(int n) { return n <= 4 ? 4 : n <= 8 ? 8 : n <= 12 ? 12 : 20; }
 int pad_coils(int n) { return n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : n <= 20 ? 20 : 32; }
 // tensor-core forms: N = 2 * CB must be a multiple of 16 with a power-of-two half for TMEM loads
 int pad_coils_tc(int n) { return n <= 8 ? 8 : n <= 16 ? 16 : 32; }
 }  // namespace
 
-int op_layout(const aexp_problem *p, int precision, OpLayout *L, int tc_target_items) {
+int op_layout(const aexp_problem *p, int precision, OpLayout *L, int target_items) {
+    if (target_items <= 0) target_items = items_target(precision, 0);
     OpLayout o{};
     o.nx = p->nx;
     o.ny = p->ny;
@@ -38,7 +37,7 @@ int op_layout(const aexp_problem *p, int precision, OpLayout *L, int tc_target_i
     o.fwd_tblocks = o.ntp / (kFwdThreads * o.fwd_mt);
     {
         int by_sum = cdiv(o.ntiles, 32);                       // <= 32 tiles (2048 voxels) per block
-        int by_occ = cdiv(kTargetBlocks, o.fwd_tblocks);
+        int by_occ = cdiv(target_items, o.fwd_tblocks);
         int s = std::max(by_sum, by_occ);
         s = std::min(s, o.ntiles);
         o.fwd_tiles_per_split = cdiv(o.ntiles, s);
@@ -50,7 +49,7 @@ int op_layout(const aexp_problem *p, int precision, OpLayout *L, int tc_target_i
     {
         int nstage = o.ntp / kAdjStageT;
         int by_sum = cdiv(o.ntp, 2048);
-        int by_occ = cdiv(kTargetBlocks, o.adj_vblocks);
+        int by_occ = cdiv(target_items, o.adj_vblocks);
         int s = std::min(std::max(by_sum, by_occ), nstage);
         int stages_per = cdiv(nstage, s);
         o.adj_t_per_split = stages_per * kAdjStageT;
@@ -61,13 +60,13 @@ int op_layout(const aexp_problem *p, int precision, OpLayout *L, int tc_target_i
         // one CTA (128 samples or 2 tiles) per SM at a time; split the reduction dimension
         // so the grid covers ~8 waves
         const int tblocks = o.ntp / 128;
-        int s = std::min(std::max(cdiv(tc_target_items, tblocks), 1), o.ntiles);
+        int s = std::min(std::max(cdiv(target_items, tblocks), 1), o.ntiles);
         o.fwd_tblocks = tblocks;
         o.fwd_tiles_per_split = cdiv(o.ntiles, s);
         o.fwd_splits = cdiv(o.ntiles, o.fwd_tiles_per_split);
         o.adj_vblocks = cdiv(o.ntiles, 2);
         const int nstage = o.ntp / kAdjStageT;
-        s = std::min(std::max(cdiv(tc_target_items, o.adj_vblocks), 1), nstage);
+        s = std::min(std::max(cdiv(target_items, o.adj_vblocks), 1), nstage);
         o.adj_t_per_split = cdiv(nstage, s) * kAdjStageT;
         o.adj_splits = cdiv(o.ntp, o.adj_t_per_split);
     }
@@ -125,10 +124,11 @@ int wave_layout(int nx, int ny, int wavelet, int levels, WaveLayout *W) {
     return AEXP_OK;
 }
 
-int rec_layout(const aexp_problem *p, const aexp_recon_opts *opt, RecLayout *R, int tc_target_items,
+int rec_layout(const aexp_problem *p, const aexp_recon_opts *opt, RecLayout *R, int target_items,
                int with_grad) {
     RecLayout r{};
-    int rc = op_layout(p, opt->precision, &r.op, tc_target_items);
+    if (target_items < 0) target_items = items_target(opt->precision, opt->items_per_sm);
+    int rc = op_layout(p, opt->precision, &r.op, target_items);
     if (rc) return rc;
     rc = wave_layout(p->nx, p->ny, opt->wavelet, opt->levels, &r.wv);
     if (rc) return rc;

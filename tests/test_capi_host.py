@@ -126,3 +126,40 @@ def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(ax, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="missing"):
         ax.lib()
+
+
+def test_items_per_sm_sizes_and_validation(L):
+    """The work-item granularity changes only the partial-sum space; the tuner's workspace
+    covers every candidate; out-of-range values are rejected on the host."""
+    import paper_2211_07532_gb300 as ax
+    p = _fake_problem(nx=200, ny=200, nt=24000, nc=32, nl=16)
+    sizes = {}
+    for prec in (ax.FP32, ax.BF16_TC, ax.FP16X2_TC):
+        for ips in (0, 2, 4, 8, 16, 32):
+            o = ax.CReconOpts()
+            L.aexp_recon_opts_default(ctypes.byref(o))
+            o.precision, o.items_per_sm = prec, ips
+            n = ctypes.c_size_t()
+            assert L.aexp_recon_workspace_size(ctypes.byref(p), ctypes.byref(o), ctypes.byref(n)) == 0
+            sizes[(prec, ips)] = n.value
+        # finer granularity -> more split partial sums -> never a smaller workspace
+        assert sizes[(prec, 2)] <= sizes[(prec, 8)] <= sizes[(prec, 32)]
+        # 0 is the default: 16 per SM for FP32, 8 for the tensor cores
+        assert sizes[(prec, 0)] == sizes[(prec, 16 if prec == ax.FP32 else 8)]
+        o.items_per_sm = 0
+        need = ctypes.c_size_t()
+        assert L.aexp_autotune_workspace_size(ctypes.byref(p), 1, ctypes.byref(o), ctypes.byref(need)) == 0
+        assert need.value == max(sizes[(prec, c)] for c in (2, 4, 8, 16, 32))
+    for bad in (-1, 257):
+        o.items_per_sm = bad
+        assert L.aexp_recon_workspace_size(ctypes.byref(p), ctypes.byref(o), ctypes.byref(n)) == -1
+    # the batched layout exists for the tensor-core precisions only
+    o.items_per_sm = 0
+    o.precision = ax.FP32
+    arr = (ax.CProblem * 2)(p, _fake_problem(nx=148, ny=148, nt=8767, nc=32, nl=16))
+    assert L.aexp_autotune_workspace_size(arr, 2, ctypes.byref(o), ctypes.byref(need)) == -3
+    o.precision = ax.BF16_TC
+    assert L.aexp_autotune_workspace_size(arr, 2, ctypes.byref(o), ctypes.byref(need)) == 0
+    # no device call is made for a null workspace
+    best = ctypes.c_int()
+    assert L.aexp_autotune(arr, 2, ctypes.byref(o), None, 0, None, ctypes.byref(best), None) == -1
