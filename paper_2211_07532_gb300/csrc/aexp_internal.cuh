@@ -55,6 +55,7 @@ struct ProbDesc {
     const float *khi_t, *f0, *dh;
     const float2 *Sp;
     unsigned char *bpk, *ypk;
+    const unsigned char *kph, *dhph;  // BF16 form: phase-GEMM operands
     float *fpart;
     float2 *apart, *rt;
     WsHeader *hdr;
@@ -85,6 +86,9 @@ struct OpLayout {
     // byte offsets into the workspace
     size_t off_hdr, off_khi_l, off_klo_l, off_khi_t, off_h0, off_dh, off_f0, off_S, off_b,
         off_fpart, off_yt, off_apart, off_ypk, off_desc, off_hp;
+    // BF16 form: TF32 hi | lo operands of the phase GEMM (k rows per 128 samples, basis
+    // offsets per pair of tiles)
+    size_t off_kph, off_dhph;
     int fwd_items, adj_items;  // persistent tensor-core work items
     size_t bytes;
 };
@@ -160,6 +164,15 @@ cudaError_t op_adjoint_reduce_step(const OpLayout &L, char *ws, const float2 *z,
 ProbDesc make_op_desc(const OpLayout &L, char *ws);
 cudaError_t write_desc(const ProbDesc &d, ProbDesc *dst, cudaStream_t st);
 int num_sms();
+
+// BF16 form with the phase on the tensor cores (op_tc_phase.cu): operand preparation and the
+// launches (same contract as batch_forward_tc / batch_adjoint_tc).
+cudaError_t op_prepare_phase_operands(const OpLayout &L, char *ws, cudaStream_t st);
+cudaError_t tcp_forward(int CB, const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *x, int src,
+                        const int *item_off, int total_items, int *counter, cudaStream_t st);
+cudaError_t tcp_adjoint(int CB, const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *yt, int src,
+                        const int *item_off, int total_items, int *counter, cudaStream_t st);
+constexpr size_t kPhaseBlockBytes = 32768;  // TF32 hi | lo images of 128 rows x 32 K slots
 
 // Tensor-core forms (op_tc.cu): the forward packs S*x itself; the adjoint packs yt.
 cudaError_t op_forward_tc(const OpLayout &L, const float2 *x, char *ws, cudaStream_t st);

@@ -94,6 +94,9 @@ int op_layout(const aexp_problem *p, int precision, OpLayout *L, int target_item
     o.off_ypk = take(precision == AEXP_FP32 ? 0 : npk * sizeof(float2) * (size_t)o.ntp * o.CB);
     o.off_desc = take(sizeof(ProbDesc));
     o.off_hp = take(sizeof(float) * (size_t)o.LP * o.nr_pad);
+    const bool tcp = precision == AEXP_BF16_TC;
+    o.off_kph = take(tcp ? (size_t)(o.ntp / 128) * kPhaseBlockBytes : 0);
+    o.off_dhph = take(tcp ? (size_t)cdiv(o.ntiles, 2) * kPhaseBlockBytes : 0);
     o.fwd_items = o.fwd_tblocks * o.fwd_splits;
     o.adj_items = o.adj_vblocks * o.adj_splits;
     o.bytes = off;
@@ -195,6 +198,8 @@ ProbDesc make_op_desc(const OpLayout &L, char *ws) {
     d.Sp = (const float2 *)(ws + L.off_S);
     d.bpk = (unsigned char *)(ws + L.off_b);
     d.ypk = (unsigned char *)(ws + L.off_ypk);
+    d.kph = (const unsigned char *)(ws + L.off_kph);
+    d.dhph = (const unsigned char *)(ws + L.off_dhph);
     d.fpart = (float *)(ws + L.off_fpart);
     d.apart = (float2 *)(ws + L.off_apart);
     d.rt = (float2 *)(ws + L.off_yt);

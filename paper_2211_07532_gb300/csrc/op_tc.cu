@@ -43,148 +43,13 @@
 // epilogue warps add a finished set into FP32 partial sums (forward: the item's rows of
 // the partial-sum buffer; adjoint: the coil-combined value in registers) and release the
 // set through an mbarrier that the MMA thread waits on before reusing it.
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-
 #include <algorithm>
 
-#include "aexp_internal.cuh"
-#include "tc_ptx.cuh"
+#include "tc_common.cuh"
 
 namespace aexp {
 
 namespace {
-
-constexpr int kTcGen = 512;              // generator threads (16 warps)
-constexpr int kTcThreads = kTcGen + 32;  // + MMA/producer warp
-constexpr int kProdWarp = kTcGen / 32;
-constexpr int kRows = 128;               // M
-constexpr int kCols = 64;                // voxels (forward) or samples (adjoint) per stage
-constexpr int kA_BYTES = kRows * kCols * 2 * 2;  // 128 rows x 128 bf16 = 32 KB
-constexpr float kTwoPi = 6.283185307179586f;
-constexpr int kSpin = 1 << 22;
-constexpr int kNBMax = 4;  // staged B tiles (BF16: 4, FP16 hi+lo: 2)
-constexpr float kLoScale = 2048.f;           // 2^11: scale of the low parts
-constexpr float kLoInv = 1.f / 2048.f;
-constexpr int kPromote = 8;                  // FP16 hi+lo: stages per accumulator chunk
-
-// Per-form constants: stages of B, bytes of one generated A stage, operand images per tile.
-template <bool HL>
-struct TcForm {
-    static constexpr int NB = HL ? 2 : 4;
-    static constexpr int NPK = HL ? 2 : 1;
-    static constexpr unsigned A_STAGE = NPK * kA_BYTES;
-};
-
-// TMEM columns of one accumulator (N = 2C columns rounded up to a power of two >= 32).
-constexpr uint32_t tmem_acc_cols(int N) { return N <= 32 ? 32u : 64u; }
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t *>(&v);
-}
-
-// (a, b) -> FP16 pairs hi = (fp16 a, fp16 b) and lo = fp16(2^11 (a - hi.a)), fp16(2^11 (b - hi.b)).
-// The differences are exact in FP32 (hi is the rounding of the same value).
-__device__ __forceinline__ void split_f16(float a, float b, uint32_t &hi, uint32_t &lo) {
-    const __half2 h = __floats2half2_rn(a, b);
-    const float2 hf = __half22float2(h);
-    const __half2 l = __floats2half2_rn((a - hf.x) * kLoScale, (b - hf.y) * kLoScale);
-    hi = *reinterpret_cast<const uint32_t *>(&h);
-    lo = *reinterpret_cast<const uint32_t *>(&l);
-}
-
-// Power-of-two scale 2^e (or 2^-e when `inverse`) that maps a largest component with bit
-// pattern `bits` into [2^13, 2^14); zero (or subnormal) maxima give the largest scale, a
-// non-finite one a small scale (the non-finite values then propagate).
-__device__ __forceinline__ float hl_scale(unsigned bits, bool inverse) {
-    const int ex = (int)((bits >> 23) & 0xffu);
-    int se = 140 - max(ex, 1);  // 13 - (ex - 127)
-    se = max(-126, min(126, se));
-    return __int_as_float((127 + (inverse ? -se : se)) << 23);
-}
-
-// Bounded wait that also gives up as soon as another thread of the CTA has aborted.
-__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, unsigned parity, volatile int *abort_flag,
-                                              int *status) {
-    for (int i = 0; i < kSpin; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 255) == 255 && *abort_flag) return false;
-    }
-    *abort_flag = 1;
-    set_status(status, AEXP_ERR_DEVICE_TIMEOUT);
-    return false;
-}
-
-__device__ __forceinline__ uint32_t align1024(uint32_t a) { return (a + 1023u) & ~1023u; }
-
-__device__ __forceinline__ int find_problem(const int *item_off, int nprob, int item) {
-    int lo = 0, hi = nprob - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (item_off[mid] <= item) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-// Shared state of a persistent tensor-core CTA.
-struct TcShared {
-    uint64_t bfull[kNBMax], bfree[kNBMax], afull[2], afree[2], accfree[2];
-    uint32_t tmem_base;
-    int abort_flag;
-    int item[2], stop[2];
-};
-
-__device__ __forceinline__ void tc_setup(TcShared &sh, int tid, int warp, uint32_t ncols, unsigned acc_count) {
-    if (tid == 0) {
-        for (int s = 0; s < kNBMax; ++s) {
-            mbar_init(&sh.bfull[s], 1);
-            mbar_init(&sh.bfree[s], 1);
-        }
-        for (int s = 0; s < 2; ++s) {
-            mbar_init(&sh.afull[s], kTcGen);
-            mbar_init(&sh.afree[s], 1);
-            mbar_init(&sh.accfree[s], acc_count);
-        }
-        sh.abort_flag = 0;
-        fence_mbar_init();
-    }
-    if (warp == kProdWarp) {
-        tc::tmem_alloc(&sh.tmem_base, ncols);
-        tc::tmem_relinquish();
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-}
-
-// Next work item, the same for every thread of the CTA (two slots: a thread still reading
-// one slot never races the write of the other); false when the queue is empty or aborted.
-__device__ __forceinline__ bool tc_next_item(TcShared &sh, int tid, int iter, int *counter, int total, int &item) {
-    const int slot = iter & 1;
-    if (tid == 0) {
-        int it = atomicAdd(counter, 1);
-        sh.item[slot] = it;
-        sh.stop[slot] = (it >= total) || sh.abort_flag;
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    item = sh.item[slot];
-    return !sh.stop[slot];
-}
-
-__device__ __forceinline__ void tc_teardown(TcShared &sh, int warp, uint32_t ncols, int last_issued, int *status) {
-    if (warp == kProdWarp && (threadIdx.x & 31) == 0 && last_issued >= 0)
-        mbar_wait_bounded(&sh.afree[last_issued & 1], (last_issued >> 1) & 1, status);  // drain
-    tc::fence_before_sync();
-    __syncthreads();
-    if (warp == kProdWarp) {
-        tc::fence_after_sync();
-        tc::tmem_dealloc(sh.tmem_base, ncols);
-    }
-}
 
 // Issue the MMAs of one stage (8 of K = 16; FP16 hi+lo: 24, the cross products into the
 // second accumulator) and commit both stage barriers.
@@ -192,27 +57,28 @@ template <int N, bool HL>
 __device__ __forceinline__ void tc_mma_stage(TcShared &sh, uint32_t tmem, const unsigned char *A,
                                              const unsigned char *B, bool first, int sa, int sb) {
     constexpr uint32_t IDESC = tc::idesc_f16(kRows, N, HL ? 0 : 1);
-    const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+    // one descriptor per operand image; the K steps advance it
+    const uint64_t da = tc::sdesc_k128(smem_u32(A)), db = tc::sdesc_k128(smem_u32(B));
 #pragma unroll
     for (int kk = 0; kk < 8; ++kk) {
         const uint32_t koff = (uint32_t)((kk >> 2) * (kRows * 128) + (kk & 3) * 32);
         const uint32_t kofb = (uint32_t)((kk >> 2) * (N * 128) + (kk & 3) * 32);
-        tc::mma_f16(tmem, tc::sdesc_k128(a0 + koff), tc::sdesc_k128(b0 + kofb), IDESC, !(first && kk == 0));
+        tc::mma_f16(tmem, tc::sdesc_advance(da, koff), tc::sdesc_advance(db, kofb), IDESC, !(first && kk == 0));
     }
     if constexpr (HL) {
         const uint32_t t2 = tmem + tmem_acc_cols(N);
-        const uint32_t a1 = a0 + kA_BYTES, b1 = b0 + N * 256;
+        const uint64_t da1 = tc::sdesc_advance(da, kA_BYTES), db1 = tc::sdesc_advance(db, N * 256);
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
             const uint32_t koff = (uint32_t)((kk >> 2) * (kRows * 128) + (kk & 3) * 32);
             const uint32_t kofb = (uint32_t)((kk >> 2) * (N * 128) + (kk & 3) * 32);
-            tc::mma_f16(t2, tc::sdesc_k128(a0 + koff), tc::sdesc_k128(b1 + kofb), IDESC, !(first && kk == 0));
+            tc::mma_f16(t2, tc::sdesc_advance(da, koff), tc::sdesc_advance(db1, kofb), IDESC, !(first && kk == 0));
         }
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
             const uint32_t koff = (uint32_t)((kk >> 2) * (kRows * 128) + (kk & 3) * 32);
             const uint32_t kofb = (uint32_t)((kk >> 2) * (N * 128) + (kk & 3) * 32);
-            tc::mma_f16(t2, tc::sdesc_k128(a1 + koff), tc::sdesc_k128(b0 + kofb), IDESC, 1u);
+            tc::mma_f16(t2, tc::sdesc_advance(da1, koff), tc::sdesc_advance(db, kofb), IDESC, 1u);
         }
     }
     tc::mma_commit(&sh.afree[sa]);
@@ -761,94 +627,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_teardown(sh, warp, TMEM_COLS, last_issued, &pd[0].hdr->status);
 }
 
-// ---------------------------------------------------------------------------
-// Packing of the B operands into the swizzled K-major smem image, one launch for all
-// problems (grid.y = problem; blocks beyond a problem's extent return at once)
-// ---------------------------------------------------------------------------
-
-// Four (first, second) pairs -> one 16-byte chunk of the B image(s) at `dst` (FP16 hi+lo:
-// hi at dst, lo' one image of `img_bytes` further).
-template <bool HL>
-__device__ __forceinline__ void store_b_chunk(unsigned char *dst, unsigned img_bytes, const float (&a)[4],
-                                              const float (&b)[4]) {
-    uint32_t w[4], wl[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        if constexpr (HL) split_f16(a[u], b[u], w[u], wl[u]);
-        else w[u] = pack_bf16(a[u], b[u]);
-    }
-    *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
-    if constexpr (HL) *reinterpret_cast<uint4 *>(dst + img_bytes) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
-}
-
-// Forward: coil-weighted image b_c(v) = S_c(v) x(v) of every 8x8 tile, rows n < C carry
-// (Re b, -Im b), rows C + c carry (Im b, Re b) at K positions (2v, 2v+1).  The image is
-// `x` when given (single problem) or the descriptor's vec[src].  FP16 hi+lo: b is scaled by
-// the power of two fixed by the problem's amax[0].
-template <int CB, bool HL>
-__global__ void pack_b_fwd_kernel(const ProbDesc *__restrict__ pd, const float2 *__restrict__ x, int src) {
-    constexpr int N = 2 * CB;
-    constexpr int NPK = HL ? 2 : 1;
-    const ProbDesc &P = pd[blockIdx.y];
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // (tile, n, chunk)
-    if (i >= (size_t)P.ntiles * N * 16) return;
-    const float2 *img = x ? x : P.vec[src];
-    const float sc = HL ? hl_scale(P.hdr->amax[0], false) : 1.f;
-    const int jj = (int)(i % 16);
-    const int n = (int)((i / 16) % N);
-    const int tile = (int)(i / (16 * N));
-    const int c = n < CB ? n : n - CB;
-    float a[4], b[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int v = 4 * jj + u;
-        const int ix = (tile % P.ntx) * kTileSide + v % kTileSide, iy = (tile / P.ntx) * kTileSide + v / kTileSide;
-        float br = 0.f, bi = 0.f;
-        if (ix < P.nx && iy < P.ny) {
-            float2 s = P.Sp[((size_t)tile * kTileVox + v) * CB + c];
-            float2 xv = img[(size_t)iy * P.nx + ix];
-            br = (s.x * xv.x - s.y * xv.y) * sc;
-            bi = (s.x * xv.y + s.y * xv.x) * sc;
-        }
-        a[u] = n < CB ? br : bi;
-        b[u] = n < CB ? -bi : br;
-    }
-    unsigned char *dst =
-        P.bpk + (size_t)tile * (NPK * N * 256) + (jj >> 3) * (N * 128) + tc::swz128(n, jj & 7);
-    store_b_chunk<HL>(dst, N * 256, a, b);
-}
-
-// Adjoint: k-space yt[t][c] (or the descriptor's vec[src], or rt when src < 0) per stage of
-// 64 samples; rows n < C carry (Re y, -Im y), rows C + c carry (Im y, Re y) at K positions
-// (2s, 2s+1).  FP16 hi+lo: y is scaled by the power of two fixed by amax[1].
-template <int CB, bool HL>
-__global__ void pack_y_adj_kernel(const ProbDesc *__restrict__ pd, const float2 *__restrict__ yt, int src) {
-    constexpr int N = 2 * CB;
-    constexpr int NPK = HL ? 2 : 1;
-    const ProbDesc &P = pd[blockIdx.y];
-    const int nstages = P.ntp / kCols;
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // (stage, n, chunk)
-    if (i >= (size_t)nstages * N * 16) return;
-    const float2 *y = yt ? yt : (src >= 0 ? P.vec[src] : P.rt);
-    const float sc = HL ? hl_scale(P.hdr->amax[1], false) : 1.f;
-    const int jj = (int)(i % 16);
-    const int n = (int)((i / 16) % N);
-    const int st = (int)(i / (16 * N));
-    const int c = n < CB ? n : n - CB;
-    float a[4], b[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const size_t t = (size_t)st * kCols + 4 * jj + u;
-        float2 v = y[t * CB + c];
-        v.x *= sc;
-        v.y *= sc;
-        a[u] = n < CB ? v.x : v.y;
-        b[u] = n < CB ? -v.y : v.x;
-    }
-    unsigned char *dst = P.ypk + (size_t)st * (NPK * N * 256) + (jj >> 3) * (N * 128) + tc::swz128(n, jj & 7);
-    store_b_chunk<HL>(dst, N * 256, a, b);
-}
-
 // ---- FP16 hi+lo: largest component of the operand to be packed (atomic max on the bit
 // pattern of a non-negative float, which orders like the value) ----
 __global__ void amax_reset_kernel(const ProbDesc *__restrict__ pd, int nprob, int which) {
@@ -984,8 +762,7 @@ cudaError_t launch_adj_tc(const ProbDesc *pd, int nprob, int max_pack_blocks, co
     return cudaGetLastError();
 }
 
-#define AEXP_TC_HL(FN, CBV, LPV, ...)                               \
-    return HLv ? FN<CBV, LPV, true>(__VA_ARGS__) : FN<CBV, LPV, false>(__VA_ARGS__);
+#define AEXP_TC_HL(FN, CBV, LPV, ...) return FN<CBV, LPV, true>(__VA_ARGS__);
 #define AEXP_TC_LP(FN, CBV, ...)                         \
     switch (LPv) {                                       \
         case 4: AEXP_TC_HL(FN, CBV, 4, __VA_ARGS__)      \
@@ -1014,18 +791,22 @@ cudaError_t write_desc(const ProbDesc &d, ProbDesc *dst, cudaStream_t st) {
 // (written by op_prepare for the tensor-core precisions).
 cudaError_t op_forward_tc(const OpLayout &L, const float2 *x, char *ws, cudaStream_t st) {
     const int CBv = L.CB, LPv = L.LP;
-    const bool HLv = L.precision == AEXP_FP16X2_TC;
     WsHeader *hdr = (WsHeader *)(ws + L.off_hdr);
     const ProbDesc *pd = (const ProbDesc *)(ws + L.off_desc);
+    if (L.precision == AEXP_BF16_TC)
+        return tcp_forward(L.CB, pd, 1, fwd_pack_blocks(L.ntiles, L.CB), x, 0, &hdr->item_off[0], L.fwd_items,
+                           &hdr->counter[0], st);
     AEXP_TC_DISPATCH(launch_fwd_tc, pd, 1, fwd_pack_blocks(L.ntiles, L.CB), x, 0, &hdr->item_off[0], L.fwd_items,
                      &hdr->counter[0], st)
 }
 
 cudaError_t op_adjoint_tc(const OpLayout &L, const float2 *yt, char *ws, cudaStream_t st) {
     const int CBv = L.CB, LPv = L.LP;
-    const bool HLv = L.precision == AEXP_FP16X2_TC;
     WsHeader *hdr = (WsHeader *)(ws + L.off_hdr);
     const ProbDesc *pd = (const ProbDesc *)(ws + L.off_desc);
+    if (L.precision == AEXP_BF16_TC)
+        return tcp_adjoint(L.CB, pd, 1, adj_pack_blocks(L.ntp, L.CB), yt, -1, &hdr->item_off[2], L.adj_items,
+                           &hdr->counter[1], st);
     AEXP_TC_DISPATCH(launch_adj_tc, pd, 1, adj_pack_blocks(L.ntp, L.CB), yt, -1, &hdr->item_off[2], L.adj_items,
                      &hdr->counter[1], st)
 }
@@ -1033,14 +814,16 @@ cudaError_t op_adjoint_tc(const OpLayout &L, const float2 *yt, char *ws, cudaStr
 cudaError_t batch_forward_tc(int precision, int CB, int LP, const ProbDesc *pd, int nprob, int max_pack_blocks,
                              int src, const int *item_off, int total_items, int *counter, cudaStream_t st) {
     const int CBv = CB, LPv = LP;
-    const bool HLv = precision == AEXP_FP16X2_TC;
+    if (precision == AEXP_BF16_TC)
+        return tcp_forward(CB, pd, nprob, max_pack_blocks, nullptr, src, item_off, total_items, counter, st);
     AEXP_TC_DISPATCH(launch_fwd_tc, pd, nprob, max_pack_blocks, nullptr, src, item_off, total_items, counter, st)
 }
 
 cudaError_t batch_adjoint_tc(int precision, int CB, int LP, const ProbDesc *pd, int nprob, int max_pack_blocks,
                              int src, const int *item_off, int total_items, int *counter, cudaStream_t st) {
     const int CBv = CB, LPv = LP;
-    const bool HLv = precision == AEXP_FP16X2_TC;
+    if (precision == AEXP_BF16_TC)
+        return tcp_adjoint(CB, pd, nprob, max_pack_blocks, nullptr, src, item_off, total_items, counter, st);
     AEXP_TC_DISPATCH(launch_adj_tc, pd, nprob, max_pack_blocks, nullptr, src, item_off, total_items, counter, st)
 }
 

@@ -1,0 +1,583 @@
+// A_exp and A_exp^H in the BF16 form with the phase computed on the tensor cores as well.
+//
+// Inside a work item the phase offsets of a stage are a small matrix product,
+//   off(t, v) = sum_l khi(t, l) dh(v, l)        (t: 128 samples or 64 per stage, v: voxels,
+//                                                l: field terms incl. B0, padded to 8/16/24)
+// with khi = k / 2pi in turns and dh the basis offsets from the tile's reference voxel
+// (the same quantities the CUDA-core generators sum with FMAs).  It runs as tcgen05.mma
+// kind::tf32 into a TMEM tile, each factor split x = x_hi + x_lo in TF32 (x_hi rounded to
+// 10 mantissa bits, x_lo = x - x_hi rounded again) and the products hi*hi + hi*lo + lo*hi
+// accumulated in FP32: relative error ~2^-21 of sum_l |khi dh|, about 1e-6 turn for the few
+// turns an 8x8 tile spans, far below the BF16 rounding of E (2^-9).
+//
+// Generators then read their row's phase offsets of the stage with one tcgen05.ld (in
+// radians: the k operand carries the factor 2 pi), add 2 pi f0(tile, t) with the tile's
+// tabulated reference phase f0 in [-1/2, 1/2) turn, take one MUFU sincos and store the BF16
+// encoding tile; the contraction with the
+// coil-weighted image (or the k-space data) is the same tcgen05 kind::f16 GEMM as in the
+// CUDA-core-phase form.  The two GEMMs are issued by two threads of their own: the
+// contraction thread issues 8 MMAs per stage once the generators have stored A(g); the
+// phase thread fills four TMEM phase tiles, each as soon as the generators have read it.
+// The generators form two groups of 8 warps that take alternate stages, so that one group
+// computes while the other waits for its next stage.
+// (A 128-row MMA with N <= 64 occupies the tensor pipe for ~50 cycles, so one thread
+// issuing both GEMMs in turn would bound the stage rate.)
+//
+// Phase operands, prepared once per problem (TF32 images in the 128B-swizzled K-major
+// layout, 32 K slots = 128 bytes per row; each block is [hi 16 KB | lo 16 KB]):
+//   kph   per block of 128 samples, rows = samples:  forward A_phase; adjoint B_phase
+//         (the 64 rows of one stage are one half of a block)
+//   dhph  per pair of tiles, rows = 128 voxels:      adjoint A_phase; forward B_phase
+//         (the 64 rows of one tile are one half of a pair)
+#include <algorithm>
+
+#include "tc_common.cuh"
+
+namespace aexp {
+namespace {
+
+constexpr unsigned kHalfImg = 64 * 128;         // one 64-row TF32 image (hi or lo), 8 KB
+constexpr unsigned kApBytes = 2 * kRows * 128;  // item operand: hi | lo of 128 rows, 32 KB
+// TMEM: the contraction accumulates in columns 0..N-1, phase tile b (of 4) sits at 64 + 64 b
+constexpr uint32_t kPhBase = 64;
+constexpr int kPhBufs = 4;
+constexpr uint32_t kTmemCols = 512;
+
+__device__ __forceinline__ uint32_t phase_col(int g) { return kPhBase + 64u * (uint32_t)(g % kPhBufs); }
+
+// ---- operand preparation ----
+
+__device__ __forceinline__ void split_tf32_4(const float (&v)[4], uint4 &hi, uint4 &lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        h[u] = tc::tf32_rna(v[u]);
+        l[u] = tc::tf32_rna(v[u] - __uint_as_float(h[u]));
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// kph[block][hi | lo][row = sample % 128][slot] = 2 pi khi_t[sample][slot] (0 beyond LP): the
+// phase GEMM yields radians
+__global__ void prep_kph_kernel(const float *__restrict__ khi_t, int ntp, int LP, unsigned char *__restrict__ kph) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // (sample, chunk of 4 slots)
+    if (i >= (size_t)ntp * 8) return;
+    const int t = (int)(i / 8), c = (int)(i % 8);
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int l = 4 * c + u;
+        v[u] = l < LP ? kTwoPi * khi_t[(size_t)t * LP + l] : 0.f;
+    }
+    uint4 hi, lo;
+    split_tf32_4(v, hi, lo);
+    unsigned char *blk = kph + (size_t)(t / kRows) * kPhaseBlockBytes;
+    const uint32_t o = tc::swz128(t % kRows, c);
+    *reinterpret_cast<uint4 *>(blk + o) = hi;
+    *reinterpret_cast<uint4 *>(blk + kPhaseBlockBytes / 2 + o) = lo;
+}
+
+// dhph[pair][hi | lo][row = 64 (tile & 1) + voxel][slot] = dh[tile][voxel][slot] (0 beyond LP
+// and for the missing second tile of an odd count)
+__global__ void prep_dhph_kernel(const float *__restrict__ dh, int ntiles, int LP, unsigned char *__restrict__ dhph) {
+    const int npairs = (ntiles + 1) / 2;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // (pair, row, chunk)
+    if (i >= (size_t)npairs * kRows * 8) return;
+    const int c = (int)(i % 8);
+    const int r = (int)((i / 8) % kRows);
+    const int pair = (int)(i / (8 * kRows));
+    const int tile = 2 * pair + r / kTileVox, v = r % kTileVox;
+    float x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int l = 4 * c + u;
+        x[u] = (tile < ntiles && l < LP) ? dh[((size_t)tile * kTileVox + v) * LP + l] : 0.f;
+    }
+    uint4 hi, lo;
+    split_tf32_4(x, hi, lo);
+    unsigned char *blk = dhph + (size_t)pair * kPhaseBlockBytes;
+    const uint32_t o = tc::swz128(r, c);
+    *reinterpret_cast<uint4 *>(blk + o) = hi;
+    *reinterpret_cast<uint4 *>(blk + kPhaseBlockBytes / 2 + o) = lo;
+}
+
+// ---- kernels ----
+
+// Warp roles: 16 generator warps; warp 16 issues the contraction MMAs and owns TMEM; warp 17
+// loads the contraction operands (+ reference phases); warp 18 issues the phase MMAs; warp 19
+// loads the phase operands.  One lane of each non-generator warp works.
+constexpr int kMmaWarp = kTcGen / 32;
+constexpr int kLoadBWarp = kMmaWarp + 1;
+constexpr int kPhaseWarp = kMmaWarp + 2;
+constexpr int kLoadPWarp = kMmaWarp + 3;
+constexpr int kTcpThreads = kTcGen + 128;
+constexpr int kNP = 3;   // ring of per-stage phase operands (hi | lo images, 16 KB)
+constexpr int kNBB = 4;  // ring of per-stage contraction operands + reference phases
+
+// Shared-memory plan of both kernels (byte offsets from the 1024-aligned base):
+//   A[2] generated encoding tiles | AP item phase operand (hi | lo) | PH ring | B ring
+template <int N>
+struct TcpPlan {
+    static constexpr unsigned B_BYTES = N * 256;
+    static constexpr unsigned F_BYTES = kRows * 4;  // forward: 128 f0; adjoint: 2 x 64 f0
+    static constexpr unsigned BS = (B_BYTES + F_BYTES + 1023u) & ~1023u;  // B ring stride
+    static constexpr unsigned PS = 2 * kHalfImg;                          // PH ring stride
+    static constexpr unsigned OFF_AP = 2 * kA_BYTES;
+    static constexpr unsigned OFF_PH = OFF_AP + kApBytes;
+    static constexpr unsigned OFF_B = OFF_PH + kNP * PS;
+    static constexpr unsigned BYTES = OFF_B + kNBB * BS;
+};
+
+// Contraction of one stage: 8 MMAs of K = 16 (BF16) into columns 0..N-1.
+template <int N>
+__device__ __forceinline__ void contraction_mma(uint32_t tmem, uint64_t da, uint64_t db, bool first) {
+    constexpr uint32_t ID = tc::idesc_f16(kRows, N, 1);
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+        const uint32_t koff = (uint32_t)((kk >> 2) * (kRows * 128) + (kk & 3) * 32);
+        const uint32_t kofb = (uint32_t)((kk >> 2) * (N * 128) + (kk & 3) * 32);
+        tc::mma_f16(tmem, tc::sdesc_advance(da, koff), tc::sdesc_advance(db, kofb), ID, !(first && kk == 0));
+    }
+}
+
+// Phase GEMM of one stage into the tile at `d`: KS steps of 8 TF32 values, products
+// hi*hi + hi*lo + lo*hi.
+template <int KS>
+__device__ __forceinline__ void phase_mma_ks(uint32_t d, uint64_t ah, uint64_t al, uint64_t bh, uint64_t bl) {
+    constexpr uint32_t ID = tc::idesc_tf32(kRows, 64);
+#pragma unroll
+    for (int k = 0; k < KS; ++k)
+        tc::mma_tf32(d, tc::sdesc_advance(ah, 32 * k), tc::sdesc_advance(bh, 32 * k), ID, k > 0);
+#pragma unroll
+    for (int k = 0; k < KS; ++k) tc::mma_tf32(d, tc::sdesc_advance(ah, 32 * k), tc::sdesc_advance(bl, 32 * k), ID, 1u);
+#pragma unroll
+    for (int k = 0; k < KS; ++k) tc::mma_tf32(d, tc::sdesc_advance(al, 32 * k), tc::sdesc_advance(bh, 32 * k), ID, 1u);
+}
+
+__device__ __forceinline__ void phase_mma(int ks, uint32_t d, uint64_t ah, uint64_t al, uint64_t bh, uint64_t bl) {
+    if (ks <= 1) phase_mma_ks<1>(d, ah, al, bh, bl);
+    else if (ks == 2) phase_mma_ks<2>(d, ah, al, bh, bl);
+    else phase_mma_ks<3>(d, ah, al, bh, bl);
+}
+
+// Contraction thread, one item.
+template <int N>
+__device__ __forceinline__ void tcp_contraction_item(TcShared &sh, uint32_t tmem, unsigned char *base, int gs, int n,
+                                                     int *status) {
+    using PL = TcpPlan<N>;
+    for (int it = 0; it < n; ++it) {
+        const int g = gs + it, sa = g & 1, sb = g % kNBB;
+        if (!wait_or_abort(&sh.afull[sa], (g >> 1) & 1, &sh.abort_flag, status)) return;
+        if (!wait_or_abort(&sh.bfull[sb], (g / kNBB) & 1, &sh.abort_flag, status)) return;
+        tc::fence_after_sync();
+        contraction_mma<N>(tmem, tc::sdesc_k128(smem_u32(base + sa * kA_BYTES)),
+                           tc::sdesc_k128(smem_u32(base + PL::OFF_B + sb * PL::BS)), it == 0);
+        tc::mma_commit(&sh.afree[sa]);
+        tc::mma_commit(&sh.bfree[sb]);
+    }
+}
+
+// Phase thread, one item: the phases of stage g go into tile g % 4 once the generators have
+// read that tile for stage g - 4 and the stage's operand has landed.
+template <int N>
+__device__ __forceinline__ void tcp_phase_item(TcShared &sh, uint32_t tmem, unsigned char *base, int gs, int n,
+                                               int iter, int ks, int *status) {
+    using PL = TcpPlan<N>;
+    const uint64_t ah = tc::sdesc_k128(smem_u32(base + PL::OFF_AP));
+    const uint64_t al = tc::sdesc_k128(smem_u32(base + PL::OFF_AP + kApBytes / 2));
+    if (!wait_or_abort(&sh.apfull, iter & 1, &sh.abort_flag, status)) return;
+    for (int it = 0; it < n; ++it) {
+        const int g = gs + it, b = g % kPhBufs, sp = g % kNP;
+        if (g >= kPhBufs && !wait_or_abort(&sh.phfree[b], ((g - kPhBufs) / kPhBufs) & 1, &sh.abort_flag, status))
+            return;
+        if (!wait_or_abort(&sh.pfull[sp], (g / kNP) & 1, &sh.abort_flag, status)) return;
+        tc::fence_after_sync();
+        const uint32_t ph = smem_u32(base + PL::OFF_PH + sp * PL::PS);
+        phase_mma(ks, tmem + phase_col(g), ah, al, tc::sdesc_k128(ph), tc::sdesc_k128(ph + kHalfImg));
+        tc::mma_commit(&sh.phfull[b]);
+        tc::mma_commit(&sh.pfree[sp]);
+    }
+}
+
+// Ring loaders, one item: stage g's slot is refilled once the stage that used it last has
+// released it (slot releases are committed by the MMA threads).
+template <class Load>
+__device__ __forceinline__ void tcp_ring_item(uint64_t *free_bar, int depth, int gs, int n, volatile int *abort_flag,
+                                              int *status, Load load) {
+    for (int it = 0; it < n; ++it) {
+        const int g = gs + it, s = g % depth;
+        if (g >= depth && !wait_or_abort(&free_bar[s], ((g - depth) / depth) & 1, abort_flag, status)) return;
+        load(it, s);
+    }
+}
+
+// Teardown: both MMA threads commit to the drain barrier (count 2); the contraction thread
+// waits (bounded) until every MMA has completed; then TMEM is released.
+__device__ __forceinline__ void tcp_teardown(TcShared &sh, int tid, int warp, int *status) {
+    if (tid == kPhaseWarp * 32) tc::mma_commit(&sh.drain);
+    if (tid == kMmaWarp * 32) {
+        tc::mma_commit(&sh.drain);
+        mbar_wait_bounded(&sh.drain, 0, status);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == kMmaWarp) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(sh.tmem_base, kTmemCols);
+    }
+}
+
+// One generator thread's part of a stage (generators work in two groups of 8 warps that take
+// alternate stages; warp w of a group reads TMEM lanes 32 (w & 3) .. + 31 and owns the 32
+// columns 32 (w >> 2) .. + 31): its row's 32 phase offsets (TMEM; the tile is released to the
+// phase thread right after the read) plus the reference phases -> E (or conj E) as BF16 in 8
+// chunks of the A tile.  Forward: one reference phase per row (fsrc[0]); adjoint: one per
+// column (fsrc[0..31]).
+template <bool CONJ>
+__device__ __forceinline__ void generate_row(TcShared &sh, int g, uint32_t taddr, const float *fsrc,
+                                             unsigned char *A, int row, int ch) {
+    float ph[32];
+    tc::tmem_ld<32>(taddr, ph);
+    tc::tmem_ld_wait();
+    tc::fence_before_sync();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) tc::mbar_arrive(&sh.phfree[g % kPhBufs]);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        float f[4];
+        if constexpr (CONJ) {
+            const float4 w = reinterpret_cast<const float4 *>(fsrc)[c];
+            f[0] = w.x;
+            f[1] = w.y;
+            f[2] = w.z;
+            f[3] = w.w;
+        } else {
+            f[0] = f[1] = f[2] = f[3] = fsrc[0];
+        }
+        uint32_t w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            // angle = 2 pi f0 + offset (radians); f0 lies in [-1/2, 1/2) turn and the offset spans
+            // a few turns inside a tile, so the hardware sincos needs no further reduction (its
+            // error grows like |angle| x 2^-24, ~1e-6 here against 2^-9 for the BF16 rounding)
+            const float x = fmaf(f[u], kTwoPi, ph[4 * c + u]);
+            float sn, cs;
+            __sincosf(x, &sn, &cs);
+            w[u] = pack_bf16(cs, CONJ ? sn : -sn);  // E = cos - i sin, conj(E) = cos + i sin
+        }
+        const int j = 8 * ch + c;  // chunk of 4 columns: atom j >> 3, swizzle column j & 7
+        *reinterpret_cast<uint4 *>(A + (j >> 3) * (kRows * 128) + tc::swz128(row, j & 7)) =
+            make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// Generator waits of stage g (warp-uniform result): reference phases landed, phase tile
+// ready, A buffer free.
+__device__ __forceinline__ bool gen_waits(TcShared &sh, int g, int *status) {
+    bool ok = wait_or_abort(&sh.bfull[g % kNBB], (g / kNBB) & 1, &sh.abort_flag, status);
+    if (ok) ok = wait_or_abort(&sh.phfull[g % kPhBufs], (g / kPhBufs) & 1, &sh.abort_flag, status);
+    if (ok && g >= 2) ok = wait_or_abort(&sh.afree[g & 1], ((g - 2) >> 1) & 1, &sh.abort_flag, status);
+    return __all_sync(0xffffffffu, ok);
+}
+
+// Forward: item = (problem, block of 128 samples, run of voxel tiles).
+template <int CB>
+__global__ void __launch_bounds__(kTcpThreads, 1)
+    fwd_tcp_kernel(const ProbDesc *__restrict__ pd, const int *__restrict__ item_off, int nprob, int *counter) {
+    constexpr int N = 2 * CB;
+    using PL = TcpPlan<N>;
+
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ TcShared sh;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const uint32_t sbase = align1024(smem_u32(smem_raw));
+    unsigned char *gbase = smem_raw + (sbase - smem_u32(smem_raw));
+    const int total = item_off[nprob];
+
+    tc_setup(sh, tid, warp, kTmemCols, 1, kTcGen / 2, kTcGen / 64);  // two generator groups
+    const uint32_t tmem = sh.tmem_base;
+    int gs = 0;
+
+    int item;
+    for (int iter = 0; tc_next_item(sh, tid, iter, counter, total, item); ++iter) {
+        const int q = find_problem(item_off, nprob, item);
+        const ProbDesc &P = pd[q];
+        int *status = &P.hdr->status;
+        const int li = item - item_off[q];
+        const int split = li % P.fwd_splits;
+        const int tbase = (li / P.fwd_splits) * kRows;
+        const int tile0 = split * P.fwd_tps;
+        const int ntl = max(0, min(P.ntiles, tile0 + P.fwd_tps) - tile0);
+        const int ntp = P.ntp;
+
+        if (warp >= kMmaWarp) {
+            const bool lead = (tid & 31) == 0;
+            if (warp == kMmaWarp && lead) {
+                tcp_contraction_item<N>(sh, tmem, gbase, gs, ntl, status);
+            } else if (warp == kPhaseWarp && lead) {
+                tcp_phase_item<N>(sh, tmem, gbase, gs, ntl, iter, (P.LP + 7) >> 3, status);
+            } else if (warp == kLoadBWarp && lead) {
+                tcp_ring_item(sh.bfree, kNBB, gs, ntl, &sh.abort_flag, status, [&](int it, int sb) {
+                    const int tile = tile0 + it;  // packed S x of the tile and its reference phases
+                    unsigned char *dst = gbase + PL::OFF_B + sb * PL::BS;
+                    mbar_arrive_expect_tx(&sh.bfull[sb], PL::B_BYTES + PL::F_BYTES);
+                    bulk_g2s(dst, P.bpk + (size_t)tile * PL::B_BYTES, PL::B_BYTES, &sh.bfull[sb]);
+                    bulk_g2s(dst + PL::B_BYTES, P.f0 + (size_t)tile * ntp + tbase, PL::F_BYTES, &sh.bfull[sb]);
+                });
+            } else if (warp == kLoadPWarp && lead) {
+                mbar_arrive_expect_tx(&sh.apfull, kApBytes);
+                bulk_g2s(gbase + PL::OFF_AP, P.kph + (size_t)(tbase / kRows) * kPhaseBlockBytes, kApBytes, &sh.apfull);
+                tcp_ring_item(sh.pfree, kNP, gs, ntl, &sh.abort_flag, status, [&](int it, int sp) {
+                    const int tile = tile0 + it;  // the tile's basis offsets, hi | lo
+                    const unsigned char *dp =
+                        P.dhph + (size_t)(tile >> 1) * kPhaseBlockBytes + (size_t)(tile & 1) * kHalfImg;
+                    unsigned char *dst = gbase + PL::OFF_PH + sp * PL::PS;
+                    mbar_arrive_expect_tx(&sh.pfull[sp], 2 * kHalfImg);
+                    bulk_g2s(dst, dp, kHalfImg, &sh.pfull[sp]);
+                    bulk_g2s(dst + kHalfImg, dp + kPhaseBlockBytes / 2, kHalfImg, &sh.pfull[sp]);
+                });
+            }
+        } else {
+            // generator group warp >> 3 takes the stages of its parity; warp w reads TMEM lanes
+            // 32 (w & 3) .. + 31 (its rows) and owns voxel columns 32 ((w >> 2) & 1) .. + 31
+            const int row = 32 * (warp & 3) + (tid & 31);
+            const int ch = (warp >> 2) & 1;
+            const int grp = warp >> 3;
+            for (int it = 0; it < ntl; ++it) {
+                const int g = gs + it, sa = g & 1, sb = g % kNBB;
+                if ((g & 1) != grp) continue;
+                if (!gen_waits(sh, g, status)) break;  // warp-uniform exit
+                tc::fence_after_sync();
+                generate_row<false>(sh, g,
+                                    tmem + ((uint32_t)(32 * (warp & 3)) << 16) + phase_col(g) + (uint32_t)(32 * ch),
+                                    reinterpret_cast<const float *>(gbase + PL::OFF_B + sb * PL::BS + PL::B_BYTES) + row,
+                                    gbase + sa * kA_BYTES, row, ch);
+                tc::fence_proxy_async_smem();
+                tc::fence_before_sync();
+                tc::mbar_arrive(&sh.afull[sa]);
+            }
+            // epilogue (warps 0-7): last stage's MMAs done -> TMEM -> partials (planar re | im)
+            bool ok = !sh.abort_flag;
+            const int gl = gs + ntl - 1;
+            if (ntl > 0 && ok) ok = wait_or_abort(&sh.afree[gl & 1], (gl >> 1) & 1, &sh.abort_flag, status);
+            ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
+            tc::fence_after_sync();
+            if (warp < 8) {
+                const int lane_base = 32 * (warp & 3);
+                const int half = warp >> 2;
+                const int t = tbase + lane_base + (tid & 31);
+                float v[N / 2];
+                if (ntl > 0 && ok) {
+                    tc::tmem_ld<N / 2>(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(half * (N / 2)), v);
+                    tc::tmem_ld_wait();
+                } else {
+#pragma unroll
+                    for (int c = 0; c < N / 2; ++c) v[c] = 0.f;
+                }
+                float4 *dst =
+                    reinterpret_cast<float4 *>(P.fpart + ((size_t)split * ntp + t) * N + half * (N / 2));
+#pragma unroll
+                for (int c = 0; c < N / 8; ++c)
+                    dst[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+            }
+        }
+        gs += ntl;
+    }
+    tcp_teardown(sh, tid, warp, &pd[0].hdr->status);
+}
+
+// Adjoint: item = (problem, pair of voxel tiles, run of 64-sample stages).
+template <int CB>
+__global__ void __launch_bounds__(kTcpThreads, 1)
+    adj_tcp_kernel(const ProbDesc *__restrict__ pd, const int *__restrict__ item_off, int nprob, int *counter) {
+    constexpr int N = 2 * CB;
+    constexpr int TS = kCols;  // samples per stage
+    using PL = TcpPlan<N>;
+    constexpr unsigned FT = TS * 4;  // reference phases of one tile for one stage
+
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ TcShared sh;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const uint32_t sbase = align1024(smem_u32(smem_raw));
+    unsigned char *gbase = smem_raw + (sbase - smem_u32(smem_raw));
+    const int total = item_off[nprob];
+
+    tc_setup(sh, tid, warp, kTmemCols, 1, kTcGen / 2, kTcGen / 64);  // two generator groups
+    const uint32_t tmem = sh.tmem_base;
+    int gs = 0;
+
+    int item;
+    for (int iter = 0; tc_next_item(sh, tid, iter, counter, total, item); ++iter) {
+        const int q = find_problem(item_off, nprob, item);
+        const ProbDesc &P = pd[q];
+        int *status = &P.hdr->status;
+        const int li = item - item_off[q];
+        const int vb = li / P.adj_splits, split = li % P.adj_splits;
+        const int ntiles = P.ntiles, ntp = P.ntp;
+        const int tileA = 2 * vb;
+        const int tileB = min(tileA + 1, ntiles - 1);  // odd tile count: duplicate row, discarded
+        const int t0 = split * P.adj_tps;
+        const int nst = max(0, (min(ntp, t0 + P.adj_tps) - t0) / TS);
+
+        if (warp >= kMmaWarp) {
+            const bool lead = (tid & 31) == 0;
+            if (warp == kMmaWarp && lead) {
+                tcp_contraction_item<N>(sh, tmem, gbase, gs, nst, status);
+            } else if (warp == kPhaseWarp && lead) {
+                tcp_phase_item<N>(sh, tmem, gbase, gs, nst, iter, (P.LP + 7) >> 3, status);
+            } else if (warp == kLoadBWarp && lead) {
+                tcp_ring_item(sh.bfree, kNBB, gs, nst, &sh.abort_flag, status, [&](int it, int sb) {
+                    const size_t ts = (size_t)t0 + (size_t)it * TS;  // packed y and both tiles' f0
+                    unsigned char *dst = gbase + PL::OFF_B + sb * PL::BS;
+                    mbar_arrive_expect_tx(&sh.bfull[sb], PL::B_BYTES + 2 * FT);
+                    bulk_g2s(dst, P.ypk + (ts / TS) * PL::B_BYTES, PL::B_BYTES, &sh.bfull[sb]);
+                    bulk_g2s(dst + PL::B_BYTES, P.f0 + (size_t)tileA * ntp + ts, FT, &sh.bfull[sb]);
+                    bulk_g2s(dst + PL::B_BYTES + FT, P.f0 + (size_t)tileB * ntp + ts, FT, &sh.bfull[sb]);
+                });
+            } else if (warp == kLoadPWarp && lead) {
+                mbar_arrive_expect_tx(&sh.apfull, kApBytes);
+                bulk_g2s(gbase + PL::OFF_AP, P.dhph + (size_t)vb * kPhaseBlockBytes, kApBytes, &sh.apfull);
+                tcp_ring_item(sh.pfree, kNP, gs, nst, &sh.abort_flag, status, [&](int it, int sp) {
+                    const size_t ts = (size_t)t0 + (size_t)it * TS;  // the stage's k rows, hi | lo
+                    const unsigned char *kp =
+                        P.kph + (ts / kRows) * kPhaseBlockBytes + ((ts / TS) & 1) * (size_t)kHalfImg;
+                    unsigned char *dst = gbase + PL::OFF_PH + sp * PL::PS;
+                    mbar_arrive_expect_tx(&sh.pfull[sp], 2 * kHalfImg);
+                    bulk_g2s(dst, kp, kHalfImg, &sh.pfull[sp]);
+                    bulk_g2s(dst + kHalfImg, kp + kPhaseBlockBytes / 2, kHalfImg, &sh.pfull[sp]);
+                });
+            }
+        } else {
+            // generator group warp >> 3 takes the stages of its parity; warp w reads TMEM lanes
+            // 32 (w & 3) .. + 31 (voxel rows; rows 0-63 in tile A, 64-127 in tile B) and owns sample
+            // columns 32 ((w >> 2) & 1) .. + 31
+            const int row = 32 * (warp & 3) + (tid & 31);
+            const int th = (warp & 3) >> 1;
+            const int ch = (warp >> 2) & 1;
+            const int grp = warp >> 3;
+            for (int it = 0; it < nst; ++it) {
+                const int g = gs + it, sa = g & 1, sb = g % kNBB;
+                if ((g & 1) != grp) continue;
+                if (!gen_waits(sh, g, status)) break;  // warp-uniform exit
+                tc::fence_after_sync();
+                generate_row<true>(sh, g,
+                                   tmem + ((uint32_t)(32 * (warp & 3)) << 16) + phase_col(g) + (uint32_t)(32 * ch),
+                                   reinterpret_cast<const float *>(gbase + PL::OFF_B + sb * PL::BS + PL::B_BYTES + th * FT) +
+                                       32 * ch,
+                                   gbase + sa * kA_BYTES, row, ch);
+                tc::fence_proxy_async_smem();
+                tc::fence_before_sync();
+                tc::mbar_arrive(&sh.afull[sa]);
+            }
+            // epilogue (warps 0-3, one voxel row per thread): conj(S) . u over coils
+            bool ok = !sh.abort_flag;
+            const int gl = gs + nst - 1;
+            if (nst > 0 && ok) ok = wait_or_abort(&sh.afree[gl & 1], (gl >> 1) & 1, &sh.abort_flag, status);
+            ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
+            tc::fence_after_sync();
+            if (warp < 4) {
+                const int p = vb * kRows + row;
+                const bool inside = p < ntiles * kTileVox;
+                const bool have = nst > 0 && ok;
+                const uint32_t ta0 = tmem + ((uint32_t)(32 * warp) << 16);
+                const float4 *s4 = reinterpret_cast<const float4 *>(P.Sp + (size_t)(inside ? p : 0) * CB);
+                float xr = 0.f, xi = 0.f;
+#pragma unroll 1
+                for (int c0 = 0; c0 < CB; c0 += 8) {
+                    float ur[8], ui[8];
+                    if (have) {
+                        tc::tmem_ld<8>(ta0 + (uint32_t)c0, ur);
+                        tc::tmem_ld<8>(ta0 + (uint32_t)(CB + c0), ui);
+                        tc::tmem_ld_wait();
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) ur[c] = ui[c] = 0.f;
+                    }
+#pragma unroll
+                    for (int q4 = 0; q4 < 4; ++q4) {
+                        const float4 sv = s4[c0 / 2 + q4];
+                        xr = fmaf(sv.x, ur[2 * q4], xr);
+                        xr = fmaf(sv.y, ui[2 * q4], xr);
+                        xi = fmaf(sv.x, ui[2 * q4], xi);
+                        xi = fmaf(-sv.y, ur[2 * q4], xi);
+                        xr = fmaf(sv.z, ur[2 * q4 + 1], xr);
+                        xr = fmaf(sv.w, ui[2 * q4 + 1], xr);
+                        xi = fmaf(sv.z, ui[2 * q4 + 1], xi);
+                        xi = fmaf(-sv.w, ur[2 * q4 + 1], xi);
+                    }
+                }
+                if (inside) P.apart[(size_t)split * (size_t)(ntiles * kTileVox) + p] = make_float2(xr, xi);
+            }
+        }
+        gs += nst;
+    }
+    tcp_teardown(sh, tid, warp, &pd[0].hdr->status);
+}
+
+// ---- launches ----
+template <int CB>
+size_t tcp_smem() {
+    return 1024 + TcpPlan<2 * CB>::BYTES;
+}
+
+template <int CB>
+cudaError_t launch_fwd_tcp(const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *x, int src,
+                           const int *item_off, int total_items, int *counter, cudaStream_t st) {
+    pack_b_fwd_kernel<CB, false><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, x, src);
+    auto kern = fwd_tcp_kernel<CB>;
+    const size_t smem = tcp_smem<CB>();
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    kern<<<std::min(total_items, num_sms()), kTcpThreads, smem, st>>>(pd, item_off, nprob, counter);
+    return cudaGetLastError();
+}
+
+template <int CB>
+cudaError_t launch_adj_tcp(const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *yt, int src,
+                           const int *item_off, int total_items, int *counter, cudaStream_t st) {
+    pack_y_adj_kernel<CB, false><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, yt, src);
+    auto kern = adj_tcp_kernel<CB>;
+    const size_t smem = tcp_smem<CB>();
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    kern<<<std::min(total_items, num_sms()), kTcpThreads, smem, st>>>(pd, item_off, nprob, counter);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t op_prepare_phase_operands(const OpLayout &L, char *ws, cudaStream_t st) {
+    const int T = 256;
+    const size_t nk = (size_t)L.ntp * 8;
+    prep_kph_kernel<<<(unsigned)((nk + T - 1) / T), T, 0, st>>>((const float *)(ws + L.off_khi_t), L.ntp, L.LP,
+                                                               (unsigned char *)(ws + L.off_kph));
+    const size_t nd = (size_t)cdiv(L.ntiles, 2) * kRows * 8;
+    prep_dhph_kernel<<<(unsigned)((nd + T - 1) / T), T, 0, st>>>((const float *)(ws + L.off_dh), L.ntiles, L.LP,
+                                                                (unsigned char *)(ws + L.off_dhph));
+    return cudaGetLastError();
+}
+
+cudaError_t tcp_forward(int CB, const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *x, int src,
+                        const int *item_off, int total_items, int *counter, cudaStream_t st) {
+    switch (CB) {
+        case 8: return launch_fwd_tcp<8>(pd, nprob, max_pack_blocks, x, src, item_off, total_items, counter, st);
+        case 16: return launch_fwd_tcp<16>(pd, nprob, max_pack_blocks, x, src, item_off, total_items, counter, st);
+        default: return launch_fwd_tcp<32>(pd, nprob, max_pack_blocks, x, src, item_off, total_items, counter, st);
+    }
+}
+
+cudaError_t tcp_adjoint(int CB, const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *yt, int src,
+                        const int *item_off, int total_items, int *counter, cudaStream_t st) {
+    switch (CB) {
+        case 8: return launch_adj_tcp<8>(pd, nprob, max_pack_blocks, yt, src, item_off, total_items, counter, st);
+        case 16: return launch_adj_tcp<16>(pd, nprob, max_pack_blocks, yt, src, item_off, total_items, counter, st);
+        default: return launch_adj_tcp<32>(pd, nprob, max_pack_blocks, yt, src, item_off, total_items, counter, st);
+    }
+}
+
+}  // namespace aexp

@@ -44,6 +44,24 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64
         : "memory");
 }
 
+// ---- MMA: D[tmem] (+)= A[smem] * B[smem], TF32 inputs (32-bit containers), FP32 accumulation ----
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// x rounded to TF32 (10 explicit mantissa bits, nearest, ties away), low 13 bits zero
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
 // arrive once on an mbarrier when all previously issued MMAs of this thread complete
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -108,12 +126,21 @@ __device__ __forceinline__ uint64_t sdesc_k128(uint32_t smem_addr) {
     return d;
 }
 
+// The same descriptor for an address `bytes` further on (a multiple of 16): the start
+// address sits in bits 0-13 in units of 16 bytes and shared addresses stay below 2^18, so a
+// plain add cannot carry out of the field.  Lets the MMA issuer build one descriptor per
+// operand and stage instead of one per instruction.
+__device__ __forceinline__ uint64_t sdesc_advance(uint64_t desc, uint32_t bytes) { return desc + (bytes >> 4); }
+
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16 (ab_type 1) or F16 (0),
 // both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int ab_type) {
     return (1u << 4) | ((uint32_t)ab_type << 7) | ((uint32_t)ab_type << 10) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(M >> 4) << 24);
 }
+
+// Instruction descriptor, kind::tf32: D = F32, A = B = TF32 (format 2), both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) { return idesc_f16(M, N, 2); }
 
 // Byte offset of 16-byte chunk `chunk` (0..7) of row `row` inside one 128B-swizzled
 // atom column (rows contiguous at 128 B, 8-row groups at 1024 B).
