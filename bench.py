@@ -115,13 +115,19 @@ def fp32_alu_peak_tflops(sm_mhz: float) -> float:
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
+def sfu_peak_gops(sm_mhz: float) -> float:
+    """MUFU (sin, cos, ...): 152 SMs x 16 results per clock x SM clock, in G results/s."""
+    return 152 * 16 * sm_mhz * 1e6 / 1e9
+
+
 def launches_per_recon(levels: int, iters: int, n_power: int, form: str = "fp32") -> int:
     """Kernel launches issued by cs_recon (mirrors the host sequence in recon.cu)."""
     # one application: FP32 forward = coil weight + contraction + reduce, adjoint = contraction
     # + reduce; tensor-core forms pack + persistent contraction + reduce each way, the FP16
     # hi+lo form two more (max reset + max reduction) per packing
     fwd, adj = {"fp32": (3, 2), "bf16": (3, 3), "fp16x2": (5, 5)}[form]
-    prep = 4 + 1 + (0 if form == "fp32" else 2)  # coef, tiles, phases, coils; y transpose; descriptor + items
+    # coef, tiles, phases, coils; y transpose; descriptor + items; BF16: the two phase-GEMM operands
+    prep = 4 + 1 + {"fp32": 0, "bf16": 4, "fp16x2": 2}[form]
     power = adj + 2 + n_power * (fwd + adj + 2) + 1  # A^H y; norm + scale; per iteration A^H A + dot + scale; finalize
     fista = iters * (fwd + adj + 2 * levels)          # A^H (A z - y) + J analysis + J synthesis levels
     return prep + power + fista
@@ -361,7 +367,13 @@ def _run_ours(args, rank, world, local, dev):
                 "achieved": ach, "unit": "TFLOP/s", "peak": bf16_peak, "frac": ach / bf16_peak,
                 "mma_passes": passes, "tensor_pipe_frac": passes * ach / bf16_peak,
                 "note": "algorithmic 8C flops per (sample, voxel) per application; the tensor pipe runs "
-                        "mma_passes x that; the bound is the CUDA-core generation of the encoding tile"}
+                        "mma_passes x that (BF16: plus the phase GEMM, 3 TF32 products of K = 8 LP/8)"}
+            # the bound of the tensor-core forms: one sincos (2 MUFU results) per (sample, voxel)
+            sfu_ach = 2.0 * nr * nt / (o_kern[o_dom] / 1e3) / 1e9
+            sfu_peak = sfu_peak_gops(sm_mhz_peak)
+            c["roofline"] = {"bound": "sfu", "achieved": sfu_ach, "peak": sfu_peak, "unit": "G MUFU results/s",
+                             "frac": sfu_ach / sfu_peak, "kernel": o_dom, "kernel_ms": o_kern[o_dom],
+                             "peak_basis": f"152 SM x 16 MUFU results/clk at {sm_mhz_peak:.0f} MHz"}
         comparison[other] = c
         del o_ws
 
