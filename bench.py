@@ -377,6 +377,30 @@ def _run_ours(args, rank, world, local, dev):
         comparison[other] = c
         del o_ws
 
+    # the paper's LS baseline on the same data: CGLS from x = 0, 20 iterations (41 applications)
+    ls_baseline = {}
+    for f in ("fp32", "bf16"):
+        lo = ax.recon_opts(precision=forms[f])
+        lws = torch.empty(ax.cgls_workspace_size(prob, lo), dtype=torch.uint8, device=dev)
+        for _ in range(max(1, args.warmup)):
+            ax.cgls_recon(prob, y, 20, opts=lo, ws=lws, x_out=x_out)
+        torch.cuda.synchronize()
+        l_ms = []
+        for i in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ax.cgls_recon(prob, y, 20, opts=lo, ws=lws, x_out=x_out)
+            b.record(stream)
+            b.synchronize()
+            l_ms.append(a.elapsed_time(b))
+        cs_s = ms_per_step / 1e3 if f == args.form else comparison[f]["s_per_slice"]
+        ls_s = float(np.mean(l_ms)) / 1e3
+        ls_baseline[f] = {"s_per_slice": ls_s, "iterations": 20, "applications": 41,
+                          "nrmse_vs_phantom": float(torch.linalg.vector_norm(x_out - x_gt) / torch.linalg.vector_norm(x_gt)),
+                          "cs_over_ls_time": cs_s / ls_s, "device_status": ax.read_status(lws)}
+        del lws
+
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -409,6 +433,7 @@ def _run_ours(args, rank, world, local, dev):
                                        "(sm_max_mhz of MEASURED_PEAKS.json)"},
             "kernels_ms": kern,
             "comparison": comparison,
+            "ls_baseline_cgls20": ls_baseline,
             "clocks": clocks,
             "cpu_baseline": cpu,
         }

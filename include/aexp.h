@@ -159,6 +159,18 @@ AEXP_API int cs_recon(const aexp_problem *prob, const void *y, float lambda, int
              const aexp_recon_opts *opts, void *x_out, double *lipschitz_out,
              void *ws, size_t ws_bytes, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Least-squares reconstruction: conjugate gradient on the normal equations A^H A x = A^H y
+ * (CGLS) from x_0 = 0 with a fixed iteration count -- the paper's LS baseline, stopped early
+ * at 20 iterations as implicit regularisation (Sec. 2.1, Supporting Information S2).  y:
+ * [nc][nt] complex64; x_out: [nr] complex64.  opts: precision, items_per_sm and use_graph
+ * are used, the wavelet and power-iteration fields are ignored.  FP64 device scalars; the
+ * whole loop is one CUDA graph (use_graph, non-default stream).  Prepares ws itself.
+ * --------------------------------------------------------------------------- */
+AEXP_API int aexp_cgls_workspace_size(const aexp_problem *prob, const aexp_recon_opts *opts, size_t *bytes);
+AEXP_API int cgls_recon(const aexp_problem *prob, const void *y, int iters, const aexp_recon_opts *opts,
+                        void *x_out, void *ws, size_t ws_bytes, void *stream);
+
 /* Estimate L_f = 2 lambda_max(A^H A) with n_power iterations from v0 ([nr] complex64,
  * not modified).  Result to the DEVICE double *lipschitz_out.  ws as for cs_recon. */
 AEXP_API int aexp_power_lipschitz(const aexp_problem *prob, int precision, const void *v0, int n_power,

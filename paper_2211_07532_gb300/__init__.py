@@ -77,6 +77,8 @@ SIGNATURES = [
     ("aexp_wavelet_prox", _I, [_I, _I, _I, _I, ctypes.c_float, _P, _P, _P, _SZ, _P]),
     ("aexp_wavelet_forward", _I, [_I, _I, _I, _I, _P, _P, _P, _SZ, _P]),
     ("aexp_wavelet_prox_static", _I, [_I, _I, _I, _I, ctypes.c_float, _P, _P, _P]),
+    ("aexp_cgls_workspace_size", _I, [_PROB, _OPTS, ctypes.POINTER(_SZ)]),
+    ("cgls_recon", _I, [_PROB, _P, _I, _OPTS, _P, _P, _SZ, _P]),
     ("aexp_autotune_workspace_size", _I, [_PROB, _I, _OPTS, ctypes.POINTER(_SZ)]),
     ("aexp_autotune", _I, [_PROB, _I, _OPTS, _P, _SZ, _P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]),
     ("aexp_read_status", _I, [_P, _P, ctypes.POINTER(_I)]),
@@ -290,6 +292,26 @@ def cs_recon_batched(probs, ys, lams, iters: int, opts: CReconOpts | None = None
     _check(lib().cs_recon_batched(probs_c, n, yp, lp, int(iters), ctypes.byref(opts), xp, _ptr(lipschitz_out),
                                   _ptr(ws), ws.numel(), _stream(stream)), "cs_recon_batched")
     return x_outs, lipschitz_out
+
+
+def cgls_workspace_size(prob: Problem, opts: CReconOpts) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().aexp_cgls_workspace_size(prob.c, ctypes.byref(opts), ctypes.byref(n)), "aexp_cgls_workspace_size")
+    return n.value
+
+
+def cgls_recon(prob: Problem, y, iters: int, opts: CReconOpts | None = None, ws=None, x_out=None, stream=None, **kw):
+    """Least squares by CGLS from x = 0 (the paper's LS baseline); returns x [nr] complex64."""
+    torch = _torch()
+    opts = recon_opts(**kw) if opts is None else opts
+    y = y.contiguous()
+    if ws is None:
+        ws = _alloc(cgls_workspace_size(prob, opts), y.device)
+    if x_out is None:
+        x_out = torch.empty(prob.nr, dtype=torch.complex64, device=y.device)
+    _check(lib().cgls_recon(prob.c, _ptr(y), int(iters), ctypes.byref(opts), _ptr(x_out), _ptr(ws), ws.numel(),
+                            _stream(stream)), "cgls_recon")
+    return x_out
 
 
 def lib_autotune_workspace_size(probs, opts: CReconOpts) -> int:

@@ -225,6 +225,19 @@ cudaError_t set_lipschitz(const OpLayout &L, char *ws, double value, double *out
 cudaError_t recon_issue(const aexp_problem *p, const RecLayout &R, const aexp_recon_opts *o, const float2 *y,
                         float lam, int iters, float2 *x_out, double *lip_out, char *ws, cudaStream_t st);
 
+// Least squares by CGLS (cgls.cu): operator workspace + image vectors x, p, s, k-space r, q,
+// FP64 partial sums and scalars.
+struct CglsLayout {
+    OpLayout op;
+    size_t off_x, off_p, off_s, off_r, off_q, off_part, off_scal;
+    size_t bytes;
+};
+int cgls_layout(const aexp_problem *p, const aexp_recon_opts *o, CglsLayout *C);
+cudaError_t cgls_issue(const aexp_problem *p, const CglsLayout &C, const float2 *y, int iters, float2 *x_out,
+                       char *ws, cudaStream_t st);
+// ||w||^2 in FP64, two-stage fixed-order reduction (partial: 256 doubles of scratch).
+cudaError_t norm2_f64(const float2 *w, size_t n, double *partial, double *out, cudaStream_t st);
+
 // Record a CUDA error for aexp_last_cuda_error() (capi.cu).
 void aexp_set_last_cuda_error(int e);
 // Drop the host-side record of what `ws` was prepared for (its contents were overwritten).

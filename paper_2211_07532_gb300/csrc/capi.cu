@@ -94,6 +94,37 @@ void put(std::vector<unsigned char> &v, const T &x) {
     v.insert(v.end(), b, b + sizeof(T));
 }
 
+// Capture `issue` on st once per (workspace, key) and replay the instantiated graph on every
+// later call with the same key.
+template <class Issue>
+cudaError_t launch_captured(const void *ws, const std::vector<unsigned char> &key, cudaStream_t st, Issue issue) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    GraphEntry &ge = g_graphs[ws];
+    if (ge.exec == nullptr || ge.key != key) {
+        if (ge.exec) {
+            cudaGraphExecDestroy(ge.exec);
+            ge.exec = nullptr;
+        }
+        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        cudaError_t ei = issue();
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(st, &g);
+        if (ei != cudaSuccess || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return ei != cudaSuccess ? ei : e;
+        }
+        e = cudaGraphInstantiate(&ge.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            ge.exec = nullptr;
+            return e;
+        }
+        ge.key = key;
+    }
+    return cudaGraphLaunch(ge.exec, st);
+}
+
 int check_opts(const aexp_recon_opts *o) {
     if (!o) return AEXP_ERR_INVALID_ARG;
     int rc = check_precision(o->precision);
@@ -285,6 +316,50 @@ int cs_recon(const aexp_problem *prob, const void *y, float lambda, int iters, c
     e = cudaGraphLaunch(ge.exec, st);
     if (e != cudaSuccess) return cuda_fail(e);
     g_prepared[ws] = PrepRecord{*prob, opts->precision, effective_items(opts->precision, opts->items_per_sm)};
+    return AEXP_OK;
+}
+
+int aexp_cgls_workspace_size(const aexp_problem *prob, const aexp_recon_opts *opts, size_t *bytes) {
+    int rc = check_problem(prob);
+    if (rc) return rc;
+    if ((rc = check_opts(opts))) return rc;
+    if (!bytes) return AEXP_ERR_INVALID_ARG;
+    CglsLayout C;
+    if ((rc = cgls_layout(prob, opts, &C))) return rc;
+    *bytes = C.bytes;
+    return AEXP_OK;
+}
+
+int cgls_recon(const aexp_problem *prob, const void *y, int iters, const aexp_recon_opts *opts, void *x_out,
+               void *ws, size_t ws_bytes, void *stream) {
+    int rc = check_problem(prob);
+    if (rc) return rc;
+    if ((rc = check_opts(opts))) return rc;
+    if (!y || !x_out || iters < 0) return AEXP_ERR_INVALID_ARG;
+    if (!aligned(y, 8) || !aligned(x_out, 8)) return AEXP_ERR_MISALIGNED;
+    CglsLayout C;
+    if ((rc = cgls_layout(prob, opts, &C))) return rc;
+    if ((rc = check_ws(ws, ws_bytes, C.bytes))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = (char *)ws;
+    cudaError_t e = cudaMemsetAsync(w + C.op.off_hdr, 0, sizeof(WsHeader), st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    auto issue = [&]() { return cgls_issue(prob, C, (const float2 *)y, iters, (float2 *)x_out, w, st); };
+    if (!opts->use_graph || st == nullptr) {
+        e = issue();
+    } else {
+        std::vector<unsigned char> key;
+        put(key, 'L');  // distinguishes this solver's graphs from cs_recon's on the same workspace
+        put(key, *prob);
+        put(key, *opts);
+        put(key, y);
+        put(key, iters);
+        put(key, x_out);
+        put(key, ws_bytes);
+        e = launch_captured(ws, key, st, issue);
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    record_prepared(ws, prob, opts->precision, opts->items_per_sm);
     return AEXP_OK;
 }
 
