@@ -76,6 +76,14 @@ typedef enum aexp_precision {
  *                   and the k-space data (adjoint) are scaled by a power of two chosen
  *                   from their largest component, so any finite FP32 input is accepted. */
 
+/* How cs_recon obtains lambda: the caller's value, or the paper's rule (Supporting
+ * Information S1, Method 2): lambda = sigma / 2 with sigma the maximum of the histogram of
+ * the detail-coefficient magnitudes of W A^H y (needs `undecimated`; one level). */
+typedef enum aexp_lambda_rule {
+    AEXP_LAMBDA_GIVEN = 0,
+    AEXP_LAMBDA_RAYLEIGH = 1
+} aexp_lambda_rule;
+
 typedef enum aexp_wavelet {
     AEXP_WAVELET_HAAR = 0, /* orthonormal Haar, 2 taps                          */
     AEXP_WAVELET_DB4 = 1   /* orthonormal Daubechies, 4 vanishing moments, 8 taps */
@@ -135,6 +143,12 @@ typedef struct aexp_recon_opts {
     const void *x0;         /* [nr] complex64 start image, or NULL for zero              */
     const void *power_init; /* [nr] complex64 power-iteration start, or NULL for A^H y   */
     int use_graph;          /* nonzero: capture the whole loop in one CUDA graph         */
+    int undecimated;        /* nonzero: the paper's regulariser W -- the one-level undecimated
+                               (stationary) transform with the same filters, a tight frame
+                               (W^H W = I); the prox step is W^H soft(W v) ("balanced"
+                               FISTA, Sec. 2.1); `levels` is ignored                      */
+    int lambda_rule;        /* aexp_lambda_rule                                          */
+    double *lambda_out;     /* optional DEVICE double: the lambda used                   */
     int items_per_sm;       /* work-item granularity of the operator launches: the sample
                                (forward) and voxel (adjoint) reductions are split until a
                                launch holds about 152 x items_per_sm blocks or persistent
@@ -158,6 +172,20 @@ AEXP_API int aexp_recon_workspace_size(const aexp_problem *prob, const aexp_reco
 AEXP_API int cs_recon(const aexp_problem *prob, const void *y, float lambda, int iters,
              const aexp_recon_opts *opts, void *x_out, double *lipschitz_out,
              void *ws, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * The undecimated one-level wavelet on its own (Sec. 2.1; tight frame, subband s = fx + 2 fy
+ * with f = lowpass 0 / highpass 1: LL, HL, LH, HH).  in/out: [ny][nx] complex64, coef:
+ * [4][ny][nx] complex64 device arrays.  aexp_swt_prox: out = W^H soft_detail(W in, tau),
+ * ws of aexp_swt_workspace_size bytes.  aexp_swt_lambda: *lambda_out (device double) =
+ * sigma / 2 of the detail coefficients of W img (the lambda rule applied to img).
+ * --------------------------------------------------------------------------- */
+AEXP_API int aexp_swt_workspace_size(int nx, int ny, size_t *bytes);
+AEXP_API int aexp_swt_forward(int nx, int ny, int wavelet, const void *in, void *coef, void *stream);
+AEXP_API int aexp_swt_prox(int nx, int ny, int wavelet, float tau, const void *in, void *out, void *ws,
+                           size_t ws_bytes, void *stream);
+AEXP_API int aexp_swt_lambda(int nx, int ny, int wavelet, const void *img, double *lambda_out, void *ws,
+                             size_t ws_bytes, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Least-squares reconstruction: conjugate gradient on the normal equations A^H A x = A^H y

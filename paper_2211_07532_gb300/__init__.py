@@ -45,7 +45,8 @@ class CProblem(ctypes.Structure):
 class CReconOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("wavelet", ctypes.c_int), ("levels", ctypes.c_int),
                 ("n_power", ctypes.c_int), ("lipschitz", ctypes.c_double), ("x0", ctypes.c_void_p),
-                ("power_init", ctypes.c_void_p), ("use_graph", ctypes.c_int), ("items_per_sm", ctypes.c_int)]
+                ("power_init", ctypes.c_void_p), ("use_graph", ctypes.c_int), ("undecimated", ctypes.c_int),
+                ("lambda_rule", ctypes.c_int), ("lambda_out", ctypes.c_void_p), ("items_per_sm", ctypes.c_int)]
 
 
 _lib = None
@@ -77,6 +78,10 @@ SIGNATURES = [
     ("aexp_wavelet_prox", _I, [_I, _I, _I, _I, ctypes.c_float, _P, _P, _P, _SZ, _P]),
     ("aexp_wavelet_forward", _I, [_I, _I, _I, _I, _P, _P, _P, _SZ, _P]),
     ("aexp_wavelet_prox_static", _I, [_I, _I, _I, _I, ctypes.c_float, _P, _P, _P]),
+    ("aexp_swt_workspace_size", _I, [_I, _I, ctypes.POINTER(_SZ)]),
+    ("aexp_swt_forward", _I, [_I, _I, _I, _P, _P, _P]),
+    ("aexp_swt_prox", _I, [_I, _I, _I, ctypes.c_float, _P, _P, _P, _SZ, _P]),
+    ("aexp_swt_lambda", _I, [_I, _I, _I, _P, _P, _P, _SZ, _P]),
     ("aexp_cgls_workspace_size", _I, [_PROB, _OPTS, ctypes.POINTER(_SZ)]),
     ("cgls_recon", _I, [_PROB, _P, _I, _OPTS, _P, _P, _SZ, _P]),
     ("aexp_autotune_workspace_size", _I, [_PROB, _I, _OPTS, ctypes.POINTER(_SZ)]),
@@ -213,8 +218,12 @@ def a_exp_adjoint(prob: Problem, y, ws, x=None, precision: int = FP32, stream=No
     return x
 
 
+LAMBDA_GIVEN, LAMBDA_RAYLEIGH = 0, 1
+
+
 def recon_opts(precision=FP32, wavelet="haar", levels=3, n_power=30, lipschitz=0.0, x0=None, power_init=None,
-               use_graph=True, items_per_sm=0) -> CReconOpts:
+               use_graph=True, items_per_sm=0, undecimated=False, lambda_rule=LAMBDA_GIVEN,
+               lambda_out=None) -> CReconOpts:
     o = CReconOpts()
     lib().aexp_recon_opts_default(ctypes.byref(o))
     o.precision = precision
@@ -226,6 +235,9 @@ def recon_opts(precision=FP32, wavelet="haar", levels=3, n_power=30, lipschitz=0
     o.power_init = None if power_init is None else power_init.data_ptr()
     o.use_graph = 1 if use_graph else 0
     o.items_per_sm = int(items_per_sm)
+    o.undecimated = 1 if undecimated else 0
+    o.lambda_rule = int(lambda_rule)
+    o.lambda_out = None if lambda_out is None else lambda_out.data_ptr()
     return o
 
 
@@ -292,6 +304,49 @@ def cs_recon_batched(probs, ys, lams, iters: int, opts: CReconOpts | None = None
     _check(lib().cs_recon_batched(probs_c, n, yp, lp, int(iters), ctypes.byref(opts), xp, _ptr(lipschitz_out),
                                   _ptr(ws), ws.numel(), _stream(stream)), "cs_recon_batched")
     return x_outs, lipschitz_out
+
+
+def swt_forward(img, wavelet="db4", stream=None):
+    """One-level undecimated transform of an [ny][nx] complex64 image -> [4][ny][nx]."""
+    torch = _torch()
+    img = img.contiguous()
+    ny, nx = img.shape
+    coef = torch.empty((4, ny, nx), dtype=torch.complex64, device=img.device)
+    w = WAVELETS[wavelet] if isinstance(wavelet, str) else int(wavelet)
+    _check(lib().aexp_swt_forward(nx, ny, w, _ptr(img), _ptr(coef), _stream(stream)), "aexp_swt_forward")
+    return coef
+
+
+def _swt_ws(nx, ny, device):
+    n = ctypes.c_size_t()
+    _check(lib().aexp_swt_workspace_size(nx, ny, ctypes.byref(n)), "aexp_swt_workspace_size")
+    return _alloc(n.value, device)
+
+
+def swt_prox(img, tau: float, wavelet="db4", ws=None, stream=None):
+    """W^H soft_detail(W img, tau) with the undecimated one-level transform."""
+    torch = _torch()
+    img = img.contiguous()
+    ny, nx = img.shape
+    ws = _swt_ws(nx, ny, img.device) if ws is None else ws
+    out = torch.empty_like(img)
+    w = WAVELETS[wavelet] if isinstance(wavelet, str) else int(wavelet)
+    _check(lib().aexp_swt_prox(nx, ny, w, float(tau), _ptr(img), _ptr(out), _ptr(ws), ws.numel(), _stream(stream)),
+           "aexp_swt_prox")
+    return out
+
+
+def swt_lambda(img, wavelet="db4", ws=None, stream=None):
+    """lambda = sigma / 2 from the detail coefficients of W img (device float64 [1])."""
+    torch = _torch()
+    img = img.contiguous()
+    ny, nx = img.shape
+    ws = _swt_ws(nx, ny, img.device) if ws is None else ws
+    out = torch.empty(1, dtype=torch.float64, device=img.device)
+    w = WAVELETS[wavelet] if isinstance(wavelet, str) else int(wavelet)
+    _check(lib().aexp_swt_lambda(nx, ny, w, _ptr(img), _ptr(out), _ptr(ws), ws.numel(), _stream(stream)),
+           "aexp_swt_lambda")
+    return out
 
 
 def cgls_workspace_size(prob: Problem, opts: CReconOpts) -> int:

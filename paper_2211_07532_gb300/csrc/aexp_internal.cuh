@@ -106,6 +106,8 @@ struct RecLayout {
     size_t off_wave, off_ymeas, off_xa, off_xb, off_z, off_v, off_w;
     // differentiation buffers (with_grad only)
     size_t off_rk, off_xbar, off_vbar, off_wave2, off_zq, off_gq, off_gpart;
+    // undecimated one-level wavelet: coefficients [4][nr] and the lambda-rule block
+    size_t off_swt, off_swtaux;
     int grad_splits, grad_tiles_per_split;
     size_t bytes;
 };
@@ -224,6 +226,19 @@ cudaError_t power_iteration(const OpLayout &L, char *ws, const float2 *v0, float
 cudaError_t set_lipschitz(const OpLayout &L, char *ws, double value, double *out, cudaStream_t st);
 cudaError_t recon_issue(const aexp_problem *p, const RecLayout &R, const aexp_recon_opts *o, const float2 *y,
                         float lam, int iters, float2 *x_out, double *lip_out, char *ws, cudaStream_t st);
+
+// The paper's undecimated one-level wavelet, tight frame W^H W = I, and lambda = sigma / 2
+// (swt.cu).  Coefficients [4][ny][nx]; analysis thresholds the detail subbands with
+// tau = *lam / *lip when lam is given, else with tau_host when >= 0; synthesis optionally
+// applies the FISTA momentum.
+size_t swt_aux_bytes();
+double *swt_lambda_slot(char *aux);
+cudaError_t swt_analysis(int wavelet, const float2 *v, float2 *c, int nx, int ny, float tau_host, const double *lam,
+                         const double *lip, cudaStream_t st);
+cudaError_t swt_synthesis(int wavelet, const float2 *c, float2 *out, int nx, int ny, int momentum, double beta,
+                          const float2 *x_old, float2 *z, cudaStream_t st);
+cudaError_t swt_rayleigh_lambda(const float2 *c, int nx, int ny, char *aux, double *lam_out, cudaStream_t st);
+cudaError_t swt_set_lambda(char *aux, double lam, double *lam_out, cudaStream_t st);
 
 // Least squares by CGLS (cgls.cu): operator workspace + image vectors x, p, s, k-space r, q,
 // FP64 partial sums and scalars.

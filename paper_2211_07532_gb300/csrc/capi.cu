@@ -133,7 +133,9 @@ int check_opts(const aexp_recon_opts *o) {
     if (o->levels < 1 || o->levels > 12) return AEXP_ERR_INVALID_ARG;
     if (!(o->lipschitz > 0.0) && o->n_power < 1) return AEXP_ERR_INVALID_ARG;
     if (o->items_per_sm < 0 || o->items_per_sm > 256) return AEXP_ERR_INVALID_ARG;
-    if (!aligned(o->x0, 8) || !aligned(o->power_init, 8)) return AEXP_ERR_MISALIGNED;
+    if (o->lambda_rule != AEXP_LAMBDA_GIVEN && o->lambda_rule != AEXP_LAMBDA_RAYLEIGH) return AEXP_ERR_INVALID_ARG;
+    if (o->lambda_rule == AEXP_LAMBDA_RAYLEIGH && !o->undecimated) return AEXP_ERR_UNSUPPORTED;
+    if (!aligned(o->x0, 8) || !aligned(o->power_init, 8) || !aligned(o->lambda_out, 8)) return AEXP_ERR_MISALIGNED;
     return AEXP_OK;
 }
 
@@ -242,6 +244,9 @@ void aexp_recon_opts_default(aexp_recon_opts *o) {
     o->x0 = nullptr;
     o->power_init = nullptr;
     o->use_graph = 1;
+    o->undecimated = 0;
+    o->lambda_rule = AEXP_LAMBDA_GIVEN;
+    o->lambda_out = nullptr;
     o->items_per_sm = 0;
 }
 
@@ -367,7 +372,7 @@ int aexp_batch_workspace_size(const aexp_problem *probs, int nprob, const aexp_r
     if (!probs || nprob < 1 || nprob > kMaxBatchProblems || !bytes) return AEXP_ERR_INVALID_ARG;
     int rc = check_opts(opts);
     if (rc) return rc;
-    if (opts->precision == AEXP_FP32) return AEXP_ERR_UNSUPPORTED;
+    if (opts->precision == AEXP_FP32 || opts->undecimated) return AEXP_ERR_UNSUPPORTED;
     for (int q = 0; q < nprob; ++q)
         if ((rc = check_problem(&probs[q]))) return rc;
     BatchLayout B;
@@ -383,7 +388,7 @@ int cs_recon_batched(const aexp_problem *probs, int nprob, const void *const *y,
         return AEXP_ERR_INVALID_ARG;
     int rc = check_opts(opts);
     if (rc) return rc;
-    if (opts->precision == AEXP_FP32) return AEXP_ERR_UNSUPPORTED;
+    if (opts->precision == AEXP_FP32 || opts->undecimated) return AEXP_ERR_UNSUPPORTED;
     if (opts->x0 || opts->power_init) return AEXP_ERR_UNSUPPORTED;
     if (!aligned(lipschitz_out, 8)) return AEXP_ERR_MISALIGNED;
     for (int q = 0; q < nprob; ++q) {
@@ -483,6 +488,7 @@ static int unroll_common(const aexp_problem *prob, const aexp_recon_opts *opts, 
     int rc = check_problem(prob);
     if (rc) return rc;
     if ((rc = check_opts(opts))) return rc;
+    if (opts->undecimated) return AEXP_ERR_UNSUPPORTED;  // the unrolled step uses the orthogonal W
     if (!y || !(lipschitz > 0.0)) return AEXP_ERR_INVALID_ARG;
     if (!aligned(y, 8)) return AEXP_ERR_MISALIGNED;
     rec_layout(prob, opts, R, -1, 1);
@@ -518,6 +524,57 @@ int aexp_fista_step_vjp(const aexp_problem *prob, const aexp_recon_opts *opts, c
     cudaError_t e = unroll_step_vjp(R, (const float2 *)y, lambda, lipschitz, (const float2 *)z, beta, beta_next,
                                     (const float2 *)xbar_in, (const float2 *)zbar_next, (const float2 *)zbar_next2,
                                     (float2 *)zbar_out, kbar, lambar, (char *)ws, (cudaStream_t)stream);
+    return e == cudaSuccess ? AEXP_OK : cuda_fail(e);
+}
+
+int aexp_swt_workspace_size(int nx, int ny, size_t *bytes) {
+    if (nx < 1 || ny < 1 || !bytes) return AEXP_ERR_INVALID_ARG;
+    if ((long long)nx * ny > (1LL << 26)) return AEXP_ERR_UNSUPPORTED;
+    *bytes = align_up(4 * sizeof(float2) * (size_t)nx * ny) + swt_aux_bytes();
+    return AEXP_OK;
+}
+
+int aexp_swt_forward(int nx, int ny, int wavelet, const void *in, void *coef, void *stream) {
+    if (nx < 1 || ny < 1 || !in || !coef) return AEXP_ERR_INVALID_ARG;
+    if (wavelet != AEXP_WAVELET_HAAR && wavelet != AEXP_WAVELET_DB4) return AEXP_ERR_INVALID_ARG;
+    if ((long long)nx * ny > (1LL << 26)) return AEXP_ERR_UNSUPPORTED;
+    if (!aligned(in, 8) || !aligned(coef, 8)) return AEXP_ERR_MISALIGNED;
+    cudaError_t e = swt_analysis(wavelet, (const float2 *)in, (float2 *)coef, nx, ny, -1.f, nullptr, nullptr,
+                                 (cudaStream_t)stream);
+    return e == cudaSuccess ? AEXP_OK : cuda_fail(e);
+}
+
+int aexp_swt_prox(int nx, int ny, int wavelet, float tau, const void *in, void *out, void *ws, size_t ws_bytes,
+                  void *stream) {
+    size_t need;
+    int rc = aexp_swt_workspace_size(nx, ny, &need);
+    if (rc) return rc;
+    if (!in || !out || !(tau >= 0.f)) return AEXP_ERR_INVALID_ARG;
+    if (wavelet != AEXP_WAVELET_HAAR && wavelet != AEXP_WAVELET_DB4) return AEXP_ERR_INVALID_ARG;
+    if (!aligned(in, 8) || !aligned(out, 8)) return AEXP_ERR_MISALIGNED;
+    if ((rc = check_ws(ws, ws_bytes, need))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    float2 *c = (float2 *)ws;
+    cudaError_t e = swt_analysis(wavelet, (const float2 *)in, c, nx, ny, tau, nullptr, nullptr, st);
+    if (e == cudaSuccess) e = swt_synthesis(wavelet, c, (float2 *)out, nx, ny, 0, 0.0, nullptr, nullptr, st);
+    return e == cudaSuccess ? AEXP_OK : cuda_fail(e);
+}
+
+int aexp_swt_lambda(int nx, int ny, int wavelet, const void *img, double *lambda_out, void *ws, size_t ws_bytes,
+                    void *stream) {
+    size_t need;
+    int rc = aexp_swt_workspace_size(nx, ny, &need);
+    if (rc) return rc;
+    if (!img || !lambda_out) return AEXP_ERR_INVALID_ARG;
+    if (wavelet != AEXP_WAVELET_HAAR && wavelet != AEXP_WAVELET_DB4) return AEXP_ERR_INVALID_ARG;
+    if (!aligned(img, 8) || !aligned(lambda_out, 8)) return AEXP_ERR_MISALIGNED;
+    if ((rc = check_ws(ws, ws_bytes, need))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = (char *)ws;
+    float2 *c = (float2 *)w;
+    char *aux = w + align_up(4 * sizeof(float2) * (size_t)nx * ny);
+    cudaError_t e = swt_analysis(wavelet, (const float2 *)img, c, nx, ny, -1.f, nullptr, nullptr, st);
+    if (e == cudaSuccess) e = swt_rayleigh_lambda(c, nx, ny, aux, lambda_out, st);
     return e == cudaSuccess ? AEXP_OK : cuda_fail(e);
 }
 

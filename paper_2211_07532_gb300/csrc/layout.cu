@@ -150,6 +150,10 @@ int rec_layout(const aexp_problem *p, const aexp_recon_opts *opt, RecLayout *R, 
     r.off_v = take(sizeof(float2) * nr);
     r.off_w = take(sizeof(float2) * nr);
     r.off_wave = take(r.wv.bytes);
+    if (opt->undecimated) {
+        r.off_swt = take(4 * sizeof(float2) * nr);
+        r.off_swtaux = take(swt_aux_bytes());
+    }
     if (with_grad) {
         const OpLayout &L = r.op;
         const int tblocks = L.ntp / 128;

@@ -142,15 +142,27 @@ cudaError_t recon_issue(const aexp_problem *p, const RecLayout &R, const aexp_re
     CK(op_prepare(p, L, ws, st));
     CK(op_transpose_y(L, y, ymeas, st));
 
+    // A^H y, the zero-filled reconstruction: the power iteration's default start and the
+    // input of the paper's lambda rule
+    const bool rayleigh = o->undecimated && o->lambda_rule == AEXP_LAMBDA_RAYLEIGH;
+    const bool need_ahy = rayleigh || (!(o->lipschitz > 0.0) && !o->power_init);
+    if (need_ahy) {
+        CK(op_apply_adjoint(L, ymeas, ws, st));
+        CK(op_adjoint_reduce(L, ws, w, st));
+    }
+    char *swt_aux = o->undecimated ? ws + R.off_swtaux : nullptr;
+    float2 *swt_c = o->undecimated ? (float2 *)(ws + R.off_swt) : nullptr;
+    if (rayleigh) {
+        CK(swt_analysis(o->wavelet, w, swt_c, L.nx, L.ny, -1.f, nullptr, nullptr, st));
+        CK(swt_rayleigh_lambda(swt_c, L.nx, L.ny, swt_aux, o->lambda_out, st));
+    } else if (o->undecimated) {
+        CK(swt_set_lambda(swt_aux, (double)lam, o->lambda_out, st));
+    }
+
     if (o->lipschitz > 0.0) {
         CK(set_lipschitz(L, ws, o->lipschitz, lip_out, st));
     } else {
-        const float2 *v0 = (const float2 *)o->power_init;
-        if (!v0) {  // A^H y, the zero-filled reconstruction
-            CK(op_apply_adjoint(L, ymeas, ws, st));
-            CK(op_adjoint_reduce(L, ws, w, st));
-            v0 = w;
-        }
+        const float2 *v0 = o->power_init ? (const float2 *)o->power_init : w;
         CK(power_iteration(L, ws, v0, v, w, o->n_power, lip_out, st));
     }
 
@@ -171,8 +183,14 @@ cudaError_t recon_issue(const aexp_problem *p, const RecLayout &R, const aexp_re
         // x_k = crop W^H soft(W pad v, lam / L_f);  z_{k+1} = x_k + beta_k (x_k - x_{k-1})
         double t_next = (1.0 + sqrt(1.0 + 4.0 * t * t)) / 2.0;
         double beta = (t - 1.0) / t_next;
-        CK(wave_forward(R.wv, v, wws, lam, &hdr->lipschitz, 1, st));
-        CK(wave_inverse(R.wv, wws, x_new, 1, beta, x_prev, z, st));
+        if (o->undecimated) {
+            // x_k = W^H soft(W v, lambda / L_f) with the tight frame ("balanced" FISTA)
+            CK(swt_analysis(o->wavelet, v, swt_c, L.nx, L.ny, -1.f, swt_lambda_slot(swt_aux), &hdr->lipschitz, st));
+            CK(swt_synthesis(o->wavelet, swt_c, x_new, L.nx, L.ny, 1, beta, x_prev, z, st));
+        } else {
+            CK(wave_forward(R.wv, v, wws, lam, &hdr->lipschitz, 1, st));
+            CK(wave_inverse(R.wv, wws, x_new, 1, beta, x_prev, z, st));
+        }
         t = t_next;
         float2 *tmp = x_prev;
         x_prev = x_new;
