@@ -41,6 +41,24 @@ def dist_info():
     return rank, world, local
 
 
+def max_over_ranks(ms: float, world: int) -> float:
+    """The slowest rank's time (all-reduce MAX over the process group; identity on one rank).
+    Every rank must call it the same number of times in the same order."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(world: int, units_per_rank_step: float, steps: int, total_ms: float) -> float:
+    """Whole-job throughput in G units/s: every rank processes its own units (its own slice),
+    the job takes as long as the slowest rank."""
+    return world * units_per_rank_step * steps / (total_ms / 1e3) / 1e9
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
 
@@ -281,13 +299,9 @@ def _run_ours(args, rank, world, local, dev):
             ev[i][1].record(stream)
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(step_ms)), world)
     ms_per_step = total_ms / args.steps
-    value = world * vsc_per_step * args.steps / (total_ms / 1e3) / 1e9
+    value = weak_scaling_value(world, vsc_per_step, args.steps, total_ms)
     status = ax.read_status(ws)
     nrmse = float(torch.linalg.vector_norm(x_out - x_gt) / torch.linalg.vector_norm(x_gt))
 
@@ -309,12 +323,8 @@ def _run_ours(args, rank, world, local, dev):
         b.record(stream)
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
-    e2e_total = float(sum(e2e_ms))
-    if world > 1:
-        t = torch.tensor([e2e_total], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = world * vsc_per_step * len(e2e_ms) / (e2e_total / 1e3) / 1e9
+    e2e_total = max_over_ranks(float(sum(e2e_ms)), world)
+    e2e_value = weak_scaling_value(world, vsc_per_step, len(e2e_ms), e2e_total)
 
     kern = _kernel_ms(ax, torch, prob, x_gt, y, precision, flush, stream)
     dom = max(kern, key=kern.get)
@@ -355,8 +365,8 @@ def _run_ours(args, rank, world, local, dev):
             o_ms.append(a.elapsed_time(b))
         o_nrmse = float(torch.linalg.vector_norm(x_out - x_gt) / torch.linalg.vector_norm(x_gt))
         o_kern = _kernel_ms(ax, torch, prob, x_gt, y, forms[other], flush, stream)
-        o_step = float(np.mean(o_ms))
-        c = {"s_per_slice": o_step / 1e3, "value": world * vsc_per_step / (o_step / 1e3) / 1e9, "unit": UNIT,
+        o_step = max_over_ranks(float(np.mean(o_ms)), world)
+        c = {"s_per_slice": o_step / 1e3, "value": weak_scaling_value(world, vsc_per_step, 1, o_step), "unit": UNIT,
              "nrmse_vs_phantom": o_nrmse, "device_status": ax.read_status(o_ws), "kernels_ms": o_kern,
              "speedup_vs_primary": ms_per_step / o_step, "items_per_sm": o_opts.items_per_sm}
         if other != "fp32":
@@ -395,7 +405,7 @@ def _run_ours(args, rank, world, local, dev):
             b.synchronize()
             l_ms.append(a.elapsed_time(b))
         cs_s = ms_per_step / 1e3 if f == args.form else comparison[f]["s_per_slice"]
-        ls_s = float(np.mean(l_ms)) / 1e3
+        ls_s = max_over_ranks(float(np.mean(l_ms)), world) / 1e3
         ls_baseline[f] = {"s_per_slice": ls_s, "iterations": 20, "applications": 41,
                           "nrmse_vs_phantom": float(torch.linalg.vector_norm(x_out - x_gt) / torch.linalg.vector_norm(x_gt)),
                           "cs_over_ls_time": cs_s / ls_s, "device_status": ax.read_status(lws)}
@@ -422,7 +432,8 @@ def _run_ours(args, rank, world, local, dev):
             b.record(stream)
             b.synchronize()
             p_ms.append(a.elapsed_time(b))
-        paper_cs[f] = {"s_per_slice": float(np.mean(p_ms)) / 1e3, "fista_iters": 100, "power_iters": n_power,
+        paper_cs[f] = {"s_per_slice": max_over_ranks(float(np.mean(p_ms)), world) / 1e3, "fista_iters": 100,
+                       "power_iters": n_power,
                        "applications": 2 * 100 + 2 * n_power + 2, "lambda": float(lam_dev.cpu()[0]),
                        "nrmse_vs_phantom": float(torch.linalg.vector_norm(x_out - x_gt) / torch.linalg.vector_norm(x_gt)),
                        "device_status": ax.read_status(pws)}
