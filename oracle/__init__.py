@@ -11,6 +11,7 @@ Contents
   plain FP64 double sums of A_exp and A_exp^H in C (``aexp_oracle.c``).
 * ``oracle.wavelet``: periodised orthonormal 2-D DWT (Haar, Daubechies-4 from
   its spectral factorisation), complex soft-threshold, the prox step.
+* ``oracle.coilcomp``: coil compression by principal components of the k-space data;
 * ``oracle.swt``: the paper's own regulariser -- one-level undecimated wavelet (a tight frame),
   the balanced-FISTA step with it and lambda = sigma / 2 from the histogram of W A^H y;
 * ``oracle.recon``: power-iteration Lipschitz estimate, FISTA, CGLS, objective,
