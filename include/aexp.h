@@ -174,6 +174,23 @@ AEXP_API int cs_recon(const aexp_problem *prob, const void *y, float lambda, int
              void *ws, size_t ws_bytes, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Coil compression (Sec. 2.2.1 compresses 32 receive channels to 20 virtual coils to speed the
+ * reconstruction up; Sec. 2.2.2 compares 8, 16 and 32; the method is not stated -- here the
+ * principal components of the k-space data): C = y y^H in FP64, its eigenvectors by cyclic
+ * Jacobi on the device, U = the nv leading ones, each scaled so that its largest component is
+ * real and positive; y_out = U^H y ([nv][nt] complex64), S_out = U^H S ([nv][nr] complex64).
+ * The compressed problem is prob with nc = nv and S = S_out (the encoding matrix does not
+ * depend on the coil).  eig_out: optional DEVICE double [nc], eigenvalues descending.
+ * Reads prob->nc, nt, nr and S; nc <= 32, 1 <= nv <= nc.  A Jacobi iteration that has not
+ * converged after 40 sweeps leaves AEXP_ERR_NONFINITE in the status word read by
+ * aexp_coil_compress_status.
+ * --------------------------------------------------------------------------- */
+AEXP_API int aexp_coil_compress_workspace_size(int nc, size_t *bytes);
+AEXP_API int aexp_coil_compress(const aexp_problem *prob, const void *y, int nv, void *y_out, void *S_out,
+                                double *eig_out, void *ws, size_t ws_bytes, void *stream);
+AEXP_API int aexp_coil_compress_status(const void *ws, int nc, void *stream, int *status);
+
+/* ---------------------------------------------------------------------------
  * The undecimated one-level wavelet on its own (Sec. 2.1; tight frame, subband s = fx + 2 fy
  * with f = lowpass 0 / highpass 1: LL, HL, LH, HH).  in/out: [ny][nx] complex64, coef:
  * [4][ny][nx] complex64 device arrays.  aexp_swt_prox: out = W^H soft_detail(W in, tau),

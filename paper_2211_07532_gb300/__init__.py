@@ -78,6 +78,9 @@ SIGNATURES = [
     ("aexp_wavelet_prox", _I, [_I, _I, _I, _I, ctypes.c_float, _P, _P, _P, _SZ, _P]),
     ("aexp_wavelet_forward", _I, [_I, _I, _I, _I, _P, _P, _P, _SZ, _P]),
     ("aexp_wavelet_prox_static", _I, [_I, _I, _I, _I, ctypes.c_float, _P, _P, _P]),
+    ("aexp_coil_compress_workspace_size", _I, [_I, ctypes.POINTER(_SZ)]),
+    ("aexp_coil_compress", _I, [_PROB, _P, _I, _P, _P, _P, _P, _SZ, _P]),
+    ("aexp_coil_compress_status", _I, [_P, _I, _P, ctypes.POINTER(_I)]),
     ("aexp_swt_workspace_size", _I, [_I, _I, ctypes.POINTER(_SZ)]),
     ("aexp_swt_forward", _I, [_I, _I, _I, _P, _P, _P]),
     ("aexp_swt_prox", _I, [_I, _I, _I, ctypes.c_float, _P, _P, _P, _SZ, _P]),
@@ -164,6 +167,10 @@ class Problem:
                    torch.as_tensor(d["S"], dtype=torch.complex64, device=dev),
                    torch.as_tensor(om, dtype=torch.float32, device=dev) if use_b0 else None,
                    torch.as_tensor(d["t"], dtype=torch.float32, device=dev) if use_b0 else None)
+
+    def with_coils(self, S):
+        """The same field model with other coil maps S [nc'][nr] (e.g. virtual coils)."""
+        return Problem(self.nx, self.ny, self.k, self.h, S, self.omega, self.t)
 
     @property
     def c(self):
@@ -304,6 +311,27 @@ def cs_recon_batched(probs, ys, lams, iters: int, opts: CReconOpts | None = None
     _check(lib().cs_recon_batched(probs_c, n, yp, lp, int(iters), ctypes.byref(opts), xp, _ptr(lipschitz_out),
                                   _ptr(ws), ws.numel(), _stream(stream)), "cs_recon_batched")
     return x_outs, lipschitz_out
+
+
+def coil_compress(prob: Problem, y, nv: int, stream=None):
+    """Principal-component coil compression: returns (compressed Problem with nc = nv,
+    y_v [nv][nt] complex64, eigenvalues float64 [nc] descending), all on the device."""
+    torch = _torch()
+    y = y.contiguous()
+    dev = y.device
+    n = ctypes.c_size_t()
+    _check(lib().aexp_coil_compress_workspace_size(prob.nc, ctypes.byref(n)), "aexp_coil_compress_workspace_size")
+    ws = _alloc(n.value, dev)
+    yv = torch.empty((nv, prob.nt), dtype=torch.complex64, device=dev)
+    Sv = torch.empty((nv, prob.nr), dtype=torch.complex64, device=dev)
+    eig = torch.empty(prob.nc, dtype=torch.float64, device=dev)
+    _check(lib().aexp_coil_compress(prob.c, _ptr(y), int(nv), _ptr(yv), _ptr(Sv), _ptr(eig), _ptr(ws), ws.numel(),
+                                    _stream(stream)), "aexp_coil_compress")
+    st = ctypes.c_int()
+    _check(lib().aexp_coil_compress_status(_ptr(ws), prob.nc, _stream(stream), ctypes.byref(st)),
+           "aexp_coil_compress_status")
+    _check(st.value, "coil compression (Jacobi)")
+    return prob.with_coils(Sv), yv, eig
 
 
 def swt_forward(img, wavelet="db4", stream=None):

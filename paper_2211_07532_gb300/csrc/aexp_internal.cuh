@@ -240,6 +240,12 @@ cudaError_t swt_synthesis(int wavelet, const float2 *c, float2 *out, int nx, int
 cudaError_t swt_rayleigh_lambda(const float2 *c, int nx, int ny, char *aux, double *lam_out, cudaStream_t st);
 cudaError_t swt_set_lambda(char *aux, double lam, double *lam_out, cudaStream_t st);
 
+// Coil compression by principal components of the data (coilcomp.cu): y [nc][nt], S [nc][nr]
+// -> y_out [nv][nt], S_out [nv][nr]; ws of coil_compress_bytes(nc).
+size_t coil_compress_bytes(int nc);
+cudaError_t coil_compress(const float2 *y, const float2 *S, int nc, int nt, int nr, int nv, float2 *y_out,
+                          float2 *S_out, double *eig_out, char *ws, cudaStream_t st);
+
 // Least squares by CGLS (cgls.cu): operator workspace + image vectors x, p, s, k-space r, q,
 // FP64 partial sums and scalars.
 struct CglsLayout {

@@ -527,6 +527,33 @@ int aexp_fista_step_vjp(const aexp_problem *prob, const aexp_recon_opts *opts, c
     return e == cudaSuccess ? AEXP_OK : cuda_fail(e);
 }
 
+int aexp_coil_compress_workspace_size(int nc, size_t *bytes) {
+    if (nc < 1 || nc > kMaxCoils || !bytes) return AEXP_ERR_INVALID_ARG;
+    *bytes = coil_compress_bytes(nc);
+    return AEXP_OK;
+}
+
+int aexp_coil_compress(const aexp_problem *prob, const void *y, int nv, void *y_out, void *S_out, double *eig_out,
+                       void *ws, size_t ws_bytes, void *stream) {
+    int rc = check_problem(prob);
+    if (rc) return rc;
+    if (!y || !y_out || !S_out || nv < 1 || nv > prob->nc) return AEXP_ERR_INVALID_ARG;
+    if (!aligned(y, 8) || !aligned(y_out, 8) || !aligned(S_out, 8) || !aligned(eig_out, 8)) return AEXP_ERR_MISALIGNED;
+    if ((rc = check_ws(ws, ws_bytes, coil_compress_bytes(prob->nc)))) return rc;
+    cudaError_t e = coil_compress((const float2 *)y, (const float2 *)prob->S, prob->nc, prob->nt, prob->nx * prob->ny,
+                                  nv, (float2 *)y_out, (float2 *)S_out, eig_out, (char *)ws, (cudaStream_t)stream);
+    return e == cudaSuccess ? AEXP_OK : cuda_fail(e);
+}
+
+int aexp_coil_compress_status(const void *ws, int nc, void *stream, int *status) {
+    if (!ws || !status || nc < 1 || nc > kMaxCoils) return AEXP_ERR_INVALID_ARG;
+    const char *p = (const char *)ws + coil_compress_bytes(nc) - align_up(sizeof(int));
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(status, p, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? AEXP_OK : cuda_fail(e);
+}
+
 int aexp_swt_workspace_size(int nx, int ny, size_t *bytes) {
     if (nx < 1 || ny < 1 || !bytes) return AEXP_ERR_INVALID_ARG;
     if ((long long)nx * ny > (1LL << 26)) return AEXP_ERR_UNSUPPORTED;
