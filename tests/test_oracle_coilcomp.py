@@ -35,6 +35,11 @@ def test_energy_and_ordering(setup):
     for nv in (1, 3, 6):
         q, yv, _ = coilcomp.compress(p, y, nv)
         assert np.isclose(np.sum(np.abs(yv) ** 2), e[:nv].sum(), rtol=1e-12)
+    # against the singular value decomposition of the data (a different factorisation): the
+    # eigenvalues are the squared singular values, the columns the left singular vectors up to phase
+    W, sv, _ = np.linalg.svd(y, full_matrices=False)
+    assert np.allclose(e, sv ** 2, rtol=1e-10)
+    assert np.allclose(np.abs(np.sum(W.conj() * U, axis=0)), 1.0, atol=1e-9)
     a = np.argmax(np.abs(U), axis=0)
     lead = U[a, np.arange(U.shape[1])]
     assert np.allclose(lead.imag, 0, atol=1e-14) and np.all(lead.real > 0)
