@@ -441,6 +441,24 @@ def _run_ours(args, rank, world, local, dev):
 
     # coil compression (Sec. 2.2.1: 20 virtual coils to speed the reconstruction up): principal
     # components of the data on the device, then the same reconstruction with nv coils
+    def solve_ms(pr, yy, lm, f):
+        """Mean event time of the 50-iteration solve of problem pr in form f (L2 flushed between runs)."""
+        o = ax.recon_opts(precision=forms[f], wavelet="db4", levels=levels, n_power=n_power)
+        w = ax.recon_workspace(pr, o)
+        for _ in range(max(1, args.warmup)):
+            ax.cs_recon(pr, yy, lm, iters, opts=o, ws=w, x_out=x_out, lipschitz_out=L_out)
+        torch.cuda.synchronize()
+        t_ms = []
+        for i in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ax.cs_recon(pr, yy, lm, iters, opts=o, ws=w, x_out=x_out, lipschitz_out=L_out)
+            b.record(stream)
+            b.synchronize()
+            t_ms.append(a.elapsed_time(b))
+        return max_over_ranks(float(np.mean(t_ms)), world), ax.read_status(w)
+
     virtual = {}
     for f, nv in (("fp32", 20), ("bf16", 16), ("bf16", 20)):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -449,27 +467,30 @@ def _run_ours(args, rank, world, local, dev):
         b.record(stream)
         b.synchronize()
         comp_ms = a.elapsed_time(b)
-        vo = ax.recon_opts(precision=forms[f], wavelet="db4", levels=levels, n_power=n_power)
-        vws = ax.recon_workspace(pv, vo)
-        for _ in range(max(1, args.warmup)):
-            ax.cs_recon(pv, yv, lam, iters, opts=vo, ws=vws, x_out=x_out, lipschitz_out=L_out)
-        torch.cuda.synchronize()
-        v_ms = []
-        for i in range(args.steps):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            ax.cs_recon(pv, yv, lam, iters, opts=vo, ws=vws, x_out=x_out, lipschitz_out=L_out)
-            b.record(stream)
-            b.synchronize()
-            v_ms.append(a.elapsed_time(b))
+        v_ms, v_st = solve_ms(pv, yv, lam, f)
         e = eig.cpu().numpy()
         virtual[f"{f}_vc{nv}"] = {
-            "s_per_slice": max_over_ranks(float(np.mean(v_ms)), world) / 1e3, "compression_ms": comp_ms,
-            "energy_kept": float(e[:nv].sum() / e.sum()),
+            "s_per_slice": v_ms / 1e3, "compression_ms": comp_ms, "energy_kept": float(e[:nv].sum() / e.sum()),
             "nrmse_vs_phantom": float(torch.linalg.vector_norm(x_out - x_gt) / torch.linalg.vector_norm(x_gt)),
-            "device_status": ax.read_status(vws)}
-        del vws
+            "device_status": v_st}
+
+    # field model beyond 3rd order: 4th-order harmonics + concomitant rows + B0 = 30 terms
+    pe = synth.slice_200_expanded(index=rank)
+    prob_e = ax.Problem.from_arrays(pe, device=dev)
+    xe_gt = torch.as_tensor(pe["x_gt"], device=dev)
+    ws_e = ax.workspace(prob_e, ax.FP32)
+    ax.prepare(prob_e, ws_e, ax.FP32)
+    ye = ax.a_exp_forward(prob_e, xe_gt, ws_e)
+    ye = (ye + float(torch.sqrt(torch.mean(ye.abs() ** 2))) / pe["snr"] * torch.as_tensor(pe["noise"], device=dev))
+    ye = ye.contiguous()
+    lam_e = 1e-3 * float(ax.a_exp_adjoint(prob_e, ye, ws_e).abs().max())
+    del ws_e
+    expanded = {"terms": pe["nl"] + 1, "workload": "200x200 slice, 4th-order harmonics + 4 concomitant rows + B0, "
+                                                   "tilted 20 deg, 32 coils, 24k samples"}
+    for f in ("fp32", "bf16"):
+        e_ms, e_st = solve_ms(prob_e, ye, lam_e, f)
+        expanded[f] = {"s_per_slice": e_ms / 1e3, "device_status": e_st,
+                       "nrmse_vs_phantom": float(torch.linalg.vector_norm(x_out - xe_gt) / torch.linalg.vector_norm(xe_gt))}
 
     if rank == 0:
         cpu = None
@@ -506,6 +527,7 @@ def _run_ours(args, rank, world, local, dev):
             "ls_baseline_cgls20": ls_baseline,
             "paper_regulariser_cs100": paper_cs,
             "virtual_coils": virtual,
+            "field_terms_30": expanded,
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
@@ -685,6 +707,21 @@ def run_op_only(args):
                       "y_norm": float(yo.abs().sum()), "x_norm": float(xo.abs().sum())}))
 
 
+def run_trends(args):
+    """NRMSE tables of the simulation study (Sec. 2.2.2, Figs. 4 and 5): no timing."""
+    import torch
+    from paper_2211_07532_gb300 import build as _b
+    _b.build()
+    import paper_2211_07532_gb300 as ax
+    from paper_2211_07532_gb300 import trends
+    t0 = time.time()
+    out = trends.run(ax, eddy_scale=args.eddy_scale)
+    torch.cuda.synchronize()
+    out.update(kind="trends", data="synthetic", wall_s=time.time() - t0,
+               workload="148x148 (1.5 mm), 32 physical coils, single-shot spiral at R, 2nd-order field + B0")
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -702,8 +739,13 @@ def main():
                     help="slice: the 200x200 paper-scale slice (default); ragged: the 372-problem batch; "
                          "diff: unrolled-FISTA gradients")
     ap.add_argument("--volumes", type=int, default=31, help="diffusion volumes per slice (ragged workload)")
+    ap.add_argument("--trends", action="store_true",
+                    help="the simulation study of Figs. 4-5 (NRMSE vs R, coils, SNR, model) instead of timing")
+    ap.add_argument("--eddy-scale", type=float, default=0.1, help="eddy amplitude of the trend inputs")
     args = ap.parse_args()
-    if args.mode == "op":
+    if args.trends:
+        run_trends(args)
+    elif args.mode == "op":
         run_op_only(args)
     elif args.workload == "ragged" and args.impl == "ours":
         run_ragged(args)

@@ -95,7 +95,9 @@ typedef struct aexp_problem {
     int nx, ny;           /* image size; nr = nx * ny                                    */
     int nt;               /* k-space samples per coil                                    */
     int nc;               /* receive coils                                               */
-    int nl;               /* spherical-harmonic field terms (Sec. 1: up to 3rd order = 16) */
+    int nl;               /* field terms: spherical harmonics (Sec. 1: up to 3rd order = 16;
+                             4th order = 25) and any extra rows such as concomitant fields
+                             (Fig. S3d); nl + (omega != NULL) <= 32                      */
     const float *k;       /* [nl][nt] field coefficients k_l(t), rad / m^deg(l)          */
     const float *h;       /* [nl][nr] basis values h_l(r), m^deg(l)                      */
     const float *omega;   /* [nr] static off-resonance (B0 map), rad/s, or NULL          */

@@ -22,7 +22,7 @@ namespace aexp {
 
 constexpr int kTileSide = 8;
 constexpr int kTileVox = 64;
-constexpr int kMaxTerms = 20;
+constexpr int kMaxTerms = 32;
 constexpr int kMaxCoils = 32;
 constexpr int kFwdThreads = 128;
 constexpr int kAdjThreads = 128;
@@ -74,7 +74,7 @@ struct ProbDesc {
 struct OpLayout {
     int nx, ny, nr, nt, nc, nl, has_b0;
     int nterms;      // nl + has_b0
-    int LP;          // padded term count (template): 4, 8, 12 or 20
+    int LP;          // padded term count (template): 4, 8, 12, 20 or 32
     int CB;          // padded coil count (template): 4, 8, 16, 20, 32 (FP32) or 8, 16, 32 (TC)
     int ntx, nty, ntiles, nr_pad;
     int ntp;         // nt padded to kTPad

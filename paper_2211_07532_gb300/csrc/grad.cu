@@ -241,7 +241,7 @@ template <int CB, int LP>
 cudaError_t launch_grad(const OpLayout &L, const RecLayout &R, char *ws, cudaStream_t st) {
     constexpr unsigned STAGE = 2 * kTileVox * LP * 4 + kTileVox * CB * 8 + 2 * kTileVox * 8;
     auto kern = grad_k_kernel<CB, LP>;
-    if (2 * STAGE > 48 * 1024) {
+    {  // always opted in: the static barriers count against the 48 KB default too
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * STAGE);
         if (e != cudaSuccess) return e;
     }
@@ -259,7 +259,8 @@ cudaError_t launch_grad(const OpLayout &L, const RecLayout &R, char *ws, cudaStr
         case 4: return launch_grad<CBV, 4>(L, R, ws, st);                  \
         case 8: return launch_grad<CBV, 8>(L, R, ws, st);                  \
         case 12: return launch_grad<CBV, 12>(L, R, ws, st);                \
-        default: return launch_grad<CBV, 20>(L, R, ws, st);                \
+        case 20: return launch_grad<CBV, 20>(L, R, ws, st);                \
+        default: return launch_grad<CBV, 32>(L, R, ws, st);                \
     }
 
 cudaError_t grad_k_launch(const RecLayout &R, char *ws, cudaStream_t st) {

@@ -6,7 +6,7 @@
 namespace aexp {
 
 namespace {
-int pad_terms(int n) { return n <= 4 ? 4 : n <= 8 ? 8 : n <= 12 ? 12 : 20; }
+int pad_terms(int n) { return n <= 4 ? 4 : n <= 8 ? 8 : n <= 12 ? 12 : n <= 20 ? 20 : 32; }
 int pad_coils(int n) { return n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : n <= 20 ? 20 : 32; }
 // tensor-core forms: N = 2 * CB must be a multiple of 16 with a power-of-two half for TMEM loads
 int pad_coils_tc(int n) { return n <= 8 ? 8 : n <= 16 ? 16 : 32; }

@@ -365,7 +365,7 @@ cudaError_t launch_fwd(const OpLayout &L, char *ws, cudaStream_t st) {
     constexpr int MT = fwd_mt_for(CB);
     constexpr unsigned STAGE = kTileVox * LP * sizeof(float) + kTileVox * CB * sizeof(float2);
     auto kern = fwd_fp32_kernel<CB, LP, MT>;
-    if (2 * STAGE > 48 * 1024) {
+    {  // always opted in: the static barriers count against the 48 KB default too
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * STAGE);
         if (e != cudaSuccess) return e;
     }
@@ -382,7 +382,7 @@ cudaError_t launch_adj(const OpLayout &L, const float2 *yt, char *ws, cudaStream
     constexpr int MR = adj_mr_for(CB);
     constexpr unsigned STAGE = kAdjStageT * (LP * sizeof(float) + CB * sizeof(float2) + 2 * MR * sizeof(float));
     auto kern = adj_fp32_kernel<CB, LP, MR>;
-    if (2 * STAGE > 48 * 1024) {
+    {  // always opted in: the static barriers count against the 48 KB default too
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * STAGE);
         if (e != cudaSuccess) return e;
     }
@@ -399,7 +399,8 @@ cudaError_t launch_adj(const OpLayout &L, const float2 *yt, char *ws, cudaStream
         case 4: return FN<CBV, 4>(__VA_ARGS__);          \
         case 8: return FN<CBV, 8>(__VA_ARGS__);          \
         case 12: return FN<CBV, 12>(__VA_ARGS__);        \
-        default: return FN<CBV, 20>(__VA_ARGS__);        \
+        case 20: return FN<CBV, 20>(__VA_ARGS__);        \
+        default: return FN<CBV, 32>(__VA_ARGS__);        \
     }
 
 #define AEXP_DISPATCH(FN, ...)                                   \

@@ -768,7 +768,8 @@ cudaError_t launch_adj_tc(const ProbDesc *pd, int nprob, int max_pack_blocks, co
         case 4: AEXP_TC_HL(FN, CBV, 4, __VA_ARGS__)      \
         case 8: AEXP_TC_HL(FN, CBV, 8, __VA_ARGS__)      \
         case 12: AEXP_TC_HL(FN, CBV, 12, __VA_ARGS__)    \
-        default: AEXP_TC_HL(FN, CBV, 20, __VA_ARGS__)    \
+        case 20: AEXP_TC_HL(FN, CBV, 20, __VA_ARGS__)    \
+        default: AEXP_TC_HL(FN, CBV, 32, __VA_ARGS__)    \
     }
 #define AEXP_TC_DISPATCH(FN, ...)                                \
     switch (CBv) {                                               \

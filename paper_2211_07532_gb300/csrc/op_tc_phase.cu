@@ -158,7 +158,8 @@ __device__ __forceinline__ void phase_mma_ks(uint32_t d, uint64_t ah, uint64_t a
 __device__ __forceinline__ void phase_mma(int ks, uint32_t d, uint64_t ah, uint64_t al, uint64_t bh, uint64_t bl) {
     if (ks <= 1) phase_mma_ks<1>(d, ah, al, bh, bl);
     else if (ks == 2) phase_mma_ks<2>(d, ah, al, bh, bl);
-    else phase_mma_ks<3>(d, ah, al, bh, bl);
+    else if (ks == 3) phase_mma_ks<3>(d, ah, al, bh, bl);
+    else phase_mma_ks<4>(d, ah, al, bh, bl);
 }
 
 // Contraction thread, one item.

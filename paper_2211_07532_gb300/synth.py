@@ -20,12 +20,16 @@ available):
              sum_c |S_c(r)|^2 = 1 (the ESPIRiT normalisation, Sec. 2.2.1);
 * field   -- nominal spiral k_x, k_y plus exponential eddy decays
              (tau 0.5-5 ms, amplitude 1-5 %) in every spherical-harmonic term
-             up to 2nd or 3rd order (Sec. 1: field dynamics to 2nd/3rd order);
+             up to 2nd, 3rd or 4th order (Sec. 1: field dynamics to 2nd/3rd order;
+             higher orders and second-order concomitant-field rows, Fig. S3d, as
+             extra terms of the same operator);
 * B0      -- a smooth sum of Gaussians rescaled to a stated +-Hz range;
 * spiral  -- variable-density Archimedean (64^2 case) or uniform single-shot
              with acceleration R (N/(2R) turns).
 
-Geometry: voxel r = iy*nx + ix sits at ((ix - nx/2)*dx, (iy - ny/2)*dy, z0).
+Geometry: voxel r = iy*nx + ix sits at (u, v cos(tilt), v sin(tilt) + z0) with
+u = (ix - nx/2)*dx, v = (iy - ny/2)*dy: an axial slice at z0, or an oblique one
+rotated by ``tilt`` about the x axis.
 Units: k_l in rad/m^deg(l), h_l in m^deg(l), omega in rad/s, t in s.
 """
 
@@ -37,28 +41,34 @@ import numpy as np
 
 BASE_SEED = 2211075320
 
-# Number of real solid harmonics up to a given order: 1, 4, 9, 16.
+GAMMA = 2.675221874e8  # proton gyromagnetic ratio, rad / s / T
+
+
+# Number of real solid harmonics up to a given order: 1, 4, 9, 16, 25.
 def n_terms(order: int) -> int:
     return (order + 1) ** 2
 
 
 def term_degree(l: int) -> int:
-    """Polynomial degree of the l-th basis term (0 | 1,2,3 | 4..8 | 9..15)."""
+    """Polynomial degree of the l-th basis term (0 | 1,2,3 | 4..8 | 9..15 | 16..24)."""
     return int(math.isqrt(l))
 
 
 def sh_basis(x: np.ndarray, y: np.ndarray, z: np.ndarray, order: int) -> np.ndarray:
-    """Unnormalised real solid harmonics up to ``order`` (<= 3), by degree.
+    """Unnormalised real solid harmonics up to ``order`` (<= 4), by degree, m = -l..l.
 
     Ordering: 1; x, y, z; xy, yz, 2z^2-x^2-y^2, xz, x^2-y^2;
     3x^2y-y^3, xyz, y(4z^2-x^2-y^2), z(2z^2-3x^2-3y^2), x(4z^2-x^2-y^2),
-    z(x^2-y^2), x^3-3xy^2.  The paper fits field dynamics to spherical
+    z(x^2-y^2), x^3-3xy^2;
+    xy(x^2-y^2), yz(3x^2-y^2), xy(7z^2-r^2), yz(7z^2-3r^2), 35z^4-30z^2r^2+3r^4,
+    xz(7z^2-3r^2), (x^2-y^2)(7z^2-r^2), xz(x^2-3y^2), x^4-6x^2y^2+y^4.
+    The paper fits field dynamics to spherical
     harmonics up to 2nd or 3rd order (Sec. 1, Sec. 2.2.1) without fixing a
     normalisation; since h_l(r) is an input array to the operator, this choice
     only shapes the synthetic data.
     """
-    if order < 0 or order > 3:
-        raise ValueError("order must be 0..3")
+    if order < 0 or order > 4:
+        raise ValueError("order must be 0..4")
     x = np.asarray(x, np.float64)
     y = np.asarray(y, np.float64)
     z = np.asarray(z, np.float64) + np.zeros_like(x)
@@ -78,10 +88,52 @@ def sh_basis(x: np.ndarray, y: np.ndarray, z: np.ndarray, order: int) -> np.ndar
             z * (x * x - y * y),
             x ** 3 - 3 * x * y * y,
         ]
+    if order >= 4:
+        z2 = z * z
+        terms += [
+            x * y * (x * x - y * y),
+            y * z * (3 * x * x - y * y),
+            x * y * (7 * z2 - r2),
+            y * z * (7 * z2 - 3 * r2),
+            35 * z2 * z2 - 30 * z2 * r2 + 3 * r2 * r2,
+            x * z * (7 * z2 - 3 * r2),
+            (x * x - y * y) * (7 * z2 - r2),
+            x * z * (x * x - 3 * y * y),
+            x ** 4 - 6 * x * x * y * y + y ** 4,
+        ]
     return np.stack(terms, axis=0)
 
 
+def concomitant_basis(x: np.ndarray, y: np.ndarray, z: np.ndarray) -> np.ndarray:
+    """Spatial rows of the second-order concomitant (Maxwell) field: z^2, x^2 + y^2, xz, yz."""
+    x = np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
+    z = np.asarray(z, np.float64) + np.zeros_like(x)
+    return np.stack([z * z, x * x + y * y, x * z, y * z], axis=0)
+
+
+def concomitant_coefficients(G: np.ndarray, dt: float, b0_tesla: float) -> np.ndarray:
+    """Phase coefficients [4][nt] (rad / m^2) of the concomitant rows for gradients G [3][nt] (T/m).
+
+    Lowest-order Maxwell field of a gradient G along a main field B0 z^:
+        B_c = [(Gx^2 + Gy^2) z^2 + Gz^2 (x^2 + y^2) / 4 - Gx Gz xz - Gy Gz yz] / (2 B0),
+    and the phase gamma * int_0^t B_c, accumulated per dwell (rectangle rule, the same as
+    the gradients drawn from the sampled trajectory).
+    """
+    gx, gy, gz = (np.asarray(g, np.float64) for g in G)
+    rate = np.stack([gx * gx + gy * gy, gz * gz / 4.0, -gx * gz, -gy * gz], axis=0) / (2.0 * b0_tesla)
+    return GAMMA * dt * np.cumsum(rate, axis=1)
+
+
+def gradients_from_k(k_phys: np.ndarray, dt: float) -> np.ndarray:
+    """G [3][nt] in T/m from physical k [3][nt] (rad/m), k = gamma int G: backward differences,
+    k before the first sample = 0."""
+    k = np.asarray(k_phys, np.float64)
+    return np.diff(k, axis=1, prepend=0.0) / (GAMMA * dt)
+
+
 def voxel_positions(nx: int, ny: int, fov_x: float, fov_y: float):
+    """In-plane coordinates (u, v) of every voxel, row-major (iy, ix)."""
     dx = fov_x / nx
     dy = fov_y / ny
     ix = np.arange(nx)
@@ -148,10 +200,11 @@ def b0_map(rng, X, Y, fov: float, max_hz: float, n_blobs: int = 6) -> np.ndarray
 
 
 def field_coefficients(rng, kxy: np.ndarray, h: np.ndarray, dt: float, order: int,
-                       rho: float, eddy: bool = True) -> np.ndarray:
-    """k_l(t) for l < (order+1)^2: nominal k_x, k_y in terms 1, 2 plus eddy decays.
+                       rho: float, eddy: bool = True, tilt: float = 0.0, eddy_scale: float = 1.0) -> np.ndarray:
+    """k_l(t) for l < (order+1)^2: nominal k_x, k_v cos(tilt), k_v sin(tilt) in terms 1, 2, 3
+    (the readout of a slice tilted about x) plus eddy decays.
 
-    Each term receives a_l * s_l * [k_src - (k_src * g_tau)](t), a_l ~ U[0.01, 0.05],
+    Each term receives a_l * s_l * [k_src - (k_src * g_tau)](t), a_l ~ eddy_scale * U[0.01, 0.05],
     tau_l ~ U[0.5, 5] ms, k_src = k_x or k_y (seeded), s_l = rho / max_r |h_l(r)|
     so that the term's phase stays below a_l * kmax * rho at the FOV edge.
     """
@@ -160,7 +213,8 @@ def field_coefficients(rng, kxy: np.ndarray, h: np.ndarray, dt: float, order: in
     k = np.zeros((L, nt))
     if L > 1:
         k[1] = kxy.real
-        k[2] = kxy.imag
+        k[2] = kxy.imag * math.cos(tilt)
+        k[3] = kxy.imag * math.sin(tilt)
     if not eddy:
         return k
     for l in range(L):
@@ -169,7 +223,7 @@ def field_coefficients(rng, kxy: np.ndarray, h: np.ndarray, dt: float, order: in
         src = kxy.real if rng.uniform() < 0.5 else kxy.imag
         hmax = np.max(np.abs(h[l]))
         scale = rho / hmax if hmax > 0 else rho ** (1 - term_degree(l))
-        k[l] += a * scale * (src - exp_smooth(src, dt, tau))
+        k[l] += eddy_scale * a * scale * (src - exp_smooth(src, dt, tau))
     return k
 
 
@@ -185,32 +239,43 @@ def make_problem(nx: int, ny: int | None = None, nt: int = 2048, nc: int = 8, or
                  fov: float = 0.22, dwell: float = 4e-6, turns: float | None = None,
                  density_power: float = 1.0, b0_hz: float = 100.0, z0: float = 0.0015,
                  seed: int = BASE_SEED, eddy: bool = True, with_b0: bool = True,
-                 shared_geometry_seed: int | None = None) -> dict:
+                 shared_geometry_seed: int | None = None, tilt: float = 0.0,
+                 concomitant: bool = False, b0_tesla: float = 7.0, eddy_scale: float = 1.0) -> dict:
     """One synthetic slice problem; every array is rounded to float32/complex64.
 
     Returned keys: nx, ny, nt, nc, nl, k[nl][nt], h[nl][nr], omega[nr], t[nt],
     S[nc][nr], x_gt[nr], noise[nc][nt] (E|n|^2 = 1), fov, dwell, z0, seed.
     ``shared_geometry_seed`` draws the phantom, coils and B0 from a second stream
     (used when many diffusion volumes share one slice and differ only in the field).
+    ``tilt`` (rad) rotates the slice about the x axis; the readout's in-plane k_v then drives
+    the physical y and z gradients (k_y = k_v cos tilt, k_z = k_v sin tilt).
+    ``concomitant`` appends the four second-order concomitant-field rows (z^2, x^2 + y^2, xz,
+    yz) of the readout gradients at ``b0_tesla`` after the spherical-harmonic rows.
     """
     ny = nx if ny is None else ny
     rng = np.random.default_rng(seed)
     grng = rng if shared_geometry_seed is None else np.random.default_rng(shared_geometry_seed)
-    X, Y = voxel_positions(nx, ny, fov, fov * ny / nx)
-    h = sh_basis(X, Y, z0, order)
+    U, V = voxel_positions(nx, ny, fov, fov * ny / nx)
+    ct, st = math.cos(tilt), math.sin(tilt)
+    X, Y, Z = U, V * ct, V * st + z0
+    h = sh_basis(X, Y, Z, order)
     kmax = math.pi / (fov / nx)
     if turns is None:
         turns = nx / 8.0
     kxy = spiral_k(nt, kmax, turns, density_power)
-    k = field_coefficients(rng, kxy, h, dwell, order, fov / 2, eddy)
+    k = field_coefficients(rng, kxy, h, dwell, order, fov / 2, eddy, tilt, eddy_scale)
     t = np.arange(nt) * dwell
-    omega = b0_map(grng, X, Y, fov, b0_hz) if with_b0 else np.zeros(X.size)
-    S = coil_maps(grng, X, Y, fov, nc)
-    x_gt = ellipse_phantom(grng, X, Y, fov)
+    omega = b0_map(grng, U, V, fov, b0_hz) if with_b0 else np.zeros(U.size)
+    S = coil_maps(grng, U, V, fov, nc)
+    x_gt = ellipse_phantom(grng, U, V, fov)
     noise = (rng.standard_normal((nc, nt)) + 1j * rng.standard_normal((nc, nt))) / math.sqrt(2)
+    if concomitant:
+        kphys = np.stack([kxy.real, kxy.imag * ct, kxy.imag * st], axis=0)
+        h = np.concatenate([h, concomitant_basis(X, Y, Z)], axis=0)
+        k = np.concatenate([k, concomitant_coefficients(gradients_from_k(kphys, dwell), dwell, b0_tesla)], axis=0)
     return dict(nx=nx, ny=ny, nt=nt, nc=nc, nl=h.shape[0], k=_f32(k), h=_f32(h),
                 omega=_f32(omega), t=_f32(t), S=_c64(S), x_gt=_c64(x_gt), noise=_c64(noise),
-                fov=fov, dwell=dwell, z0=z0, seed=seed)
+                fov=fov, dwell=dwell, z0=z0, seed=seed, tilt=tilt)
 
 
 # --------------------------------------------------------------------------
@@ -233,6 +298,17 @@ def slice_200(index: int = 0) -> dict:
     Reconstructed with a 4-level Daubechies-4 wavelet, 50 FISTA iterations, SNR 10."""
     p = make_problem(200, nt=24000, nc=32, order=3, dwell=1e-6, turns=200 / 8.0,
                      density_power=1.0, b0_hz=150.0, seed=BASE_SEED + 1000 * 2 + index)
+    p.update(snr=10.0, wavelet="db4", levels=4, iters=50, lambda_rel=1e-3)
+    return p
+
+
+def slice_200_expanded(index: int = 0) -> dict:
+    """The 200x200 slice with a field model beyond 3rd order: 4th-order solid harmonics
+    (25 terms), the four second-order concomitant-field rows of the readout at 7 T, plus B0
+    (30 terms), on a slice tilted by 20 degrees about x, 20 mm off isocentre."""
+    p = make_problem(200, nt=24000, nc=32, order=4, dwell=1e-6, turns=200 / 8.0,
+                     density_power=1.0, b0_hz=150.0, seed=BASE_SEED + 1000 * 2 + index,
+                     tilt=math.radians(20.0), z0=0.02, concomitant=True)
     p.update(snr=10.0, wavelet="db4", levels=4, iters=50, lambda_rel=1e-3)
     return p
 

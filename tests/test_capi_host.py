@@ -79,8 +79,16 @@ def test_workspace_size_is_host_arithmetic(L):
     assert n2.value > n.value
 
 
+def test_term_count_limit(L):
+    """Up to 32 field terms with B0 (4th order = 25 harmonics, plus concomitant rows)."""
+    n = ctypes.c_size_t()
+    assert L.aexp_workspace_size(ctypes.byref(_fake_problem(nl=31)), 0, ctypes.byref(n)) == 0
+    assert L.aexp_workspace_size(ctypes.byref(_fake_problem(nl=32, omega=False)), 0, ctypes.byref(n)) == 0
+    assert L.aexp_workspace_size(ctypes.byref(_fake_problem(nl=32)), 0, ctypes.byref(n)) == -3
+
+
 @pytest.mark.parametrize("field,value,code", [
-    ("nx", 0, -1), ("nt", -3, -1), ("nc", 0, -1), ("nc", 33, -3), ("nl", 20, -3),
+    ("nx", 0, -1), ("nt", -3, -1), ("nc", 0, -1), ("nc", 33, -3), ("nl", 32, -3),
 ])
 def test_invalid_problems_are_rejected(L, field, value, code):
     p = _fake_problem()
