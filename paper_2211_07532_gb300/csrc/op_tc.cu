@@ -116,6 +116,8 @@ __device__ __forceinline__ void fwd_promote(uint32_t ta, float inv, float4 *dst,
         tc::tmem_ld<CH>(ta + (uint32_t)c0, v);
         tc::tmem_ld<CH>(ta + tmem_acc_cols(N) + (uint32_t)c0, w);
         tc::tmem_ld_wait();
+        tc::tmem_regs_ready<CH>(v);
+        tc::tmem_regs_ready<CH>(w);
 #pragma unroll
         for (int c = 0; c < CH / 4; ++c) {
             float4 o = make_float4(fmaf(w[4 * c], kLoInv, v[4 * c]) * inv, fmaf(w[4 * c + 1], kLoInv, v[4 * c + 1]) * inv,
@@ -146,6 +148,10 @@ __device__ __forceinline__ void adj_promote(uint32_t ta, const float4 *s4, float
         tc::tmem_ld<8>(ta + TM + (uint32_t)c0, wr);
         tc::tmem_ld<8>(ta + TM + (uint32_t)(CB + c0), wi);
         tc::tmem_ld_wait();
+        tc::tmem_regs_ready<8>(ur);
+        tc::tmem_regs_ready<8>(ui);
+        tc::tmem_regs_ready<8>(wr);
+        tc::tmem_regs_ready<8>(wi);
 #pragma unroll
         for (int q4 = 0; q4 < 4; ++q4) {
             const float4 sv = s4[c0 / 2 + q4];
@@ -358,6 +364,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     if (ntl > 0 && ok) {
                         tc::tmem_ld<N / 2>(ta0, v);
                         tc::tmem_ld_wait();
+                        tc::tmem_regs_ready<N / 2>(v);
                     } else {
 #pragma unroll
                         for (int c = 0; c < N / 2; ++c) v[c] = 0.f;
@@ -601,6 +608,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                             tc::tmem_ld<8>(ta0 + (uint32_t)c0, ur);
                             tc::tmem_ld<8>(ta0 + (uint32_t)(CB + c0), ui);
                             tc::tmem_ld_wait();
+                            tc::tmem_regs_ready<8>(ur);
+                            tc::tmem_regs_ready<8>(ui);
                         } else {
 #pragma unroll
                             for (int c = 0; c < 8; ++c) ur[c] = ui[c] = 0.f;

@@ -241,6 +241,7 @@ __device__ __forceinline__ void generate_row(TcShared &sh, int g, uint32_t taddr
     float ph[32];
     tc::tmem_ld<32>(taddr, ph);
     tc::tmem_ld_wait();
+    tc::tmem_regs_ready<32>(ph);
     tc::fence_before_sync();
     __syncwarp();
     if ((threadIdx.x & 31) == 0) tc::mbar_arrive(&sh.phfree[g % kPhBufs]);
@@ -373,6 +374,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
                 if (ntl > 0 && ok) {
                     tc::tmem_ld<N / 2>(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(half * (N / 2)), v);
                     tc::tmem_ld_wait();
+                    tc::tmem_regs_ready<N / 2>(v);
                 } else {
 #pragma unroll
                     for (int c = 0; c < N / 2; ++c) v[c] = 0.f;
@@ -493,6 +495,8 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
                         tc::tmem_ld<8>(ta0 + (uint32_t)c0, ur);
                         tc::tmem_ld<8>(ta0 + (uint32_t)(CB + c0), ui);
                         tc::tmem_ld_wait();
+                        tc::tmem_regs_ready<8>(ur);
+                        tc::tmem_regs_ready<8>(ui);
                     } else {
 #pragma unroll
                         for (int c = 0; c < 8; ++c) ur[c] = ui[c] = 0.f;

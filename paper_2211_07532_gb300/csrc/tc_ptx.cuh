@@ -111,6 +111,16 @@ __device__ __forceinline__ void tmem_ld_wait() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// The registers a tcgen05.ld writes look ready to the compiler as soon as the load is issued;
+// only tcgen05.wait::ld makes them valid.  After the wait, pass every loaded array through this
+// (an empty volatile asm that redefines each register, ordered after the wait), so that no use
+// of the values can be scheduled before the wait.
+template <int N>
+__device__ __forceinline__ void tmem_regs_ready(float *v) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) asm volatile("" : "+f"(v[i]));
+}
+
 // ---- descriptors ----
 // Shared-memory matrix descriptor for a K-major operand in the 128-byte swizzled
 // canonical layout: rows of 128 bytes (64 16-bit elements of K), 8-row groups of
