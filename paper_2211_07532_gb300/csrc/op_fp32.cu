@@ -10,6 +10,14 @@
 // and 4 FMAs per coil into register accumulators.  Partial sums per run of tiles are
 // reduced afterwards in a fixed order (deterministic).
 //
+// The FMAs are issued as packed FP32x2 (FFMA2: two lanes of one instruction, each rounded
+// like fmaf, so results equal the scalar form bit for bit): two coils per instruction in
+// the contractions, even/odd terms per instruction in the phase sums.  This halves the
+// instruction count of the FMA work, which otherwise leaves the issue slots, not the FMA
+// pipe, as the limit.  The coil-weighted image is stored as coil pairs
+// (re c, re c+1, im c, im c+1) so that one 16-byte load yields both packed operands; the
+// adjoint permutes each staged block of y into the same order in shared memory.
+//
 // Adjoint (x(r) = sum_c conj S_c(r) sum_t exp(+i phi) y_c(t)):  a block owns two tiles
 // (one voxel per thread, basis offsets in registers) and a run of samples, staged by
 // bulk copies of k/2pi [TS][LP], y [TS][CB] and the two tiles' reference phases.
@@ -22,6 +30,9 @@ namespace aexp {
 namespace {
 
 constexpr float kTwoPi = 6.283185307179586f;
+
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
 
 // Smallest of the per-voxel work: phase in turns -> (cos, sin) of 2 pi * frac.
 __device__ __forceinline__ void turns_sincos(float ph, float &s, float &c) {
@@ -46,17 +57,19 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
     const int ntl = min(ntiles, tile0 + tiles_per_split) - tile0;
     const int tbase = blockIdx.x * kFwdThreads * MT + tid;
 
-    float kh[MT][LP];
+    float2 kh[MT][LP / 2];  // (even term, odd term)
 #pragma unroll
     for (int j = 0; j < MT; ++j)
 #pragma unroll
-        for (int l = 0; l < LP; ++l) kh[j][l] = khi_l[(size_t)l * ntp + tbase + j * kFwdThreads];
+        for (int l = 0; l < LP / 2; ++l)
+            kh[j][l] = make_float2(khi_l[(size_t)(2 * l) * ntp + tbase + j * kFwdThreads],
+                                   khi_l[(size_t)(2 * l + 1) * ntp + tbase + j * kFwdThreads]);
 
-    float are[MT][CB], aim[MT][CB];
+    float2 are[MT][CB / 2], aim[MT][CB / 2];  // coils (2q, 2q+1)
 #pragma unroll
     for (int j = 0; j < MT; ++j)
 #pragma unroll
-        for (int c = 0; c < CB; ++c) are[j][c] = aim[j][c] = 0.f;
+        for (int q = 0; q < CB / 2; ++q) are[j][q] = aim[j][q] = make_float2(0.f, 0.f);
 
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -96,41 +109,33 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
 
 #pragma unroll 2
         for (int v = 0; v < kTileVox; ++v) {
-            float d[LP];
+            float2 d[LP / 2];
 #pragma unroll
             for (int q = 0; q < LP / 4; ++q) {
                 float4 w = sdh[v * (LP / 4) + q];
-                d[4 * q] = w.x;
-                d[4 * q + 1] = w.y;
-                d[4 * q + 2] = w.z;
-                d[4 * q + 3] = w.w;
+                d[2 * q] = make_float2(w.x, w.y);
+                d[2 * q + 1] = make_float2(w.z, w.w);
             }
             float cr[MT], sr[MT];
 #pragma unroll
             for (int j = 0; j < MT; ++j) {
-                // two interleaved chains halve the dependent-FMA latency
-                float p0 = f[j], p1 = 0.f;
+                // even and odd terms in the two lanes: two interleaved chains
+                float2 p = make_float2(f[j], 0.f);
 #pragma unroll
-                for (int l = 0; l < LP; l += 2) {
-                    p0 = fmaf(kh[j][l], d[l], p0);
-                    p1 = fmaf(kh[j][l + 1], d[l + 1], p1);
-                }
-                turns_sincos(p0 + p1, sr[j], cr[j]);
+                for (int l = 0; l < LP / 2; ++l) p = ffma2(kh[j][l], d[l], p);
+                turns_sincos(p.x + p.y, sr[j], cr[j]);
             }
             // E = cos - i sin;  acc += E * b
 #pragma unroll
             for (int q = 0; q < CB / 2; ++q) {
-                float4 bb = sb[v * (CB / 2) + q];  // coils 2q, 2q+1
+                const float4 bb = sb[v * (CB / 2) + q];  // (re 2q, re 2q+1, im 2q, im 2q+1)
+                const float2 bre = make_float2(bb.x, bb.y), bim = make_float2(bb.z, bb.w);
 #pragma unroll
                 for (int j = 0; j < MT; ++j) {
-                    are[j][2 * q] = fmaf(cr[j], bb.x, are[j][2 * q]);
-                    are[j][2 * q] = fmaf(sr[j], bb.y, are[j][2 * q]);
-                    aim[j][2 * q] = fmaf(cr[j], bb.y, aim[j][2 * q]);
-                    aim[j][2 * q] = fmaf(-sr[j], bb.x, aim[j][2 * q]);
-                    are[j][2 * q + 1] = fmaf(cr[j], bb.z, are[j][2 * q + 1]);
-                    are[j][2 * q + 1] = fmaf(sr[j], bb.w, are[j][2 * q + 1]);
-                    aim[j][2 * q + 1] = fmaf(cr[j], bb.w, aim[j][2 * q + 1]);
-                    aim[j][2 * q + 1] = fmaf(-sr[j], bb.z, aim[j][2 * q + 1]);
+                    are[j][q] = ffma2(dup2(cr[j]), bre, are[j][q]);
+                    are[j][q] = ffma2(dup2(sr[j]), bim, are[j][q]);
+                    aim[j][q] = ffma2(dup2(cr[j]), bim, aim[j][q]);
+                    aim[j][q] = ffma2(dup2(-sr[j]), bre, aim[j][q]);
                 }
             }
         }
@@ -142,8 +147,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
     for (int j = 0; j < MT; ++j) {
         float4 *dst = reinterpret_cast<float4 *>(part + ((size_t)split * ntp + tbase + j * kFwdThreads) * CB);
 #pragma unroll
-        for (int q = 0; q < CB / 2; ++q)
-            dst[q] = make_float4(are[j][2 * q], aim[j][2 * q], are[j][2 * q + 1], aim[j][2 * q + 1]);
+        for (int q = 0; q < CB / 2; ++q) dst[q] = make_float4(are[j][q].x, aim[j][q].x, are[j][q].y, aim[j][q].y);
     }
 }
 
@@ -167,7 +171,7 @@ __global__ void __launch_bounds__(kAdjThreads, 2)
     const int t0 = split * t_per_split;
     const int nst = (min(ntp, t0 + t_per_split) - t0) / TS;
 
-    float d[MR][LP];
+    float2 d[MR][LP / 2];  // (even term, odd term)
     bool valid[MR];
     int pv[MR];
 #pragma unroll
@@ -178,17 +182,15 @@ __global__ void __launch_bounds__(kAdjThreads, 2)
 #pragma unroll
         for (int q = 0; q < LP / 4; ++q) {
             float4 w = src[q];
-            d[m][4 * q] = valid[m] ? w.x : 0.f;
-            d[m][4 * q + 1] = valid[m] ? w.y : 0.f;
-            d[m][4 * q + 2] = valid[m] ? w.z : 0.f;
-            d[m][4 * q + 3] = valid[m] ? w.w : 0.f;
+            d[m][2 * q] = valid[m] ? make_float2(w.x, w.y) : make_float2(0.f, 0.f);
+            d[m][2 * q + 1] = valid[m] ? make_float2(w.z, w.w) : make_float2(0.f, 0.f);
         }
     }
-    float ure[MR][CB], uim[MR][CB];
+    float2 ure[MR][CB / 2], uim[MR][CB / 2];  // coils (2q, 2q+1)
 #pragma unroll
     for (int m = 0; m < MR; ++m)
 #pragma unroll
-        for (int c = 0; c < CB; ++c) ure[m][c] = uim[m][c] = 0.f;
+        for (int q = 0; q < CB / 2; ++q) ure[m][q] = uim[m][q] = make_float2(0.f, 0.f);
 
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -225,24 +227,29 @@ __global__ void __launch_bounds__(kAdjThreads, 2)
             return;
         }
         const float4 *sk = reinterpret_cast<const float4 *>(smem + buf * STAGE);
-        const float4 *sy = reinterpret_cast<const float4 *>(smem + buf * STAGE + K_BYTES);
+        float4 *sy = reinterpret_cast<float4 *>(smem + buf * STAGE + K_BYTES);
         const float *sf = reinterpret_cast<const float *>(smem + buf * STAGE + K_BYTES + Y_BYTES);
+        // the staged y rows to coil-pair planar order (re c, re c+1, im c, im c+1), in place, so that
+        // one 16-byte load yields both packed operands (each thread permutes its own 16-byte words)
+        for (int k = tid; k < TS * CB / 2; k += kAdjThreads) {
+            const float4 w = sy[k];
+            sy[k] = make_float4(w.x, w.z, w.y, w.w);
+        }
+        __syncthreads();
 
         // phase + sincos of sample s for each of this thread's voxels
         auto encode = [&](int s, float *cs, float *sn) {
 #pragma unroll
             for (int m = 0; m < MR; ++m) {
                 // the voxel's tile within the block is uniform per warp: 2m + tid/64
-                float p0 = sf[(2 * m + tid / kTileVox) * TS + s], p1 = 0.f;
+                float2 p = make_float2(sf[(2 * m + tid / kTileVox) * TS + s], 0.f);
 #pragma unroll
                 for (int q = 0; q < LP / 4; ++q) {
                     float4 kk = sk[s * (LP / 4) + q];
-                    p0 = fmaf(kk.x, d[m][4 * q], p0);
-                    p1 = fmaf(kk.y, d[m][4 * q + 1], p1);
-                    p0 = fmaf(kk.z, d[m][4 * q + 2], p0);
-                    p1 = fmaf(kk.w, d[m][4 * q + 3], p1);
+                    p = ffma2(make_float2(kk.x, kk.y), d[m][2 * q], p);
+                    p = ffma2(make_float2(kk.z, kk.w), d[m][2 * q + 1], p);
                 }
-                turns_sincos(p0 + p1, sn[m], cs[m]);
+                turns_sincos(p.x + p.y, sn[m], cs[m]);
             }
         };
         // software pipeline as in the forward kernel: sample s+1 is encoded before the
@@ -261,20 +268,20 @@ __global__ void __launch_bounds__(kAdjThreads, 2)
             // conj(E) = cos + i sin;  u += conj(E) * y
 #pragma unroll
             for (int q = 0; q < CB / 2; ++q) {
-                float4 yy = sy[s * (CB / 2) + q];
+                const float4 yy = sy[s * (CB / 2) + q];  // (re 2q, re 2q+1, im 2q, im 2q+1)
+                const float2 yre = make_float2(yy.x, yy.y), yim = make_float2(yy.z, yy.w);
 #pragma unroll
                 for (int m = 0; m < MR; ++m) {
-                    ure[m][2 * q] = fmaf(cs[m], yy.x, ure[m][2 * q]);
-                    ure[m][2 * q] = fmaf(-sn[m], yy.y, ure[m][2 * q]);
-                    uim[m][2 * q] = fmaf(cs[m], yy.y, uim[m][2 * q]);
-                    uim[m][2 * q] = fmaf(sn[m], yy.x, uim[m][2 * q]);
-                    ure[m][2 * q + 1] = fmaf(cs[m], yy.z, ure[m][2 * q + 1]);
-                    ure[m][2 * q + 1] = fmaf(-sn[m], yy.w, ure[m][2 * q + 1]);
-                    uim[m][2 * q + 1] = fmaf(cs[m], yy.w, uim[m][2 * q + 1]);
-                    uim[m][2 * q + 1] = fmaf(sn[m], yy.z, uim[m][2 * q + 1]);
+                    ure[m][q] = ffma2(dup2(cs[m]), yre, ure[m][q]);
+                    ure[m][q] = ffma2(dup2(-sn[m]), yim, ure[m][q]);
+                    uim[m][q] = ffma2(dup2(cs[m]), yim, uim[m][q]);
+                    uim[m][q] = ffma2(dup2(sn[m]), yre, uim[m][q]);
                 }
             }
         }
+        // the permuted words were written through the generic proxy; the bulk copy that refills
+        // this buffer writes through the async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0 && i + 2 < nst) issue(i + 2);
     }
@@ -288,14 +295,14 @@ __global__ void __launch_bounds__(kAdjThreads, 2)
         for (int q = 0; q < CB / 2; ++q) {
             float4 sv = s4[q];
             // conj(S) * u
-            xr = fmaf(sv.x, ure[m][2 * q], xr);
-            xr = fmaf(sv.y, uim[m][2 * q], xr);
-            xi = fmaf(sv.x, uim[m][2 * q], xi);
-            xi = fmaf(-sv.y, ure[m][2 * q], xi);
-            xr = fmaf(sv.z, ure[m][2 * q + 1], xr);
-            xr = fmaf(sv.w, uim[m][2 * q + 1], xr);
-            xi = fmaf(sv.z, uim[m][2 * q + 1], xi);
-            xi = fmaf(-sv.w, ure[m][2 * q + 1], xi);
+            xr = fmaf(sv.x, ure[m][q].x, xr);
+            xr = fmaf(sv.y, uim[m][q].x, xr);
+            xi = fmaf(sv.x, uim[m][q].x, xi);
+            xi = fmaf(-sv.y, ure[m][q].x, xi);
+            xr = fmaf(sv.z, ure[m][q].y, xr);
+            xr = fmaf(sv.w, uim[m][q].y, xr);
+            xi = fmaf(sv.z, uim[m][q].y, xi);
+            xi = fmaf(-sv.w, ure[m][q].y, xi);
         }
         part[(size_t)split * (size_t)(ntiles * kTileVox) + pv[m]] = make_float2(xr, xi);
     }

@@ -113,8 +113,9 @@ __global__ void prep_coil_kernel(const float2 *S, int nc, int nx, int ny, int nt
 }
 
 // b[p][c] = S_c(r(p)) x(r(p)) in tile order (the coil-weighted images of the forward model).
+// b[p][coil pair q] = (re c, re c+1, im c, im c+1), c = 2q: the FP32 forward's packed operands
 __global__ void coil_weight_kernel(const float2 *Sp, const float2 *x, int nx, int ny, int ntx, int nr_pad, int CB,
-                                   float2 *b) {
+                                   float *b) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (size_t)nr_pad * CB) return;
     int p = (int)(i / CB);
@@ -127,7 +128,9 @@ __global__ void coil_weight_kernel(const float2 *Sp, const float2 *x, int nx, in
         out.x = s.x * xv.x - s.y * xv.y;
         out.y = s.x * xv.y + s.y * xv.x;
     }
-    b[i] = out;
+    float *dst = b + (size_t)p * CB * 2 + ((i % CB) >> 1) * 4 + (i & 1);
+    dst[0] = out.x;
+    dst[2] = out.y;
 }
 
 __global__ void set_items_kernel(WsHeader *hdr, int fwd_items, int adj_items) {
@@ -181,7 +184,7 @@ cudaError_t op_coil_weight(const OpLayout &L, const float2 *x, char *ws, cudaStr
     size_t n = (size_t)L.nr_pad * L.CB;
     const int T = 256;
     coil_weight_kernel<<<(unsigned)((n + T - 1) / T), T, 0, st>>>((const float2 *)(ws + L.off_S), x, L.nx, L.ny,
-                                                                 L.ntx, L.nr_pad, L.CB, (float2 *)(ws + L.off_b));
+                                                                 L.ntx, L.nr_pad, L.CB, (float *)(ws + L.off_b));
     return cudaGetLastError();
 }
 
