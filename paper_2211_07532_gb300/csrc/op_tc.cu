@@ -51,12 +51,12 @@ namespace aexp {
 
 namespace {
 
-// Issue the MMAs of one stage (8 of K = 16; FP16 hi+lo: 24, the cross products into the
-// second accumulator) and commit both stage barriers.
-template <int N, bool HL>
+// Issue the 24 MMAs of one stage (A_hi B_hi into the first accumulator, the cross products
+// A_hi B_lo' and A_lo' B_hi into the second; K = 16 each) and commit both stage barriers.
+template <int N>
 __device__ __forceinline__ void tc_mma_stage(TcShared &sh, uint32_t tmem, const unsigned char *A,
                                              const unsigned char *B, bool first, int sa, int sb) {
-    constexpr uint32_t IDESC = tc::idesc_f16(kRows, N, HL ? 0 : 1);
+    constexpr uint32_t IDESC = tc::idesc_f16(kRows, N, 0);  // FP16 operands
     // one descriptor per operand image; the K steps advance it
     const uint64_t da = tc::sdesc_k128(smem_u32(A)), db = tc::sdesc_k128(smem_u32(B));
 #pragma unroll
@@ -65,29 +65,26 @@ __device__ __forceinline__ void tc_mma_stage(TcShared &sh, uint32_t tmem, const 
         const uint32_t kofb = (uint32_t)((kk >> 2) * (N * 128) + (kk & 3) * 32);
         tc::mma_f16(tmem, tc::sdesc_advance(da, koff), tc::sdesc_advance(db, kofb), IDESC, !(first && kk == 0));
     }
-    if constexpr (HL) {
-        const uint32_t t2 = tmem + tmem_acc_cols(N);
-        const uint64_t da1 = tc::sdesc_advance(da, kA_BYTES), db1 = tc::sdesc_advance(db, N * 256);
+    const uint32_t t2 = tmem + tmem_acc_cols(N);
+    const uint64_t da1 = tc::sdesc_advance(da, kA_BYTES), db1 = tc::sdesc_advance(db, N * 256);
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-            const uint32_t koff = (uint32_t)((kk >> 2) * (kRows * 128) + (kk & 3) * 32);
-            const uint32_t kofb = (uint32_t)((kk >> 2) * (N * 128) + (kk & 3) * 32);
-            tc::mma_f16(t2, tc::sdesc_advance(da, koff), tc::sdesc_advance(db1, kofb), IDESC, !(first && kk == 0));
-        }
+    for (int kk = 0; kk < 8; ++kk) {
+        const uint32_t koff = (uint32_t)((kk >> 2) * (kRows * 128) + (kk & 3) * 32);
+        const uint32_t kofb = (uint32_t)((kk >> 2) * (N * 128) + (kk & 3) * 32);
+        tc::mma_f16(t2, tc::sdesc_advance(da, koff), tc::sdesc_advance(db1, kofb), IDESC, !(first && kk == 0));
+    }
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-            const uint32_t koff = (uint32_t)((kk >> 2) * (kRows * 128) + (kk & 3) * 32);
-            const uint32_t kofb = (uint32_t)((kk >> 2) * (N * 128) + (kk & 3) * 32);
-            tc::mma_f16(t2, tc::sdesc_advance(da1, koff), tc::sdesc_advance(db, kofb), IDESC, 1u);
-        }
+    for (int kk = 0; kk < 8; ++kk) {
+        const uint32_t koff = (uint32_t)((kk >> 2) * (kRows * 128) + (kk & 3) * 32);
+        const uint32_t kofb = (uint32_t)((kk >> 2) * (N * 128) + (kk & 3) * 32);
+        tc::mma_f16(t2, tc::sdesc_advance(da1, koff), tc::sdesc_advance(db, kofb), IDESC, 1u);
     }
     tc::mma_commit(&sh.afree[sa]);
     tc::mma_commit(&sh.bfree[sb]);
 }
 
-// Store the 2 x 4 generated pairs of one 16-byte chunk column of both row slots: BF16, or
-// FP16 hi into the first A image and lo' into the second.
-template <bool HL>
+// Store the 2 x 4 generated pairs of one 16-byte chunk column of both row slots: FP16 hi into
+// the first A image and lo' into the second.
 __device__ __forceinline__ void store_a_chunk(unsigned char *A, int hh, int r0, int jp, const float (&re)[2][4],
                                               const float (&im)[2][4]) {
     unsigned char *atom_base = A + hh * (kRows * 128);
@@ -96,12 +93,11 @@ __device__ __forceinline__ void store_a_chunk(unsigned char *A, int hh, int r0, 
         uint32_t w[4], wl[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            if constexpr (HL) split_f16(re[i][u], im[i][u], w[u], wl[u]);
-            else w[u] = pack_bf16(re[i][u], im[i][u]);
+            split_f16(re[i][u], im[i][u], w[u], wl[u]);
         }
         const uint32_t o = tc::swz128(r0 + 32 * i, jp);
         *reinterpret_cast<uint4 *>(atom_base + o) = make_uint4(w[0], w[1], w[2], w[3]);
-        if constexpr (HL) *reinterpret_cast<uint4 *>(atom_base + kA_BYTES + o) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+        *reinterpret_cast<uint4 *>(atom_base + kA_BYTES + o) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
     }
 }
 
@@ -183,13 +179,13 @@ __device__ __forceinline__ void acc_advance(int (&base)[2], int nch) {
 // ---------------------------------------------------------------------------
 // Forward: item = (problem, block of 128 samples, run of voxel tiles)
 // ---------------------------------------------------------------------------
-template <int CB, int LP, bool HL>
+template <int CB, int LP>
 __global__ void __launch_bounds__(kTcThreads, 1)
     fwd_tc_kernel(const ProbDesc *__restrict__ pd, const int *__restrict__ item_off, int nprob, int *counter) {
     constexpr int N = 2 * CB;
-    constexpr int NB = TcForm<HL>::NB;
+    constexpr int NB = TcForm<true>::NB;
     constexpr unsigned B_BYTES = N * 256;  // N rows x 128 16-bit values
-    constexpr unsigned B_ALL = TcForm<HL>::NPK * B_BYTES;
+    constexpr unsigned B_ALL = TcForm<true>::NPK * B_BYTES;
     constexpr unsigned DH_BYTES = kTileVox * LP * 4;
     constexpr unsigned F_BYTES = kRows * 4;
     // one staged tile (B [hi | lo'] | dh | f0 rows): S_DATA bytes arrive per stage; the
@@ -198,7 +194,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     constexpr unsigned S_BYTES = (S_DATA + 1023u) & ~1023u;
     // FP16 hi+lo: two accumulator sets of (D1 | D2), alternating by chunk of kPromote stages
     constexpr uint32_t SET_COLS = 2 * tmem_acc_cols(N);
-    constexpr unsigned TMEM_COLS = HL ? 2 * SET_COLS : tmem_acc_cols(N);
+    constexpr unsigned TMEM_COLS = 2 * SET_COLS;
 
     extern __shared__ unsigned char smem_raw[];
     __shared__ TcShared sh;
@@ -206,8 +202,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int warp = tid >> 5;
     const uint32_t sbase = align1024(smem_u32(smem_raw));
     unsigned char *gbase = smem_raw + (sbase - smem_u32(smem_raw));
-    unsigned char *A[2] = {gbase, gbase + TcForm<HL>::A_STAGE};
-    unsigned char *stage0 = gbase + 2 * TcForm<HL>::A_STAGE;
+    unsigned char *A[2] = {gbase, gbase + TcForm<true>::A_STAGE};
+    unsigned char *stage0 = gbase + 2 * TcForm<true>::A_STAGE;
     const int total = item_off[nprob];
 
     tc_setup(sh, tid, warp, TMEM_COLS, 256);  // accumulator sets are released by warps 0-7
@@ -243,25 +239,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 for (int it = 0; it < ntl; ++it) {
                     const int g = gs + it, sa = g & 1, sb = g % NB;
                     const int m = it / kPromote;
-                    if (HL && it % kPromote == 0 && m >= 2 &&
+                    if (it % kPromote == 0 && m >= 2 &&
                         !wait_or_abort(&sh.accfree[m & 1], (acc_base[m & 1] + ((m - 2) >> 1)) & 1, &sh.abort_flag,
                                        status))
                         break;  // set m & 1 still holds chunk m - 2
                     if (!wait_or_abort(&sh.afull[sa], (g >> 1) & 1, &sh.abort_flag, status)) break;
                     if (!wait_or_abort(&sh.bfull[sb], (g / NB) & 1, &sh.abort_flag, status)) break;
                     tc::fence_after_sync();
-                    if constexpr (HL)
-                        tc_mma_stage<N, HL>(sh, tmem + (uint32_t)(m & 1) * SET_COLS, A[sa], stage0 + sb * S_BYTES,
-                                            it % kPromote == 0, sa, sb);
-                    else
-                        tc_mma_stage<N, HL>(sh, tmem, A[sa], stage0 + sb * S_BYTES, it == 0, sa, sb);
+                    tc_mma_stage<N>(sh, tmem + (uint32_t)(m & 1) * SET_COLS, A[sa], stage0 + sb * S_BYTES,
+                                    it % kPromote == 0, sa, sb);
                     last_issued = g;
                     if (it + NB < ntl) {
                         if (!wait_or_abort(&sh.bfree[sb], (g / NB) & 1, &sh.abort_flag, status)) break;
                         load(it + NB);
                     }
                 }
-                if constexpr (HL) acc_advance(acc_base, (ntl + kPromote - 1) / kPromote);
+                acc_advance(acc_base, (ntl + kPromote - 1) / kPromote);
             }
         } else {
             // generator: warp w owns chunk columns (w & 7) and (w & 7) + 8, lane g owns rows
@@ -295,18 +288,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 bool w_ok = wait_or_abort(&sh.bfull[sb], (g / NB) & 1, &sh.abort_flag, status);
                 if (w_ok && g >= 2) w_ok = wait_or_abort(&sh.afree[sa], ((g - 2) >> 1) & 1, &sh.abort_flag, status);
                 if (!__all_sync(0xffffffffu, w_ok)) break;  // warp-uniform exit
-                if constexpr (HL) {
-                    // stages <= it - 2 are complete: promote a finished chunk and release its set
-                    if (next_promo < (it - 1) / kPromote) {
-                        if (warp < 8) {
-                            tc::fence_after_sync();
-                            fwd_promote<N>(epi_tmem() + (uint32_t)(next_promo & 1) * SET_COLS,
-                                           hl_scale(P.hdr->amax[0], true), epi_dst(), next_promo > 0);
-                            tc::fence_before_sync();
-                            tc::mbar_arrive(&sh.accfree[next_promo & 1]);
-                        }
-                        ++next_promo;
+                // stages <= it - 2 are complete: promote a finished chunk and release its set
+                if (next_promo < (it - 1) / kPromote) {
+                    if (warp < 8) {
+                        tc::fence_after_sync();
+                        fwd_promote<N>(epi_tmem() + (uint32_t)(next_promo & 1) * SET_COLS,
+                                       hl_scale(P.hdr->amax[0], true), epi_dst(), next_promo > 0);
+                        tc::fence_before_sync();
+                        tc::mbar_arrive(&sh.accfree[next_promo & 1]);
                     }
+                    ++next_promo;
                 }
                 const unsigned char *stg = stage0 + sb * S_BYTES;
                 const float4 *DH = reinterpret_cast<const float4 *>(stg + B_ALL);
@@ -345,7 +336,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                             ei[i][u] = -sn;
                         }
                     }
-                    store_a_chunk<HL>(A[sa], hh, r0, jp, er, ei);
+                    store_a_chunk(A[sa], hh, r0, jp, er, ei);
                 }
                 tc::fence_proxy_async_smem();
                 tc::mbar_arrive(&sh.afull[sa]);
@@ -359,20 +350,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (warp < 8) {
                 float4 *dst = epi_dst();
                 const uint32_t ta0 = epi_tmem();
-                if constexpr (!HL) {
-                    float v[N / 2];
-                    if (ntl > 0 && ok) {
-                        tc::tmem_ld<N / 2>(ta0, v);
-                        tc::tmem_ld_wait();
-                        tc::tmem_regs_ready<N / 2>(v);
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < N / 2; ++c) v[c] = 0.f;
-                    }
-#pragma unroll
-                    for (int c = 0; c < N / 8; ++c)
-                        dst[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
-                } else if (ntl > 0 && ok) {
+                if (ntl > 0 && ok) {
                     // the remaining (at most two) chunks; all but the item's last release their set
                     const int nch = (ntl + kPromote - 1) / kPromote;
                     const float inv = hl_scale(P.hdr->amax[0], true);
@@ -397,14 +375,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // ---------------------------------------------------------------------------
 // Adjoint: item = (problem, two voxel tiles, run of 64-sample stages)
 // ---------------------------------------------------------------------------
-template <int CB, int LP, bool HL>
+template <int CB, int LP>
 __global__ void __launch_bounds__(kTcThreads, 1)
     adj_tc_kernel(const ProbDesc *__restrict__ pd, const int *__restrict__ item_off, int nprob, int *counter) {
     constexpr int N = 2 * CB;
     constexpr int TS = kCols;  // samples per stage
-    constexpr int NB = TcForm<HL>::NB;
+    constexpr int NB = TcForm<true>::NB;
     constexpr unsigned B_BYTES = N * 256;
-    constexpr unsigned B_ALL = TcForm<HL>::NPK * B_BYTES;
+    constexpr unsigned B_ALL = TcForm<true>::NPK * B_BYTES;
     constexpr unsigned K_BYTES = TS * LP * 4;
     constexpr unsigned F_BYTES = TS * 4;
     // B [hi | lo'] | k rows | f0 (2 tiles): S_DATA bytes arrive per stage; the stride
@@ -413,7 +391,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     constexpr unsigned S_BYTES = (S_DATA + 1023u) & ~1023u;
     // FP16 hi+lo: two accumulator sets of (D1 | D2), alternating by chunk of kPromote stages
     constexpr uint32_t SET_COLS = 2 * tmem_acc_cols(N);
-    constexpr unsigned TMEM_COLS = HL ? 2 * SET_COLS : tmem_acc_cols(N);
+    constexpr unsigned TMEM_COLS = 2 * SET_COLS;
 
     extern __shared__ unsigned char smem_raw[];
     __shared__ TcShared sh;
@@ -421,8 +399,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int warp = tid >> 5;
     const uint32_t sbase = align1024(smem_u32(smem_raw));
     unsigned char *gbase = smem_raw + (sbase - smem_u32(smem_raw));
-    unsigned char *A[2] = {gbase, gbase + TcForm<HL>::A_STAGE};
-    unsigned char *stage0 = gbase + 2 * TcForm<HL>::A_STAGE;
+    unsigned char *A[2] = {gbase, gbase + TcForm<true>::A_STAGE};
+    unsigned char *stage0 = gbase + 2 * TcForm<true>::A_STAGE;
     const int total = item_off[nprob];
 
     tc_setup(sh, tid, warp, TMEM_COLS, 128);  // accumulator sets are released by warps 0-3
@@ -461,25 +439,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 for (int it = 0; it < nst; ++it) {
                     const int g = gs + it, sa = g & 1, sb = g % NB;
                     const int m = it / kPromote;
-                    if (HL && it % kPromote == 0 && m >= 2 &&
+                    if (it % kPromote == 0 && m >= 2 &&
                         !wait_or_abort(&sh.accfree[m & 1], (acc_base[m & 1] + ((m - 2) >> 1)) & 1, &sh.abort_flag,
                                        status))
                         break;  // set m & 1 still holds chunk m - 2
                     if (!wait_or_abort(&sh.afull[sa], (g >> 1) & 1, &sh.abort_flag, status)) break;
                     if (!wait_or_abort(&sh.bfull[sb], (g / NB) & 1, &sh.abort_flag, status)) break;
                     tc::fence_after_sync();
-                    if constexpr (HL)
-                        tc_mma_stage<N, HL>(sh, tmem + (uint32_t)(m & 1) * SET_COLS, A[sa], stage0 + sb * S_BYTES,
-                                            it % kPromote == 0, sa, sb);
-                    else
-                        tc_mma_stage<N, HL>(sh, tmem, A[sa], stage0 + sb * S_BYTES, it == 0, sa, sb);
+                    tc_mma_stage<N>(sh, tmem + (uint32_t)(m & 1) * SET_COLS, A[sa], stage0 + sb * S_BYTES,
+                                    it % kPromote == 0, sa, sb);
                     last_issued = g;
                     if (it + NB < nst) {
                         if (!wait_or_abort(&sh.bfree[sb], (g / NB) & 1, &sh.abort_flag, status)) break;
                         load(it + NB);
                     }
                 }
-                if constexpr (HL) acc_advance(acc_base, (nst + kPromote - 1) / kPromote);
+                acc_advance(acc_base, (nst + kPromote - 1) / kPromote);
             }
         } else {
             // generator: warp w owns sample chunks (w & 7) and (w & 7) + 8 of each stage; lane g
@@ -517,17 +492,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 bool w_ok = wait_or_abort(&sh.bfull[sb], (g / NB) & 1, &sh.abort_flag, status);
                 if (w_ok && g >= 2) w_ok = wait_or_abort(&sh.afree[sa], ((g - 2) >> 1) & 1, &sh.abort_flag, status);
                 if (!__all_sync(0xffffffffu, w_ok)) break;  // warp-uniform exit
-                if constexpr (HL) {
-                    // stages <= it - 2 are complete: promote a finished chunk and release its set
-                    if (next_promo < (it - 1) / kPromote) {
-                        if (warp < 4) {
-                            tc::fence_after_sync();
-                            adj_promote<CB>(epi_tmem() + (uint32_t)(next_promo & 1) * SET_COLS, epi_s4(), xr, xi);
-                            tc::fence_before_sync();
-                            tc::mbar_arrive(&sh.accfree[next_promo & 1]);
-                        }
-                        ++next_promo;
+                // stages <= it - 2 are complete: promote a finished chunk and release its set
+                if (next_promo < (it - 1) / kPromote) {
+                    if (warp < 4) {
+                        tc::fence_after_sync();
+                        adj_promote<CB>(epi_tmem() + (uint32_t)(next_promo & 1) * SET_COLS, epi_s4(), xr, xi);
+                        tc::fence_before_sync();
+                        tc::mbar_arrive(&sh.accfree[next_promo & 1]);
                     }
+                    ++next_promo;
                 }
                 const unsigned char *stg = stage0 + sb * S_BYTES;
                 const float4 *KS = reinterpret_cast<const float4 *>(stg + B_ALL);
@@ -565,7 +538,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                             ei[i][u] = sn;
                         }
                     }
-                    store_a_chunk<HL>(A[sa], hh, r0, jp, er, ei);
+                    store_a_chunk(A[sa], hh, r0, jp, er, ei);
                 }
                 tc::fence_proxy_async_smem();
                 tc::mbar_arrive(&sh.afull[sa]);
@@ -583,50 +556,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const bool inside = p_row < ntiles * kTileVox;
                 const uint32_t ta0 = epi_tmem();
                 const float4 *s4 = epi_s4();
-                if constexpr (HL) {
-                    if (have) {
-                        // the remaining (at most two) chunks; all but the item's last release their set
-                        const int nch = (nst + kPromote - 1) / kPromote;
-                        for (int m = next_promo; m < nch; ++m) {
-                            adj_promote<CB>(ta0 + (uint32_t)(m & 1) * SET_COLS, s4, xr, xi);
-                            if (m < nch - 1) {
-                                tc::fence_before_sync();
-                                tc::mbar_arrive(&sh.accfree[m & 1]);
-                            }
+                if (have) {
+                    // the remaining (at most two) chunks; all but the item's last release their set
+                    const int nch = (nst + kPromote - 1) / kPromote;
+                    for (int m = next_promo; m < nch; ++m) {
+                        adj_promote<CB>(ta0 + (uint32_t)(m & 1) * SET_COLS, s4, xr, xi);
+                        if (m < nch - 1) {
+                            tc::fence_before_sync();
+                            tc::mbar_arrive(&sh.accfree[m & 1]);
                         }
-                        const float inv = hl_scale(P.hdr->amax[1], true);
-                        xr *= inv;
-                        xi *= inv;
-                    } else {
-                        xr = xi = 0.f;
                     }
+                    const float inv = hl_scale(P.hdr->amax[1], true);
+                    xr *= inv;
+                    xi *= inv;
                 } else {
-#pragma unroll 1
-                    for (int c0 = 0; c0 < CB; c0 += 8) {
-                        float ur[8], ui[8];
-                        if (have) {
-                            tc::tmem_ld<8>(ta0 + (uint32_t)c0, ur);
-                            tc::tmem_ld<8>(ta0 + (uint32_t)(CB + c0), ui);
-                            tc::tmem_ld_wait();
-                            tc::tmem_regs_ready<8>(ur);
-                            tc::tmem_regs_ready<8>(ui);
-                        } else {
-#pragma unroll
-                            for (int c = 0; c < 8; ++c) ur[c] = ui[c] = 0.f;
-                        }
-#pragma unroll
-                        for (int q4 = 0; q4 < 4; ++q4) {
-                            const float4 sv = s4[c0 / 2 + q4];
-                            xr = fmaf(sv.x, ur[2 * q4], xr);
-                            xr = fmaf(sv.y, ui[2 * q4], xr);
-                            xi = fmaf(sv.x, ui[2 * q4], xi);
-                            xi = fmaf(-sv.y, ur[2 * q4], xi);
-                            xr = fmaf(sv.z, ur[2 * q4 + 1], xr);
-                            xr = fmaf(sv.w, ui[2 * q4 + 1], xr);
-                            xi = fmaf(sv.z, ui[2 * q4 + 1], xi);
-                            xi = fmaf(-sv.w, ur[2 * q4 + 1], xi);
-                        }
-                    }
+                    xr = xi = 0.f;
                 }
                 if (inside) P.apart[(size_t)split * (size_t)(ntiles * kTileVox) + p_row] = make_float2(xr, xi);
             }
@@ -724,29 +668,27 @@ __global__ void write_desc_kernel(ProbDesc d, ProbDesc *dst) { *dst = d; }
 
 // ---- launch helpers ----
 constexpr size_t round1k(size_t v) { return (v + 1023) & ~size_t(1023); }
-template <int CB, int LP, bool HL>
+template <int CB, int LP>
 size_t fwd_tc_smem() {
-    using F = TcForm<HL>;
+    using F = TcForm<true>;
     return 1024 + 2 * F::A_STAGE + F::NB * round1k(F::NPK * 2 * CB * 256 + kTileVox * LP * 4 + kRows * 4);
 }
-template <int CB, int LP, bool HL>
+template <int CB, int LP>
 size_t adj_tc_smem() {
-    using F = TcForm<HL>;
+    using F = TcForm<true>;
     return 1024 + 2 * F::A_STAGE + F::NB * round1k(F::NPK * 2 * CB * 256 + kCols * LP * 4 + 2 * kCols * 4);
 }
 
 // The max-reduction grids equal the packing grids: both cover ntiles * 64 * CB / 2 (forward)
 // and ntp * CB / 2 (adjoint) threads.
-template <int CB, int LP, bool HL>
+template <int CB, int LP>
 cudaError_t launch_fwd_tc(const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *x, int src,
                           const int *item_off, int total_items, int *counter, cudaStream_t st) {
-    if constexpr (HL) {
-        amax_reset_kernel<<<cdiv(nprob, 256), 256, 0, st>>>(pd, nprob, 0);
-        amax_b_kernel<CB><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, x, src);
-    }
-    pack_b_fwd_kernel<CB, HL><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, x, src);
-    auto kern = fwd_tc_kernel<CB, LP, HL>;
-    const size_t smem = fwd_tc_smem<CB, LP, HL>();
+    amax_reset_kernel<<<cdiv(nprob, 256), 256, 0, st>>>(pd, nprob, 0);
+    amax_b_kernel<CB><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, x, src);
+    pack_b_fwd_kernel<CB, true><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, x, src);
+    auto kern = fwd_tc_kernel<CB, LP>;
+    const size_t smem = fwd_tc_smem<CB, LP>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
@@ -754,16 +696,14 @@ cudaError_t launch_fwd_tc(const ProbDesc *pd, int nprob, int max_pack_blocks, co
     return cudaGetLastError();
 }
 
-template <int CB, int LP, bool HL>
+template <int CB, int LP>
 cudaError_t launch_adj_tc(const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *yt, int src,
                           const int *item_off, int total_items, int *counter, cudaStream_t st) {
-    if constexpr (HL) {
-        amax_reset_kernel<<<cdiv(nprob, 256), 256, 0, st>>>(pd, nprob, 1);
-        amax_y_kernel<CB><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, yt, src);
-    }
-    pack_y_adj_kernel<CB, HL><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, yt, src);
-    auto kern = adj_tc_kernel<CB, LP, HL>;
-    const size_t smem = adj_tc_smem<CB, LP, HL>();
+    amax_reset_kernel<<<cdiv(nprob, 256), 256, 0, st>>>(pd, nprob, 1);
+    amax_y_kernel<CB><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, yt, src);
+    pack_y_adj_kernel<CB, true><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, yt, src);
+    auto kern = adj_tc_kernel<CB, LP>;
+    const size_t smem = adj_tc_smem<CB, LP>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
@@ -771,14 +711,13 @@ cudaError_t launch_adj_tc(const ProbDesc *pd, int nprob, int max_pack_blocks, co
     return cudaGetLastError();
 }
 
-#define AEXP_TC_HL(FN, CBV, LPV, ...) return FN<CBV, LPV, true>(__VA_ARGS__);
 #define AEXP_TC_LP(FN, CBV, ...)                         \
     switch (LPv) {                                       \
-        case 4: AEXP_TC_HL(FN, CBV, 4, __VA_ARGS__)      \
-        case 8: AEXP_TC_HL(FN, CBV, 8, __VA_ARGS__)      \
-        case 12: AEXP_TC_HL(FN, CBV, 12, __VA_ARGS__)    \
-        case 20: AEXP_TC_HL(FN, CBV, 20, __VA_ARGS__)    \
-        default: AEXP_TC_HL(FN, CBV, 32, __VA_ARGS__)    \
+        case 4: return FN<CBV, 4>(__VA_ARGS__);          \
+        case 8: return FN<CBV, 8>(__VA_ARGS__);          \
+        case 12: return FN<CBV, 12>(__VA_ARGS__);        \
+        case 20: return FN<CBV, 20>(__VA_ARGS__);        \
+        default: return FN<CBV, 32>(__VA_ARGS__);        \
     }
 #define AEXP_TC_DISPATCH(FN, ...)                                \
     switch (CBv) {                                               \
