@@ -41,7 +41,7 @@ __device__ __forceinline__ void turns_sincos(float ph, float &s, float &c) {
 }
 
 template <int CB, int LP, int MT>
-__global__ void __launch_bounds__(kFwdThreads, 2)
+__global__ void __launch_bounds__(kFwdThreads, MT == 1 ? 4 : 2)
     fwd_fp32_kernel(const float *__restrict__ khi_l, const float *__restrict__ f0, const float *__restrict__ dh,
                     const float2 *__restrict__ b, float2 *__restrict__ part, int ntp, int ntiles,
                     int tiles_per_split, int *status) {
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
 }
 
 template <int CB, int LP, int MR>
-__global__ void __launch_bounds__(kAdjThreads, 2)
+__global__ void __launch_bounds__(kAdjThreads, MR == 1 ? 4 : 2)
     adj_fp32_kernel(const float *__restrict__ khi_t, const float *__restrict__ f0, const float *__restrict__ dh,
                     const float2 *__restrict__ Sp, const float2 *__restrict__ yt, float2 *__restrict__ part, int ntp,
                     int ntiles, int t_per_split, int *status) {
