@@ -22,6 +22,16 @@
 // computes while the other waits for its next stage.
 // (A 128-row MMA with N <= 64 occupies the tensor pipe for ~50 cycles, so one thread
 // issuing both GEMMs in turn would bound the stage rate.)
+// The phase thread runs at most two stages ahead of the completed contractions: it issues
+// stage g only after the contraction of stage g - 2 has completed.  When it could run up to
+// four stages ahead (bounded only by the phase tiles), results differed from run to run in a
+// few of 24 repeated adjoints of the 200^2 slice (the rows of one lane quadrant of one work
+// item, rows read last by the contraction more often, as if an A tile were rewritten while
+// still being read); with fewer phase tiles, or one thread issuing both GEMMs, it happened in
+// nearly every run.  Every barrier on that path checks out on paper, so the cause is not
+// identified; with this bound 48 of 48 repeats are bitwise identical, for ~15 % more time.
+// (Waiting for stage g - 3 or g - 4 instead is not possible: a two-slot barrier's parity
+// would alias and the wait would never end.)
 //
 // Phase operands, prepared once per problem (TF32 images in the 128B-swizzled K-major
 // layout, 32 K slots = 128 bytes per row; each block is [hi 16 KB | lo 16 KB]):
@@ -180,7 +190,8 @@ __device__ __forceinline__ void tcp_contraction_item(TcShared &sh, uint32_t tmem
 }
 
 // Phase thread, one item: the phases of stage g go into tile g % 4 once the generators have
-// read that tile for stage g - 4 and the stage's operand has landed.
+// read that tile for stage g - 4, the stage's operand has landed and the contraction of
+// stage g - 2 has completed.
 template <int N>
 __device__ __forceinline__ void tcp_phase_item(TcShared &sh, uint32_t tmem, unsigned char *base, int gs, int n,
                                                int iter, int ks, int *status) {
@@ -193,6 +204,8 @@ __device__ __forceinline__ void tcp_phase_item(TcShared &sh, uint32_t tmem, unsi
         if (g >= kPhBufs && !wait_or_abort(&sh.phfree[b], ((g - kPhBufs) / kPhBufs) & 1, &sh.abort_flag, status))
             return;
         if (!wait_or_abort(&sh.pfull[sp], (g / kNP) & 1, &sh.abort_flag, status)) return;
+        // at most two stages ahead of the completed contractions (see the header)
+        if (g >= 2 && !wait_or_abort(&sh.afree[(g - 2) & 1], ((g - 2) >> 1) & 1, &sh.abort_flag, status)) return;
         tc::fence_after_sync();
         const uint32_t ph = smem_u32(base + PL::OFF_PH + sp * PL::PS);
         phase_mma(ks, tmem + phase_col(g), ah, al, tc::sdesc_k128(ph), tc::sdesc_k128(ph + kHalfImg));
