@@ -261,16 +261,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             // r0 = 64 (w >> 3) + g and r0 + 32 with their coefficients in registers
             const int jp = warp & 7;
             const int r0 = 64 * (warp >> 3) + (tid & 31);
-            float k[2][LP];
+            float2 k[2][LP / 2];  // (even term, odd term)
 #pragma unroll
             for (int i = 0; i < 2; ++i)
 #pragma unroll
                 for (int q4 = 0; q4 < LP / 4; ++q4) {
                     float4 w = reinterpret_cast<const float4 *>(P.khi_t + (size_t)(tbase + r0 + 32 * i) * LP)[q4];
-                    k[i][4 * q4] = w.x;
-                    k[i][4 * q4 + 1] = w.y;
-                    k[i][4 * q4 + 2] = w.z;
-                    k[i][4 * q4 + 3] = w.w;
+                    k[i][2 * q4] = make_float2(w.x, w.y);
+                    k[i][2 * q4 + 1] = make_float2(w.z, w.w);
                 }
             // epilogue rows and columns (warps 0-7): 32 samples x N/2 columns per warp, computed
             // where used so that they hold no registers during the generation
@@ -311,24 +309,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     float er[2][4], ei[2][4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        float d[LP];
+                        float2 d[LP / 2];
 #pragma unroll
                         for (int q4 = 0; q4 < LP / 4; ++q4) {
                             float4 w = DH[(4 * j + u) * (LP / 4) + q4];
-                            d[4 * q4] = w.x;
-                            d[4 * q4 + 1] = w.y;
-                            d[4 * q4 + 2] = w.z;
-                            d[4 * q4 + 3] = w.w;
+                            d[2 * q4] = make_float2(w.x, w.y);
+                            d[2 * q4 + 1] = make_float2(w.z, w.w);
                         }
 #pragma unroll
                         for (int i = 0; i < 2; ++i) {
-                            float p0 = f[i], p1 = 0.f;
+                            // even and odd terms in the two lanes of packed FMAs (each lane as fmaf)
+                            float2 pp = make_float2(f[i], 0.f);
 #pragma unroll
-                            for (int l = 0; l < LP; l += 2) {
-                                p0 = fmaf(k[i][l], d[l], p0);
-                                p1 = fmaf(k[i][l + 1], d[l + 1], p1);
-                            }
-                            float ph = p0 + p1;
+                            for (int l = 0; l < LP / 2; ++l) pp = __ffma2_rn(k[i][l], d[l], pp);
+                            float ph = pp.x + pp.y;
                             ph = ph - rintf(ph);
                             float sn, cs;
                             __sincosf(ph * kTwoPi, &sn, &cs);
@@ -463,7 +457,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int jp = warp & 7;
             const int th = warp >> 3;
             const int r0 = 64 * th + (tid & 31);
-            float d[2][LP];
+            float2 d[2][LP / 2];  // (even term, odd term)
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
                 const int p = vb * kRows + r0 + 32 * i;
@@ -471,10 +465,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
                 for (int q4 = 0; q4 < LP / 4; ++q4) {
                     float4 w = reinterpret_cast<const float4 *>(P.dh + (size_t)(valid ? p : 0) * LP)[q4];
-                    d[i][4 * q4] = valid ? w.x : 0.f;
-                    d[i][4 * q4 + 1] = valid ? w.y : 0.f;
-                    d[i][4 * q4 + 2] = valid ? w.z : 0.f;
-                    d[i][4 * q4 + 3] = valid ? w.w : 0.f;
+                    d[i][2 * q4] = valid ? make_float2(w.x, w.y) : make_float2(0.f, 0.f);
+                    d[i][2 * q4 + 1] = valid ? make_float2(w.z, w.w) : make_float2(0.f, 0.f);
                 }
             }
             // epilogue row (warps 0-3): voxel p = vb * 128 + 32 warp + lane; addressing computed
@@ -513,24 +505,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     float er[2][4], ei[2][4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        float kk[LP];
+                        float2 kk[LP / 2];
 #pragma unroll
                         for (int q4 = 0; q4 < LP / 4; ++q4) {
                             float4 w = KS[(4 * j + u) * (LP / 4) + q4];
-                            kk[4 * q4] = w.x;
-                            kk[4 * q4 + 1] = w.y;
-                            kk[4 * q4 + 2] = w.z;
-                            kk[4 * q4 + 3] = w.w;
+                            kk[2 * q4] = make_float2(w.x, w.y);
+                            kk[2 * q4 + 1] = make_float2(w.z, w.w);
                         }
 #pragma unroll
                         for (int i = 0; i < 2; ++i) {
-                            float p0 = fA[u], p1 = 0.f;
+                            // even and odd terms in the two lanes of packed FMAs (each lane as fmaf)
+                            float2 pp = make_float2(fA[u], 0.f);
 #pragma unroll
-                            for (int l = 0; l < LP; l += 2) {
-                                p0 = fmaf(kk[l], d[i][l], p0);
-                                p1 = fmaf(kk[l + 1], d[i][l + 1], p1);
-                            }
-                            float ph = p0 + p1;
+                            for (int l = 0; l < LP / 2; ++l) pp = __ffma2_rn(kk[l], d[i][l], pp);
+                            float ph = pp.x + pp.y;
                             ph = ph - rintf(ph);
                             float sn, cs;
                             __sincosf(ph * kTwoPi, &sn, &cs);
