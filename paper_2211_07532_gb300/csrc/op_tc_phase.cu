@@ -22,16 +22,12 @@
 // computes while the other waits for its next stage.
 // (A 128-row MMA with N <= 64 occupies the tensor pipe for ~50 cycles, so one thread
 // issuing both GEMMs in turn would bound the stage rate.)
-// The phase thread runs at most two stages ahead of the completed contractions: it issues
-// stage g only after the contraction of stage g - 2 has completed.  When it could run up to
-// four stages ahead (bounded only by the phase tiles), results differed from run to run in a
-// few of 24 repeated adjoints of the 200^2 slice (the rows of one lane quadrant of one work
-// item, rows read last by the contraction more often, as if an A tile were rewritten while
-// still being read); with fewer phase tiles, or one thread issuing both GEMMs, it happened in
-// nearly every run.  Every barrier on that path checks out on paper, so the cause is not
-// identified; with this bound 48 of 48 repeats are bitwise identical, for ~15 % more time.
-// (Waiting for stage g - 3 or g - 4 instead is not possible: a two-slot barrier's parity
-// would alias and the wait would never end.)
+// The epilogue waits for the item's last contraction on a barrier of its own (accdone, one
+// completion per item with stages, waited for by the same warps every item).  Waiting on the
+// A-release barrier of the last stage instead was wrong for the generator group that did not
+// produce that stage: it had not followed that barrier's phases, and when the contraction two
+// stages back was still running the parity test passed one phase early, so that warp read
+// partial accumulators (seen as run-to-run differences in one lane quadrant of one item).
 //
 // Phase operands, prepared once per problem (TF32 images in the 128B-swizzled K-major
 // layout, 32 K slots = 128 bytes per row; each block is [hi 16 KB | lo 16 KB]):
@@ -187,11 +183,11 @@ __device__ __forceinline__ void tcp_contraction_item(TcShared &sh, uint32_t tmem
         tc::mma_commit(&sh.afree[sa]);
         tc::mma_commit(&sh.bfree[sb]);
     }
+    if (n > 0) tc::mma_commit(&sh.accdone);  // the item's accumulators are final
 }
 
 // Phase thread, one item: the phases of stage g go into tile g % 4 once the generators have
-// read that tile for stage g - 4, the stage's operand has landed and the contraction of
-// stage g - 2 has completed.
+// read that tile for stage g - 4 and the stage's operand has landed.
 template <int N>
 __device__ __forceinline__ void tcp_phase_item(TcShared &sh, uint32_t tmem, unsigned char *base, int gs, int n,
                                                int iter, int ks, int *status) {
@@ -204,8 +200,6 @@ __device__ __forceinline__ void tcp_phase_item(TcShared &sh, uint32_t tmem, unsi
         if (g >= kPhBufs && !wait_or_abort(&sh.phfree[b], ((g - kPhBufs) / kPhBufs) & 1, &sh.abort_flag, status))
             return;
         if (!wait_or_abort(&sh.pfull[sp], (g / kNP) & 1, &sh.abort_flag, status)) return;
-        // at most two stages ahead of the completed contractions (see the header)
-        if (g >= 2 && !wait_or_abort(&sh.afree[(g - 2) & 1], ((g - 2) >> 1) & 1, &sh.abort_flag, status)) return;
         tc::fence_after_sync();
         const uint32_t ph = smem_u32(base + PL::OFF_PH + sp * PL::PS);
         phase_mma(ks, tmem + phase_col(g), ah, al, tc::sdesc_k128(ph), tc::sdesc_k128(ph + kHalfImg));
@@ -314,6 +308,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
     tc_setup(sh, tid, warp, kTmemCols, 1, kTcGen / 2, kTcGen / 64);  // two generator groups
     const uint32_t tmem = sh.tmem_base;
     int gs = 0;
+    int nacc = 0;  // items with stages so far: the accdone phase this CTA waits for next
 
     int item;
     for (int iter = 0; tc_next_item(sh, tid, iter, counter, total, item); ++iter) {
@@ -375,8 +370,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
             }
             // epilogue (warps 0-7): last stage's MMAs done -> TMEM -> partials (planar re | im)
             bool ok = !sh.abort_flag;
-            const int gl = gs + ntl - 1;
-            if (ntl > 0 && ok) ok = wait_or_abort(&sh.afree[gl & 1], (gl >> 1) & 1, &sh.abort_flag, status);
+            if (ntl > 0 && ok) ok = wait_or_abort(&sh.accdone, nacc & 1, &sh.abort_flag, status);
             ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
             tc::fence_after_sync();
             if (warp < 8) {
@@ -400,6 +394,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
             }
         }
         gs += ntl;
+        nacc += ntl > 0;
     }
     tcp_teardown(sh, tid, warp, &pd[0].hdr->status);
 }
@@ -424,6 +419,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
     tc_setup(sh, tid, warp, kTmemCols, 1, kTcGen / 2, kTcGen / 64);  // two generator groups
     const uint32_t tmem = sh.tmem_base;
     int gs = 0;
+    int nacc = 0;  // items with stages so far: the accdone phase this CTA waits for next
 
     int item;
     for (int iter = 0; tc_next_item(sh, tid, iter, counter, total, item); ++iter) {
@@ -490,8 +486,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
             }
             // epilogue (warps 0-3, one voxel row per thread): conj(S) . u over coils
             bool ok = !sh.abort_flag;
-            const int gl = gs + nst - 1;
-            if (nst > 0 && ok) ok = wait_or_abort(&sh.afree[gl & 1], (gl >> 1) & 1, &sh.abort_flag, status);
+            if (nst > 0 && ok) ok = wait_or_abort(&sh.accdone, nacc & 1, &sh.abort_flag, status);
             ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
             tc::fence_after_sync();
             if (warp < 4) {
@@ -531,6 +526,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
             }
         }
         gs += nst;
+        nacc += nst > 0;
     }
     tcp_teardown(sh, tid, warp, &pd[0].hdr->status);
 }

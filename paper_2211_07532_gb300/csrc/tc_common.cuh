@@ -92,6 +92,7 @@ struct TcShared {
     uint64_t phfull[4], phfree[4], apfull;  // tensor-core phases: tile ready / read, item operand loaded
     uint64_t pfull[kNBMax], pfree[kNBMax];  // tensor-core phases: ring of per-stage phase operands
     uint64_t drain;              // teardown: every MMA of the issuing thread has completed
+    uint64_t accdone;            // tensor-core phases: an item's last contraction has completed
     uint32_t tmem_base;
     int abort_flag;
     int item[2], stop[2];
@@ -118,6 +119,7 @@ __device__ __forceinline__ void tc_setup(TcShared &sh, int tid, int warp, uint32
             mbar_init(&sh.phfree[s], phfree_count);  // one arrival per generator warp
         }
         mbar_init(&sh.apfull, 1);
+        mbar_init(&sh.accdone, 1);
         mbar_init(&sh.drain, 2);  // tensor-core-phase kernels: both MMA-issuing threads commit
         sh.abort_flag = 0;
         fence_mbar_init();
