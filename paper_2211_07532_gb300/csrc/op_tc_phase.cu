@@ -243,8 +243,8 @@ __device__ __forceinline__ void tcp_teardown(TcShared &sh, int tid, int warp, in
 // chunks of the A tile.  Forward: one reference phase per row (fsrc[0]); adjoint: one per
 // column (fsrc[0..31]).
 template <bool CONJ>
-__device__ __forceinline__ void generate_row(TcShared &sh, int g, uint32_t taddr, const float *fsrc,
-                                             unsigned char *A, int row, int ch) {
+__device__ __forceinline__ bool generate_row(TcShared &sh, int g, uint32_t taddr, const float *fsrc,
+                                             unsigned char *A, int row, int ch, int *status) {
     float ph[32];
     tc::tmem_ld<32>(taddr, ph);
     tc::tmem_ld_wait();
@@ -252,19 +252,19 @@ __device__ __forceinline__ void generate_row(TcShared &sh, int g, uint32_t taddr
     tc::fence_before_sync();
     __syncwarp();
     if ((threadIdx.x & 31) == 0) tc::mbar_arrive(&sh.phfree[g % kPhBufs]);
+    uint32_t w[32];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         float f[4];
         if constexpr (CONJ) {
-            const float4 w = reinterpret_cast<const float4 *>(fsrc)[c];
-            f[0] = w.x;
-            f[1] = w.y;
-            f[2] = w.z;
-            f[3] = w.w;
+            const float4 fw = reinterpret_cast<const float4 *>(fsrc)[c];
+            f[0] = fw.x;
+            f[1] = fw.y;
+            f[2] = fw.z;
+            f[3] = fw.w;
         } else {
             f[0] = f[1] = f[2] = f[3] = fsrc[0];
         }
-        uint32_t w[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             // angle = 2 pi f0 + offset (radians); f0 lies in [-1/2, 1/2) turn and the offset spans
@@ -273,20 +273,29 @@ __device__ __forceinline__ void generate_row(TcShared &sh, int g, uint32_t taddr
             const float x = fmaf(f[u], kTwoPi, ph[4 * c + u]);
             float sn, cs;
             __sincosf(x, &sn, &cs);
-            w[u] = pack_bf16(cs, CONJ ? sn : -sn);  // E = cos - i sin, conj(E) = cos + i sin
+            w[4 * c + u] = pack_bf16(cs, CONJ ? sn : -sn);  // E = cos - i sin, conj(E) = cos + i sin
         }
+    }
+    // The A buffer is claimed only now: the contraction of stage g - 2, which frees it,
+    // overlaps the sincos work above.  This group waited on the barrier for stage g - 2's
+    // previous use (stage g - 4), so the parity is unambiguous.
+    bool ok = g < 2 || wait_or_abort(&sh.afree[g & 1], ((g - 2) >> 1) & 1, &sh.abort_flag, status);
+    if (!__all_sync(0xffffffffu, ok)) return false;
+    tc::fence_after_sync();
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
         const int j = 8 * ch + c;  // chunk of 4 columns: atom j >> 3, swizzle column j & 7
         *reinterpret_cast<uint4 *>(A + (j >> 3) * (kRows * 128) + tc::swz128(row, j & 7)) =
-            make_uint4(w[0], w[1], w[2], w[3]);
+            make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
     }
+    return true;
 }
 
-// Generator waits of stage g (warp-uniform result): reference phases landed, phase tile
-// ready, A buffer free.
+// Generator waits of stage g before its TMEM read (warp-uniform result): reference phases
+// landed, phase tile ready.  The A buffer is waited for inside generate_row.
 __device__ __forceinline__ bool gen_waits(TcShared &sh, int g, int *status) {
     bool ok = wait_or_abort(&sh.bfull[g % kNBB], (g / kNBB) & 1, &sh.abort_flag, status);
     if (ok) ok = wait_or_abort(&sh.phfull[g % kPhBufs], (g / kPhBufs) & 1, &sh.abort_flag, status);
-    if (ok && g >= 2) ok = wait_or_abort(&sh.afree[g & 1], ((g - 2) >> 1) & 1, &sh.abort_flag, status);
     return __all_sync(0xffffffffu, ok);
 }
 
@@ -360,10 +369,11 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
                 if ((g & 1) != grp) continue;
                 if (!gen_waits(sh, g, status)) break;  // warp-uniform exit
                 tc::fence_after_sync();
-                generate_row<false>(sh, g,
+                if (!generate_row<false>(sh, g,
                                     tmem + ((uint32_t)(32 * (warp & 3)) << 16) + phase_col(g) + (uint32_t)(32 * ch),
                                     reinterpret_cast<const float *>(gbase + PL::OFF_B + sb * PL::BS + PL::B_BYTES) + row,
-                                    gbase + sa * kA_BYTES, row, ch);
+                                    gbase + sa * kA_BYTES, row, ch, status))
+                    break;  // warp-uniform exit
                 tc::fence_proxy_async_smem();
                 tc::fence_before_sync();
                 tc::mbar_arrive(&sh.afull[sa]);
@@ -475,11 +485,12 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
                 if ((g & 1) != grp) continue;
                 if (!gen_waits(sh, g, status)) break;  // warp-uniform exit
                 tc::fence_after_sync();
-                generate_row<true>(sh, g,
+                if (!generate_row<true>(sh, g,
                                    tmem + ((uint32_t)(32 * (warp & 3)) << 16) + phase_col(g) + (uint32_t)(32 * ch),
                                    reinterpret_cast<const float *>(gbase + PL::OFF_B + sb * PL::BS + PL::B_BYTES + th * FT) +
                                        32 * ch,
-                                   gbase + sa * kA_BYTES, row, ch);
+                                   gbase + sa * kA_BYTES, row, ch, status))
+                    break;  // warp-uniform exit
                 tc::fence_proxy_async_smem();
                 tc::fence_before_sync();
                 tc::mbar_arrive(&sh.afull[sa]);
