@@ -11,8 +11,9 @@
 // reduced afterwards in a fixed order (deterministic).
 //
 // The FMAs are issued as packed FP32x2 (FFMA2: two lanes of one instruction, each rounded
-// like fmaf, so results equal the scalar form bit for bit): two coils per instruction in
-// the contractions, even/odd terms per instruction in the phase sums.  This halves the
+// like fmaf): two coils per instruction in the contractions, even/odd terms per instruction
+// in the phase sums (the one-voxel-per-thread adjoint at 32 coils keeps two such pairs of
+// partial phase sums, to halve the dependent latency).  This halves the
 // instruction count of the FMA work, which otherwise leaves the issue slots, not the FMA
 // pipe, as the limit.  The coil-weighted image is stored as coil pairs
 // (re c, re c+1, im c, im c+1) so that one 16-byte load yields both packed operands; the
@@ -244,12 +245,25 @@ __global__ void __launch_bounds__(kAdjThreads, MR == 1 ? 4 : 2)
                 // the voxel's tile within the block is uniform per warp: 2m + tid/64
                 float2 p = make_float2(sf[(2 * m + tid / kTileVox) * TS + s], 0.f);
 #pragma unroll
-                for (int q = 0; q < LP / 4; ++q) {
-                    float4 kk = sk[s * (LP / 4) + q];
-                    p = ffma2(make_float2(kk.x, kk.y), d[m][2 * q], p);
-                    p = ffma2(make_float2(kk.z, kk.w), d[m][2 * q + 1], p);
+                if constexpr (MR == 1) {
+                    // one voxel per thread: a second pair of chains halves the dependent latency
+                    float2 pb = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int q = 0; q < LP / 4; ++q) {
+                        float4 kk = sk[s * (LP / 4) + q];
+                        p = ffma2(make_float2(kk.x, kk.y), d[m][2 * q], p);
+                        pb = ffma2(make_float2(kk.z, kk.w), d[m][2 * q + 1], pb);
+                    }
+                    turns_sincos((p.x + p.y) + (pb.x + pb.y), sn[m], cs[m]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < LP / 4; ++q) {
+                        float4 kk = sk[s * (LP / 4) + q];
+                        p = ffma2(make_float2(kk.x, kk.y), d[m][2 * q], p);
+                        p = ffma2(make_float2(kk.z, kk.w), d[m][2 * q + 1], p);
+                    }
+                    turns_sincos(p.x + p.y, sn[m], cs[m]);
                 }
-                turns_sincos(p.x + p.y, sn[m], cs[m]);
             }
         };
         // software pipeline as in the forward kernel: sample s+1 is encoded before the
