@@ -89,3 +89,20 @@ def test_batch_rejects_mixed_paddings(ax, batch):
     Y = [torch.as_tensor(ys[0], device="cuda"), torch.zeros((20, 256), dtype=torch.complex64, device="cuda")]
     with pytest.raises(ax.AexpError, match="UNSUPPORTED"):
         ax.cs_recon_batched(P, Y, [1.0, 1.0], 2, precision=ax.BF16_TC)
+
+
+def test_batch_reconstruction_is_repeatable(ax, batch):
+    """The ragged batch runs the persistent tensor-core kernels over all problems at once;
+    three runs of the whole batched solve must agree bit for bit."""
+    import torch
+    probs, ys, lams = batch
+    P = [ax.Problem.from_arrays(p) for p in probs]
+    Y = [torch.as_tensor(y, device="cuda") for y in ys]
+    runs = []
+    for _ in range(3):
+        xs, L = ax.cs_recon_batched(P, Y, lams, 8, precision=ax.BF16_TC, wavelet="db4", levels=2, n_power=20)
+        torch.cuda.synchronize()
+        runs.append(([x.clone() for x in xs], L.clone()))
+    for xs, L in runs[1:]:
+        assert torch.equal(L, runs[0][1])
+        assert all(torch.equal(a, b) for a, b in zip(xs, runs[0][0]))

@@ -160,3 +160,18 @@ def test_unprepared_workspace_is_rejected(ax):
     x = torch.zeros(64, dtype=torch.complex64, device="cuda")
     with pytest.raises(ax.AexpError, match="NOT_PREPARED"):
         ax.a_exp_forward(prob, x, ws)
+
+
+def test_slice200_operator_is_repeatable(ax, slice200):
+    """Partial sums are reduced in a fixed order: repeated applications agree bit for bit."""
+    import torch
+    p = slice200[0]
+    prob = ax.Problem.from_arrays(p)
+    ws = ax.workspace(prob)
+    ax.prepare(prob, ws)
+    x = torch.as_tensor(p["x_gt"], device="cuda")
+    y = torch.as_tensor(p["noise"], device="cuda")
+    f0, a0 = ax.a_exp_forward(prob, x, ws).clone(), ax.a_exp_adjoint(prob, y, ws).clone()
+    for _ in range(4):
+        assert torch.equal(ax.a_exp_forward(prob, x, ws), f0)
+        assert torch.equal(ax.a_exp_adjoint(prob, y, ws), a0)
