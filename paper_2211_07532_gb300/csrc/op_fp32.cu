@@ -244,7 +244,6 @@ __global__ void __launch_bounds__(kAdjThreads, MR == 1 ? 4 : 2)
             for (int m = 0; m < MR; ++m) {
                 // the voxel's tile within the block is uniform per warp: 2m + tid/64
                 float2 p = make_float2(sf[(2 * m + tid / kTileVox) * TS + s], 0.f);
-#pragma unroll
                 if constexpr (MR == 1) {
                     // one voxel per thread: a second pair of chains halves the dependent latency
                     float2 pb = make_float2(0.f, 0.f);
