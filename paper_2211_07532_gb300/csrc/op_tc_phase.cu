@@ -120,6 +120,11 @@ constexpr int kLoadPWarp = kMmaWarp + 3;
 constexpr int kTcpThreads = kTcGen + 128;
 constexpr int kNP = 3;   // ring of per-stage phase operands (hi | lo images, 16 KB)
 constexpr int kNBB = 4;  // ring of per-stage contraction operands + reference phases
+// A generator group waits only on the stages of its parity, so each B slot and each phase tile
+// must belong to one group: with an odd count a slot would alternate between the groups, a
+// group would skip every other phase of that slot's barrier and its parity test could pass a
+// phase early.  (The MMA thread and the loaders wait on every stage; kNP may be anything.)
+static_assert(kNBB % 2 == 0 && kPhBufs % 2 == 0, "each generator group must own its B slots and phase tiles");
 
 // Shared-memory plan of both kernels (byte offsets from the 1024-aligned base):
 //   A[2] generated encoding tiles | AP item phase operand (hi | lo) | PH ring | B ring
