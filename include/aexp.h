@@ -31,7 +31,9 @@
  *   and read with aexp_read_status().
  * - Calls sharing one workspace must be ordered (same stream or explicit events);
  *   concurrent calls need separate workspaces.
- * - Limits: 1 <= nc <= 32, 1 <= nl + (omega != NULL) <= 20, nx, ny, nt >= 1.
+ * - Limits: 1 <= nc <= 32, 1 <= nl + (omega != NULL) <= 32, nx, ny, nt >= 1.
+ * - Results are bitwise repeatable for a given problem, precision and work-item layout:
+ *   every reduction runs in a fixed order, also in the persistent tensor-core kernels.
  */
 #ifndef AEXP_H
 #define AEXP_H
