@@ -183,69 +183,88 @@ __device__ __forceinline__ void store_b_chunk(unsigned char *dst, unsigned img_b
 // Forward: coil-weighted image b_c(v) = S_c(v) x(v) of every 8x8 tile, rows n < C carry
 // (Re b, -Im b), rows C + c carry (Im b, Re b) at K positions (2v, 2v+1).  The image is
 // `x` when given (single problem) or the descriptor's vec[src].  FP16 hi+lo: b is scaled by
-// the power of two fixed by the problem's amax[0].
+// the power of two fixed by the problem's amax[0].  One block per tile (grid-stride): the
+// tile's coil maps are read coalesced (coils fastest) into shared memory, then every thread
+// writes 16-byte chunks of the swizzled operand rows.
 template <int CB, bool HL>
-__global__ void pack_b_fwd_kernel(const ProbDesc *__restrict__ pd, const float2 *__restrict__ x, int src) {
+__global__ void __launch_bounds__(256) pack_b_fwd_kernel(const ProbDesc *__restrict__ pd, const float2 *__restrict__ x,
+                                                         int src) {
     constexpr int N = 2 * CB;
     constexpr int NPK = HL ? 2 : 1;
+    __shared__ float2 sb[kTileVox * CB];
     const ProbDesc &P = pd[blockIdx.y];
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // (tile, n, chunk)
-    if (i >= (size_t)P.ntiles * N * 16) return;
     const float2 *img = x ? x : P.vec[src];
     const float sc = HL ? hl_scale(P.hdr->amax[0], false) : 1.f;
-    const int jj = (int)(i % 16);
-    const int n = (int)((i / 16) % N);
-    const int tile = (int)(i / (16 * N));
-    const int c = n < CB ? n : n - CB;
-    float a[4], b[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int v = 4 * jj + u;
-        const int ix = (tile % P.ntx) * kTileSide + v % kTileSide, iy = (tile / P.ntx) * kTileSide + v / kTileSide;
-        float br = 0.f, bi = 0.f;
-        if (ix < P.nx && iy < P.ny) {
-            float2 s = P.Sp[((size_t)tile * kTileVox + v) * CB + c];
-            float2 xv = img[(size_t)iy * P.nx + ix];
-            br = (s.x * xv.x - s.y * xv.y) * sc;
-            bi = (s.x * xv.y + s.y * xv.x) * sc;
+    for (int tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
+        const int tx = (tile % P.ntx) * kTileSide, ty = (tile / P.ntx) * kTileSide;
+        for (int k = threadIdx.x; k < kTileVox * CB; k += blockDim.x) {
+            const int v = k / CB;
+            const int ix = tx + v % kTileSide, iy = ty + v / kTileSide;
+            float2 b = make_float2(0.f, 0.f);
+            if (ix < P.nx && iy < P.ny) {
+                const float2 s = P.Sp[(size_t)tile * kTileVox * CB + k];
+                const float2 xv = img[(size_t)iy * P.nx + ix];
+                b = make_float2((s.x * xv.x - s.y * xv.y) * sc, (s.x * xv.y + s.y * xv.x) * sc);
+            }
+            sb[k] = b;
         }
-        a[u] = n < CB ? br : bi;
-        b[u] = n < CB ? -bi : br;
+        __syncthreads();
+        for (int k = threadIdx.x; k < N * 16; k += blockDim.x) {  // (n, chunk of 4 voxels)
+            const int jj = k % 16, n = k / 16;
+            const int c = n < CB ? n : n - CB;
+            float a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float2 v = sb[(4 * jj + u) * CB + c];
+                a[u] = n < CB ? v.x : v.y;
+                b[u] = n < CB ? -v.y : v.x;
+            }
+            unsigned char *dst =
+                P.bpk + (size_t)tile * (NPK * N * 256) + (jj >> 3) * (N * 128) + tc::swz128(n, jj & 7);
+            store_b_chunk<HL>(dst, N * 256, a, b);
+        }
+        __syncthreads();
     }
-    unsigned char *dst =
-        P.bpk + (size_t)tile * (NPK * N * 256) + (jj >> 3) * (N * 128) + tc::swz128(n, jj & 7);
-    store_b_chunk<HL>(dst, N * 256, a, b);
 }
 
 // Adjoint: k-space yt[t][c] (or the descriptor's vec[src], or rt when src < 0) per stage of
 // 64 samples; rows n < C carry (Re y, -Im y), rows C + c carry (Im y, Re y) at K positions
-// (2s, 2s+1).  FP16 hi+lo: y is scaled by the power of two fixed by amax[1].
+// (2s, 2s+1).  FP16 hi+lo: y is scaled by the power of two fixed by amax[1].  One block per
+// stage (grid-stride): the stage's 64 x C values are contiguous and read coalesced into shared
+// memory, then written as 16-byte chunks of the swizzled operand rows.
 template <int CB, bool HL>
-__global__ void pack_y_adj_kernel(const ProbDesc *__restrict__ pd, const float2 *__restrict__ yt, int src) {
+__global__ void __launch_bounds__(256) pack_y_adj_kernel(const ProbDesc *__restrict__ pd, const float2 *__restrict__ yt,
+                                                         int src) {
     constexpr int N = 2 * CB;
     constexpr int NPK = HL ? 2 : 1;
+    __shared__ float2 sy[kCols * CB];
     const ProbDesc &P = pd[blockIdx.y];
     const int nstages = P.ntp / kCols;
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // (stage, n, chunk)
-    if (i >= (size_t)nstages * N * 16) return;
     const float2 *y = yt ? yt : (src >= 0 ? P.vec[src] : P.rt);
     const float sc = HL ? hl_scale(P.hdr->amax[1], false) : 1.f;
-    const int jj = (int)(i % 16);
-    const int n = (int)((i / 16) % N);
-    const int st = (int)(i / (16 * N));
-    const int c = n < CB ? n : n - CB;
-    float a[4], b[4];
+    for (int st = blockIdx.x; st < nstages; st += gridDim.x) {
+        for (int k = threadIdx.x; k < kCols * CB; k += blockDim.x) {
+            float2 v = y[(size_t)st * kCols * CB + k];
+            v.x *= sc;
+            v.y *= sc;
+            sy[k] = v;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < N * 16; k += blockDim.x) {  // (n, chunk of 4 samples)
+            const int jj = k % 16, n = k / 16;
+            const int c = n < CB ? n : n - CB;
+            float a[4], b[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const size_t t = (size_t)st * kCols + 4 * jj + u;
-        float2 v = y[t * CB + c];
-        v.x *= sc;
-        v.y *= sc;
-        a[u] = n < CB ? v.x : v.y;
-        b[u] = n < CB ? -v.y : v.x;
+            for (int u = 0; u < 4; ++u) {
+                const float2 v = sy[(4 * jj + u) * CB + c];
+                a[u] = n < CB ? v.x : v.y;
+                b[u] = n < CB ? -v.y : v.x;
+            }
+            unsigned char *dst = P.ypk + (size_t)st * (NPK * N * 256) + (jj >> 3) * (N * 128) + tc::swz128(n, jj & 7);
+            store_b_chunk<HL>(dst, N * 256, a, b);
+        }
+        __syncthreads();
     }
-    unsigned char *dst = P.ypk + (size_t)st * (NPK * N * 256) + (jj >> 3) * (N * 128) + tc::swz128(n, jj & 7);
-    store_b_chunk<HL>(dst, N * 256, a, b);
 }
 
 }  // namespace
