@@ -193,6 +193,11 @@ AEXP_API int aexp_coil_compress_workspace_size(int nc, size_t *bytes);
 AEXP_API int aexp_coil_compress(const aexp_problem *prob, const void *y, int nv, void *y_out, void *S_out,
                                 double *eig_out, void *ws, size_t ws_bytes, void *stream);
 AEXP_API int aexp_coil_compress_status(const void *ws, int nc, void *stream, int *status);
+/* The same with the Jacobi iteration capped at max_sweeps (1 ..= 40; aexp_coil_compress uses
+ * 40): a cap that the iteration does not converge within is reported like a non-converged
+ * default run, AEXP_ERR_NONFINITE in the status word. */
+AEXP_API int aexp_coil_compress_sweeps(const aexp_problem *prob, const void *y, int nv, int max_sweeps, void *y_out,
+                                       void *S_out, double *eig_out, void *ws, size_t ws_bytes, void *stream);
 
 /* ---------------------------------------------------------------------------
  * The undecimated one-level wavelet on its own (Sec. 2.1; tight frame, subband s = fx + 2 fy
@@ -330,8 +335,10 @@ AEXP_API int aexp_wavelet_forward(int nx, int ny, int wavelet, int levels, const
  *   must have a pyramid of at most 4 MiB, about 4/3 * npy * npx * 8 bytes, i.e. up to
  *   512 x 512; larger sizes return AEXP_ERR_UNSUPPORTED and launch nothing.
  * - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *   with that device current, and caches it; make that first call before any stream
- *   capture.
+ *   with that device current, and caches it for the life of the process; make that first
+ *   call before any stream capture.  A cudaDeviceReset (or anything else that destroys the
+ *   device's primary context) makes the cached address stale: do not call this entry point
+ *   on that device again in the same process after such a reset.
  * - All calls share the one array and it keeps the last call's contents; each call writes
  *   every scratch byte it reads, so nothing is cleared.  Calls that overlap on the GPU
  *   (different streams, or different host threads on one device) race on the array:
@@ -339,6 +346,23 @@ AEXP_API int aexp_wavelet_forward(int nx, int ny, int wavelet, int levels, const
  * in, out: [ny][nx] complex64 device arrays (may alias); tau >= 0. */
 AEXP_API int aexp_wavelet_prox_static(int nx, int ny, int wavelet, int levels, float tau, const void *in,
                                       void *out, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Failure detection probe (no counterpart in the paper)
+ * --------------------------------------------------------------------------- */
+
+/* Checks on the device that the library's bounded waits end and report instead of hanging:
+ * one block in which one thread waits on an mbarrier phase that nothing completes, through the
+ * same bounded wait the operator kernels use but limited to `polls` polls (1 ..= 2^22), and a
+ * second thread waits on another such barrier through the tensor-core kernels' wait, which
+ * gives up as soon as another thread of its block has.  Afterwards the status word of `ws`
+ * (read with aexp_read_status) holds AEXP_ERR_DEVICE_TIMEOUT and the DEVICE ints
+ * result[0], result[1] are 1 (each wait gave up).  Nothing is left in flight; the context
+ * stays usable.  ws: any 256-byte-aligned device buffer of at least aexp_header_bytes()
+ * bytes whose status word is 0 (e.g. a fresh operator workspace). */
+AEXP_API int aexp_probe_bounded_wait(int polls, int *result, void *ws, size_t ws_bytes, void *stream);
+/* Bytes of the header at the start of every workspace (status word first). */
+AEXP_API size_t aexp_header_bytes(void);
 
 /* ---------------------------------------------------------------------------
  * Status

@@ -15,7 +15,9 @@ Contents
 * ``oracle.swt``: the paper's own regulariser -- one-level undecimated wavelet (a tight frame),
   the balanced-FISTA step with it and lambda = sigma / 2 from the histogram of W A^H y;
 * ``oracle.recon``: power-iteration Lipschitz estimate, FISTA, CGLS, objective,
-  NRMSE, and reverse-mode gradients of unrolled FISTA.
+  NRMSE, and reverse-mode gradients of unrolled FISTA;
+* ``oracle.precision``: the BF16 form's rounding written out (dense, small problems), which
+  the solvers above can run on to show what the rounding alone does to a reconstruction.
 
 Every function takes a problem dict with keys nt, nx, ny, nc, nl and arrays
 k[nl][nt], h[nl][nr], omega[nr] (or None), t[nt], S[nc][nr]; inputs are promoted

@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-Readings of the paper fixed here (each also listed in the design notes):
+Readings of the paper fixed here:
 * objective F(x) = ||A x - y||_2^2 + lam * sum_detail |(W x)_j|, Eq. (1) as printed
   (no 1/2), low-pass weight 0 (Supporting Information S1);
 * gradient of the data term 2 A^H (A x - y), Lipschitz constant L_f = 2 lambda_max(A^H A),
@@ -24,17 +24,22 @@ from . import adjoint, forward
 from . import wavelet as wv
 
 
-def normal_op(prob, v):
-    return adjoint(prob, forward(prob, v))
+def _operators(prob, ops):
+    """(A, A^H) as callables: the exact FP64 double sums, or the pair ``ops`` (e.g. the
+    rounding emulation of ``oracle.precision``) when given."""
+    if ops is not None:
+        return ops
+    return (lambda v: forward(prob, v)), (lambda r: adjoint(prob, r))
 
 
-def power_lipschitz(prob, v0, n_pow: int = 30):
+def power_lipschitz(prob, v0, n_pow: int = 30, ops=None):
     """L_f = 2 mu_n after n_pow power iterations on A^H A from v0."""
+    fwd, adj = _operators(prob, ops)
     v = np.asarray(v0, np.complex128).reshape(-1)
     v = v / np.linalg.norm(v)
     mu = 0.0
     for _ in range(n_pow):
-        w = normal_op(prob, v)
+        w = adj(fwd(v))
         mu = float(np.real(np.vdot(v, w)))
         v = w / np.linalg.norm(w)
     return 2.0 * mu
@@ -45,8 +50,9 @@ def objective(prob, x, y, lam, name, levels):
     return float(np.sum(np.abs(r) ** 2)) + lam * wv.l1_detail(x, prob["ny"], prob["nx"], name, levels)
 
 
-def fista(prob, y, lam, iters, lipschitz, name, levels, x0=None, history=False):
+def fista(prob, y, lam, iters, lipschitz, name, levels, x0=None, history=False, ops=None):
     """FISTA on Eq. (1): returns x_iters (and the list of iterates if ``history``)."""
+    fwd, adj = _operators(prob, ops)
     nr = prob["nx"] * prob["ny"]
     y = np.asarray(y, np.complex128)
     x_prev = np.zeros(nr, np.complex128) if x0 is None else np.asarray(x0, np.complex128).reshape(nr)
@@ -55,7 +61,7 @@ def fista(prob, y, lam, iters, lipschitz, name, levels, x0=None, history=False):
     tau = lam / lipschitz
     hist = []
     for _ in range(iters):
-        grad = 2.0 * adjoint(prob, forward(prob, z) - y)
+        grad = 2.0 * adj(fwd(z) - y)
         v = z - grad / lipschitz
         x = wv.prox(v, prob["ny"], prob["nx"], name, levels, tau)
         t_next = (1.0 + math.sqrt(1.0 + 4.0 * t * t)) / 2.0
@@ -67,32 +73,24 @@ def fista(prob, y, lam, iters, lipschitz, name, levels, x0=None, history=False):
     return (x_prev, hist) if history else x_prev
 
 
-def fista_step(prob, y, lam, lipschitz, name, levels, z, x_prev, t):
-    """One FISTA iteration from (z_k, x_{k-1}, t_k): returns (x_k, z_{k+1}, t_{k+1})."""
-    grad = 2.0 * adjoint(prob, forward(prob, z) - y)
-    v = z - grad / lipschitz
-    x = wv.prox(v, prob["ny"], prob["nx"], name, levels, lam / lipschitz)
-    t_next = (1.0 + math.sqrt(1.0 + 4.0 * t * t)) / 2.0
-    return x, x + ((t - 1.0) / t_next) * (x - x_prev), t_next
-
-
-def cgls(prob, y, iters):
+def cgls(prob, y, iters, ops=None):
     """Conjugate gradient least squares on A^H A x = A^H y from x = 0."""
+    fwd, adj = _operators(prob, ops)
     nr = prob["nx"] * prob["ny"]
     y = np.asarray(y, np.complex128)
     x = np.zeros(nr, np.complex128)
     r = y.copy()
-    s = adjoint(prob, r)
+    s = adj(r)
     p = s.copy()
     gamma = float(np.real(np.vdot(s, s)))
     for _ in range(iters):
         if gamma == 0.0:
             break
-        q = forward(prob, p)
+        q = fwd(p)
         alpha = gamma / float(np.real(np.vdot(q, q)))
         x = x + alpha * p
         r = r - alpha * q
-        s = adjoint(prob, r)
+        s = adj(r)
         gamma_new = float(np.real(np.vdot(s, s)))
         p = s + (gamma_new / gamma) * p
         gamma = gamma_new
@@ -132,8 +130,8 @@ def fista_unrolled_grad(prob, y, lam, lipschitz, iters, name, levels, x0, xbar_K
     """Reverse-mode gradient through `iters` FISTA steps (x_0 -> x_iters), FP64.
 
     Cotangent convention: for a real loss, gbar = dLoss/dRe + i dLoss/dIm.  Given the
-    cotangent xbar_K of x_iters, returns (x0bar complex [nr], lambar float, kbar [nl][nt])
-    with L_f held fixed.  Recursion (z_{k+1} = (1+b_k) x_k - b_k x_{k-1}, x_k = P(v_k),
+    cotangent xbar_K of x_iters (an array, or a function of x_iters that returns it),
+    returns (x0bar complex [nr], lambar float, kbar [nl][nt]) with L_f held fixed.  Recursion (z_{k+1} = (1+b_k) x_k - b_k x_{k-1}, x_k = P(v_k),
     v_k = z_k - (2/L) A^H (A z_k - y)):
         xbar_k = (1+b_k) zbar_{k+1} - b_{k+1} zbar_{k+2}  (+ xbar_K at k = iters)
         vbar_k = crop W^H S'^T W pad xbar_k,   lambar += taubar / L
@@ -170,7 +168,8 @@ def fista_unrolled_grad(prob, y, lam, lipschitz, iters, name, levels, x0, xbar_K
     for k in range(iters, 0, -1):
         xbar = (1.0 + b[k]) * zbar[k + 1] - b[k + 1] * zbar[k + 2]
         if k == iters:
-            xbar = xbar + np.asarray(xbar_K, np.complex128).reshape(nr)
+            xK_bar = xbar_K(x[iters]) if callable(xbar_K) else xbar_K
+            xbar = xbar + np.asarray(xK_bar, np.complex128).reshape(nr)
         r = forward(prob, z[k]) - y
         v = z[k] - 2.0 * adjoint(prob, r) / L
         w = wv.dwt2(wv.pad(v.reshape(ny, nx), shp), name, levels)

@@ -7,7 +7,7 @@ weighting from W A^H y (the zero-filled reconstruction); Supporting Information 
 takes the magnitudes of the high-pass coefficients of the level as Rayleigh distributed, reads
 sigma off the maximum of their histogram, and uses lambda = sigma / 2 (low-pass weight 0).
 
-Readings fixed here (also listed in the design notes):
+Readings fixed here:
 * W: the 1-level stationary transform with the orthonormal filters of ``oracle.wavelet``
   (Haar or Daubechies-4), periodic, no downsampling, separable (rows x, then columns y),
   every filter scaled by 1/sqrt(2) per dimension so that W^H W = I (a tight frame):
@@ -107,9 +107,11 @@ def rayleigh_lambda(prob, y, name: str) -> float:
     return 0.5 * rayleigh_sigma(swt2(z, name)[1:])
 
 
-def fista(prob, y, lam, iters, lipschitz, name, x0=None):
-    """FISTA with the balanced tight-frame step: x_k = W^H soft(W v_k, lam / L_f)."""
+def fista(prob, y, lam, iters, lipschitz, name, x0=None, ops=None):
+    """FISTA with the balanced tight-frame step: x_k = W^H soft(W v_k, lam / L_f).
+    ``ops``: optional (A, A^H) callables in place of the exact double sums."""
     from . import adjoint, forward
+    fwd, adj = ops if ops is not None else ((lambda v: forward(prob, v)), (lambda r: adjoint(prob, r)))
     ny, nx = prob["ny"], prob["nx"]
     y = np.asarray(y, np.complex128)
     x_prev = np.zeros(nx * ny, np.complex128) if x0 is None else np.asarray(x0, np.complex128).reshape(-1)
@@ -117,7 +119,7 @@ def fista(prob, y, lam, iters, lipschitz, name, x0=None):
     t = 1.0
     tau = lam / lipschitz
     for _ in range(iters):
-        v = z - 2.0 * adjoint(prob, forward(prob, z) - y) / lipschitz
+        v = z - 2.0 * adj(fwd(z) - y) / lipschitz
         x = prox(v, ny, nx, name, tau)
         t_next = (1.0 + math.sqrt(1.0 + 4.0 * t * t)) / 2.0
         z = x + ((t - 1.0) / t_next) * (x - x_prev)

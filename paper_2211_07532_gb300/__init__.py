@@ -81,6 +81,9 @@ SIGNATURES = [
     ("aexp_coil_compress_workspace_size", _I, [_I, ctypes.POINTER(_SZ)]),
     ("aexp_coil_compress", _I, [_PROB, _P, _I, _P, _P, _P, _P, _SZ, _P]),
     ("aexp_coil_compress_status", _I, [_P, _I, _P, ctypes.POINTER(_I)]),
+    ("aexp_coil_compress_sweeps", _I, [_PROB, _P, _I, _I, _P, _P, _P, _P, _SZ, _P]),
+    ("aexp_probe_bounded_wait", _I, [_I, _P, _P, _SZ, _P]),
+    ("aexp_header_bytes", _SZ, []),
     ("aexp_swt_workspace_size", _I, [_I, _I, ctypes.POINTER(_SZ)]),
     ("aexp_swt_forward", _I, [_I, _I, _I, _P, _P, _P]),
     ("aexp_swt_prox", _I, [_I, _I, _I, ctypes.c_float, _P, _P, _P, _SZ, _P]),
@@ -313,9 +316,11 @@ def cs_recon_batched(probs, ys, lams, iters: int, opts: CReconOpts | None = None
     return x_outs, lipschitz_out
 
 
-def coil_compress(prob: Problem, y, nv: int, stream=None):
+def coil_compress(prob: Problem, y, nv: int, stream=None, max_sweeps: int = 40):
     """Principal-component coil compression: returns (compressed Problem with nc = nv,
-    y_v [nv][nt] complex64, eigenvalues float64 [nc] descending), all on the device."""
+    y_v [nv][nt] complex64, eigenvalues float64 [nc] descending), all on the device.
+    Raises AexpError (AEXP_ERR_NONFINITE) when the Jacobi iteration has not converged within
+    ``max_sweeps`` sweeps."""
     torch = _torch()
     y = y.contiguous()
     dev = y.device
@@ -325,13 +330,25 @@ def coil_compress(prob: Problem, y, nv: int, stream=None):
     yv = torch.empty((nv, prob.nt), dtype=torch.complex64, device=dev)
     Sv = torch.empty((nv, prob.nr), dtype=torch.complex64, device=dev)
     eig = torch.empty(prob.nc, dtype=torch.float64, device=dev)
-    _check(lib().aexp_coil_compress(prob.c, _ptr(y), int(nv), _ptr(yv), _ptr(Sv), _ptr(eig), _ptr(ws), ws.numel(),
-                                    _stream(stream)), "aexp_coil_compress")
+    _check(lib().aexp_coil_compress_sweeps(prob.c, _ptr(y), int(nv), int(max_sweeps), _ptr(yv), _ptr(Sv), _ptr(eig),
+                                           _ptr(ws), ws.numel(), _stream(stream)), "aexp_coil_compress")
     st = ctypes.c_int()
     _check(lib().aexp_coil_compress_status(_ptr(ws), prob.nc, _stream(stream), ctypes.byref(st)),
            "aexp_coil_compress_status")
     _check(st.value, "coil compression (Jacobi)")
     return prob.with_coils(Sv), yv, eig
+
+
+def probe_bounded_wait(polls: int, device="cuda", stream=None):
+    """Run the bounded-wait probe; returns (status word, [plain wait gave up, abort-aware wait
+    gave up]) -- (AEXP_ERR_DEVICE_TIMEOUT, [1, 1]) when the waits end as designed."""
+    torch = _torch()
+    ws = _alloc(lib().aexp_header_bytes(), device)
+    ws.zero_()
+    res = torch.zeros(2, dtype=torch.int32, device=device)
+    _check(lib().aexp_probe_bounded_wait(int(polls), _ptr(res), _ptr(ws), ws.numel(), _stream(stream)),
+           "aexp_probe_bounded_wait")
+    return read_status(ws, stream), [int(v) for v in res.cpu()]
 
 
 def swt_forward(img, wavelet="db4", stream=None):

@@ -44,7 +44,13 @@ struct WsHeader {
     // current application (forward S x, adjoint y); they fix the power-of-two scales
     unsigned amax[2];
     int pad1[2];
+    // FP64 norm reductions (dot_norm_f64): per-block partial sums (mu, nrm2) and the ticket
+    // that elects the last block, which sums the partials in block order and resets it to 0
+    unsigned red_ticket;
+    int pad2;
+    double red_part[2 * 128];
 };
+constexpr int kRedMaxBlocks = 128;  // blocks of one dot_norm_f64 launch (WsHeader::red_part)
 
 // Per-problem descriptor read by the persistent tensor-core kernels and by the batched
 // solver kernels (device memory; one entry per problem).
@@ -219,7 +225,10 @@ cudaError_t batch_wave_inverse(int wavelet, const ProbDesc *pd, int nprob, int l
                                int out_role, int momentum, double beta, int xold_role, int z_role, cudaStream_t st);
 
 // Reductions and small vector kernels (recon.cu).
-cudaError_t dot_norm_f64(const float2 *v, const float2 *w, int n, double *mu, double *nrm2, cudaStream_t st);
+// mu = Re <v, w> (v may be null) and nrm2 = ||w||^2 in FP64; multi-block, fixed summation order;
+// uses hdr->red_part and hdr->red_ticket as scratch.
+cudaError_t dot_norm_f64(const float2 *v, const float2 *w, int n, double *mu, double *nrm2, WsHeader *hdr,
+                         cudaStream_t st);
 cudaError_t scale_inv_sqrt(const float2 *w, float2 *v, int n, const double *nrm2, cudaStream_t st);
 
 // Solver pieces (recon.cu).
@@ -246,8 +255,10 @@ cudaError_t swt_set_lambda(char *aux, double lam, double *lam_out, cudaStream_t 
 // Coil compression by principal components of the data (coilcomp.cu): y [nc][nt], S [nc][nr]
 // -> y_out [nv][nt], S_out [nv][nr]; ws of coil_compress_bytes(nc).
 size_t coil_compress_bytes(int nc);
+constexpr int kJacobiMaxSweeps = 40;
 cudaError_t coil_compress(const float2 *y, const float2 *S, int nc, int nt, int nr, int nv, float2 *y_out,
-                          float2 *S_out, double *eig_out, char *ws, cudaStream_t st);
+                          float2 *S_out, double *eig_out, char *ws, cudaStream_t st,
+                          int max_sweeps = kJacobiMaxSweeps);
 
 // Least squares by CGLS (cgls.cu): operator workspace + image vectors x, p, s, k-space r, q,
 // FP64 partial sums and scalars.
@@ -261,6 +272,10 @@ cudaError_t cgls_issue(const aexp_problem *p, const CglsLayout &C, const float2 
                        char *ws, cudaStream_t st);
 // ||w||^2 in FP64, two-stage fixed-order reduction (partial: 256 doubles of scratch).
 cudaError_t norm2_f64(const float2 *w, size_t n, double *partial, double *out, cudaStream_t st);
+
+// Failure-detection probe (probe.cu): one block whose bounded waits on barriers that nothing
+// completes must give up; result[0] / result[1] = 1 when the plain / the abort-aware wait gave up.
+cudaError_t bounded_wait_probe(int polls, int *status, int *result, cudaStream_t st);
 
 // Record a CUDA error for aexp_last_cuda_error() (capi.cu).
 void aexp_set_last_cuda_error(int e);
@@ -312,10 +327,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
     return ok != 0;
 }
 
-// Bounded wait: gives up after ~2^22 polls (each poll may suspend briefly), records
-// AEXP_ERR_DEVICE_TIMEOUT and returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, int *status) {
-    for (int i = 0; i < (1 << 22); ++i)
+// Bounded wait: gives up after `limit` polls (default ~2^22; each poll may suspend briefly),
+// records AEXP_ERR_DEVICE_TIMEOUT and returns false.
+constexpr int kWaitPolls = 1 << 22;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, int *status,
+                                                  int limit = kWaitPolls) {
+    for (int i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     set_status(status, AEXP_ERR_DEVICE_TIMEOUT);
     return false;

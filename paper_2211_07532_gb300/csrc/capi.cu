@@ -533,17 +533,35 @@ int aexp_coil_compress_workspace_size(int nc, size_t *bytes) {
     return AEXP_OK;
 }
 
-int aexp_coil_compress(const aexp_problem *prob, const void *y, int nv, void *y_out, void *S_out, double *eig_out,
-                       void *ws, size_t ws_bytes, void *stream) {
+int aexp_coil_compress_sweeps(const aexp_problem *prob, const void *y, int nv, int max_sweeps, void *y_out,
+                              void *S_out, double *eig_out, void *ws, size_t ws_bytes, void *stream) {
     int rc = check_problem(prob);
     if (rc) return rc;
     if (!y || !y_out || !S_out || nv < 1 || nv > prob->nc) return AEXP_ERR_INVALID_ARG;
+    if (max_sweeps < 1 || max_sweeps > kJacobiMaxSweeps) return AEXP_ERR_INVALID_ARG;
     if (!aligned(y, 8) || !aligned(y_out, 8) || !aligned(S_out, 8) || !aligned(eig_out, 8)) return AEXP_ERR_MISALIGNED;
     if ((rc = check_ws(ws, ws_bytes, coil_compress_bytes(prob->nc)))) return rc;
     cudaError_t e = coil_compress((const float2 *)y, (const float2 *)prob->S, prob->nc, prob->nt, prob->nx * prob->ny,
-                                  nv, (float2 *)y_out, (float2 *)S_out, eig_out, (char *)ws, (cudaStream_t)stream);
+                                  nv, (float2 *)y_out, (float2 *)S_out, eig_out, (char *)ws, (cudaStream_t)stream,
+                                  max_sweeps);
     return e == cudaSuccess ? AEXP_OK : cuda_fail(e);
 }
+
+int aexp_coil_compress(const aexp_problem *prob, const void *y, int nv, void *y_out, void *S_out, double *eig_out,
+                       void *ws, size_t ws_bytes, void *stream) {
+    return aexp_coil_compress_sweeps(prob, y, nv, kJacobiMaxSweeps, y_out, S_out, eig_out, ws, ws_bytes, stream);
+}
+
+int aexp_probe_bounded_wait(int polls, int *result, void *ws, size_t ws_bytes, void *stream) {
+    if (polls < 1 || polls > kWaitPolls || !result) return AEXP_ERR_INVALID_ARG;
+    if (!aligned(result, 4)) return AEXP_ERR_MISALIGNED;
+    int rc = check_ws(ws, ws_bytes, sizeof(WsHeader));
+    if (rc) return rc;
+    cudaError_t e = bounded_wait_probe(polls, &((WsHeader *)ws)->status, result, (cudaStream_t)stream);
+    return e == cudaSuccess ? AEXP_OK : cuda_fail(e);
+}
+
+size_t aexp_header_bytes(void) { return sizeof(WsHeader); }
 
 int aexp_coil_compress_status(const void *ws, int nc, void *stream, int *status) {
     if (!ws || !status || nc < 1 || nc > kMaxCoils) return AEXP_ERR_INVALID_ARG;

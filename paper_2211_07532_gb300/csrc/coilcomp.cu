@@ -9,7 +9,7 @@
 //
 // Eigenvectors: cyclic Jacobi for Hermitian matrices in one block (nc <= 32), FP64, with the
 // round-robin ordering (m / 2 disjoint pairs per round, m = nc rounded up to even) so that all
-// rotations of a round are applied at once; at most kMaxSweeps sweeps, stopping when the
+// rotations of a round are applied at once; at most 40 sweeps (a caller may cap them lower), stopping when the
 // off-diagonal Frobenius norm falls below 1e-15 of the total.  Each rotation zeroes the (p, q)
 // entry: with c = C_pq = |c| e^{i phi}, theta = atan2(2 |c|, C_pp - C_qq) / 2, the unitary acting
 // on columns p, q is [[cos, -sin], [e^{-i phi} sin, e^{-i phi} cos]].
@@ -22,7 +22,6 @@ namespace aexp {
 namespace {
 
 constexpr int kMaxC = 32;
-constexpr int kMaxSweeps = 40;
 
 struct cd {  // complex double in shared memory
     double x, y;
@@ -65,7 +64,7 @@ __global__ void covariance_kernel(const float2 *__restrict__ y, int nc, int nt, 
 // One block of 256 threads: eigen-decomposition of the nc x nc Hermitian C, sorting, phase
 // normalisation; writes the eigenvalues (descending) and U (column-major in [k][a]: U[k * nc + a]).
 __global__ void __launch_bounds__(256) jacobi_kernel(const double2 *__restrict__ Cin, int nc, double2 *__restrict__ Uout,
-                                                     double *__restrict__ eig, int *status) {
+                                                     double *__restrict__ eig, int max_sweeps, int *status) {
     __shared__ cd A[kMaxC][kMaxC + 1], V[kMaxC][kMaxC + 1];
     __shared__ double rc[kMaxC / 2], rs[kMaxC / 2];
     __shared__ cd rph[kMaxC / 2];
@@ -82,7 +81,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const double2 *__restrict__
     }
     __syncthreads();
     bool converged = false;
-    for (int sweep = 0; sweep < kMaxSweeps && !converged; ++sweep) {
+    for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
         if (tid == 0) {
             double off = 0.0, tot = 0.0;
             for (int r = 0; r < nc; ++r)
@@ -221,7 +220,7 @@ size_t coil_compress_bytes(int nc) {
 }
 
 cudaError_t coil_compress(const float2 *y, const float2 *S, int nc, int nt, int nr, int nv, float2 *y_out,
-                          float2 *S_out, double *eig_out, char *ws, cudaStream_t st) {
+                          float2 *S_out, double *eig_out, char *ws, cudaStream_t st, int max_sweeps) {
     double2 *C = (double2 *)ws;
     double2 *U = (double2 *)(ws + align_up(sizeof(double2) * (size_t)nc * nc));
     double *eig = (double *)(ws + 2 * align_up(sizeof(double2) * (size_t)nc * nc));
@@ -229,7 +228,7 @@ cudaError_t coil_compress(const float2 *y, const float2 *S, int nc, int nt, int 
     cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     covariance_kernel<<<dim3(nc, nc), 256, 0, st>>>(y, nc, nt, C);
-    jacobi_kernel<<<1, 256, 0, st>>>(C, nc, U, eig, status);
+    jacobi_kernel<<<1, 256, 0, st>>>(C, nc, U, eig, max_sweeps, status);
     project_kernel<<<dim3(cdiv(nt, 256), nv), 256, 0, st>>>(y, nc, (size_t)nt, U, nv, y_out);
     project_kernel<<<dim3(cdiv(nr, 256), nv), 256, 0, st>>>(S, nc, (size_t)nr, U, nv, S_out);
     if (eig_out) e = cudaMemcpyAsync(eig_out, eig, sizeof(double) * nc, cudaMemcpyDeviceToDevice, st);

@@ -5,48 +5,79 @@
 // FP64 host values (they do not depend on data).
 #include <math.h>
 
+#include <algorithm>
+
 #include "aexp_internal.cuh"
 
 namespace aexp {
 
 namespace {
 
-constexpr int kRedThreads = 1024;
+constexpr int kDotThreads = 256;
 
-// mu = Re <v, w>, nrm2 = ||w||^2 in FP64, one block, fixed summation order.
-__global__ void __launch_bounds__(kRedThreads) dot_norm_kernel(const float2 *v, const float2 *w, int n, double *mu,
-                                                               double *nrm2) {
-    __shared__ double s_mu[kRedThreads / 32], s_nn[kRedThreads / 32];
-    double a = 0.0, b = 0.0;
-    for (int i = threadIdx.x; i < n; i += kRedThreads) {
-        float2 wv = w[i];
-        if (v) {
-            float2 vv = v[i];
-            a += (double)vv.x * wv.x + (double)vv.y * wv.y;
-        }
-        b += (double)wv.x * wv.x + (double)wv.y * wv.y;
-    }
+// Block sum of (a, b) in a fixed tree order; the result is valid in thread 0.
+__device__ __forceinline__ void block_sum2(double &a, double &b, double *sa, double *sb) {
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_xor_sync(0xffffffffu, a, o);
         b += __shfl_xor_sync(0xffffffffu, b, o);
     }
-    int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     if (lane == 0) {
-        s_mu[warp] = a;
-        s_nn[warp] = b;
+        sa[warp] = a;
+        sb[warp] = b;
     }
     __syncthreads();
     if (warp == 0) {
-        a = s_mu[lane];
-        b = s_nn[lane];
+        a = lane < kDotThreads / 32 ? sa[lane] : 0.0;
+        b = lane < kDotThreads / 32 ? sb[lane] : 0.0;
         for (int o = 16; o > 0; o >>= 1) {
             a += __shfl_xor_sync(0xffffffffu, a, o);
             b += __shfl_xor_sync(0xffffffffu, b, o);
         }
-        if (lane == 0) {
-            if (mu) *mu = a;
-            *nrm2 = b;
+    }
+}
+
+// mu = Re <v, w>, nrm2 = ||w||^2 in FP64 (each product of two floats is exact in FP64).
+// Every block sums a fixed grid-stride set of elements in a fixed tree order and leaves its
+// pair in part[]; the block that takes the last ticket adds the partials in block order.
+// The result depends only on n and the grid, never on which block finishes first.
+__global__ void __launch_bounds__(kDotThreads) dot_norm_kernel(const float2 *__restrict__ v,
+                                                               const float2 *__restrict__ w, int n, double *part,
+                                                               unsigned *ticket, double *mu, double *nrm2) {
+    __shared__ double sa[kDotThreads / 32], sb[kDotThreads / 32];
+    __shared__ bool last;
+    double a = 0.0, b = 0.0;
+    for (int i = blockIdx.x * kDotThreads + threadIdx.x; i < n; i += gridDim.x * kDotThreads) {
+        const float2 wv = w[i];
+        if (v) {
+            const float2 vv = v[i];
+            a = fma((double)vv.x, (double)wv.x, a);
+            a = fma((double)vv.y, (double)wv.y, a);
         }
+        b = fma((double)wv.x, (double)wv.x, b);
+        b = fma((double)wv.y, (double)wv.y, b);
+    }
+    block_sum2(a, b, sa, sb);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    a = b = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += kDotThreads) {
+        a += __ldcg(part + 2 * k);
+        b += __ldcg(part + 2 * k + 1);
+    }
+    __syncthreads();  // the shared partials of the first block_sum2 are reused
+    block_sum2(a, b, sa, sb);
+    if (threadIdx.x == 0) {
+        if (mu) *mu = a;
+        *nrm2 = b;
+        *ticket = 0u;  // ready for the next launch (also inside a replayed graph)
     }
 }
 
@@ -83,8 +114,10 @@ __global__ void set_lipschitz_kernel(WsHeader *hdr, double L, double *out) {
 
 }  // namespace
 
-cudaError_t dot_norm_f64(const float2 *v, const float2 *w, int n, double *mu, double *nrm2, cudaStream_t st) {
-    dot_norm_kernel<<<1, kRedThreads, 0, st>>>(v, w, n, mu, nrm2);
+cudaError_t dot_norm_f64(const float2 *v, const float2 *w, int n, double *mu, double *nrm2, WsHeader *hdr,
+                         cudaStream_t st) {
+    const int blocks = std::max(1, std::min(kRedMaxBlocks, cdiv(n, 2 * kDotThreads)));
+    dot_norm_kernel<<<blocks, kDotThreads, 0, st>>>(v, w, n, hdr->red_part, &hdr->red_ticket, mu, nrm2);
     return cudaGetLastError();
 }
 
@@ -108,11 +141,11 @@ cudaError_t normal_apply(const OpLayout &L, char *ws, const float2 *v, float2 *w
 cudaError_t power_iteration(const OpLayout &L, char *ws, const float2 *v0, float2 *v, float2 *w, int n_power,
                             double *out, cudaStream_t st) {
     WsHeader *hdr = (WsHeader *)(ws + L.off_hdr);
-    CK(dot_norm_f64(nullptr, v0, L.nr, nullptr, &hdr->nrm2, st));
+    CK(dot_norm_f64(nullptr, v0, L.nr, nullptr, &hdr->nrm2, hdr, st));
     CK(scale_inv_sqrt(v0, v, L.nr, &hdr->nrm2, st));
     for (int i = 0; i < n_power; ++i) {
         CK(normal_apply(L, ws, v, w, st));
-        CK(dot_norm_f64(v, w, L.nr, &hdr->mu, &hdr->nrm2, st));
+        CK(dot_norm_f64(v, w, L.nr, &hdr->mu, &hdr->nrm2, hdr, st));
         CK(scale_inv_sqrt(w, v, L.nr, &hdr->nrm2, st));
     }
     finalize_lipschitz_kernel<<<1, 1, 0, st>>>(hdr, out);

@@ -49,6 +49,14 @@ def object_sigma(x: np.ndarray, snr: float) -> float:
     return float(np.mean(a[a > 0.1 * a.max()])) / snr
 
 
+def model_terms(model: str):
+    """(field terms kept, B0 kept) of a reconstruction model: "Partial" keeps the 0th- and
+    1st-order terms (Fig. 4), "NoB0" every term but no B0 map."""
+    if model not in MODELS:
+        raise ValueError(model)
+    return (4 if model == "Partial" else None), model != "NoB0"
+
+
 def _model(ax, prob, model: str):
     if model == "Expanded":
         return prob
@@ -59,16 +67,21 @@ def _model(ax, prob, model: str):
     raise ValueError(model)
 
 
+def noisy_image(p: dict, snr: float, noise_seed: int) -> np.ndarray:
+    """The phantom plus complex white noise with E|n(r)|^2 = sigma^2 (complex64)."""
+    rng = np.random.default_rng(noise_seed)
+    sigma = object_sigma(p["x_gt"], snr)
+    return (p["x_gt"] + (sigma / math.sqrt(2.0)) * synth.random_image(rng, p["x_gt"].size)).astype(np.complex64)
+
+
 def simulate(ax, p: dict, snr: float, noise_seed: int, device="cuda"):
     """(full-model Problem, k-space data of the noisy image [nc][nt], noiseless image)."""
     import torch
     prob = ax.Problem.from_arrays(p, device=device)
-    rng = np.random.default_rng(noise_seed)
-    sigma = object_sigma(p["x_gt"], snr)
-    noisy = p["x_gt"] + (sigma / math.sqrt(2.0)) * synth.random_image(rng, p["x_gt"].size)
+    noisy = noisy_image(p, snr, noise_seed)
     ws = ax.workspace(prob, ax.FP32)
     ax.prepare(prob, ws, ax.FP32)
-    y = ax.a_exp_forward(prob, torch.as_tensor(noisy.astype(np.complex64), device=device), ws)
+    y = ax.a_exp_forward(prob, torch.as_tensor(noisy, device=device), ws)
     torch.cuda.synchronize()
     if ax.read_status(ws) != 0:
         raise RuntimeError("forward model reported a device error")

@@ -2,8 +2,9 @@
 
 Each problem of a small ragged batch (different image sizes, sample counts, field
 coefficients) must reproduce (a) the single-problem reconstruction of the same problem and
-(b) the FP64 oracle's FISTA iterate with the same Lipschitz constant, within the BF16
-bounds of the tensor-core tests."""
+(b) the FP64 oracle's FISTA iterate (its own power-iteration L_f), within 3x the image error
+of the oracle's BF16 rounding emulation run the same way (power iteration and FISTA on the
+emulated operator; ``oracle.precision``)."""
 
 import numpy as np
 import pytest
@@ -12,7 +13,7 @@ from paper_2211_07532_gb300 import synth
 from tests._data import rel
 
 pytestmark = pytest.mark.gpu
-TOL_RECON = 2e-2
+RECON_MARGIN = 3.0
 TOL_OP = 5e-3
 
 SHAPES = [(24, 24, 700), (17, 13, 333), (32, 32, 1200), (9, 21, 512), (40, 28, 901)]
@@ -47,7 +48,8 @@ def batch(ax):
 
 def test_batch_matches_single_problem_and_oracle(ax, batch):
     import torch
-    from oracle import recon
+    import oracle
+    from oracle import precision, recon
     probs, ys, lams = batch
     P = [ax.Problem.from_arrays(p) for p in probs]
     Y = [torch.as_tensor(y, device="cuda") for y in ys]
@@ -60,11 +62,16 @@ def test_batch_matches_single_problem_and_oracle(ax, batch):
             xs1, L1 = ax.cs_recon(P[q], Y[q], lam, 8, precision=ax.BF16_TC, wavelet="db4", levels=2, n_power=20)
             e_single = rel(xs[q].cpu().numpy(), xs1.cpu().numpy())
             assert abs(Ls[q] - float(L1.cpu().numpy()[0])) <= 1e-4 * Ls[q]
-            ref = recon.fista(p, y, lam, 8, float(Ls[q]), "db4", 2)
-            e_oracle = rel(xs[q].cpu().numpy(), ref)
-            print(f"batch problem {q} {SHAPES[q]}: vs single {e_single:.2e}, vs oracle {e_oracle:.2e}, L_f {Ls[q]:.4e}")
+            Lo = recon.power_lipschitz(p, oracle.adjoint(p, y), 20)
+            ref = recon.fista(p, y, lam, 8, Lo, "db4", 2)
+            ops = precision.bf16_operators(p)
+            Le = recon.power_lipschitz(p, ops[1](y), 20, ops=ops)
+            emul = recon.fista(p, y, lam, 8, Le, "db4", 2, ops=ops)
+            e_oracle, e_emul = rel(xs[q].cpu().numpy(), ref), rel(emul, ref)
+            print(f"batch problem {q} {SHAPES[q]}: vs single {e_single:.2e}, vs oracle {e_oracle:.2e} "
+                  f"(BF16 emulation {e_emul:.2e}), L_f {Ls[q]:.4e} (oracle {Lo:.4e})")
             assert e_single < 1e-4
-            assert e_oracle < TOL_RECON
+            assert e_oracle < RECON_MARGIN * e_emul
 
 
 def test_batch_lipschitz_matches_oracle(ax, batch):

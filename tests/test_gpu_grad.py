@@ -1,7 +1,10 @@
-"""Gradients through unrolled FISTA on the GPU (FP32): against the FP64 oracle's reverse
-mode on a small problem, and against central finite differences of the GPU forward unroll
-at the 170x170 / 16-coil / 12k-sample / 2nd-order + B0 workload (batch of 8 slices,
-10 iterations).  Bar: relative error < 1e-3."""
+"""Gradients through unrolled FISTA on the GPU (FP32) with respect to the start image, lambda
+and every k_l(t):
+* against the FP64 oracle's reverse mode (``oracle.recon.fista_unrolled_grad``) on small
+  problems and on one slice of the 170x170 / 16-coil / 12k-sample / 2nd-order + B0 workload
+  (3 unrolled iterations; the oracle's own data, lambda, L_f and loss cotangent), bar 1e-3;
+* against central finite differences of the GPU forward unroll on the full workload (batch of
+  8 slices, 10 iterations), with the bars the piecewise-smooth loss admits (see that test)."""
 
 import numpy as np
 import pytest
@@ -65,7 +68,8 @@ def test_gradients_match_oracle_reverse_mode(ax, nx, ny, wavelet, levels):
     xK = unrolled_fista(p, yg, x0g, lam_t, k, iters, L, wavelet=wavelet, levels=levels)
     loss = torch.mean(torch.abs(xK - xgt) ** 2)
     loss.backward()
-    gK = 2.0 * (xK.detach().cpu().numpy().astype(np.complex128) - p["x_gt"]) / (nx * ny)
+    xK_o = recon.fista(p, y, lam, iters, L, wavelet, levels, x0=x0)
+    gK = 2.0 * (xK_o - p["x_gt"]) / (nx * ny)          # the oracle's own loss cotangent
     x0bar, lambar, kbar = recon.fista_unrolled_grad(p, y, lam, L, iters, wavelet, levels, x0, gK)
     ex = rel(x0g.grad.cpu().numpy(), x0bar)
     el = abs(float(lam_t.grad) - lambar) / abs(lambar)
@@ -74,19 +78,67 @@ def test_gradients_match_oracle_reverse_mode(ax, nx, ny, wavelet, levels):
     assert ex < TOL and el < TOL and ek < TOL
 
 
+def test_gradients_match_oracle_diff170(ax):
+    """One slice of the differentiation workload at full size (170^2, 16 coils, 12 000 samples,
+    2nd order + B0, db4 J=4), 3 unrolled iterations from x0 = 0: the GPU's gradients of
+    mean |x_K - x_gt|^2 against the FP64 oracle's reverse mode.  Everything the oracle uses is
+    its own: the data (oracle forward + seeded noise), lambda = 1e-3 ||A^H y||_inf, L_f (1.05 x a
+    4-step power iteration; any fixed value serves, both sides use it) and the loss cotangent.
+    This runs the k-gradient kernel in its full-size configuration (16 coils, split sample runs)."""
+    import torch
+    import oracle
+    from oracle import recon
+    from paper_2211_07532_gb300.autograd import unrolled_fista
+    p = synth.diff_170(index=0)
+    nr = 170 * 170
+    y0 = oracle.forward(p, p["x_gt"])
+    y = (y0 + np.sqrt(np.mean(np.abs(y0) ** 2)) / p["snr"] * p["noise"]).astype(np.complex64)
+    aty = oracle.adjoint(p, y)
+    lam = float(np.float32(1e-3 * np.max(np.abs(aty))))
+    L = 1.05 * recon.power_lipschitz(p, aty, 4)
+    iters = 3
+    x0 = np.zeros(nr, np.complex64)
+    xK_o = []
+
+    def loss_cotangent(xK):                               # the oracle's own x_K
+        xK_o.append(xK)
+        return 2.0 * (xK - p["x_gt"]) / nr
+
+    x0bar, lambar, kbar = recon.fista_unrolled_grad(p, y, lam, L, iters, "db4", 4, x0, loss_cotangent)
+    xK_o = xK_o[0]
+
+    x0g = torch.as_tensor(x0, device="cuda").requires_grad_(True)
+    lam_t = torch.tensor(lam, dtype=torch.float64, requires_grad=True)
+    k = torch.as_tensor(p["k"], device="cuda").requires_grad_(True)
+    xgt = torch.as_tensor(p["x_gt"], device="cuda")
+    xK = unrolled_fista(p, torch.as_tensor(y, device="cuda"), x0g, lam_t, k, iters, L, wavelet="db4", levels=4)
+    torch.mean(torch.abs(xK - xgt) ** 2).backward()
+    ef = rel(xK.detach().cpu().numpy(), xK_o)
+    ex = rel(x0g.grad.cpu().numpy(), x0bar)
+    el = abs(float(lam_t.grad) - lambar) / abs(lambar)
+    ek = rel(k.grad.cpu().numpy(), kbar)
+    print(f"diff170 vs oracle: x_K {ef:.2e}; gradients x0 {ex:.2e} lambda {el:.2e} k {ek:.2e}")
+    assert ef < 1e-5
+    assert ex < TOL and el < TOL and ek < TOL
+
+
 def test_gradients_match_finite_differences_diff170(ax):
     """170^2, 16 coils, 12k samples, 2nd order + B0, 10 unrolled iterations, batch of 8 slices;
     loss = mean over slices of mean |x_K - x_gt|^2 (accumulated in FP64); central differences
-    along the normalised gradient of each parameter group.
+    with step h = 1e-3 along the normalised gradient of each parameter group.
 
     The loss is only piecewise smooth: every soft-threshold |w| = tau is a kink, and a
     difference quotient over [p - h, p + h] straddles the kinks it crosses, so its error is
-    O(h) rather than O(h^2); at small h the FP32 rounding of x_K (a few 1e-9 of the loss)
-    takes over.  Measured on this workload (relative error at h = 1e-3 / 5e-4 / 2.5e-4):
-    x0 2.0e-3 / 8.7e-4 / 3.7e-4 (O(h) kinks), k 8.1e-4 / 1.7e-3 / 3.9e-3 (rounding), lambda
-    6.3e-3 / 6.6e-4 / 8.8e-2 (every change of lambda moves all thresholds; its derivative is
-    the smallest, 1.6e-4).  The analytic gradient itself agrees with the FP64 oracle's reverse
-    mode to ~1e-6 (test above), and that one with FP64 finite differences to ~1e-7
+    O(h) rather than O(h^2); and the FP32 rounding of x_K puts noise of ~7e-9 on the loss
+    (measured as the scatter of the quotient at small h).  The bars at h = 1e-3 follow:
+    * k: the quotient is smooth enough (few kinks move per unit of field change): < 1e-3;
+    * x0: kink-limited, O(h): < 5e-3 at h = 1e-3 (measured 2.0e-3), and the error must shrink
+      with h (8.7e-4 at 5e-4, 3.7e-4 at 2.5e-4 measured);
+    * lambda: every change of lambda moves all thresholds and its derivative is the smallest
+      (1.6e-4), so the rounding noise 7e-9 / (2h 1.6e-4) ~ 2e-2 dominates at h = 1e-3: < 5e-2
+      at that single step (measured 6.3e-3).
+    The analytic gradients themselves are held to 1e-3 against the FP64 oracle's reverse mode
+    at this size (test above), and the oracle's against FP64 finite differences to ~1e-7
     (tests/test_oracle_grad.py)."""
     import torch
     import paper_2211_07532_gb300 as axm
@@ -136,13 +188,14 @@ def test_gradients_match_finite_differences_diff170(ax):
                  "k": lambda h: (total_loss(x0s, lam_s, [k + h * d for k, d in zip(ks, dk)]),
                                  total_loss(x0s, lam_s, [k - h * d for k, d in zip(ks, dk)]))}
         err = {}
+        steps = {"x0": (1e-3, 5e-4, 2.5e-4), "k": (1e-3,), "lambda": (1e-3,)}
         for name in pred:
-            for h in (1e-3, 5e-4, 2.5e-4):
+            for h in steps[name]:
                 lp, lm = shift[name](h)
                 fd = (float(lp) - float(lm)) / (2 * h)
                 err[(name, h)] = abs(fd - pred[name]) / abs(pred[name])
                 print(f"FD {name} h={h:.2e}: analytic {pred[name]:.6e} fd {fd:.6e} rel {err[(name, h)]:.2e}")
     assert err[("k", 1e-3)] < TOL
-    assert err[("x0", 2.5e-4)] < TOL
+    assert err[("x0", 1e-3)] < 5 * TOL
     assert err[("x0", 2.5e-4)] < err[("x0", 5e-4)] < err[("x0", 1e-3)]   # the O(h) kink error shrinks
-    assert np.median([err[("lambda", h)] for h in (1e-3, 5e-4, 2.5e-4)]) < 10 * TOL
+    assert err[("lambda", 1e-3)] < 50 * TOL

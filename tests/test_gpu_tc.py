@@ -1,12 +1,16 @@
 """Parity of the BF16 tensor-core form (tcgen05) with the FP64 oracle.
 
-Bound (BF16, round to nearest): every encoding element and every coil-weighted image
-value is rounded once to 8 significant bits, relative error uniform in +-2^-9, rms
-2^-9/sqrt(3) = 1.1e-3 each; a product of two rounded factors has rms relative error
-~1.6e-3 and the independent errors of the sum add in quadrature, so the relative L2
-error of A x or A^H y is ~1.6e-3.  The test bound is 5e-3 (3x margin).  The FISTA image
-after 20 iterations is held to 2e-2 (the per-application error enters every gradient).
-Measured values are printed and recorded in the design notes."""
+Operator bound (BF16, round to nearest): every real component of the encoding elements and of
+the contraction operand is rounded once to 8 significant bits.  The rounding error is uniform in
++-ulp/2 and ulp/|v| lies between 2^-8 and 2^-7, so for mantissas spread over an octave the rms
+relative error of one rounding is 2^-8/sqrt(6) = 1.6e-3; a product of two rounded factors has
+sqrt(2) times that, 2.3e-3, and the independent errors of a sum add in quadrature, so the
+relative L2 error of A x or A^H y for white inputs is ~2.3e-3.  The test bound is 5e-3.
+
+Reconstruction bound: the oracle runs the same FISTA on its BF16 emulation
+(``oracle.precision``: the same two roundings written out, everything else exact); the
+emulated image's distance to the exact FP64 image is what the rounding alone does after this
+many iterations, and the GPU image must stay within 3x that distance."""
 
 import numpy as np
 import pytest
@@ -16,7 +20,7 @@ from tests._data import rel, simulated
 
 pytestmark = pytest.mark.gpu
 TOL_OP = 5e-3
-TOL_RECON = 2e-2
+RECON_MARGIN = 3.0   # GPU image error / emulated BF16 image error
 
 
 @pytest.fixture(scope="module")
@@ -84,11 +88,14 @@ def test_bf16_tiny64_error_table(ax):
     prob = ax.Problem.from_arrays(p)
     x, L = ax.cs_recon(prob, torch.as_tensor(y, device="cuda"), lam, p["iters"], precision=ax.BF16_TC,
                        wavelet="haar", levels=3, lipschitz=Lf)
+    from oracle import precision
     ref = recon.fista(p, y, lam, p["iters"], Lf, "haar", 3)
-    ex = rel(x.cpu().numpy(), ref)
-    print(f"bf16 tiny64: A x rel {ef:.2e}, A^H y rel {ea:.2e}, FISTA image rel {ex:.2e}; "
-          f"nrmse vs phantom {rel(x.cpu().numpy(), p['x_gt']):.4f} (oracle {rel(ref, p['x_gt']):.4f})")
-    assert ef < TOL_OP and ea < TOL_OP and ex < TOL_RECON
+    emul = recon.fista(p, y, lam, p["iters"], Lf, "haar", 3, ops=precision.bf16_operators(p))
+    ex, ee = rel(x.cpu().numpy(), ref), rel(emul, ref)
+    print(f"bf16 tiny64: A x rel {ef:.2e}, A^H y rel {ea:.2e}, FISTA image rel {ex:.2e} "
+          f"(BF16 emulation {ee:.2e}); nrmse vs phantom {rel(x.cpu().numpy(), p['x_gt']):.4f} "
+          f"(oracle {rel(ref, p['x_gt']):.4f})")
+    assert ef < TOL_OP and ea < TOL_OP and ex < RECON_MARGIN * ee
 
 
 def test_bf16_power_iteration(ax):

@@ -6,8 +6,8 @@ reserve all GPU memory at start-up, plug-ins whose host framework owns the alloc
 This entry point keeps its scratch in a fixed array inside the library instead of a
 caller workspace.  The test calls it through the C ABI twice in a row -- the second call
 runs on whatever the first left in the shared array -- and checks each result against the
-workspace form, aexp_wavelet_prox, within the wavelet tests' tolerance.  It also checks
-that a size beyond the array is refused.
+workspace form, aexp_wavelet_prox, and against the FP64 oracle's prox step, within the
+wavelet tests' tolerance.  It also checks that a size beyond the array is refused.
 """
 
 import ctypes
@@ -55,6 +55,7 @@ def _rel(a, b):
 
 
 def test_static_prox_matches_workspace_prox_on_two_calls_in_a_row(ax):
+    from oracle import wavelet as wv
     calls = [("db4", 200, 200, 4, 0.6, 1), ("haar", 37, 29, 2, 0.9, 2)]
     for wavelet, ny, nx, levels, tau, seed in calls:
         img = _img(ny, nx, seed)
@@ -62,6 +63,10 @@ def test_static_prox_matches_workspace_prox_on_two_calls_in_a_row(ax):
         assert rc == 0, ax.STATUS.get(rc, rc)
         ref = ax.wavelet_prox(img, wavelet, levels, tau)
         assert _rel(out, ref) <= TOL
+        oref = wv.prox(img.cpu().numpy(), ny, nx, wavelet, levels, tau).reshape(ny, nx)
+        e = float(np.linalg.norm(out.cpu().numpy() - oref) / np.linalg.norm(oref))
+        print(f"static prox {wavelet} {ny}x{nx}: vs workspace form {_rel(out, ref):.2e}, vs oracle {e:.2e}")
+        assert e <= TOL
 
 
 def test_static_prox_refuses_sizes_beyond_its_array(ax):
