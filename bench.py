@@ -492,6 +492,14 @@ def _run_ours(args, rank, world, local, dev):
         expanded[f] = {"s_per_slice": e_ms / 1e3, "device_status": e_st,
                        "nrmse_vs_phantom": float(torch.linalg.vector_norm(x_out - xe_gt) / torch.linalg.vector_norm(xe_gt))}
 
+    # the ragged many-problem batch and the unrolled-FISTA gradients, one timed step each
+    ragged = diff = None
+    if not args.no_extras:
+        if world > 1:
+            dist.barrier()
+        ragged = measure_ragged(ax, torch, dev, args.volumes, 1, 1)
+        diff = measure_diff(ax, torch, 1, 1)
+
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -528,104 +536,133 @@ def _run_ours(args, rank, world, local, dev):
             "paper_regulariser_cs100": paper_cs,
             "virtual_coils": virtual,
             "field_terms_30": expanded,
-            "clocks": clocks,
-            "cpu_baseline": cpu,
+            "ragged_batch": ragged,
+            "diff": diff,
         }
+        # compact summaries last, so that a reader of the line's tail sees them
+        summary = {}
+        for f, c in comparison.items():
+            summary[f] = {"s_per_slice": round(c["s_per_slice"], 4), "speedup_vs_fp32": round(ms_per_step / 1e3 /
+                                                                                                 c["s_per_slice"], 2)
+                          if args.form == "fp32" else None,
+                          "nrmse": round(c["nrmse_vs_phantom"], 4),
+                          "sfu_frac": round(c["roofline"]["frac"], 3) if "roofline" in c else None,
+                          "op_ms": round(c["roofline"]["kernel_ms"], 3) if "roofline" in c else None}
+        out["tc_summary"] = {"fp32_s_per_slice": round(ms_per_step / 1e3, 4), "fp32_nrmse": round(nrmse, 4),
+                             "fp32_fma_frac": round(achieved / peak, 3), **summary}
+        if ragged:
+            out["ragged_summary"] = {"problems": ragged["config"]["problems"], "s_per_batch": round(ragged["ms_per_step"] / 1e3, 2),
+                                     "s_per_slice": round(ragged["s_per_slice"], 4), "gvsc_per_s": round(ragged["value"], 1),
+                                     "sfu_frac_whole_step": round(ragged["sfu_frac_whole_step"], 3),
+                                     "nrmse_median": round(ragged["nrmse_vs_phantom_median"], 4),
+                                     "device_status": ragged["device_status"]}
+        if diff:
+            out["diff_summary"] = {"forward_ms": round(diff["forward_ms"], 1), "backward_ms": round(diff["backward_ms"], 1),
+                                   "backward_over_forward": round(diff["backward_over_forward"], 2)}
+        out["clocks"] = clocks
+        out["cpu_baseline"] = cpu
         print(json.dumps(out))
 
 
-def run_ragged(args):
-    """372 ragged problems (148/170/200 px x 31 diffusion volumes x 4 slices, 32 coils, 3rd-order
-    field + B0, each volume with its own coefficients), BF16 tensor cores, one persistent launch
-    per operator application, whole 30-power + 50-FISTA solve captured in one CUDA graph."""
-    import torch
-    from paper_2211_07532_gb300 import build as _b
-    _b.build()
-    import paper_2211_07532_gb300 as ax
+def measure_ragged(ax, torch, dev, volumes: int, steps: int, warmup: int, form: str = "bf16"):
+    """372 ragged problems (148/170/200 px x `volumes` diffusion volumes x 4 slices, 32 coils,
+    3rd-order field + B0, each volume with its own coefficients), tensor cores, one persistent
+    launch per operator application, whole 30-power + 50-FISTA solve captured in one CUDA graph.
+    Returns the full record (inputs generated on the device, autotuned layout, CUDA events)."""
     from paper_2211_07532_gb300 import synth
-
-    dev = torch.device("cuda")
-    side = torch.cuda.Stream()
-    nvol, nsl = args.volumes, 4
+    nvol, nsl = volumes, 4
     t0 = time.time()
-    probs, ys, lams, gts, vsc = [], [], [], [], 0
-    with torch.cuda.stream(side):
-        ws_sim = None
-        for res in range(3):
-            for sl in range(nsl):
-                for vol in range(nvol):
-                    p = synth.ragged_problem(res, vol, sl)
-                    pr = ax.Problem.from_arrays(p, device=dev)
-                    need = ax.workspace_size(pr)
-                    if ws_sim is None or ws_sim.numel() < need:
-                        ws_sim = torch.empty(need, dtype=torch.uint8, device=dev)
-                    ax.prepare(pr, ws_sim)
-                    xg = torch.as_tensor(p["x_gt"], device=dev)
-                    y0 = ax.a_exp_forward(pr, xg, ws_sim)
-                    sigma = float(torch.sqrt(torch.mean(y0.abs() ** 2))) / p["snr"]
-                    y = (y0 + sigma * torch.as_tensor(p["noise"], device=dev)).contiguous()
-                    lams.append(1e-3 * float(ax.a_exp_adjoint(pr, y, ws_sim).abs().max()))
-                    probs.append(pr)
-                    ys.append(y)
-                    gts.append(xg)
-                    vsc += pr.nr * pr.nt * pr.nc
-        del ws_sim
-        gen_s = time.time() - t0
-        iters, n_power, levels = 50, 30, 4
-        tc_form = args.form if args.form != "fp32" else "bf16"   # the batched path runs on the tensor cores
-        opts = ax.recon_opts(precision={"bf16": ax.BF16_TC, "fp16x2": ax.FP16X2_TC}[tc_form], wavelet="db4",
-                             levels=levels, n_power=n_power)
-        # one workspace serves the autotuner (every candidate layout) and the solve
-        tune_bytes = ax.lib_autotune_workspace_size(probs, opts)
-        ws = torch.empty(tune_bytes, dtype=torch.uint8, device=dev)
-        t0 = time.time()
-        best_ips, best_ms = ax.autotune(probs, opts, ws=ws)
-        tune_s = time.time() - t0
-        opts.items_per_sm = best_ips
-        xs = [torch.empty(pr.nr, dtype=torch.complex64, device=dev) for pr in probs]
-        L = torch.empty(len(probs), dtype=torch.float64, device=dev)
-        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-        for _ in range(max(1, args.warmup)):
+    probs, ys, lams, gts, vsc, pairs = [], [], [], [], 0, 0
+    ws_sim = None
+    for res in range(3):
+        for sl in range(nsl):
+            for vol in range(nvol):
+                p = synth.ragged_problem(res, vol, sl)
+                pr = ax.Problem.from_arrays(p, device=dev)
+                need = ax.workspace_size(pr)
+                if ws_sim is None or ws_sim.numel() < need:
+                    ws_sim = torch.empty(need, dtype=torch.uint8, device=dev)
+                ax.prepare(pr, ws_sim)
+                xg = torch.as_tensor(p["x_gt"], device=dev)
+                y0 = ax.a_exp_forward(pr, xg, ws_sim)
+                sigma = float(torch.sqrt(torch.mean(y0.abs() ** 2))) / p["snr"]
+                y = (y0 + sigma * torch.as_tensor(p["noise"], device=dev)).contiguous()
+                lams.append(1e-3 * float(ax.a_exp_adjoint(pr, y, ws_sim).abs().max()))
+                probs.append(pr)
+                ys.append(y)
+                gts.append(xg)
+                vsc += pr.nr * pr.nt * pr.nc
+                pairs += pr.nr * pr.nt
+    del ws_sim
+    gen_s = time.time() - t0
+    iters, n_power, levels = 50, 30, 4
+    opts = ax.recon_opts(precision={"bf16": ax.BF16_TC, "fp16x2": ax.FP16X2_TC}[form], wavelet="db4",
+                         levels=levels, n_power=n_power)
+    # one workspace serves the autotuner (every candidate layout) and the solve
+    ws = torch.empty(ax.lib_autotune_workspace_size(probs, opts), dtype=torch.uint8, device=dev)
+    t0 = time.time()
+    best_ips, best_ms = ax.autotune(probs, opts, ws=ws)
+    tune_s = time.time() - t0
+    opts.items_per_sm = best_ips
+    xs = [torch.empty(pr.nr, dtype=torch.complex64, device=dev) for pr in probs]
+    L = torch.empty(len(probs), dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(1, warmup)):
+        ax.cs_recon_batched(probs, ys, lams, iters, opts=opts, ws=ws, x_outs=xs, lipschitz_out=L)
+    torch.cuda.synchronize()
+    ms = []
+    with ClockSampler(dev.index or 0) as clk:
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
             ax.cs_recon_batched(probs, ys, lams, iters, opts=opts, ws=ws, x_outs=xs, lipschitz_out=L)
-        torch.cuda.synchronize()
-        ms = []
-        with ClockSampler(0) as clk:
-            for _ in range(args.steps):
-                flush.zero_()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record()
-                ax.cs_recon_batched(probs, ys, lams, iters, opts=opts, ws=ws, x_outs=xs, lipschitz_out=L)
-                b.record()
-                b.synchronize()
-                ms.append(a.elapsed_time(b))
-        status = ax.read_status(ws)
-        nrmse = [float(torch.linalg.vector_norm(x - g) / torch.linalg.vector_norm(g)) for x, g in zip(xs, gts)]
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+    status = ax.read_status(ws)
+    nrmse = [float(torch.linalg.vector_norm(x - g) / torch.linalg.vector_norm(g)) for x, g in zip(xs, gts)]
+    ws_gb = ws.numel() / 1e9
+    del ws, xs, ys, probs, flush
+    torch.cuda.empty_cache()
     step = float(np.mean(ms))
     applications = 2 * iters + 2 * n_power + 1
-    print(json.dumps({
-        "metric": METRIC, "workload": "ragged", "value": applications * vsc / (step / 1e3) / 1e9, "unit": UNIT,
-        "n_gpus": 1, "steps": args.steps, "warmup": max(1, args.warmup), "ms_per_step": step,
-        "higher_is_better": True, "dtype": {"bf16": "bf16", "fp16x2": "f16x2"}[tc_form], "data": "synthetic",
+    sm_mhz = measured_peaks().get("sm_max_mhz", 2070.0)
+    sfu = 2.0 * pairs * applications / (step / 1e3) / 1e9
+    return {
+        "value": applications * vsc / (step / 1e3) / 1e9, "unit": UNIT, "steps": steps, "warmup": max(1, warmup),
+        "ms_per_step": step, "s_per_slice": step / 1e3 / len(gts), "dtype": {"bf16": "bf16", "fp16x2": "f16x2"}[form],
+        "nrmse_vs_phantom_median": float(np.median(nrmse)), "device_status": status,
+        "sfu_frac_whole_step": sfu / sfu_peak_gops(sm_mhz),
         "config": {"workload": f"ragged batch: 3 resolutions (148/170/200) x {nvol} volumes x {nsl} slices = "
-                               f"{len(probs)} problems, 32 coils, 3rd-order SH + B0, db4 J=4, 50 FISTA + 30 power",
-                   "problems": len(probs), "vsc_per_application": vsc, "applications_per_step": applications,
-                   "workspace_gb": ws.numel() / 1e9, "generation_s": gen_s,
+                               f"{len(gts)} problems, 32 coils, 3rd-order SH + B0, db4 J=4, 50 FISTA + 30 power",
+                   "problems": len(gts), "vsc_per_application": vsc, "applications_per_step": applications,
+                   "workspace_gb": ws_gb, "generation_s": gen_s,
                    "autotune": {"items_per_sm": best_ips, "ms_per_AhA": best_ms, "seconds": tune_s}},
-        "s_per_slice": step / 1e3 / len(probs), "nrmse_vs_phantom_median": float(np.median(nrmse)),
-        "device_status": status, "clocks": clk.summary()}))
+        "clocks": clk.summary()}
 
 
-def run_diff(args):
-    """Unrolled-FISTA gradients: 170x170, 16 coils, 12k samples, 2nd order + B0, 10 iterations,
-    batch of 8 slices; forward unroll and backward (x0, lambda, k) timed with CUDA events."""
+def run_ragged(args):
     import torch
     from paper_2211_07532_gb300 import build as _b
     _b.build()
     import paper_2211_07532_gb300 as ax
+    dev = torch.device("cuda", 0)
+    form = args.form if args.form != "fp32" else "bf16"   # the batched path runs on the tensor cores
+    with torch.cuda.stream(torch.cuda.Stream(dev)):
+        r = measure_ragged(ax, torch, dev, args.volumes, args.steps, args.warmup, form)
+    r.update(metric=METRIC, workload="ragged", n_gpus=1, higher_is_better=True, data="synthetic")
+    print(json.dumps(r))
+
+
+def measure_diff(ax, torch, steps: int, warmup: int, B: int = 8):
+    """Unrolled-FISTA gradients: 170x170, 16 coils, 12k samples, 2nd order + B0, 10 iterations,
+    batch of B slices; forward unroll and backward (x0, lambda, k) timed with CUDA events."""
     from paper_2211_07532_gb300 import synth
     from paper_2211_07532_gb300.autograd import unrolled_fista
 
-    iters, B = 10, 8
+    iters = 10
     slices = []
     for i in range(B):
         p = synth.diff_170(index=i)
@@ -639,34 +676,45 @@ def run_diff(args):
         _, L = ax.cs_recon(prob, y, 0.0, 0, n_power=30)
         lam = 1e-3 * float(ax.a_exp_adjoint(prob, y, ws).abs().max())
         slices.append((p, y, xg, float(L.cpu()[0]), lam))
+    stream = torch.cuda.current_stream()
 
     def run():
         x0s = [torch.zeros(170 * 170, dtype=torch.complex64, device="cuda").requires_grad_(True) for _ in slices]
         lam_s = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
         ks = [torch.as_tensor(s[0]["k"], device="cuda").requires_grad_(True) for s in slices]
         a, m, b = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        a.record()
+        a.record(stream)
         loss = 0.0
         for (p, y, xg, L, lam), x0, k in zip(slices, x0s, ks):
             xK = unrolled_fista(p, y, x0, lam_s * lam, k, iters, L, wavelet="db4", levels=4)
             loss = loss + torch.mean(torch.abs(xK - xg) ** 2)
-        m.record()
+        m.record(stream)
         (loss / B).backward()
-        b.record()
+        b.record(stream)
         b.synchronize()
         return a.elapsed_time(m), m.elapsed_time(b)
 
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, warmup)):
         run()
-    f, bw = zip(*[run() for _ in range(args.steps)])
+    f, bw = zip(*[run() for _ in range(steps)])
     vsc = 170 * 170 * 12000 * 16
-    print(json.dumps({
-        "workload": "diff", "metric": "unrolled FISTA forward + backward time", "unit": "ms", "dtype": "f32",
-        "config": {"workload": "170x170, 16 coils, 12k samples, 2nd-order SH + B0, 10 unrolled FISTA, batch of 8",
-                   "applications_forward": B * iters * 2, "applications_backward": B * iters * 4 + B * iters * 2},
-        "forward_ms": float(np.mean(f)), "backward_ms": float(np.mean(bw)),
-        "backward_over_forward": float(np.mean(bw) / np.mean(f)),
-        "forward_gvsc_per_s": B * iters * 2 * vsc / (np.mean(f) / 1e3) / 1e9}))
+    return {"forward_ms": float(np.mean(f)), "backward_ms": float(np.mean(bw)),
+            "backward_over_forward": float(np.mean(bw) / np.mean(f)),
+            "forward_gvsc_per_s": B * iters * 2 * vsc / (np.mean(f) / 1e3) / 1e9, "dtype": "f32",
+            "steps": steps, "warmup": max(1, warmup),
+            "config": {"workload": f"170x170, 16 coils, 12k samples, 2nd-order SH + B0, 10 unrolled FISTA, batch of {B}",
+                       "applications_forward": B * iters * 2,
+                       "applications_backward": B * iters * 4 + B * iters * 2}}
+
+
+def run_diff(args):
+    import torch
+    from paper_2211_07532_gb300 import build as _b
+    _b.build()
+    import paper_2211_07532_gb300 as ax
+    r = measure_diff(ax, torch, args.steps, args.warmup)
+    r.update(workload="diff", metric="unrolled FISTA forward + backward time", unit="ms")
+    print(json.dumps(r))
 
 
 def run_op_only(args):
@@ -732,6 +780,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the ragged-batch and gradient sub-measurements of the default run")
     ap.add_argument("--mode", choices=["recon", "op"], default="recon",
                     help="op: only prepare + `--reps` forward/adjoint applications (profiling target)")
     ap.add_argument("--reps", type=int, default=2)

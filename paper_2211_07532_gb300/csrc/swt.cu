@@ -39,10 +39,6 @@ struct SwtAux {
     double lam;          // lambda in use
 };
 
-__device__ __forceinline__ float2 cmad(float a, float2 v, float2 acc) {
-    return make_float2(fmaf(a, v.x, acc.x), fmaf(a, v.y, acc.y));
-}
-
 __device__ __forceinline__ float2 soft(float2 w, float tau) {
     const float m = sqrtf(w.x * w.x + w.y * w.y);
     const float s = m > tau ? 1.f - tau / m : 0.f;
@@ -65,14 +61,14 @@ __global__ void swt_analysis_kernel(const float2 *__restrict__ v, float2 *__rest
 #pragma unroll
         for (int mx = 0; mx < TAPS; ++mx) {
             const float2 s = row[(x + mx) % nx];
-            lo = cmad(tap_h<TAPS>(mx), s, lo);
-            hi = cmad(tap_g<TAPS>(mx), s, hi);
+            lo = tmad(tap_h<TAPS>(mx), s, lo);
+            hi = tmad(tap_g<TAPS>(mx), s, hi);
         }
-        const float hy = tap_h<TAPS>(my), gy = tap_g<TAPS>(my);
-        a[0] = cmad(hy, lo, a[0]);
-        a[1] = cmad(hy, hi, a[1]);
-        a[2] = cmad(gy, lo, a[2]);
-        a[3] = cmad(gy, hi, a[3]);
+        const Tap hy = tap_h<TAPS>(my), gy = tap_g<TAPS>(my);
+        a[0] = tmad(hy, lo, a[0]);
+        a[1] = tmad(hy, hi, a[1]);
+        a[2] = tmad(gy, lo, a[2]);
+        a[3] = tmad(gy, hi, a[3]);
     }
     const float tau = lam ? (float)(*lam / *lip) : tau_host;
     const size_t plane = (size_t)nx * ny;
@@ -102,14 +98,14 @@ __global__ void swt_synthesis_kernel(const float2 *__restrict__ c, float2 *__res
 #pragma unroll
         for (int mx = 0; mx < TAPS; ++mx) {
             const size_t j = r + pmod(x - mx, nx);
-            const float hx = tap_h<TAPS>(mx), gx = tap_g<TAPS>(mx);
-            lo = cmad(hx, c[j], lo);
-            lo = cmad(gx, c[plane + j], lo);
-            hi = cmad(hx, c[2 * plane + j], hi);
-            hi = cmad(gx, c[3 * plane + j], hi);
+            const Tap hx = tap_h<TAPS>(mx), gx = tap_g<TAPS>(mx);
+            lo = tmad(hx, c[j], lo);
+            lo = tmad(gx, c[plane + j], lo);
+            hi = tmad(hx, c[2 * plane + j], hi);
+            hi = tmad(gx, c[3 * plane + j], hi);
         }
-        acc = cmad(tap_h<TAPS>(my), lo, acc);
-        acc = cmad(tap_g<TAPS>(my), hi, acc);
+        acc = tmad(tap_h<TAPS>(my), lo, acc);
+        acc = tmad(tap_g<TAPS>(my), hi, acc);
     }
     acc = make_float2(0.5f * acc.x, 0.5f * acc.y);
     out[i] = acc;

@@ -59,11 +59,11 @@ __device__ __forceinline__ void dwt_fwd_level_body(const float2 *__restrict__ in
 #pragma unroll
         for (int m = 0; m < TAPS; ++m) {
             float2 a = s_in[i][2 * q + m];
-            float hm = tap_h<TAPS>(m), gm = tap_g<TAPS>(m);
-            lo.x = fmaf(hm, a.x, lo.x);
-            lo.y = fmaf(hm, a.y, lo.y);
-            hi.x = fmaf(gm, a.x, hi.x);
-            hi.y = fmaf(gm, a.y, hi.y);
+            const Tap hm = tap_h<TAPS>(m), gm = tap_g<TAPS>(m);
+            lo.x = tfma(hm, a.x, lo.x);
+            lo.y = tfma(hm, a.y, lo.y);
+            hi.x = tfma(gm, a.x, hi.x);
+            hi.y = tfma(gm, a.y, hi.y);
         }
         s_row[i][q] = lo;
         s_row[i][OB + q] = hi;
@@ -75,11 +75,11 @@ __device__ __forceinline__ void dwt_fwd_level_body(const float2 *__restrict__ in
 #pragma unroll
         for (int m = 0; m < TAPS; ++m) {
             float2 a = s_row[2 * oy + m][col];
-            float hm = tap_h<TAPS>(m), gm = tap_g<TAPS>(m);
-            lo.x = fmaf(hm, a.x, lo.x);
-            lo.y = fmaf(hm, a.y, lo.y);
-            hi.x = fmaf(gm, a.x, hi.x);
-            hi.y = fmaf(gm, a.y, hi.y);
+            const Tap hm = tap_h<TAPS>(m), gm = tap_g<TAPS>(m);
+            lo.x = tfma(hm, a.x, lo.x);
+            lo.y = tfma(hm, a.y, lo.y);
+            hi.x = tfma(gm, a.x, hi.x);
+            hi.y = tfma(gm, a.y, hi.y);
         }
         int gy = oy0 + oy, gx = ox0 + (col % OB);
         if (gy >= my || gx >= mx) continue;
@@ -146,9 +146,9 @@ __device__ __forceinline__ void dwt_inv_level_body(const float2 *__restrict__ ll
             int i = ((q - m) >> 1) - jy0;
             float2 lo = s_sb[xband == 0 ? 0 : 1][i][j];
             float2 hi = s_sb[xband == 0 ? 2 : 3][i][j];
-            float hm = tap_h<TAPS>(m), gm = tap_g<TAPS>(m);
-            acc.x = fmaf(hm, lo.x, fmaf(gm, hi.x, acc.x));
-            acc.y = fmaf(hm, lo.y, fmaf(gm, hi.y, acc.y));
+            const Tap hm = tap_h<TAPS>(m), gm = tap_g<TAPS>(m);
+            acc.x = tfma(hm, lo.x, tfma(gm, hi.x, acc.x));
+            acc.y = tfma(hm, lo.y, tfma(gm, hi.y, acc.y));
         }
         s_col[a][col] = acc;
     }
@@ -164,9 +164,9 @@ __device__ __forceinline__ void dwt_inv_level_body(const float2 *__restrict__ ll
             int j = ((qx - m) >> 1) - jx0;
             float2 lo = s_col[a][j];
             float2 hi = s_col[a][SB + j];
-            float hm = tap_h<TAPS>(m), gm = tap_g<TAPS>(m);
-            acc.x = fmaf(hm, lo.x, fmaf(gm, hi.x, acc.x));
-            acc.y = fmaf(hm, lo.y, fmaf(gm, hi.y, acc.y));
+            const Tap hm = tap_h<TAPS>(m), gm = tap_g<TAPS>(m);
+            acc.x = tfma(hm, lo.x, tfma(gm, hi.x, acc.x));
+            acc.y = tfma(hm, lo.y, tfma(gm, hi.y, acc.y));
         }
         size_t o = (size_t)qy * out_stride + qx;
         if (momentum) {  // FISTA: z_{k+1} = x_k + beta_k (x_k - x_{k-1})

@@ -9,11 +9,14 @@ follow from the model, checked on the GPU reconstructions.
 And one cell per model (Expanded, Partial, NoB0) recomputed end to end by the FP64 oracle on
 a reduced grid (32^2, R = 4, 8 physical coils compressed to 4, SNR 20): image-domain noise,
 the full-model forward, coil compression, the model cut, LS (CGLS) and CS (undecimated db4,
-lambda = sigma / 2, 100 iterations).  CS is compared element-wise at the FP32 bar (the
-oracle's own perturbation study: a 1e-7 relative change of the data moves the 100-iteration
-image by ~6e-8); CGLS is not stable enough for that at 20 iterations (the same change moves
-it by 0.4-0.7 %), so its iterates 1-5 are compared element-wise and the 20th through its
-NRMSE against the phantom, to 2 %."""
+lambda = sigma / 2, 100 iterations).  lambda's histogram decisions must agree (lambda and L_f
+to 1e-5) and the CS image is compared element-wise at the FP32 bar 1e-5: the oracle's own
+perturbation studies move the 100-iteration image by < 4e-7 for 1e-6 relative noise on every
+operator application, on lambda and on L_f (the wavelet taps must be exact to well below FP32:
+FP32-rounded taps alone move it by 6e-6 - 1.1e-5).  CGLS is not stable enough for an
+element-wise bar at 20 iterations (a 1e-7 change of the data moves the oracle's 20th iterate by
+0.4-0.7 %), so its iterates 1-5 are compared element-wise and the 20th through its NRMSE
+against the phantom, to 2 %."""
 
 import numpy as np
 import pytest
