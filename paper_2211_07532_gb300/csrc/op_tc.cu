@@ -1,5 +1,6 @@
-// A_exp and A_exp^H on the tcgen05 tensor cores: BF16 encoding tile, or the FP16 hi+lo
-// split of both operands; FP32 accumulation in TMEM.
+// A_exp and A_exp^H on the tcgen05 tensor cores in the FP16 hi+lo form (both operands split
+// into FP16 hi and lo parts; FP32 accumulation in TMEM), plus the launches that the BF16 form
+// (op_tc_phase.cu) shares: descriptors, dispatch and the planar partial-sum reductions.
 //
 // The complex contraction is embedded in a real GEMM whose A operand is generated on
 // the fly and never leaves shared memory:
@@ -19,14 +20,14 @@
 // counter runs across items, so the mbarrier phases and the staged operands flow from one
 // item into the next.
 //
-// CTA = 16 generator warps + 1 MMA/producer warp.  Generators compute the FP32 phase
-// (tabulated reference phase + local offset, as in the CUDA-core kernels), reduce it to
-// [-1/2, 1/2] turns, take one MUFU sincos, round to BF16 and store 16-byte chunks straight
-// into the 128B-swizzled K-major layout; each thread owns 2 rows x 8 columns.  The producer
-// warp brings the packed B tile (plus basis offsets or coefficient rows and reference
-// phases) with bulk TMA copies up to NB - 1 tiles ahead, issues the MMAs from one thread,
-// and two tcgen05.commit per tile release the A and B stages.  Every wait is bounded; on a
-// timeout the CTA records AEXP_ERR_DEVICE_TIMEOUT, drains its MMAs, frees TMEM and exits.
+// CTA = 16 generator warps + an MMA warp + two loader warps (see the warp-role note below).
+// Generators compute the FP32 phase in radians (tabulated reference phase + local offset, the
+// coefficient or basis operand held in registers pre-multiplied by 2 pi), take one MUFU sincos
+// of it (the angle spans a few turns, within the hardware's unreduced range), split E into
+// FP16 hi + lo' and store 16-byte chunks straight into the 128B-swizzled K-major layout; each
+// thread owns 2 rows x 8 columns.  The A tile is double buffered: the MMAs of stage g - 1 run
+// while stage g is generated.  Every wait is bounded; on a timeout the CTA records
+// AEXP_ERR_DEVICE_TIMEOUT, drains its MMAs, frees TMEM and exits.
 //
 // FP16 hi+lo form (HL): every operand value v is split into v_hi = fp16(v) and
 // v_lo' = fp16(2^11 (v - v_hi)), so v = v_hi + 2^-11 v_lo' to about 2^-22 relative.  Per
@@ -36,7 +37,7 @@
 // its largest component so that it lies below 2^14 (FP16 tops out at 65504), and the
 // epilogue multiplies by 2^-e.  The largest component is found by a reduction kernel before
 // the packing (an atomic max on the float bit pattern in the problem's header).  Stages
-// carry twice the operand bytes, so two B stages are kept instead of four.
+// carry twice the operand bytes, so two B stages are kept.
 // The tensor core's FP32 accumulation loses about 2^-24 of the running sum per MMA, which
 // over a long item (hundreds of MMAs) would dominate the hi+lo error; so the accumulator is
 // promoted every kPromote stages: two accumulator sets alternate by chunk of stages, the
@@ -83,21 +84,29 @@ __device__ __forceinline__ void tc_mma_stage(TcShared &sh, uint32_t tmem, const 
     tc::mma_commit(&sh.bfree[sb]);
 }
 
-// Store the 2 x 4 generated pairs of one 16-byte chunk column of both row slots: FP16 hi into
-// the first A image and lo' into the second.
-__device__ __forceinline__ void store_a_chunk(unsigned char *A, int hh, int r0, int jp, const float (&re)[2][4],
-                                              const float (&im)[2][4]) {
+// (a, b) -> FP16 pairs hi = (fp16 a, fp16 b) and lo' = fp16(2^11 (a - hi.a)), fp16(2^11 (b - hi.b)),
+// the low parts from one packed FMA: a - hi.a is exact in FP32 (hi.a is the rounding of a to
+// fewer bits), and so is its product with 2^11.
+__device__ __forceinline__ void split_hl(float a, float b, uint32_t &hi, uint32_t &lo) {
+    const float2 v = make_float2(a, b);
+    const __half2 h = __float22half2_rn(v);
+    const float2 hf = __half22float2(h);
+    const float2 l = __ffma2_rn(v, make_float2(kLoScale, kLoScale), __fmul2_rn(hf, make_float2(-kLoScale, -kLoScale)));
+    const __half2 lh = __float22half2_rn(l);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&lh);
+}
+
+// Store one 16-byte chunk column (4 pairs) of both row slots: FP16 hi into the first A image,
+// lo' into the second.
+__device__ __forceinline__ void store_hl_chunks(unsigned char *A, int hh, int r0, int jp, const uint32_t (&whi)[2][4],
+                                                const uint32_t (&wlo)[2][4]) {
     unsigned char *atom_base = A + hh * (kRows * 128);
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-        uint32_t w[4], wl[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            split_f16(re[i][u], im[i][u], w[u], wl[u]);
-        }
         const uint32_t o = tc::swz128(r0 + 32 * i, jp);
-        *reinterpret_cast<uint4 *>(atom_base + o) = make_uint4(w[0], w[1], w[2], w[3]);
-        *reinterpret_cast<uint4 *>(atom_base + kA_BYTES + o) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+        *reinterpret_cast<uint4 *>(atom_base + o) = make_uint4(whi[i][0], whi[i][1], whi[i][2], whi[i][3]);
+        *reinterpret_cast<uint4 *>(atom_base + kA_BYTES + o) = make_uint4(wlo[i][0], wlo[i][1], wlo[i][2], wlo[i][3]);
     }
 }
 
@@ -177,22 +186,70 @@ __device__ __forceinline__ void acc_advance(int (&base)[2], int nch) {
 }
 
 // ---------------------------------------------------------------------------
+// Warp roles and shared-memory plan of the FP16 hi+lo kernels
+// ---------------------------------------------------------------------------
+// Warps 0-15 generate the encoding tile of every stage (FP32 phases, sincos, hi/lo split);
+// warp 16 issues the MMAs and owns TMEM; warp 17 loads the contraction operand B (hi | lo')
+// into a 2-deep ring; warp 18 loads the generators' own operands (forward: the tile's basis
+// offsets and the 128 rows' reference phases; adjoint: the stage's coefficient rows and both
+// tiles' reference phases) into a ring of their own, 2-4 deep, which the generators release
+// as soon as they have read it.  Keeping the generators' small operands out of the B ring
+// lets them run ahead of the MMAs: a stage's B slot frees only when its 24 MMAs complete,
+// its generator slot as soon as the tile has been generated.
+constexpr int kHlMmaWarp = kTcGen / 32;
+constexpr int kHlLoadBWarp = kHlMmaWarp + 1;
+constexpr int kHlLoadGWarp = kHlMmaWarp + 2;
+constexpr int kHlThreads = kTcGen + 96;
+static_assert(kHlMmaWarp == kProdWarp, "the MMA warp allocates TMEM in tc_setup");
+
+//   A[2] (hi | lo' images of a stage, 64 KB each) | B ring | generator-operand ring
+template <int N, int LP, bool FWD>
+struct HlPlan {
+    static constexpr unsigned A_STAGE = 2 * kA_BYTES;
+    static constexpr unsigned B_ALL = 2 * N * 256;                       // hi | lo', N rows x 128 K
+    static constexpr unsigned G_OP = (FWD ? kTileVox : kCols) * LP * 4;  // basis offsets or coefficient rows
+    static constexpr unsigned G_F0 = kRows * 4;                          // 128 reference phases
+    static constexpr unsigned GS = (G_OP + G_F0 + 127u) & ~127u;
+    static constexpr int NB = 2;
+    static constexpr int NG = LP <= 20 ? 4 : 2;
+    static constexpr unsigned OFF_B = 2 * A_STAGE;
+    static constexpr unsigned OFF_G = OFF_B + NB * B_ALL;
+    static constexpr unsigned BYTES = OFF_G + NG * GS;
+    static_assert(NG <= kNBMax && NB <= kNBMax, "ring depths exceed the CTA's barriers");
+};
+
+// MMA thread, one item of n stages starting at CTA stage gs.
+template <int N, int LP, bool FWD>
+__device__ __forceinline__ int hl_mma_item(TcShared &sh, uint32_t tmem, unsigned char *gbase, int gs, int n,
+                                           int (&acc_base)[2], int last_issued, int *status) {
+    using PL = HlPlan<N, LP, FWD>;
+    constexpr uint32_t SET_COLS = 2 * tmem_acc_cols(N);
+    for (int it = 0; it < n; ++it) {
+        const int g = gs + it, sa = g & 1, sb = g % PL::NB;
+        const int m = it / kPromote;
+        if (it % kPromote == 0 && m >= 2 &&
+            !wait_or_abort(&sh.accfree[m & 1], (acc_base[m & 1] + ((m - 2) >> 1)) & 1, &sh.abort_flag, status))
+            break;  // set m & 1 still holds chunk m - 2
+        if (!wait_or_abort(&sh.afull[sa], (g >> 1) & 1, &sh.abort_flag, status)) break;
+        if (!wait_or_abort(&sh.bfull[sb], (g / PL::NB) & 1, &sh.abort_flag, status)) break;
+        tc::fence_after_sync();
+        tc_mma_stage<N>(sh, tmem + (uint32_t)(m & 1) * SET_COLS, gbase + sa * PL::A_STAGE,
+                        gbase + PL::OFF_B + sb * PL::B_ALL, it % kPromote == 0, sa, sb);
+        last_issued = g;
+    }
+    acc_advance(acc_base, (n + kPromote - 1) / kPromote);
+    return last_issued;
+}
+
+// ---------------------------------------------------------------------------
 // Forward: item = (problem, block of 128 samples, run of voxel tiles)
 // ---------------------------------------------------------------------------
 template <int CB, int LP>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kHlThreads, 1)
     fwd_tc_kernel(const ProbDesc *__restrict__ pd, const int *__restrict__ item_off, int nprob, int *counter) {
     constexpr int N = 2 * CB;
-    constexpr int NB = TcForm<true>::NB;
-    constexpr unsigned B_BYTES = N * 256;  // N rows x 128 16-bit values
-    constexpr unsigned B_ALL = TcForm<true>::NPK * B_BYTES;
-    constexpr unsigned DH_BYTES = kTileVox * LP * 4;
-    constexpr unsigned F_BYTES = kRows * 4;
-    // one staged tile (B [hi | lo'] | dh | f0 rows): S_DATA bytes arrive per stage; the
-    // stride S_BYTES keeps every B tile 1024-byte aligned
-    constexpr unsigned S_DATA = B_ALL + DH_BYTES + F_BYTES;
-    constexpr unsigned S_BYTES = (S_DATA + 1023u) & ~1023u;
-    // FP16 hi+lo: two accumulator sets of (D1 | D2), alternating by chunk of kPromote stages
+    using PL = HlPlan<N, LP, true>;
+    // two accumulator sets of (D1 | D2), alternating by chunk of kPromote stages
     constexpr uint32_t SET_COLS = 2 * tmem_acc_cols(N);
     constexpr unsigned TMEM_COLS = 2 * SET_COLS;
 
@@ -202,14 +259,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int warp = tid >> 5;
     const uint32_t sbase = align1024(smem_u32(smem_raw));
     unsigned char *gbase = smem_raw + (sbase - smem_u32(smem_raw));
-    unsigned char *A[2] = {gbase, gbase + TcForm<true>::A_STAGE};
-    unsigned char *stage0 = gbase + 2 * TcForm<true>::A_STAGE;
     const int total = item_off[nprob];
 
-    tc_setup(sh, tid, warp, TMEM_COLS, 256);  // accumulator sets are released by warps 0-7
+    // accumulator sets are released by warps 0-7; A stages and generator slots by every generator
+    tc_setup(sh, tid, warp, TMEM_COLS, 256, kTcGen, kTcGen / 32, kTcGen);
     const uint32_t tmem = sh.tmem_base;
     int gs = 0;            // stages (tiles) this CTA has processed
-    int last_issued = -1;  // producer: last stage whose MMAs were committed
+    int last_issued = -1;  // MMA thread: last stage whose MMAs were committed
     int acc_base[2] = {0, 0};
 
     int item;
@@ -224,41 +280,29 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int ntl = max(0, min(P.ntiles, tile0 + P.fwd_tps) - tile0);
         const int ntp = P.ntp;
 
-        if (warp == kProdWarp) {
-            if (tid == kTcGen) {
-                auto load = [&](int it) {
-                    const int sb = (gs + it) % NB;
-                    unsigned char *dst = stage0 + sb * S_BYTES;
-                    const size_t tile = (size_t)(tile0 + it);
-                    mbar_arrive_expect_tx(&sh.bfull[sb], S_DATA);
-                    bulk_g2s(dst, P.bpk + tile * B_ALL, B_ALL, &sh.bfull[sb]);
-                    bulk_g2s(dst + B_ALL, P.dh + tile * kTileVox * LP, DH_BYTES, &sh.bfull[sb]);
-                    bulk_g2s(dst + B_ALL + DH_BYTES, P.f0 + tile * ntp + tbase, F_BYTES, &sh.bfull[sb]);
-                };
-                for (int j = 0; j < min(NB, ntl); ++j) load(j);
-                for (int it = 0; it < ntl; ++it) {
-                    const int g = gs + it, sa = g & 1, sb = g % NB;
-                    const int m = it / kPromote;
-                    if (it % kPromote == 0 && m >= 2 &&
-                        !wait_or_abort(&sh.accfree[m & 1], (acc_base[m & 1] + ((m - 2) >> 1)) & 1, &sh.abort_flag,
-                                       status))
-                        break;  // set m & 1 still holds chunk m - 2
-                    if (!wait_or_abort(&sh.afull[sa], (g >> 1) & 1, &sh.abort_flag, status)) break;
-                    if (!wait_or_abort(&sh.bfull[sb], (g / NB) & 1, &sh.abort_flag, status)) break;
-                    tc::fence_after_sync();
-                    tc_mma_stage<N>(sh, tmem + (uint32_t)(m & 1) * SET_COLS, A[sa], stage0 + sb * S_BYTES,
-                                    it % kPromote == 0, sa, sb);
-                    last_issued = g;
-                    if (it + NB < ntl) {
-                        if (!wait_or_abort(&sh.bfree[sb], (g / NB) & 1, &sh.abort_flag, status)) break;
-                        load(it + NB);
-                    }
-                }
-                acc_advance(acc_base, (ntl + kPromote - 1) / kPromote);
+        if (warp >= kHlMmaWarp) {
+            const bool lead = (tid & 31) == 0;
+            if (warp == kHlMmaWarp && lead) {
+                last_issued = hl_mma_item<N, LP, true>(sh, tmem, gbase, gs, ntl, acc_base, last_issued, status);
+            } else if (warp == kHlLoadBWarp && lead) {
+                ring_load_item(sh.bfree, PL::NB, gs, ntl, &sh.abort_flag, status, [&](int it, int sb) {
+                    const size_t tile = (size_t)(tile0 + it);  // packed S x of the tile, hi | lo'
+                    mbar_arrive_expect_tx(&sh.bfull[sb], PL::B_ALL);
+                    bulk_g2s(gbase + PL::OFF_B + sb * PL::B_ALL, P.bpk + tile * PL::B_ALL, PL::B_ALL, &sh.bfull[sb]);
+                });
+            } else if (warp == kHlLoadGWarp && lead) {
+                ring_load_item(sh.pfree, PL::NG, gs, ntl, &sh.abort_flag, status, [&](int it, int sg) {
+                    const size_t tile = (size_t)(tile0 + it);  // basis offsets and the rows' reference phases
+                    unsigned char *dst = gbase + PL::OFF_G + sg * PL::GS;
+                    mbar_arrive_expect_tx(&sh.pfull[sg], PL::G_OP + PL::G_F0);
+                    bulk_g2s(dst, P.dh + tile * kTileVox * LP, PL::G_OP, &sh.pfull[sg]);
+                    bulk_g2s(dst + PL::G_OP, P.f0 + tile * ntp + tbase, PL::G_F0, &sh.pfull[sg]);
+                });
             }
         } else {
             // generator: warp w owns chunk columns (w & 7) and (w & 7) + 8, lane g owns rows
-            // r0 = 64 (w >> 3) + g and r0 + 32 with their coefficients in registers
+            // r0 = 64 (w >> 3) + g and r0 + 32 with their coefficients (times 2 pi: phases in
+            // radians) in registers
             const int jp = warp & 7;
             const int r0 = 64 * (warp >> 3) + (tid & 31);
             float2 k[2][LP / 2];  // (even term, odd term)
@@ -267,8 +311,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
                 for (int q4 = 0; q4 < LP / 4; ++q4) {
                     float4 w = reinterpret_cast<const float4 *>(P.khi_t + (size_t)(tbase + r0 + 32 * i) * LP)[q4];
-                    k[i][2 * q4] = make_float2(w.x, w.y);
-                    k[i][2 * q4 + 1] = make_float2(w.z, w.w);
+                    k[i][2 * q4] = make_float2(kTwoPi * w.x, kTwoPi * w.y);
+                    k[i][2 * q4 + 1] = make_float2(kTwoPi * w.z, kTwoPi * w.w);
                 }
             // epilogue rows and columns (warps 0-7): 32 samples x N/2 columns per warp, computed
             // where used so that they hold no registers during the generation
@@ -280,10 +324,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             auto epi_tmem = [&]() {
                 return tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(((warp >> 2) & 1) * (N / 2));
             };
-            int next_promo = 0;  // FP16 hi+lo: next accumulator chunk to promote
+            int next_promo = 0;  // next accumulator chunk to promote
             for (int it = 0; it < ntl; ++it) {
-                const int g = gs + it, sa = g & 1, sb = g % NB;
-                bool w_ok = wait_or_abort(&sh.bfull[sb], (g / NB) & 1, &sh.abort_flag, status);
+                const int g = gs + it, sa = g & 1, sg = g % PL::NG;
+                bool w_ok = wait_or_abort(&sh.pfull[sg], (g / PL::NG) & 1, &sh.abort_flag, status);
                 if (w_ok && g >= 2) w_ok = wait_or_abort(&sh.afree[sa], ((g - 2) >> 1) & 1, &sh.abort_flag, status);
                 if (!__all_sync(0xffffffffu, w_ok)) break;  // warp-uniform exit
                 // stages <= it - 2 are complete: promote a finished chunk and release its set
@@ -297,16 +341,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     }
                     ++next_promo;
                 }
-                const unsigned char *stg = stage0 + sb * S_BYTES;
-                const float4 *DH = reinterpret_cast<const float4 *>(stg + B_ALL);
-                const float *F0 = reinterpret_cast<const float *>(stg + B_ALL + DH_BYTES);
-                float f[2];
-#pragma unroll
-                for (int i = 0; i < 2; ++i) f[i] = F0[r0 + 32 * i];
+                const unsigned char *gsl = gbase + PL::OFF_G + sg * PL::GS;
+                const float4 *DH = reinterpret_cast<const float4 *>(gsl);
+                const float *F0 = reinterpret_cast<const float *>(gsl + PL::G_OP);
+                const float f[2] = {kTwoPi * F0[r0], kTwoPi * F0[r0 + 32]};
+                unsigned char *A = gbase + sa * PL::A_STAGE;
 #pragma unroll
                 for (int hh = 0; hh < 2; ++hh) {
                     const int j = jp + 8 * hh;  // chunk of 4 voxels; atom hh, swizzle column jp
-                    float er[2][4], ei[2][4];
+                    uint32_t whi[2][4], wlo[2][4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         float2 d[LP / 2];
@@ -322,16 +365,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                             float2 pp = make_float2(f[i], 0.f);
 #pragma unroll
                             for (int l = 0; l < LP / 2; ++l) pp = __ffma2_rn(k[i][l], d[l], pp);
-                            float ph = pp.x + pp.y;
-                            ph = ph - rintf(ph);
+                            // E = cos phi - i sin phi = cos(-phi) + i sin(-phi); the angle spans a few
+                            // turns (reference phase in [-pi, pi) plus the tile's offset), within the
+                            // range where the hardware sincos needs no reduction of our own
                             float sn, cs;
-                            __sincosf(ph * kTwoPi, &sn, &cs);
-                            er[i][u] = cs;  // E = cos - i sin
-                            ei[i][u] = -sn;
+                            __sincosf(-(pp.x + pp.y), &sn, &cs);
+                            split_hl(cs, sn, whi[i][u], wlo[i][u]);
                         }
                     }
-                    store_a_chunk(A[sa], hh, r0, jp, er, ei);
+                    store_hl_chunks(A, hh, r0, jp, whi, wlo);
                 }
+                tc::mbar_arrive(&sh.pfree[sg]);  // the generator slot has been read
                 tc::fence_proxy_async_smem();
                 tc::mbar_arrive(&sh.afull[sa]);
             }
@@ -370,20 +414,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // Adjoint: item = (problem, two voxel tiles, run of 64-sample stages)
 // ---------------------------------------------------------------------------
 template <int CB, int LP>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kHlThreads, 1)
     adj_tc_kernel(const ProbDesc *__restrict__ pd, const int *__restrict__ item_off, int nprob, int *counter) {
     constexpr int N = 2 * CB;
     constexpr int TS = kCols;  // samples per stage
-    constexpr int NB = TcForm<true>::NB;
-    constexpr unsigned B_BYTES = N * 256;
-    constexpr unsigned B_ALL = TcForm<true>::NPK * B_BYTES;
-    constexpr unsigned K_BYTES = TS * LP * 4;
-    constexpr unsigned F_BYTES = TS * 4;
-    // B [hi | lo'] | k rows | f0 (2 tiles): S_DATA bytes arrive per stage; the stride
-    // S_BYTES keeps every B tile 1024-byte aligned
-    constexpr unsigned S_DATA = B_ALL + K_BYTES + 2 * F_BYTES;
-    constexpr unsigned S_BYTES = (S_DATA + 1023u) & ~1023u;
-    // FP16 hi+lo: two accumulator sets of (D1 | D2), alternating by chunk of kPromote stages
+    using PL = HlPlan<N, LP, false>;
     constexpr uint32_t SET_COLS = 2 * tmem_acc_cols(N);
     constexpr unsigned TMEM_COLS = 2 * SET_COLS;
 
@@ -393,11 +428,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int warp = tid >> 5;
     const uint32_t sbase = align1024(smem_u32(smem_raw));
     unsigned char *gbase = smem_raw + (sbase - smem_u32(smem_raw));
-    unsigned char *A[2] = {gbase, gbase + TcForm<true>::A_STAGE};
-    unsigned char *stage0 = gbase + 2 * TcForm<true>::A_STAGE;
     const int total = item_off[nprob];
 
-    tc_setup(sh, tid, warp, TMEM_COLS, 128);  // accumulator sets are released by warps 0-3
+    // accumulator sets are released by warps 0-3; A stages and generator slots by every generator
+    tc_setup(sh, tid, warp, TMEM_COLS, 128, kTcGen, kTcGen / 32, kTcGen);
     const uint32_t tmem = sh.tmem_base;
     int gs = 0;
     int last_issued = -1;
@@ -416,44 +450,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int t0 = split * P.adj_tps;
         const int nst = max(0, (min(ntp, t0 + P.adj_tps) - t0) / TS);
 
-        if (warp == kProdWarp) {
-            if (tid == kTcGen) {
-                auto load = [&](int it) {
-                    const int sb = (gs + it) % NB;
-                    unsigned char *dst = stage0 + sb * S_BYTES;
-                    const size_t ts = (size_t)t0 + (size_t)it * TS;
-                    mbar_arrive_expect_tx(&sh.bfull[sb], S_DATA);
-                    bulk_g2s(dst, P.ypk + (ts / TS) * B_ALL, B_ALL, &sh.bfull[sb]);
-                    bulk_g2s(dst + B_ALL, P.khi_t + ts * LP, K_BYTES, &sh.bfull[sb]);
-                    bulk_g2s(dst + B_ALL + K_BYTES, P.f0 + (size_t)tileA * ntp + ts, F_BYTES, &sh.bfull[sb]);
-                    bulk_g2s(dst + B_ALL + K_BYTES + F_BYTES, P.f0 + (size_t)tileB * ntp + ts, F_BYTES,
+        if (warp >= kHlMmaWarp) {
+            const bool lead = (tid & 31) == 0;
+            if (warp == kHlMmaWarp && lead) {
+                last_issued = hl_mma_item<N, LP, false>(sh, tmem, gbase, gs, nst, acc_base, last_issued, status);
+            } else if (warp == kHlLoadBWarp && lead) {
+                ring_load_item(sh.bfree, PL::NB, gs, nst, &sh.abort_flag, status, [&](int it, int sb) {
+                    const size_t ts = (size_t)t0 + (size_t)it * TS;  // packed k-space of the stage, hi | lo'
+                    mbar_arrive_expect_tx(&sh.bfull[sb], PL::B_ALL);
+                    bulk_g2s(gbase + PL::OFF_B + sb * PL::B_ALL, P.ypk + (ts / TS) * PL::B_ALL, PL::B_ALL,
                              &sh.bfull[sb]);
-                };
-                for (int j = 0; j < min(NB, nst); ++j) load(j);
-                for (int it = 0; it < nst; ++it) {
-                    const int g = gs + it, sa = g & 1, sb = g % NB;
-                    const int m = it / kPromote;
-                    if (it % kPromote == 0 && m >= 2 &&
-                        !wait_or_abort(&sh.accfree[m & 1], (acc_base[m & 1] + ((m - 2) >> 1)) & 1, &sh.abort_flag,
-                                       status))
-                        break;  // set m & 1 still holds chunk m - 2
-                    if (!wait_or_abort(&sh.afull[sa], (g >> 1) & 1, &sh.abort_flag, status)) break;
-                    if (!wait_or_abort(&sh.bfull[sb], (g / NB) & 1, &sh.abort_flag, status)) break;
-                    tc::fence_after_sync();
-                    tc_mma_stage<N>(sh, tmem + (uint32_t)(m & 1) * SET_COLS, A[sa], stage0 + sb * S_BYTES,
-                                    it % kPromote == 0, sa, sb);
-                    last_issued = g;
-                    if (it + NB < nst) {
-                        if (!wait_or_abort(&sh.bfree[sb], (g / NB) & 1, &sh.abort_flag, status)) break;
-                        load(it + NB);
-                    }
-                }
-                acc_advance(acc_base, (nst + kPromote - 1) / kPromote);
+                });
+            } else if (warp == kHlLoadGWarp && lead) {
+                ring_load_item(sh.pfree, PL::NG, gs, nst, &sh.abort_flag, status, [&](int it, int sg) {
+                    const size_t ts = (size_t)t0 + (size_t)it * TS;  // coefficient rows, both tiles' f0
+                    unsigned char *dst = gbase + PL::OFF_G + sg * PL::GS;
+                    mbar_arrive_expect_tx(&sh.pfull[sg], PL::G_OP + 2 * TS * 4);
+                    bulk_g2s(dst, P.khi_t + ts * LP, PL::G_OP, &sh.pfull[sg]);
+                    bulk_g2s(dst + PL::G_OP, P.f0 + (size_t)tileA * ntp + ts, TS * 4, &sh.pfull[sg]);
+                    bulk_g2s(dst + PL::G_OP + TS * 4, P.f0 + (size_t)tileB * ntp + ts, TS * 4, &sh.pfull[sg]);
+                });
             }
         } else {
             // generator: warp w owns sample chunks (w & 7) and (w & 7) + 8 of each stage; lane g
             // owns voxel rows r0 = 64 (w >> 3) + g and r0 + 32 (both in tile w >> 3 of the item)
-            // with their basis offsets in registers
+            // with their basis offsets (times 2 pi: phases in radians) in registers
             const int jp = warp & 7;
             const int th = warp >> 3;
             const int r0 = 64 * th + (tid & 31);
@@ -465,8 +486,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
                 for (int q4 = 0; q4 < LP / 4; ++q4) {
                     float4 w = reinterpret_cast<const float4 *>(P.dh + (size_t)(valid ? p : 0) * LP)[q4];
-                    d[i][2 * q4] = valid ? make_float2(w.x, w.y) : make_float2(0.f, 0.f);
-                    d[i][2 * q4 + 1] = valid ? make_float2(w.z, w.w) : make_float2(0.f, 0.f);
+                    d[i][2 * q4] = valid ? make_float2(kTwoPi * w.x, kTwoPi * w.y) : make_float2(0.f, 0.f);
+                    d[i][2 * q4 + 1] = valid ? make_float2(kTwoPi * w.z, kTwoPi * w.w) : make_float2(0.f, 0.f);
                 }
             }
             // epilogue row (warps 0-3): voxel p = vb * 128 + 32 warp + lane; addressing computed
@@ -477,11 +498,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 return reinterpret_cast<const float4 *>(P.Sp + (size_t)(pr < ntiles * kTileVox ? pr : 0) * CB);
             };
             auto epi_tmem = [&]() { return tmem + ((uint32_t)(32 * (warp & 3)) << 16); };
-            float xr = 0.f, xi = 0.f;  // FP16 hi+lo: promoted, coil-combined partial sum
+            float xr = 0.f, xi = 0.f;  // promoted, coil-combined partial sum
             int next_promo = 0;
             for (int it = 0; it < nst; ++it) {
-                const int g = gs + it, sa = g & 1, sb = g % NB;
-                bool w_ok = wait_or_abort(&sh.bfull[sb], (g / NB) & 1, &sh.abort_flag, status);
+                const int g = gs + it, sa = g & 1, sg = g % PL::NG;
+                bool w_ok = wait_or_abort(&sh.pfull[sg], (g / PL::NG) & 1, &sh.abort_flag, status);
                 if (w_ok && g >= 2) w_ok = wait_or_abort(&sh.afree[sa], ((g - 2) >> 1) & 1, &sh.abort_flag, status);
                 if (!__all_sync(0xffffffffu, w_ok)) break;  // warp-uniform exit
                 // stages <= it - 2 are complete: promote a finished chunk and release its set
@@ -494,15 +515,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     }
                     ++next_promo;
                 }
-                const unsigned char *stg = stage0 + sb * S_BYTES;
-                const float4 *KS = reinterpret_cast<const float4 *>(stg + B_ALL);
-                const float4 *FS = reinterpret_cast<const float4 *>(stg + B_ALL + K_BYTES);
+                const unsigned char *gsl = gbase + PL::OFF_G + sg * PL::GS;
+                const float4 *KS = reinterpret_cast<const float4 *>(gsl);
+                const float4 *FS = reinterpret_cast<const float4 *>(gsl + PL::G_OP);
+                unsigned char *A = gbase + sa * PL::A_STAGE;
 #pragma unroll
                 for (int hh = 0; hh < 2; ++hh) {
                     const int j = jp + 8 * hh;  // samples 4j..4j+3 of the stage
                     const float4 fa = FS[th * (TS / 4) + j];
-                    const float fA[4] = {fa.x, fa.y, fa.z, fa.w};
-                    float er[2][4], ei[2][4];
+                    const float fA[4] = {kTwoPi * fa.x, kTwoPi * fa.y, kTwoPi * fa.z, kTwoPi * fa.w};
+                    uint32_t whi[2][4], wlo[2][4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         float2 kk[LP / 2];
@@ -514,25 +536,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         }
 #pragma unroll
                         for (int i = 0; i < 2; ++i) {
-                            // even and odd terms in the two lanes of packed FMAs (each lane as fmaf)
                             float2 pp = make_float2(fA[u], 0.f);
 #pragma unroll
                             for (int l = 0; l < LP / 2; ++l) pp = __ffma2_rn(kk[l], d[i][l], pp);
-                            float ph = pp.x + pp.y;
-                            ph = ph - rintf(ph);
                             float sn, cs;
-                            __sincosf(ph * kTwoPi, &sn, &cs);
-                            er[i][u] = cs;  // conj(E) = cos + i sin
-                            ei[i][u] = sn;
+                            __sincosf(pp.x + pp.y, &sn, &cs);  // conj(E) = cos phi + i sin phi
+                            split_hl(cs, sn, whi[i][u], wlo[i][u]);
                         }
                     }
-                    store_a_chunk(A[sa], hh, r0, jp, er, ei);
+                    store_hl_chunks(A, hh, r0, jp, whi, wlo);
                 }
+                tc::mbar_arrive(&sh.pfree[sg]);  // the generator slot has been read
                 tc::fence_proxy_async_smem();
                 tc::mbar_arrive(&sh.afull[sa]);
             }
             // epilogue (warps 0-3, one voxel row per thread): conj(S) . u over coils, read
-            // from TMEM in chunks of 8 coils (FP16 hi+lo: u = (D1 + 2^-11 D2) 2^-e)
+            // from TMEM in chunks of 8 coils (u = (D1 + 2^-11 D2) 2^-e)
             bool ok = !sh.abort_flag;
             const int gl = gs + nst - 1;
             if (nst > 0 && ok) ok = wait_or_abort(&sh.afree[gl & 1], (gl >> 1) & 1, &sh.abort_flag, status);
@@ -655,16 +674,13 @@ __global__ void fwd_reduce_planar_residual_kernel(const float *part, int splits,
 __global__ void write_desc_kernel(ProbDesc d, ProbDesc *dst) { *dst = d; }
 
 // ---- launch helpers ----
-constexpr size_t round1k(size_t v) { return (v + 1023) & ~size_t(1023); }
 template <int CB, int LP>
 size_t fwd_tc_smem() {
-    using F = TcForm<true>;
-    return 1024 + 2 * F::A_STAGE + F::NB * round1k(F::NPK * 2 * CB * 256 + kTileVox * LP * 4 + kRows * 4);
+    return 1024 + HlPlan<2 * CB, LP, true>::BYTES;
 }
 template <int CB, int LP>
 size_t adj_tc_smem() {
-    using F = TcForm<true>;
-    return 1024 + 2 * F::A_STAGE + F::NB * round1k(F::NPK * 2 * CB * 256 + kCols * LP * 4 + 2 * kCols * 4);
+    return 1024 + HlPlan<2 * CB, LP, false>::BYTES;
 }
 
 // The max-reduction grids equal the packing grids: both cover ntiles * 64 * CB / 2 (forward)
@@ -680,7 +696,7 @@ cudaError_t launch_fwd_tc(const ProbDesc *pd, int nprob, int max_pack_blocks, co
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    kern<<<std::min(total_items, num_sms()), kTcThreads, smem, st>>>(pd, item_off, nprob, counter);
+    kern<<<std::min(total_items, num_sms()), kHlThreads, smem, st>>>(pd, item_off, nprob, counter);
     return cudaGetLastError();
 }
 
@@ -695,7 +711,7 @@ cudaError_t launch_adj_tc(const ProbDesc *pd, int nprob, int max_pack_blocks, co
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    kern<<<std::min(total_items, num_sms()), kTcThreads, smem, st>>>(pd, item_off, nprob, counter);
+    kern<<<std::min(total_items, num_sms()), kHlThreads, smem, st>>>(pd, item_off, nprob, counter);
     return cudaGetLastError();
 }
 

@@ -213,18 +213,6 @@ __device__ __forceinline__ void tcp_phase_item(TcShared &sh, uint32_t tmem, unsi
     }
 }
 
-// Ring loaders, one item: stage g's slot is refilled once the stage that used it last has
-// released it (slot releases are committed by the MMA threads).
-template <class Load>
-__device__ __forceinline__ void tcp_ring_item(uint64_t *free_bar, int depth, int gs, int n, volatile int *abort_flag,
-                                              int *status, Load load) {
-    for (int it = 0; it < n; ++it) {
-        const int g = gs + it, s = g % depth;
-        if (g >= depth && !wait_or_abort(&free_bar[s], ((g - depth) / depth) & 1, abort_flag, status)) return;
-        load(it, s);
-    }
-}
-
 // Teardown: both MMA threads commit to the drain barrier (count 2); the contraction thread
 // waits (bounded) until every MMA has completed; then TMEM is released.
 __device__ __forceinline__ void tcp_teardown(TcShared &sh, int tid, int warp, int *status) {
@@ -343,7 +331,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
             } else if (warp == kPhaseWarp && lead) {
                 tcp_phase_item<N>(sh, tmem, gbase, gs, ntl, iter, (P.LP + 7) >> 3, status);
             } else if (warp == kLoadBWarp && lead) {
-                tcp_ring_item(sh.bfree, kNBB, gs, ntl, &sh.abort_flag, status, [&](int it, int sb) {
+                ring_load_item(sh.bfree, kNBB, gs, ntl, &sh.abort_flag, status, [&](int it, int sb) {
                     const int tile = tile0 + it;  // packed S x of the tile and its reference phases
                     unsigned char *dst = gbase + PL::OFF_B + sb * PL::BS;
                     mbar_arrive_expect_tx(&sh.bfull[sb], PL::B_BYTES + PL::F_BYTES);
@@ -353,7 +341,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
             } else if (warp == kLoadPWarp && lead) {
                 mbar_arrive_expect_tx(&sh.apfull, kApBytes);
                 bulk_g2s(gbase + PL::OFF_AP, P.kph + (size_t)(tbase / kRows) * kPhaseBlockBytes, kApBytes, &sh.apfull);
-                tcp_ring_item(sh.pfree, kNP, gs, ntl, &sh.abort_flag, status, [&](int it, int sp) {
+                ring_load_item(sh.pfree, kNP, gs, ntl, &sh.abort_flag, status, [&](int it, int sp) {
                     const int tile = tile0 + it;  // the tile's basis offsets, hi | lo
                     const unsigned char *dp =
                         P.dhph + (size_t)(tile >> 1) * kPhaseBlockBytes + (size_t)(tile & 1) * kHalfImg;
@@ -456,7 +444,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
             } else if (warp == kPhaseWarp && lead) {
                 tcp_phase_item<N>(sh, tmem, gbase, gs, nst, iter, (P.LP + 7) >> 3, status);
             } else if (warp == kLoadBWarp && lead) {
-                tcp_ring_item(sh.bfree, kNBB, gs, nst, &sh.abort_flag, status, [&](int it, int sb) {
+                ring_load_item(sh.bfree, kNBB, gs, nst, &sh.abort_flag, status, [&](int it, int sb) {
                     const size_t ts = (size_t)t0 + (size_t)it * TS;  // packed y and both tiles' f0
                     unsigned char *dst = gbase + PL::OFF_B + sb * PL::BS;
                     mbar_arrive_expect_tx(&sh.bfull[sb], PL::B_BYTES + 2 * FT);
@@ -467,7 +455,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
             } else if (warp == kLoadPWarp && lead) {
                 mbar_arrive_expect_tx(&sh.apfull, kApBytes);
                 bulk_g2s(gbase + PL::OFF_AP, P.dhph + (size_t)vb * kPhaseBlockBytes, kApBytes, &sh.apfull);
-                tcp_ring_item(sh.pfree, kNP, gs, nst, &sh.abort_flag, status, [&](int it, int sp) {
+                ring_load_item(sh.pfree, kNP, gs, nst, &sh.abort_flag, status, [&](int it, int sp) {
                     const size_t ts = (size_t)t0 + (size_t)it * TS;  // the stage's k rows, hi | lo
                     const unsigned char *kp =
                         P.kph + (ts / kRows) * kPhaseBlockBytes + ((ts / TS) & 1) * (size_t)kHalfImg;

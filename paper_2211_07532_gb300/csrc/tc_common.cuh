@@ -14,25 +14,16 @@ namespace aexp {
 namespace {
 
 constexpr int kTcGen = 512;              // generator threads (16 warps)
-constexpr int kTcThreads = kTcGen + 32;  // + MMA/producer warp
-constexpr int kProdWarp = kTcGen / 32;
+constexpr int kProdWarp = kTcGen / 32;   // the first non-generator warp: MMA issue, owns TMEM
 constexpr int kRows = 128;               // M
 constexpr int kCols = 64;                // voxels (forward) or samples (adjoint) per stage
 constexpr int kA_BYTES = kRows * kCols * 2 * 2;  // 128 rows x 128 bf16 = 32 KB
 constexpr float kTwoPi = 6.283185307179586f;
 constexpr int kSpin = 1 << 22;
-constexpr int kNBMax = 4;  // staged B tiles (BF16: 4, FP16 hi+lo: 2)
+constexpr int kNBMax = 4;  // deepest operand ring (slots with their own full / free barriers)
 constexpr float kLoScale = 2048.f;           // 2^11: scale of the low parts
 constexpr float kLoInv = 1.f / 2048.f;
 constexpr int kPromote = 8;                  // FP16 hi+lo: stages per accumulator chunk
-
-// Per-form constants: stages of B, bytes of one generated A stage, operand images per tile.
-template <bool HL>
-struct TcForm {
-    static constexpr int NB = HL ? 2 : 4;
-    static constexpr int NPK = HL ? 2 : 1;
-    static constexpr unsigned A_STAGE = NPK * kA_BYTES;
-};
 
 // TMEM columns of one accumulator (N = 2C columns rounded up to a power of two >= 32).
 constexpr uint32_t tmem_acc_cols(int N) { return N <= 32 ? 32u : 64u; }
@@ -99,15 +90,18 @@ struct TcShared {
 };
 
 // afull_count: generator threads that fill one A stage (all of them, or one group of two
-// that take alternate stages); phfree_count: generator warps that read one phase tile.
+// that take alternate stages); phfree_count: generator warps that read one phase tile;
+// pfree_count: arrivals that release one slot of the per-stage operand ring (the phase-GEMM
+// issuer, or every generator thread when the generators read the slot themselves).
 __device__ __forceinline__ void tc_setup(TcShared &sh, int tid, int warp, uint32_t ncols, unsigned acc_count,
-                                         unsigned afull_count = kTcGen, unsigned phfree_count = kTcGen / 32) {
+                                         unsigned afull_count = kTcGen, unsigned phfree_count = kTcGen / 32,
+                                         unsigned pfree_count = 1) {
     if (tid == 0) {
         for (int s = 0; s < kNBMax; ++s) {
             mbar_init(&sh.bfull[s], 1);
             mbar_init(&sh.bfree[s], 1);
             mbar_init(&sh.pfull[s], 1);
-            mbar_init(&sh.pfree[s], 1);
+            mbar_init(&sh.pfree[s], pfree_count);
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(&sh.afull[s], afull_count);
@@ -147,6 +141,18 @@ __device__ __forceinline__ bool tc_next_item(TcShared &sh, int tid, int iter, in
     tc::fence_after_sync();
     item = sh.item[slot];
     return !sh.stop[slot];
+}
+
+// Ring loader, one item: stage g's slot (g mod depth) is refilled once the stage that used it
+// last has released it; `load(it, slot)` issues the copies for the item's stage `it`.
+template <class Load>
+__device__ __forceinline__ void ring_load_item(uint64_t *free_bar, int depth, int gs, int n, volatile int *abort_flag,
+                                               int *status, Load load) {
+    for (int it = 0; it < n; ++it) {
+        const int g = gs + it, s = g % depth;
+        if (g >= depth && !wait_or_abort(&free_bar[s], ((g - depth) / depth) & 1, abort_flag, status)) return;
+        load(it, s);
+    }
 }
 
 __device__ __forceinline__ void tc_teardown(TcShared &sh, int warp, uint32_t ncols, int last_issued, int *status) {
