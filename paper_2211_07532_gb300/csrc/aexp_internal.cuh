@@ -92,7 +92,7 @@ struct OpLayout {
     // byte offsets into the workspace
     size_t off_hdr, off_khi_l, off_klo_l, off_khi_t, off_h0, off_dh, off_f0, off_S, off_b,
         off_fpart, off_yt, off_apart, off_ypk, off_desc, off_hp;
-    // BF16 form: TF32 hi | lo operands of the phase GEMM (k rows per 128 samples, basis
+    // BF16 form: BF16 hi | lo operands of the phase GEMM (k rows per 128 samples, basis
     // offsets per pair of tiles)
     size_t off_kph, off_dhph;
     int fwd_items, adj_items;  // persistent tensor-core work items
@@ -183,7 +183,7 @@ cudaError_t tcp_forward(int CB, const ProbDesc *pd, int nprob, int max_pack_bloc
                         const int *item_off, int total_items, int *counter, cudaStream_t st);
 cudaError_t tcp_adjoint(int CB, const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *yt, int src,
                         const int *item_off, int total_items, int *counter, cudaStream_t st);
-constexpr size_t kPhaseBlockBytes = 32768;  // TF32 hi | lo images of 128 rows x 32 K slots
+constexpr size_t kPhaseBlockBytes = 16384;  // 128 rows x 128 B: BF16 hi (32 K slots) | lo (32 K slots)
 
 // Tensor-core forms (op_tc.cu): the forward packs S*x itself; the adjoint packs yt.
 cudaError_t op_forward_tc(const OpLayout &L, const float2 *x, char *ws, cudaStream_t st);

@@ -2,20 +2,22 @@
 //
 // Inside a work item the phase offsets of a stage are a small matrix product,
 //   off(t, v) = sum_l khi(t, l) dh(v, l)        (t: 128 samples or 64 per stage, v: voxels,
-//                                                l: field terms incl. B0, padded to 8/16/24)
+//                                                l: field terms incl. B0, padded to 16 or 32)
 // with khi = k / 2pi in turns and dh the basis offsets from the tile's reference voxel
 // (the same quantities the CUDA-core generators sum with FMAs).  It runs as tcgen05.mma
-// kind::tf32 into a TMEM tile, each factor split x = x_hi + x_lo in TF32 (x_hi rounded to
-// 10 mantissa bits, x_lo = x - x_hi rounded again) and the products hi*hi + hi*lo + lo*hi
-// accumulated in FP32: relative error ~2^-21 of sum_l |khi dh|, about 1e-6 turn for the few
-// turns an 8x8 tile spans, far below the BF16 rounding of E (2^-9).
+// kind::f16 with BF16 operands into a TMEM tile, each factor split x = x_hi + x_lo in BF16
+// (x_hi rounded to 8 significant bits, x_lo = x - x_hi rounded again) and the products
+// hi*hi + hi*lo + lo*hi accumulated in FP32: relative error ~2^-17 of sum_l |khi dh|, about
+// 1e-4 rad for the ~12 rad an 8x8 tile spans at the Nyquist edge of k-space, twenty times
+// below the BF16 rounding of E (2^-9).  Each K step takes 16 terms, so up to 16 terms cost
+// 3 MMAs per stage and up to 32 terms 6 (TF32 operands, 8 terms per step, took 9).
 //
 // Generators then read their row's phase offsets of the stage with one tcgen05.ld (in
 // radians: the k operand carries the factor 2 pi), add 2 pi f0(tile, t) with the tile's
 // tabulated reference phase f0 in [-1/2, 1/2) turn, take one MUFU sincos and store the BF16
 // encoding tile; the contraction with the
-// coil-weighted image (or the k-space data) is the same tcgen05 kind::f16 GEMM as in the
-// CUDA-core-phase form.  The two GEMMs are issued by two threads of their own: the
+// coil-weighted image (or the k-space data) is a tcgen05 kind::f16 GEMM of BF16 operands.
+// The two GEMMs are issued by two threads of their own: the
 // contraction thread issues 8 MMAs per stage once the generators have stored A(g); the
 // phase thread fills four TMEM phase tiles, each as soon as the generators have read it.
 // The generators form two groups of 8 warps that take alternate stages, so that one group
@@ -29,8 +31,8 @@
 // stages back was still running the parity test passed one phase early, so that warp read
 // partial accumulators (seen as run-to-run differences in one lane quadrant of one item).
 //
-// Phase operands, prepared once per problem (TF32 images in the 128B-swizzled K-major
-// layout, 32 K slots = 128 bytes per row; each block is [hi 16 KB | lo 16 KB]):
+// Phase operands, prepared once per problem (BF16 images in the 128B-swizzled K-major
+// layout, 64 K slots = 128 bytes per row: slots 0-31 hold the hi parts, 32-63 the lo parts):
 //   kph   per block of 128 samples, rows = samples:  forward A_phase; adjoint B_phase
 //         (the 64 rows of one stage are one half of a block)
 //   dhph  per pair of tiles, rows = 128 voxels:      adjoint A_phase; forward B_phase
@@ -42,8 +44,9 @@
 namespace aexp {
 namespace {
 
-constexpr unsigned kHalfImg = 64 * 128;         // one 64-row TF32 image (hi or lo), 8 KB
-constexpr unsigned kApBytes = 2 * kRows * 128;  // item operand: hi | lo of 128 rows, 32 KB
+constexpr unsigned kHalfImg = 64 * 128;         // the hi | lo image of 64 rows, 8 KB
+constexpr unsigned kApBytes = kRows * 128;      // item operand: hi | lo image of 128 rows, 16 KB
+constexpr uint32_t kLoBytes = 64;               // the lo parts start 32 slots (64 B) into a row
 // TMEM: the contraction accumulates in columns 0..N-1, phase tile b (of 4) sits at 64 + 64 b
 constexpr uint32_t kPhBase = 64;
 constexpr int kPhBufs = 4;
@@ -53,59 +56,61 @@ __device__ __forceinline__ uint32_t phase_col(int g) { return kPhBase + 64u * (u
 
 // ---- operand preparation ----
 
-__device__ __forceinline__ void split_tf32_4(const float (&v)[4], uint4 &hi, uint4 &lo) {
+// Eight values -> 16-byte chunks of BF16 hi parts and of BF16 lo parts (lo = x - hi, rounded).
+__device__ __forceinline__ void split_bf16_8(const float (&v)[8], uint4 &hi, uint4 &lo) {
     uint32_t h[4], l[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        h[u] = tc::tf32_rna(v[u]);
-        l[u] = tc::tf32_rna(v[u] - __uint_as_float(h[u]));
+        const __nv_bfloat162 hb = __floats2bfloat162_rn(v[2 * u], v[2 * u + 1]);
+        const float2 hf = __bfloat1622float2(hb);
+        const __nv_bfloat162 lb = __floats2bfloat162_rn(v[2 * u] - hf.x, v[2 * u + 1] - hf.y);
+        h[u] = *reinterpret_cast<const uint32_t *>(&hb);
+        l[u] = *reinterpret_cast<const uint32_t *>(&lb);
     }
     hi = make_uint4(h[0], h[1], h[2], h[3]);
     lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// kph[block][hi | lo][row = sample % 128][slot] = 2 pi khi_t[sample][slot] (0 beyond LP): the
-// phase GEMM yields radians
+// kph[block][row = sample % 128][hi slots 0-31 | lo slots 0-31] = 2 pi khi_t[sample][slot]
+// (0 beyond LP): the phase GEMM yields radians
 __global__ void prep_kph_kernel(const float *__restrict__ khi_t, int ntp, int LP, unsigned char *__restrict__ kph) {
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // (sample, chunk of 4 slots)
-    if (i >= (size_t)ntp * 8) return;
-    const int t = (int)(i / 8), c = (int)(i % 8);
-    float v[4];
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // (sample, chunk of 8 slots)
+    if (i >= (size_t)ntp * 4) return;
+    const int t = (int)(i / 4), c = (int)(i % 4);
+    float v[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int l = 4 * c + u;
+    for (int u = 0; u < 8; ++u) {
+        const int l = 8 * c + u;
         v[u] = l < LP ? kTwoPi * khi_t[(size_t)t * LP + l] : 0.f;
     }
     uint4 hi, lo;
-    split_tf32_4(v, hi, lo);
+    split_bf16_8(v, hi, lo);
     unsigned char *blk = kph + (size_t)(t / kRows) * kPhaseBlockBytes;
-    const uint32_t o = tc::swz128(t % kRows, c);
-    *reinterpret_cast<uint4 *>(blk + o) = hi;
-    *reinterpret_cast<uint4 *>(blk + kPhaseBlockBytes / 2 + o) = lo;
+    *reinterpret_cast<uint4 *>(blk + tc::swz128(t % kRows, c)) = hi;
+    *reinterpret_cast<uint4 *>(blk + tc::swz128(t % kRows, c + 4)) = lo;
 }
 
-// dhph[pair][hi | lo][row = 64 (tile & 1) + voxel][slot] = dh[tile][voxel][slot] (0 beyond LP
-// and for the missing second tile of an odd count)
+// dhph[pair][row = 64 (tile & 1) + voxel][hi slots | lo slots] = dh[tile][voxel][slot] (0 beyond
+// LP and for the missing second tile of an odd count)
 __global__ void prep_dhph_kernel(const float *__restrict__ dh, int ntiles, int LP, unsigned char *__restrict__ dhph) {
     const int npairs = (ntiles + 1) / 2;
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // (pair, row, chunk)
-    if (i >= (size_t)npairs * kRows * 8) return;
-    const int c = (int)(i % 8);
-    const int r = (int)((i / 8) % kRows);
-    const int pair = (int)(i / (8 * kRows));
+    if (i >= (size_t)npairs * kRows * 4) return;
+    const int c = (int)(i % 4);
+    const int r = (int)((i / 4) % kRows);
+    const int pair = (int)(i / (4 * kRows));
     const int tile = 2 * pair + r / kTileVox, v = r % kTileVox;
-    float x[4];
+    float x[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int l = 4 * c + u;
+    for (int u = 0; u < 8; ++u) {
+        const int l = 8 * c + u;
         x[u] = (tile < ntiles && l < LP) ? dh[((size_t)tile * kTileVox + v) * LP + l] : 0.f;
     }
     uint4 hi, lo;
-    split_tf32_4(x, hi, lo);
+    split_bf16_8(x, hi, lo);
     unsigned char *blk = dhph + (size_t)pair * kPhaseBlockBytes;
-    const uint32_t o = tc::swz128(r, c);
-    *reinterpret_cast<uint4 *>(blk + o) = hi;
-    *reinterpret_cast<uint4 *>(blk + kPhaseBlockBytes / 2 + o) = lo;
+    *reinterpret_cast<uint4 *>(blk + tc::swz128(r, c)) = hi;
+    *reinterpret_cast<uint4 *>(blk + tc::swz128(r, c + 4)) = lo;
 }
 
 // ---- kernels ----
@@ -118,7 +123,7 @@ constexpr int kLoadBWarp = kMmaWarp + 1;
 constexpr int kPhaseWarp = kMmaWarp + 2;
 constexpr int kLoadPWarp = kMmaWarp + 3;
 constexpr int kTcpThreads = kTcGen + 128;
-constexpr int kNP = 3;   // ring of per-stage phase operands (hi | lo images, 16 KB)
+constexpr int kNP = 3;   // ring of per-stage phase operands (hi | lo image, 8 KB)
 constexpr int kNBB = 4;  // ring of per-stage contraction operands + reference phases
 // A generator group waits only on the stages of its parity, so each B slot and each phase tile
 // must belong to one group: with an odd count a slot would alternate between the groups, a
@@ -133,7 +138,7 @@ struct TcpPlan {
     static constexpr unsigned B_BYTES = N * 256;
     static constexpr unsigned F_BYTES = kRows * 4;  // forward: 128 f0; adjoint: 2 x 64 f0
     static constexpr unsigned BS = (B_BYTES + F_BYTES + 1023u) & ~1023u;  // B ring stride
-    static constexpr unsigned PS = 2 * kHalfImg;                          // PH ring stride
+    static constexpr unsigned PS = kHalfImg;                              // PH ring stride
     static constexpr unsigned OFF_AP = 2 * kA_BYTES;
     static constexpr unsigned OFF_PH = OFF_AP + kApBytes;
     static constexpr unsigned OFF_B = OFF_PH + kNP * PS;
@@ -152,25 +157,24 @@ __device__ __forceinline__ void contraction_mma(uint32_t tmem, uint64_t da, uint
     }
 }
 
-// Phase GEMM of one stage into the tile at `d`: KS steps of 8 TF32 values, products
-// hi*hi + hi*lo + lo*hi.
+// Phase GEMM of one stage into the tile at `d`: KS steps of 16 BF16 values, products
+// hi*hi + hi*lo + lo*hi (the lo parts sit kLoBytes further along each row).
 template <int KS>
-__device__ __forceinline__ void phase_mma_ks(uint32_t d, uint64_t ah, uint64_t al, uint64_t bh, uint64_t bl) {
-    constexpr uint32_t ID = tc::idesc_tf32(kRows, 64);
+__device__ __forceinline__ void phase_mma_ks(uint32_t d, uint64_t a, uint64_t b) {
+    constexpr uint32_t ID = tc::idesc_f16(kRows, 64, 1);
+#pragma unroll
+    for (int k = 0; k < KS; ++k) tc::mma_f16(d, tc::sdesc_advance(a, 32 * k), tc::sdesc_advance(b, 32 * k), ID, k > 0);
 #pragma unroll
     for (int k = 0; k < KS; ++k)
-        tc::mma_tf32(d, tc::sdesc_advance(ah, 32 * k), tc::sdesc_advance(bh, 32 * k), ID, k > 0);
+        tc::mma_f16(d, tc::sdesc_advance(a, 32 * k), tc::sdesc_advance(b, kLoBytes + 32 * k), ID, 1u);
 #pragma unroll
-    for (int k = 0; k < KS; ++k) tc::mma_tf32(d, tc::sdesc_advance(ah, 32 * k), tc::sdesc_advance(bl, 32 * k), ID, 1u);
-#pragma unroll
-    for (int k = 0; k < KS; ++k) tc::mma_tf32(d, tc::sdesc_advance(al, 32 * k), tc::sdesc_advance(bh, 32 * k), ID, 1u);
+    for (int k = 0; k < KS; ++k)
+        tc::mma_f16(d, tc::sdesc_advance(a, kLoBytes + 32 * k), tc::sdesc_advance(b, 32 * k), ID, 1u);
 }
 
-__device__ __forceinline__ void phase_mma(int ks, uint32_t d, uint64_t ah, uint64_t al, uint64_t bh, uint64_t bl) {
-    if (ks <= 1) phase_mma_ks<1>(d, ah, al, bh, bl);
-    else if (ks == 2) phase_mma_ks<2>(d, ah, al, bh, bl);
-    else if (ks == 3) phase_mma_ks<3>(d, ah, al, bh, bl);
-    else phase_mma_ks<4>(d, ah, al, bh, bl);
+__device__ __forceinline__ void phase_mma(int ks, uint32_t d, uint64_t a, uint64_t b) {
+    if (ks <= 1) phase_mma_ks<1>(d, a, b);
+    else phase_mma_ks<2>(d, a, b);
 }
 
 // Contraction thread, one item.
@@ -197,8 +201,7 @@ template <int N>
 __device__ __forceinline__ void tcp_phase_item(TcShared &sh, uint32_t tmem, unsigned char *base, int gs, int n,
                                                int iter, int ks, int *status) {
     using PL = TcpPlan<N>;
-    const uint64_t ah = tc::sdesc_k128(smem_u32(base + PL::OFF_AP));
-    const uint64_t al = tc::sdesc_k128(smem_u32(base + PL::OFF_AP + kApBytes / 2));
+    const uint64_t ad = tc::sdesc_k128(smem_u32(base + PL::OFF_AP));
     if (!wait_or_abort(&sh.apfull, iter & 1, &sh.abort_flag, status)) return;
     for (int it = 0; it < n; ++it) {
         const int g = gs + it, b = g % kPhBufs, sp = g % kNP;
@@ -206,8 +209,7 @@ __device__ __forceinline__ void tcp_phase_item(TcShared &sh, uint32_t tmem, unsi
             return;
         if (!wait_or_abort(&sh.pfull[sp], (g / kNP) & 1, &sh.abort_flag, status)) return;
         tc::fence_after_sync();
-        const uint32_t ph = smem_u32(base + PL::OFF_PH + sp * PL::PS);
-        phase_mma(ks, tmem + phase_col(g), ah, al, tc::sdesc_k128(ph), tc::sdesc_k128(ph + kHalfImg));
+        phase_mma(ks, tmem + phase_col(g), ad, tc::sdesc_k128(smem_u32(base + PL::OFF_PH + sp * PL::PS)));
         tc::mma_commit(&sh.phfull[b]);
         tc::mma_commit(&sh.pfree[sp]);
     }
@@ -329,7 +331,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
             if (warp == kMmaWarp && lead) {
                 tcp_contraction_item<N>(sh, tmem, gbase, gs, ntl, status);
             } else if (warp == kPhaseWarp && lead) {
-                tcp_phase_item<N>(sh, tmem, gbase, gs, ntl, iter, (P.LP + 7) >> 3, status);
+                tcp_phase_item<N>(sh, tmem, gbase, gs, ntl, iter, (P.LP + 15) >> 4, status);
             } else if (warp == kLoadBWarp && lead) {
                 ring_load_item(sh.bfree, kNBB, gs, ntl, &sh.abort_flag, status, [&](int it, int sb) {
                     const int tile = tile0 + it;  // packed S x of the tile and its reference phases
@@ -345,10 +347,8 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
                     const int tile = tile0 + it;  // the tile's basis offsets, hi | lo
                     const unsigned char *dp =
                         P.dhph + (size_t)(tile >> 1) * kPhaseBlockBytes + (size_t)(tile & 1) * kHalfImg;
-                    unsigned char *dst = gbase + PL::OFF_PH + sp * PL::PS;
-                    mbar_arrive_expect_tx(&sh.pfull[sp], 2 * kHalfImg);
-                    bulk_g2s(dst, dp, kHalfImg, &sh.pfull[sp]);
-                    bulk_g2s(dst + kHalfImg, dp + kPhaseBlockBytes / 2, kHalfImg, &sh.pfull[sp]);
+                    mbar_arrive_expect_tx(&sh.pfull[sp], kHalfImg);
+                    bulk_g2s(gbase + PL::OFF_PH + sp * PL::PS, dp, kHalfImg, &sh.pfull[sp]);
                 });
             }
         } else {
@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
             if (warp == kMmaWarp && lead) {
                 tcp_contraction_item<N>(sh, tmem, gbase, gs, nst, status);
             } else if (warp == kPhaseWarp && lead) {
-                tcp_phase_item<N>(sh, tmem, gbase, gs, nst, iter, (P.LP + 7) >> 3, status);
+                tcp_phase_item<N>(sh, tmem, gbase, gs, nst, iter, (P.LP + 15) >> 4, status);
             } else if (warp == kLoadBWarp && lead) {
                 ring_load_item(sh.bfree, kNBB, gs, nst, &sh.abort_flag, status, [&](int it, int sb) {
                     const size_t ts = (size_t)t0 + (size_t)it * TS;  // packed y and both tiles' f0
@@ -459,10 +459,8 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
                     const size_t ts = (size_t)t0 + (size_t)it * TS;  // the stage's k rows, hi | lo
                     const unsigned char *kp =
                         P.kph + (ts / kRows) * kPhaseBlockBytes + ((ts / TS) & 1) * (size_t)kHalfImg;
-                    unsigned char *dst = gbase + PL::OFF_PH + sp * PL::PS;
-                    mbar_arrive_expect_tx(&sh.pfull[sp], 2 * kHalfImg);
-                    bulk_g2s(dst, kp, kHalfImg, &sh.pfull[sp]);
-                    bulk_g2s(dst + kHalfImg, kp + kPhaseBlockBytes / 2, kHalfImg, &sh.pfull[sp]);
+                    mbar_arrive_expect_tx(&sh.pfull[sp], kHalfImg);
+                    bulk_g2s(gbase + PL::OFF_PH + sp * PL::PS, kp, kHalfImg, &sh.pfull[sp]);
                 });
             }
         } else {
@@ -571,10 +569,10 @@ cudaError_t launch_adj_tcp(const ProbDesc *pd, int nprob, int max_pack_blocks, c
 
 cudaError_t op_prepare_phase_operands(const OpLayout &L, char *ws, cudaStream_t st) {
     const int T = 256;
-    const size_t nk = (size_t)L.ntp * 8;
+    const size_t nk = (size_t)L.ntp * 4;
     prep_kph_kernel<<<(unsigned)((nk + T - 1) / T), T, 0, st>>>((const float *)(ws + L.off_khi_t), L.ntp, L.LP,
                                                                (unsigned char *)(ws + L.off_kph));
-    const size_t nd = (size_t)cdiv(L.ntiles, 2) * kRows * 8;
+    const size_t nd = (size_t)cdiv(L.ntiles, 2) * kRows * 4;
     prep_dhph_kernel<<<(unsigned)((nd + T - 1) / T), T, 0, st>>>((const float *)(ws + L.off_dh), L.ntiles, L.LP,
                                                                 (unsigned char *)(ws + L.off_dhph));
     return cudaGetLastError();
