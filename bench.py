@@ -755,6 +755,84 @@ def run_op_only(args):
                       "y_norm": float(yo.abs().sum()), "x_norm": float(xo.abs().sum())}))
 
 
+def run_solve_only(args):
+    """One reconstruction of the bench slice in the chosen form (a bounded profiling target:
+    preparation, 30 power + 50 FISTA iterations, no autotuning, no graph replay)."""
+    import torch
+    from paper_2211_07532_gb300 import build as _b
+    _b.build()
+    import paper_2211_07532_gb300 as ax
+    from paper_2211_07532_gb300 import synth
+    precision = {"fp32": ax.FP32, "bf16": ax.BF16_TC, "fp16x2": ax.FP16X2_TC}[args.form]
+    dev = torch.device("cuda")
+    with torch.cuda.stream(torch.cuda.Stream(dev)):
+        p = synth.slice_200()
+        prob = ax.Problem.from_arrays(p, device=dev)
+        x = torch.as_tensor(p["x_gt"], device=dev)
+        ws = ax.workspace(prob)
+        ax.prepare(prob, ws)
+        y = ax.a_exp_forward(prob, x, ws)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        xr, _ = ax.cs_recon(prob, y, 1.0, p["iters"], precision=precision, wavelet="db4", levels=p["levels"],
+                            n_power=30, use_graph=False)
+        b.record()
+        b.synchronize()
+    print(json.dumps({"mode": "solve", "form": args.form, "ms": a.elapsed_time(b)}))
+
+
+def run_kernel_classes(args):
+    """One small invocation of every kernel class outside the operator (a bounded profiling
+    target): the orthogonal wavelet levels and FP64 norms of a 2-iteration FISTA on the 200^2
+    slice, the undecimated wavelet and lambda-rule kernels, coil compression 32 -> 20, one
+    unrolled-FISTA step and its VJP on the 170^2 / 16-coil slice (k-gradient kernel), and a
+    2-iteration batched solve of six ragged problems (persistent batch kernels)."""
+    import torch
+    from paper_2211_07532_gb300 import build as _b
+    _b.build()
+    import paper_2211_07532_gb300 as ax
+    from paper_2211_07532_gb300 import synth
+    from paper_2211_07532_gb300.autograd import unrolled_fista
+
+    dev = torch.device("cuda")
+    with torch.cuda.stream(torch.cuda.Stream(dev)):
+        p = synth.slice_200()
+        prob = ax.Problem.from_arrays(p, device=dev)
+        x = torch.as_tensor(p["x_gt"], device=dev)
+        ws = ax.workspace(prob)
+        ax.prepare(prob, ws)
+        y = ax.a_exp_forward(prob, x, ws)
+        ax.cs_recon(prob, y, 1.0, 2, wavelet="db4", levels=4, n_power=2, use_graph=False)
+        lam = torch.zeros(1, dtype=torch.float64, device=dev)
+        ax.cs_recon(prob, y, 0.0, 2, wavelet="db4", undecimated=True, lambda_rule=ax.LAMBDA_RAYLEIGH,
+                    lambda_out=lam, n_power=2, use_graph=False)
+        ax.coil_compress(prob, y, 20)
+        q = synth.diff_170()
+        pq = ax.Problem.from_arrays(q, device=dev)
+        wq = ax.workspace(pq)
+        ax.prepare(pq, wq)
+        yq = ax.a_exp_forward(pq, torch.as_tensor(q["x_gt"], device=dev), wq)
+        x0 = torch.zeros(170 * 170, dtype=torch.complex64, device=dev).requires_grad_(True)
+        k = torch.as_tensor(q["k"], device=dev).requires_grad_(True)
+        lam_t = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+        xK = unrolled_fista(q, yq, x0, lam_t, k, 1, 1e6, wavelet="db4", levels=4)
+        torch.mean(torch.abs(xK) ** 2).backward()
+        probs, ys = [], []
+        for res in range(3):
+            for vol in range(2):
+                r = synth.ragged_problem(res, vol, 0)
+                pr = ax.Problem.from_arrays(r, device=dev)
+                w = ax.workspace(pr)
+                ax.prepare(pr, w)
+                probs.append(pr)
+                ys.append(ax.a_exp_forward(pr, torch.as_tensor(r["x_gt"], device=dev), w))
+        ax.cs_recon_batched(probs, ys, [1.0] * len(probs), 2, precision=ax.BF16_TC, wavelet="db4", levels=4,
+                            n_power=2)
+        torch.cuda.synchronize()
+        assert ax.read_status(ws) == 0
+    print(json.dumps({"mode": "kernels", "ok": True}))
+
+
 def run_trends(args):
     """NRMSE tables of the simulation study (Sec. 2.2.2, Figs. 4 and 5): no timing."""
     import torch
@@ -782,8 +860,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the ragged-batch and gradient sub-measurements of the default run")
-    ap.add_argument("--mode", choices=["recon", "op"], default="recon",
-                    help="op: only prepare + `--reps` forward/adjoint applications (profiling target)")
+    ap.add_argument("--mode", choices=["recon", "op", "kernels", "solve"], default="recon",
+                    help="op: only prepare + `--reps` forward/adjoint applications (profiling target); "
+                         "kernels: one small run of every non-operator kernel class; solve: one reconstruction "
+                         "in --form (profiling targets)")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--workload", choices=["slice", "ragged", "diff"], default="slice",
                     help="slice: the 200x200 paper-scale slice (default); ragged: the 372-problem batch; "
@@ -797,6 +877,10 @@ def main():
         run_trends(args)
     elif args.mode == "op":
         run_op_only(args)
+    elif args.mode == "kernels":
+        run_kernel_classes(args)
+    elif args.mode == "solve":
+        run_solve_only(args)
     elif args.workload == "ragged" and args.impl == "ours":
         run_ragged(args)
     elif args.workload == "diff" and args.impl == "ours":

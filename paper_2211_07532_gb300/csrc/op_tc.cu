@@ -683,14 +683,13 @@ size_t adj_tc_smem() {
     return 1024 + HlPlan<2 * CB, LP, false>::BYTES;
 }
 
-// The max-reduction grids equal the packing grids: both cover ntiles * 64 * CB / 2 (forward)
-// and ntp * CB / 2 (adjoint) threads.
+// max_pack_blocks: the amax grid of the largest problem (see pack_grid for the packing grid).
 template <int CB, int LP>
 cudaError_t launch_fwd_tc(const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *x, int src,
                           const int *item_off, int total_items, int *counter, cudaStream_t st) {
     amax_reset_kernel<<<cdiv(nprob, 256), 256, 0, st>>>(pd, nprob, 0);
     amax_b_kernel<CB><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, x, src);
-    pack_b_fwd_kernel<CB, true><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, x, src);
+    pack_b_fwd_kernel<CB, true><<<dim3(pack_grid(max_pack_blocks, CB), nprob), 256, 0, st>>>(pd, x, src);
     auto kern = fwd_tc_kernel<CB, LP>;
     const size_t smem = fwd_tc_smem<CB, LP>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -705,7 +704,7 @@ cudaError_t launch_adj_tc(const ProbDesc *pd, int nprob, int max_pack_blocks, co
                           const int *item_off, int total_items, int *counter, cudaStream_t st) {
     amax_reset_kernel<<<cdiv(nprob, 256), 256, 0, st>>>(pd, nprob, 1);
     amax_y_kernel<CB><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, yt, src);
-    pack_y_adj_kernel<CB, true><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, yt, src);
+    pack_y_adj_kernel<CB, true><<<dim3(pack_grid(max_pack_blocks, CB), nprob), 256, 0, st>>>(pd, yt, src);
     auto kern = adj_tc_kernel<CB, LP>;
     const size_t smem = adj_tc_smem<CB, LP>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

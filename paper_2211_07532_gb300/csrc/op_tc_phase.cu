@@ -542,7 +542,7 @@ size_t tcp_smem() {
 template <int CB>
 cudaError_t launch_fwd_tcp(const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *x, int src,
                            const int *item_off, int total_items, int *counter, cudaStream_t st) {
-    pack_b_fwd_kernel<CB, false><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, x, src);
+    pack_b_fwd_kernel<CB, false><<<dim3(pack_grid(max_pack_blocks, CB), nprob), 256, 0, st>>>(pd, x, src);
     auto kern = fwd_tcp_kernel<CB>;
     const size_t smem = tcp_smem<CB>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -555,7 +555,7 @@ cudaError_t launch_fwd_tcp(const ProbDesc *pd, int nprob, int max_pack_blocks, c
 template <int CB>
 cudaError_t launch_adj_tcp(const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *yt, int src,
                            const int *item_off, int total_items, int *counter, cudaStream_t st) {
-    pack_y_adj_kernel<CB, false><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, yt, src);
+    pack_y_adj_kernel<CB, false><<<dim3(pack_grid(max_pack_blocks, CB), nprob), 256, 0, st>>>(pd, yt, src);
     auto kern = adj_tcp_kernel<CB>;
     const size_t smem = tcp_smem<CB>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

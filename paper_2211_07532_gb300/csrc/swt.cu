@@ -50,6 +50,10 @@ __device__ __forceinline__ float2 soft(float2 w, float tau) {
 template <int TAPS>
 __global__ void swt_analysis_kernel(const float2 *__restrict__ v, float2 *__restrict__ c, int ny, int nx,
                                     float tau_host, const double *lam, const double *lip) {
+    __shared__ float s_tau;  // formed once per block: an FP64 division per thread is slow here
+    if (threadIdx.x == 0) s_tau = lam ? (float)(*lam / *lip) : tau_host;
+    __syncthreads();
+    const float tau = s_tau;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nx * ny) return;
     const int y = i / nx, x = i % nx;
@@ -70,7 +74,6 @@ __global__ void swt_analysis_kernel(const float2 *__restrict__ v, float2 *__rest
         a[2] = tmad(gy, lo, a[2]);
         a[3] = tmad(gy, hi, a[3]);
     }
-    const float tau = lam ? (float)(*lam / *lip) : tau_host;
     const size_t plane = (size_t)nx * ny;
 #pragma unroll
     for (int s = 0; s < 4; ++s) {

@@ -186,25 +186,39 @@ __device__ __forceinline__ void store_b_chunk(unsigned char *dst, unsigned img_b
     if constexpr (HL) *reinterpret_cast<uint4 *>(dst + img_bytes) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
 }
 
+// Shared staging of one tile (64 voxels) or stage (64 samples) of C coil values, coil-major
+// with the 64 positions stored as (position & 3) * 16 + position / 4: the packing loop reads
+// positions 4 jj + u with jj across the lanes, which are then consecutive words (no bank
+// conflicts); rows of 65 entries keep the coil-fastest fill conflict-free too.
+constexpr int kStageRow = kCols + 1;
+__device__ __forceinline__ int stage_slot(int c, int pos) { return c * kStageRow + (pos & 3) * 16 + (pos >> 2); }
+
+// Blocks of a packing launch: one per tile (forward) or stage (adjoint) of the largest problem.
+// The amax launches of the FP16 hi+lo form cover ntiles * 64 * CB / 2 (forward) and
+// ntp * CB / 2 (adjoint) threads instead: fwd_pack_blocks / adj_pack_blocks count those, i.e.
+// CB / 8 blocks per tile or stage.
+inline int pack_grid(int amax_blocks, int CB) { return amax_blocks * 8 / CB; }
+
 // Forward: coil-weighted image b_c(v) = S_c(v) x(v) of every 8x8 tile, rows n < C carry
 // (Re b, -Im b), rows C + c carry (Im b, Re b) at K positions (2v, 2v+1).  The image is
 // `x` when given (single problem) or the descriptor's vec[src].  FP16 hi+lo: b is scaled by
 // the power of two fixed by the problem's amax[0].  One block per tile (grid-stride): the
 // tile's coil maps are read coalesced (coils fastest) into shared memory, then every thread
-// writes 16-byte chunks of the swizzled operand rows.
+// writes 16-byte chunks of the swizzled operand rows (a row's chunks across the lanes, so
+// that the global writes are coalesced).
 template <int CB, bool HL>
 __global__ void __launch_bounds__(256) pack_b_fwd_kernel(const ProbDesc *__restrict__ pd, const float2 *__restrict__ x,
                                                          int src) {
     constexpr int N = 2 * CB;
     constexpr int NPK = HL ? 2 : 1;
-    __shared__ float2 sb[kTileVox * CB];
+    __shared__ float2 sb[CB * kStageRow];
     const ProbDesc &P = pd[blockIdx.y];
     const float2 *img = x ? x : P.vec[src];
     const float sc = HL ? hl_scale(P.hdr->amax[0], false) : 1.f;
     for (int tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
         const int tx = (tile % P.ntx) * kTileSide, ty = (tile / P.ntx) * kTileSide;
         for (int k = threadIdx.x; k < kTileVox * CB; k += blockDim.x) {
-            const int v = k / CB;
+            const int v = k / CB, c = k % CB;
             const int ix = tx + v % kTileSide, iy = ty + v / kTileSide;
             float2 b = make_float2(0.f, 0.f);
             if (ix < P.nx && iy < P.ny) {
@@ -212,7 +226,7 @@ __global__ void __launch_bounds__(256) pack_b_fwd_kernel(const ProbDesc *__restr
                 const float2 xv = img[(size_t)iy * P.nx + ix];
                 b = make_float2((s.x * xv.x - s.y * xv.y) * sc, (s.x * xv.y + s.y * xv.x) * sc);
             }
-            sb[k] = b;
+            sb[stage_slot(c, v)] = b;
         }
         __syncthreads();
         for (int k = threadIdx.x; k < N * 16; k += blockDim.x) {  // (n, chunk of 4 voxels)
@@ -221,7 +235,7 @@ __global__ void __launch_bounds__(256) pack_b_fwd_kernel(const ProbDesc *__restr
             float a[4], b[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const float2 v = sb[(4 * jj + u) * CB + c];
+                const float2 v = sb[c * kStageRow + u * 16 + jj];  // voxel 4 jj + u
                 a[u] = n < CB ? v.x : v.y;
                 b[u] = n < CB ? -v.y : v.x;
             }
@@ -243,7 +257,7 @@ __global__ void __launch_bounds__(256) pack_y_adj_kernel(const ProbDesc *__restr
                                                          int src) {
     constexpr int N = 2 * CB;
     constexpr int NPK = HL ? 2 : 1;
-    __shared__ float2 sy[kCols * CB];
+    __shared__ float2 sy[CB * kStageRow];
     const ProbDesc &P = pd[blockIdx.y];
     const int nstages = P.ntp / kCols;
     const float2 *y = yt ? yt : (src >= 0 ? P.vec[src] : P.rt);
@@ -253,7 +267,7 @@ __global__ void __launch_bounds__(256) pack_y_adj_kernel(const ProbDesc *__restr
             float2 v = y[(size_t)st * kCols * CB + k];
             v.x *= sc;
             v.y *= sc;
-            sy[k] = v;
+            sy[stage_slot(k % CB, k / CB)] = v;
         }
         __syncthreads();
         for (int k = threadIdx.x; k < N * 16; k += blockDim.x) {  // (n, chunk of 4 samples)
@@ -262,7 +276,7 @@ __global__ void __launch_bounds__(256) pack_y_adj_kernel(const ProbDesc *__restr
             float a[4], b[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const float2 v = sy[(4 * jj + u) * CB + c];
+                const float2 v = sy[c * kStageRow + u * 16 + jj];  // sample 4 jj + u
                 a[u] = n < CB ? v.x : v.y;
                 b[u] = n < CB ? -v.y : v.x;
             }

@@ -26,8 +26,13 @@ __device__ __forceinline__ float2 shrink(float2 w, float tau) {
     return make_float2(w.x * s, w.y * s);
 }
 
-__device__ __forceinline__ float thresh_tau(float lam, const double *lipschitz) {
-    return lipschitz ? (float)((double)lam / *lipschitz) : lam;
+// tau = lam / L_f, formed once per block (an FP64 division per thread costs more than the
+// level's filtering on this part's FP64 pipe); every thread of the block must call it.
+__device__ __forceinline__ float block_tau(float lam, const double *lipschitz) {
+    __shared__ float s_tau;
+    if (threadIdx.x == 0) s_tau = lipschitz ? (float)((double)lam / *lipschitz) : lam;
+    __syncthreads();
+    return s_tau;
 }
 
 constexpr int OB = 16;   // forward: output coefficients per subband per block side
@@ -100,7 +105,7 @@ __global__ void __launch_bounds__(256)
     dwt_fwd_level(const float2 *__restrict__ in, int in_stride, int valid_y, int valid_x, int n_y, int n_x,
                   float2 *__restrict__ ll, int ll_stride, float2 *__restrict__ pyr, int pyr_stride, float lam,
                   const double *lipschitz, int threshold) {
-    const float tau = threshold ? thresh_tau(lam, lipschitz) : 0.f;
+    const float tau = threshold ? block_tau(lam, lipschitz) : 0.f;
     dwt_fwd_level_body<TAPS>(in, in_stride, valid_y, valid_x, n_y, n_x, ll, ll_stride, pyr, pyr_stride, tau,
                              threshold, blockIdx.x, blockIdx.y);
 }
@@ -209,7 +214,7 @@ __global__ void __launch_bounds__(256)
     float2 *pyr = (float2 *)(P.wws + P.off_pyr);
     float2 *llp = j == P.levels ? pyr : (float2 *)(P.wws + P.off_approx[j]);
     const int ll_stride = j == P.levels ? P.npx : n_x / 2;
-    const float tau = threshold ? thresh_tau(P.lam, &P.hdr->lipschitz) : 0.f;
+    const float tau = threshold ? block_tau(P.lam, &P.hdr->lipschitz) : 0.f;
     dwt_fwd_level_body<TAPS>(in, in_stride, vy, vx, n_y, n_x, llp, ll_stride, pyr, P.npx, tau, threshold, blockIdx.x,
                              blockIdx.y);
 }
