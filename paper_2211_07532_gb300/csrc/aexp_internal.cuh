@@ -217,6 +217,17 @@ cudaError_t wave_forward(const WaveLayout &W, const float2 *img, char *wws, floa
 cudaError_t wave_inverse(const WaveLayout &W, char *wws, float2 *out, int momentum, double beta,
                          const float2 *x_old, float2 *z_out, cudaStream_t st);
 
+// Prox step crop(W^H soft(W pad img)) into out (natural [ny][nx]), with the momentum step when
+// asked: level 1 each way plus one launch for levels 2..J when the level-1 approximation fits a
+// CTA's shared memory (wave_mid_fits), else one launch per level.  Leaves the level-1 details in
+// the pyramid; the coarser levels stay in shared memory.
+bool wave_mid_fits(int npx, int npy, int levels);
+cudaError_t wave_prox(const WaveLayout &W, const float2 *img, char *wws, float lam, const double *lipschitz,
+                      float2 *out, int momentum, double beta, const float2 *x_old, float2 *z_out, cudaStream_t st);
+cudaError_t batch_wave_prox(int wavelet, const ProbDesc *pd, int nprob, int levels, int max_npx, int max_npy,
+                            int img_role, int out_role, int momentum, double beta, int xold_role, int z_role,
+                            cudaStream_t st);
+
 // Batched wavelet levels over a descriptor table (uniform wavelet and levels; grid sized
 // for the largest padded image max_npy x max_npx).  Roles index ProbDesc::vec.
 cudaError_t batch_wave_forward(int wavelet, const ProbDesc *pd, int nprob, int levels, int max_npx, int max_npy,

@@ -350,8 +350,7 @@ cudaError_t batch_recon_issue(const aexp_problem *probs, const BatchLayout &B, c
         batch_adj_reduce_kernel<<<g_nr, T, 0, st>>>(pd, Z, V);
         const double t_next = (1.0 + sqrt(1.0 + 4.0 * t * t)) / 2.0;
         const double beta = (t - 1.0) / t_next;
-        CK(batch_wave_forward(o->wavelet, pd, n, o->levels, B.max_npx, B.max_npy, V, 1, st));
-        CK(batch_wave_inverse(o->wavelet, pd, n, o->levels, B.max_npx, B.max_npy, next, 1, beta, prev, Z, st));
+        CK(batch_wave_prox(o->wavelet, pd, n, o->levels, B.max_npx, B.max_npy, V, next, 1, beta, prev, Z, st));
         t = t_next;
         std::swap(prev, next);
     }

@@ -643,8 +643,7 @@ int aexp_wavelet_prox(int nx, int ny, int wavelet, int levels, float tau, const 
     WaveLayout W;
     wave_layout(nx, ny, wavelet, levels, &W);
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = wave_forward(W, (const float2 *)in, (char *)ws, tau, nullptr, 1, st);
-    if (e == cudaSuccess) e = wave_inverse(W, (char *)ws, (float2 *)out, 0, 0.0, nullptr, nullptr, st);
+    cudaError_t e = wave_prox(W, (const float2 *)in, (char *)ws, tau, nullptr, (float2 *)out, 0, 0.0, nullptr, nullptr, st);
     return e == cudaSuccess ? AEXP_OK : cuda_fail(e);
 }
 

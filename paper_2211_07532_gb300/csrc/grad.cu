@@ -295,8 +295,7 @@ cudaError_t unroll_step(const RecLayout &R, const float2 *y, float lam, double l
     CK(op_reduce_forward_residual(L, ws, ymeas, rt, st));
     CK(op_apply_adjoint(L, rt, ws, st));
     CK(op_adjoint_reduce_step(L, ws, z, v, st));
-    CK(wave_forward(R.wv, v, ws + R.off_wave, lam, &hdr->lipschitz, 1, st));
-    CK(wave_inverse(R.wv, ws + R.off_wave, x_out, 1, beta, x_prev, z_out, st));
+    CK(wave_prox(R.wv, v, ws + R.off_wave, lam, &hdr->lipschitz, x_out, 1, beta, x_prev, z_out, st));
     return cudaSuccess;
 }
 

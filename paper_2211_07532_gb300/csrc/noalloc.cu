@@ -56,11 +56,11 @@ extern "C" AEXP_API int aexp_wavelet_prox_static(int nx, int ny, int wavelet, in
         aexp_set_last_cuda_error((int)e);
         return AEXP_ERR_CUDA;
     }
-    // Every scratch byte read below is written earlier in the same call (all subbands and
-    // approximations of every level), so nothing needs clearing between calls.
+    // Every scratch byte read below is written earlier in the same call (the level-1 subbands and
+    // approximation; the coarser levels live in the CTA's shared memory, or, for images too large
+    // for that, in the array as well, each written before it is read), so nothing needs clearing.
     cudaStream_t st = (cudaStream_t)stream;
-    e = wave_forward(W, (const float2 *)in, (char *)scratch, tau, nullptr, 1, st);
-    if (e == cudaSuccess) e = wave_inverse(W, (char *)scratch, (float2 *)out, 0, 0.0, nullptr, nullptr, st);
+    e = wave_prox(W, (const float2 *)in, (char *)scratch, tau, nullptr, (float2 *)out, 0, 0.0, nullptr, nullptr, st);
     if (e != cudaSuccess) {
         aexp_set_last_cuda_error((int)e);
         return AEXP_ERR_CUDA;

@@ -221,8 +221,7 @@ cudaError_t recon_issue(const aexp_problem *p, const RecLayout &R, const aexp_re
             CK(swt_analysis(o->wavelet, v, swt_c, L.nx, L.ny, -1.f, swt_lambda_slot(swt_aux), &hdr->lipschitz, st));
             CK(swt_synthesis(o->wavelet, swt_c, x_new, L.nx, L.ny, 1, beta, x_prev, z, st));
         } else {
-            CK(wave_forward(R.wv, v, wws, lam, &hdr->lipschitz, 1, st));
-            CK(wave_inverse(R.wv, wws, x_new, 1, beta, x_prev, z, st));
+            CK(wave_prox(R.wv, v, wws, lam, &hdr->lipschitz, x_new, 1, beta, x_prev, z, st));
         }
         t = t_next;
         float2 *tmp = x_prev;

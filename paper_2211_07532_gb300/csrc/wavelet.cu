@@ -7,9 +7,14 @@
 // top-right, (hi-y, lo-x) bottom-left, HH bottom-right.  The synthesis is the transpose.
 // The image is zero-padded to npy x npx (multiples of 2^J) and cropped after synthesis.
 //
-// Each level is one launch; a block loads the input patch it needs (with periodic halo)
-// into shared memory, filters rows then columns there, and writes four OB x OB output
-// blocks, thresholding detail coefficients on the way out.
+// The first level is one launch each way; a block loads the input patch it needs (with periodic
+// halo) into shared memory, filters rows then columns there, and writes four OB x OB output
+// blocks, thresholding detail coefficients on the way out.  The prox step (analysis, threshold,
+// synthesis) runs levels 2..J in one more launch: one CTA per image holds the level-1
+// approximation (N_p/2 x N_p/2) and a scratch copy in shared memory and runs every coarser level
+// of analysis, threshold and synthesis there, so a prox step is three launches instead of 2J
+// (each level launch is latency bound at these sizes, ~8-11 us whatever its grid).  Images whose
+// level-1 approximation does not fit (over 12800 coefficients) take one launch per level.
 #include "aexp_internal.cuh"
 #include "wavelet_taps.cuh"
 
@@ -30,7 +35,7 @@ __device__ __forceinline__ float2 shrink(float2 w, float tau) {
 // level's filtering on this part's FP64 pipe); every thread of the block must call it.
 __device__ __forceinline__ float block_tau(float lam, const double *lipschitz) {
     __shared__ float s_tau;
-    if (threadIdx.x == 0) s_tau = lipschitz ? (float)((double)lam / *lipschitz) : lam;
+    if (threadIdx.x == 0 && threadIdx.y == 0) s_tau = lipschitz ? (float)((double)lam / *lipschitz) : lam;
     __syncthreads();
     return s_tau;
 }
@@ -249,6 +254,138 @@ __global__ void __launch_bounds__(256)
                              blockIdx.y);
 }
 
+// ---- levels 2..J of the prox step in one CTA (shared memory) ----
+constexpr int kMidTx = 32, kMidTy = 32;  // 1024 threads: x across a row, y across rows
+constexpr int kMidThreads = kMidTx * kMidTy;
+constexpr int kMidMaxCoef = 12800;  // level-1 approximation coefficients held: 2 x 100 KB of shared memory
+
+// acc + t v on both components of a complex value, as packed FP32x2 FMAs (tap lo part first)
+__device__ __forceinline__ float2 tmad2(Tap t, float2 v, float2 acc) {
+    return __ffma2_rn(make_float2(t.hi, t.hi), v, __ffma2_rn(make_float2(t.lo, t.lo), v, acc));
+}
+
+// v reduced into [0, n) for 0 <= v < 2n (one subtraction) when n >= TAPS; regions narrower
+// than the filter (n < TAPS) take the general periodic reduction
+template <int TAPS>
+__device__ __forceinline__ int wrap(int v, int n) {
+    return n >= TAPS ? (v >= n ? v - n : v) : pmod(v, n);
+}
+
+// A: the level-1 approximation (m1y x m1x, row stride m1x) in shared memory, B: scratch of the
+// same size.  Analysis of levels 2..levels in place in A (Mallat layout inside the region),
+// details shrunk by tau, then synthesis back to the level-1 approximation in A.  The same
+// filters, periodic extension and order (rows before columns; synthesis the transpose) as the
+// per-level kernels.
+template <int TAPS>
+__device__ void mid_levels(float2 *A, float2 *B, int m1y, int m1x, int levels, float tau) {
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int j = 2; j <= levels; ++j) {
+        const int my = m1y >> (j - 2), mx = m1x >> (j - 2);
+        const int hy = my / 2, hx = mx / 2;
+        // rows (x): B[i][q] = sum_t h[t] A[i][(2q + t) mod mx], B[i][hx + q] the same with g
+        for (int i = ty; i < my; i += kMidTy) {
+            const float2 *row = A + i * m1x;
+            for (int q = tx; q < hx; q += kMidTx) {
+                float2 lo = make_float2(0.f, 0.f), hi = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int t = 0; t < TAPS; ++t) {
+                    const float2 v = row[wrap<TAPS>(2 * q + t, mx)];
+                    lo = tmad2(tap_h<TAPS>(t), v, lo);
+                    hi = tmad2(tap_g<TAPS>(t), v, hi);
+                }
+                B[i * m1x + q] = lo;
+                B[i * m1x + hx + q] = hi;
+            }
+        }
+        __syncthreads();
+        // columns (y): A[o][c] = sum_t h[t] B[(2o + t) mod my][c], A[hy + o][c] the same with g;
+        // every quadrant but the top-left (the next level's approximation) is a detail band
+        for (int o = ty; o < hy; o += kMidTy) {
+            for (int c = tx; c < mx; c += kMidTx) {
+                float2 lo = make_float2(0.f, 0.f), hi = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int t = 0; t < TAPS; ++t) {
+                    const float2 v = B[wrap<TAPS>(2 * o + t, my) * m1x + c];
+                    lo = tmad2(tap_h<TAPS>(t), v, lo);
+                    hi = tmad2(tap_g<TAPS>(t), v, hi);
+                }
+                A[o * m1x + c] = c < hx ? lo : shrink(lo, tau);
+                A[(hy + o) * m1x + c] = shrink(hi, tau);
+            }
+        }
+        __syncthreads();
+    }
+    for (int j = levels; j >= 2; --j) {
+        const int my = m1y >> (j - 2), mx = m1x >> (j - 2);
+        const int hy = my / 2, hx = mx / 2;
+        // columns (y): B[q][c] = sum over t with q - t even of h[t] A[k][c] + g[t] A[hy + k][c],
+        // k = (q - t) / 2 mod hy; output rows q = 2a and 2a + 1 take the even and odd taps
+        for (int a = ty; a < hy; a += kMidTy) {
+            for (int c = tx; c < mx; c += kMidTx) {
+                float2 ev = make_float2(0.f, 0.f), od = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int t = 0; t < TAPS; t += 2) {
+                    const int k = wrap<TAPS>(a - t / 2 + hy, hy);  // (2a - t) / 2 mod hy, also (2a + 1 - (t + 1)) / 2
+                    const float2 lo = A[k * m1x + c], hi = A[(hy + k) * m1x + c];
+                    ev = tmad2(tap_h<TAPS>(t), lo, tmad2(tap_g<TAPS>(t), hi, ev));
+                    od = tmad2(tap_h<TAPS>(t + 1), lo, tmad2(tap_g<TAPS>(t + 1), hi, od));
+                }
+                B[2 * a * m1x + c] = ev;
+                B[(2 * a + 1) * m1x + c] = od;
+            }
+        }
+        __syncthreads();
+        // rows (x): A[r][p] = sum over t with p - t even of h[t] B[r][k] + g[t] B[r][hx + k]
+        for (int r = ty; r < my; r += kMidTy) {
+            const float2 *row = B + r * m1x;
+            for (int a = tx; a < hx; a += kMidTx) {
+                float2 ev = make_float2(0.f, 0.f), od = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int t = 0; t < TAPS; t += 2) {
+                    const int k = wrap<TAPS>(a - t / 2 + hx, hx);
+                    const float2 lo = row[k], hi = row[hx + k];
+                    ev = tmad2(tap_h<TAPS>(t), lo, tmad2(tap_g<TAPS>(t), hi, ev));
+                    od = tmad2(tap_h<TAPS>(t + 1), lo, tmad2(tap_g<TAPS>(t + 1), hi, od));
+                }
+                A[r * m1x + 2 * a] = ev;
+                A[r * m1x + 2 * a + 1] = od;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// One CTA: approx (the level-1 approximation, m1y x m1x in global memory) -> levels 2..levels
+// -> approx (overwritten with the synthesised level-1 approximation).
+template <int TAPS>
+__global__ void __launch_bounds__(kMidThreads)
+    dwt_mid_kernel(float2 *__restrict__ approx, int m1y, int m1x, int levels, float lam, const double *lipschitz) {
+    extern __shared__ float2 smid[];
+    const float tau = block_tau(lam, lipschitz);
+    float2 *A = smid, *B = smid + m1y * m1x;
+    const int tid = threadIdx.y * kMidTx + threadIdx.x;
+    for (int i = tid; i < m1y * m1x; i += kMidThreads) A[i] = approx[i];
+    __syncthreads();
+    mid_levels<TAPS>(A, B, m1y, m1x, levels, tau);
+    for (int i = tid; i < m1y * m1x; i += kMidThreads) approx[i] = A[i];
+}
+
+// The same per problem of a batch (grid.x = problem).
+template <int TAPS>
+__global__ void __launch_bounds__(kMidThreads) batch_dwt_mid_kernel(const ProbDesc *__restrict__ pd) {
+    extern __shared__ float2 smid[];
+    const ProbDesc &P = pd[blockIdx.x];
+    const float tau = block_tau(P.lam, &P.hdr->lipschitz);
+    const int m1y = P.npy / 2, m1x = P.npx / 2;
+    float2 *approx = (float2 *)(P.wws + P.off_approx[1]);
+    float2 *A = smid, *B = smid + m1y * m1x;
+    const int tid = threadIdx.y * kMidTx + threadIdx.x;
+    for (int i = tid; i < m1y * m1x; i += kMidThreads) A[i] = approx[i];
+    __syncthreads();
+    mid_levels<TAPS>(A, B, m1y, m1x, P.levels, tau);
+    for (int i = tid; i < m1y * m1x; i += kMidThreads) approx[i] = A[i];
+}
+
 template <int TAPS>
 cudaError_t run_forward(const WaveLayout &W, const float2 *img, char *wws, float lam, const double *lipschitz,
                         int threshold, cudaStream_t st) {
@@ -343,7 +480,84 @@ cudaError_t run_batch_inverse(const ProbDesc *pd, int nprob, int levels, int max
     return cudaGetLastError();
 }
 
+// Prox step: level 1 analysis (threshold), levels 2..J in one CTA, level 1 synthesis (momentum).
+template <int TAPS>
+cudaError_t run_prox(const WaveLayout &W, const float2 *img, char *wws, float lam, const double *lipschitz,
+                     float2 *out, int momentum, double beta, const float2 *x_old, float2 *z_out, cudaStream_t st) {
+    WaveLayout W1 = W;
+    W1.levels = 1;  // level 1 of the full pyramid: LL into the level-1 approximation, details into pyr
+    float2 *pyr = (float2 *)(wws + W.off_pyr);
+    float2 *ll1 = (float2 *)(wws + W.off_approx[1]);
+    const int m1y = W.npy / 2, m1x = W.npx / 2;
+    {
+        dim3 grid(cdiv(m1x, OB), cdiv(m1y, OB));
+        dwt_fwd_level<TAPS><<<grid, 256, 0, st>>>(img, W.nx, W.ny, W.nx, W.npy, W.npx, ll1, m1x, pyr, W.npx, lam,
+                                                 lipschitz, 1);
+    }
+    const size_t smem = 2 * sizeof(float2) * (size_t)m1y * m1x;
+    auto kern = dwt_mid_kernel<TAPS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<1, dim3(kMidTx, kMidTy), smem, st>>>(ll1, m1y, m1x, W.levels, lam, lipschitz);
+    {
+        dim3 grid(cdiv(W.npx, OBI), cdiv(W.npy, OBI));
+        dwt_inv_level<TAPS><<<grid, 256, 0, st>>>(ll1, m1x, pyr, W.npx, W.npy, W.npx, out, W.nx, W.ny, W.nx, momentum,
+                                                 (float)beta, x_old, z_out);
+    }
+    return cudaGetLastError();
+}
+
+template <int TAPS>
+cudaError_t run_batch_prox(const ProbDesc *pd, int nprob, int levels, int max_npx, int max_npy, int img_role,
+                           int out_role, int momentum, double beta, int xold_role, int z_role, cudaStream_t st) {
+    {
+        dim3 grid(cdiv(max_npx / 2, OB), cdiv(max_npy / 2, OB), nprob);
+        batch_dwt_fwd_level<TAPS><<<grid, 256, 0, st>>>(pd, 1, img_role, 1);
+    }
+    const size_t smem = 2 * sizeof(float2) * (size_t)(max_npy / 2) * (max_npx / 2);
+    auto kern = batch_dwt_mid_kernel<TAPS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<nprob, dim3(kMidTx, kMidTy), smem, st>>>(pd);
+    {
+        dim3 grid(cdiv(max_npx, OBI), cdiv(max_npy, OBI), nprob);
+        batch_dwt_inv_level<TAPS><<<grid, 256, 0, st>>>(pd, 1, out_role, momentum, (float)beta, xold_role, z_role);
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+bool wave_mid_fits(int npx, int npy, int levels) {
+    return levels >= 2 && (npx / 2) * (npy / 2) <= kMidMaxCoef;
+}
+
+cudaError_t wave_prox(const WaveLayout &W, const float2 *img, char *wws, float lam, const double *lipschitz,
+                      float2 *out, int momentum, double beta, const float2 *x_old, float2 *z_out, cudaStream_t st) {
+    if (!wave_mid_fits(W.npx, W.npy, W.levels)) {
+        cudaError_t e = wave_forward(W, img, wws, lam, lipschitz, 1, st);
+        return e == cudaSuccess ? wave_inverse(W, wws, out, momentum, beta, x_old, z_out, st) : e;
+    }
+    return W.wavelet == AEXP_WAVELET_HAAR
+               ? run_prox<2>(W, img, wws, lam, lipschitz, out, momentum, beta, x_old, z_out, st)
+               : run_prox<8>(W, img, wws, lam, lipschitz, out, momentum, beta, x_old, z_out, st);
+}
+
+cudaError_t batch_wave_prox(int wavelet, const ProbDesc *pd, int nprob, int levels, int max_npx, int max_npy,
+                            int img_role, int out_role, int momentum, double beta, int xold_role, int z_role,
+                            cudaStream_t st) {
+    if (!wave_mid_fits(max_npx, max_npy, levels)) {
+        cudaError_t e = batch_wave_forward(wavelet, pd, nprob, levels, max_npx, max_npy, img_role, 1, st);
+        return e == cudaSuccess ? batch_wave_inverse(wavelet, pd, nprob, levels, max_npx, max_npy, out_role, momentum,
+                                                     beta, xold_role, z_role, st)
+                                : e;
+    }
+    return wavelet == AEXP_WAVELET_HAAR
+               ? run_batch_prox<2>(pd, nprob, levels, max_npx, max_npy, img_role, out_role, momentum, beta, xold_role,
+                                   z_role, st)
+               : run_batch_prox<8>(pd, nprob, levels, max_npx, max_npy, img_role, out_role, momentum, beta, xold_role,
+                                   z_role, st);
+}
 
 cudaError_t batch_wave_forward(int wavelet, const ProbDesc *pd, int nprob, int levels, int max_npx, int max_npy,
                                int img_role, int threshold, cudaStream_t st) {
