@@ -280,7 +280,7 @@ def _run_ours(args, rank, world, local, dev):
         # autotuned work-item granularity (untimed); the tuner's workspace then serves the solve
         o = ax.recon_opts(precision=prec, wavelet="db4", levels=levels, n_power=n_power)
         w = torch.empty(ax.lib_autotune_workspace_size(prob, o), dtype=torch.uint8, device=dev)
-        o.items_per_sm, _ = ax.autotune(prob, o, ws=w)
+        o.items_per_sm, o.tile_variant, _ = ax.autotune(prob, o, ws=w)
         return o, w
 
     opts, ws = recon_ws(precision)
@@ -368,7 +368,8 @@ def _run_ours(args, rank, world, local, dev):
         o_step = max_over_ranks(float(np.mean(o_ms)), world)
         c = {"s_per_slice": o_step / 1e3, "value": weak_scaling_value(world, vsc_per_step, 1, o_step), "unit": UNIT,
              "nrmse_vs_phantom": o_nrmse, "device_status": ax.read_status(o_ws), "kernels_ms": o_kern,
-             "speedup_vs_primary": ms_per_step / o_step, "items_per_sm": o_opts.items_per_sm}
+             "speedup_vs_primary": ms_per_step / o_step, "items_per_sm": o_opts.items_per_sm,
+             "tile_variant": o_opts.tile_variant}
         if other != "fp32":
             o_dom = max(o_kern, key=o_kern.get)
             passes = 3 if other == "fp16x2" else 1    # hi.hi + hi.lo + lo.hi MMA passes
@@ -418,7 +419,8 @@ def _run_ours(args, rank, world, local, dev):
         lam_dev = torch.zeros(1, dtype=torch.float64, device=dev)
         po = ax.recon_opts(precision=forms[f], wavelet="db4", n_power=n_power, undecimated=True,
                            lambda_rule=ax.LAMBDA_RAYLEIGH, lambda_out=lam_dev,
-                           items_per_sm=(opts.items_per_sm if f == args.form else comparison[f]["items_per_sm"]))
+                           items_per_sm=(opts.items_per_sm if f == args.form else comparison[f]["items_per_sm"]),
+                           tile_variant=(opts.tile_variant if f == args.form else comparison[f]["tile_variant"]))
         pws = ax.recon_workspace(prob, po)
         for _ in range(max(1, args.warmup)):
             ax.cs_recon(prob, y, 0.0, 100, opts=po, ws=pws, x_out=x_out, lipschitz_out=L_out)
@@ -517,7 +519,7 @@ def _run_ours(args, rank, world, local, dev):
             "config": {"workload": WORKLOAD, "form": args.form, "nx": p["nx"], "nt": nt, "nc": nc,
                        "terms": nterms, "fista_iters": iters, "power_iters": n_power,
                        "applications_per_step": applications, "l2": "flushed between timed steps (512 MB write)",
-                       "items_per_sm": opts.items_per_sm,
+                       "items_per_sm": opts.items_per_sm, "tile_variant": opts.tile_variant,
                        "parallelism": f"replicas x{world} (independent slices)"},
             "s_per_slice": ms_per_step / 1e3,
             "nrmse_vs_phantom": nrmse,
@@ -601,9 +603,10 @@ def measure_ragged(ax, torch, dev, volumes: int, steps: int, warmup: int, form: 
     # one workspace serves the autotuner (every candidate layout) and the solve
     ws = torch.empty(ax.lib_autotune_workspace_size(probs, opts), dtype=torch.uint8, device=dev)
     t0 = time.time()
-    best_ips, best_ms = ax.autotune(probs, opts, ws=ws)
+    best_ips, best_var, best_ms = ax.autotune(probs, opts, ws=ws)
     tune_s = time.time() - t0
     opts.items_per_sm = best_ips
+    opts.tile_variant = best_var
     xs = [torch.empty(pr.nr, dtype=torch.complex64, device=dev) for pr in probs]
     L = torch.empty(len(probs), dtype=torch.float64, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -639,7 +642,8 @@ def measure_ragged(ax, torch, dev, volumes: int, steps: int, warmup: int, form: 
                                f"{len(gts)} problems, 32 coils, 3rd-order SH + B0, db4 J=4, 50 FISTA + 30 power",
                    "problems": len(gts), "vsc_per_application": vsc, "applications_per_step": applications,
                    "workspace_gb": ws_gb, "generation_s": gen_s,
-                   "autotune": {"items_per_sm": best_ips, "ms_per_AhA": best_ms, "seconds": tune_s}},
+                   "autotune": {"items_per_sm": best_ips, "tile_variant": best_var, "ms_per_AhA": best_ms,
+                                "seconds": tune_s}},
         "clocks": clk.summary()}
 
 

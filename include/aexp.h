@@ -158,6 +158,13 @@ typedef struct aexp_recon_opts {
                                launch holds about 152 x items_per_sm blocks or persistent
                                work items (shared among the problems of a batch); 0 = the
                                default (FP32 16, tensor cores 8); aexp_autotune picks one */
+    int tile_variant;       /* kernel tiling of the operator launches: 0 = the default; 1 = the
+                               alternative -- FP32 form at more than 20 coils: two samples per
+                               forward thread and two voxels per adjoint thread at 2 blocks per
+                               SM (default: one each at 4 blocks per SM); BF16 form: a 6-deep
+                               contraction-operand ring and 4 phase-operand stages (default 4
+                               and 3).  The FP16 hi+lo form has one tiling.  aexp_autotune picks
+                               it; a workspace must be used with the tiling it was prepared for */
 } aexp_recon_opts;
 
 /* Fill opts with defaults: FP32, Haar, 3 levels, 30 power iterations, estimate L_f,
@@ -231,22 +238,29 @@ AEXP_API int aexp_power_lipschitz(const aexp_problem *prob, int precision, const
                          double *lipschitz_out, void *ws, size_t ws_bytes, void *stream);
 
 /* ---------------------------------------------------------------------------
- * Autotuning of the work-item granularity (no counterpart in the paper; it serves the
- * ragged many-problem workload of Sec. 2.2.1's protocol grid).  For each candidate
- * items_per_sm in {2, 4, 8, 16, 32} the call lays out the workspace, prepares the
- * problem(s) and times (CUDA events, best of 3 after one warm-up) one A^H A
- * application: of `probs[0]` alone when nprob == 1 (the cs_recon layout, any precision),
- * of the whole batch when nprob > 1 (the cs_recon_batched layout, tensor-core
- * precisions only).  The fastest candidate goes to *best_items_per_sm, its time in ms
- * to *best_ms (optional).  ws: device memory of aexp_autotune_workspace_size bytes, whose
- * contents are overwritten (a preparation of ws for the operator calls is void afterwards).
- * The call synchronizes `stream` and returns AEXP_ERR_INVALID_ARG while it is being captured;
- * a device-side error status met while timing is returned as it is.
+ * Autotuning of the operator's launch shape (no counterpart in the paper; it serves the
+ * ragged many-problem workload of Sec. 2.2.1's protocol grid).  Candidates: the work-item
+ * granularity items_per_sm in {2, 4, 8, 16, 32} times the kernel tilings of the precision
+ * (tile_variant 0 and 1 where the form has two, see aexp_recon_opts).  For each candidate
+ * the call lays out the workspace, prepares the problem(s) and times one A^H A application
+ * with CUDA events, after one warm-up, 5 times (3 for a batch): of `probs[0]` alone when
+ * nprob == 1 (the cs_recon layout, any precision), of the whole batch when nprob > 1 (the
+ * cs_recon_batched layout, tensor-core precisions only).  The candidate with the smallest
+ * median wins, except that the default (items_per_sm 0's value, tile_variant 0) is kept when
+ * it is within 1 % of it, so that near-ties do not flip between runs.  The choice goes to
+ * *best_items_per_sm and *best_tile_variant, its median time in ms to *best_ms (optional),
+ * and is remembered per device, precision and problem shape(s) for the life of the process:
+ * a later call for the same shapes returns it without timing.  ws: device memory of
+ * aexp_autotune_workspace_size bytes, whose contents are overwritten (a preparation of ws
+ * for the operator calls is void afterwards).  The call synchronizes `stream` and returns
+ * AEXP_ERR_INVALID_ARG while it is being captured; a device-side error status met while
+ * timing is returned as it is.
  * --------------------------------------------------------------------------- */
 AEXP_API int aexp_autotune_workspace_size(const aexp_problem *probs, int nprob, const aexp_recon_opts *opts,
                                           size_t *bytes);
 AEXP_API int aexp_autotune(const aexp_problem *probs, int nprob, const aexp_recon_opts *opts, void *ws,
-                           size_t ws_bytes, void *stream, int *best_items_per_sm, float *best_ms);
+                           size_t ws_bytes, void *stream, int *best_items_per_sm, int *best_tile_variant,
+                           float *best_ms);
 
 /* ---------------------------------------------------------------------------
  * Ragged batches: many independent slice problems (several resolutions, diffusion volumes

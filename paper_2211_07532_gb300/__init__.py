@@ -46,7 +46,8 @@ class CReconOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("wavelet", ctypes.c_int), ("levels", ctypes.c_int),
                 ("n_power", ctypes.c_int), ("lipschitz", ctypes.c_double), ("x0", ctypes.c_void_p),
                 ("power_init", ctypes.c_void_p), ("use_graph", ctypes.c_int), ("undecimated", ctypes.c_int),
-                ("lambda_rule", ctypes.c_int), ("lambda_out", ctypes.c_void_p), ("items_per_sm", ctypes.c_int)]
+                ("lambda_rule", ctypes.c_int), ("lambda_out", ctypes.c_void_p), ("items_per_sm", ctypes.c_int),
+                ("tile_variant", ctypes.c_int)]
 
 
 _lib = None
@@ -91,7 +92,8 @@ SIGNATURES = [
     ("aexp_cgls_workspace_size", _I, [_PROB, _OPTS, ctypes.POINTER(_SZ)]),
     ("cgls_recon", _I, [_PROB, _P, _I, _OPTS, _P, _P, _SZ, _P]),
     ("aexp_autotune_workspace_size", _I, [_PROB, _I, _OPTS, ctypes.POINTER(_SZ)]),
-    ("aexp_autotune", _I, [_PROB, _I, _OPTS, _P, _SZ, _P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]),
+    ("aexp_autotune", _I, [_PROB, _I, _OPTS, _P, _SZ, _P, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                           ctypes.POINTER(ctypes.c_float)]),
     ("aexp_read_status", _I, [_P, _P, ctypes.POINTER(_I)]),
     ("aexp_status_string", ctypes.c_char_p, [_I]),
     ("aexp_last_cuda_error", _I, []),
@@ -233,7 +235,7 @@ LAMBDA_GIVEN, LAMBDA_RAYLEIGH = 0, 1
 
 def recon_opts(precision=FP32, wavelet="haar", levels=3, n_power=30, lipschitz=0.0, x0=None, power_init=None,
                use_graph=True, items_per_sm=0, undecimated=False, lambda_rule=LAMBDA_GIVEN,
-               lambda_out=None) -> CReconOpts:
+               lambda_out=None, tile_variant=0) -> CReconOpts:
     o = CReconOpts()
     lib().aexp_recon_opts_default(ctypes.byref(o))
     o.precision = precision
@@ -245,6 +247,7 @@ def recon_opts(precision=FP32, wavelet="haar", levels=3, n_power=30, lipschitz=0
     o.power_init = None if power_init is None else power_init.data_ptr()
     o.use_graph = 1 if use_graph else 0
     o.items_per_sm = int(items_per_sm)
+    o.tile_variant = int(tile_variant)
     o.undecimated = 1 if undecimated else 0
     o.lambda_rule = int(lambda_rule)
     o.lambda_out = None if lambda_out is None else lambda_out.data_ptr()
@@ -424,19 +427,21 @@ def lib_autotune_workspace_size(probs, opts: CReconOpts) -> int:
 
 
 def autotune(probs, opts: CReconOpts, ws=None, stream=None):
-    """Time the candidate work-item granularities for `probs` (one problem: cs_recon's layout;
-    several: cs_recon_batched's) and return (best items_per_sm, ms per A^H A application).
-    Synchronizes the stream; `opts` is not modified."""
+    """Time the candidate launch shapes (work-item granularity x kernel tiling) for `probs`
+    (one problem: cs_recon's layout; several: cs_recon_batched's) and return
+    (items_per_sm, tile_variant, median ms per A^H A application).  Synchronizes the stream;
+    `opts` is not modified."""
     probs = list(probs) if isinstance(probs, (list, tuple)) else [probs]
     n = len(probs)
     probs_c = _prob_array(probs)
     if ws is None:
         ws = _alloc(lib_autotune_workspace_size(probs, opts), probs[0].device)
     best = ctypes.c_int()
+    variant = ctypes.c_int()
     ms = ctypes.c_float()
     _check(lib().aexp_autotune(probs_c, n, ctypes.byref(opts), _ptr(ws), ws.numel(), _stream(stream),
-                               ctypes.byref(best), ctypes.byref(ms)), "aexp_autotune")
-    return best.value, ms.value
+                               ctypes.byref(best), ctypes.byref(variant), ctypes.byref(ms)), "aexp_autotune")
+    return best.value, variant.value, ms.value
 
 
 def power_lipschitz(prob: Problem, v0, n_power: int, ws=None, precision: int = FP32, stream=None):

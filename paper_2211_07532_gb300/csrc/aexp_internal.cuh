@@ -85,6 +85,7 @@ struct OpLayout {
     int ntx, nty, ntiles, nr_pad;
     int ntp;         // nt padded to kTPad
     int precision;
+    int variant;     // kernel tiling (aexp_recon_opts::tile_variant)
     // forward split
     int fwd_mt, fwd_tblocks, fwd_splits, fwd_tiles_per_split;
     // adjoint split
@@ -131,6 +132,9 @@ struct RecLayout {
 #endif
 constexpr int fwd_mt_for(int CB) { return CB >= 32 ? AEXP_FWD_MT32 : CB >= 16 ? 2 : 4; }
 constexpr int adj_mr_for(int CB) { return CB >= 32 ? AEXP_ADJ_MR32 : CB >= 16 ? 2 : CB >= 8 ? 2 : 4; }
+// tiling variant 1 of the FP32 form at 32 coils: two samples / voxels per thread, 2 blocks per SM
+constexpr int kFp32AltBlocking = 2;
+constexpr int kTileVariants = 2;
 
 inline size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
 inline int cdiv(int a, int b) { return (a + b - 1) / b; }
@@ -145,7 +149,7 @@ inline int default_items_per_sm(int precision) { return precision == AEXP_FP32 ?
 inline int items_target(int precision, int items_per_sm) {
     return kLayoutSMs * (items_per_sm > 0 ? items_per_sm : default_items_per_sm(precision));
 }
-int op_layout(const aexp_problem *p, int precision, OpLayout *L, int target_items = -1);
+int op_layout(const aexp_problem *p, int precision, OpLayout *L, int target_items = -1, int variant = 0);
 int wave_layout(int nx, int ny, int wavelet, int levels, WaveLayout *W);
 // target_items < 0: taken from o->items_per_sm
 int rec_layout(const aexp_problem *p, const aexp_recon_opts *o, RecLayout *R, int target_items = -1,
@@ -179,10 +183,11 @@ int num_sms();
 // BF16 form with the phase on the tensor cores (op_tc_phase.cu): operand preparation and the
 // launches (same contract as batch_forward_tc / batch_adjoint_tc).
 cudaError_t op_prepare_phase_operands(const OpLayout &L, char *ws, cudaStream_t st);
-cudaError_t tcp_forward(int CB, const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *x, int src,
-                        const int *item_off, int total_items, int *counter, cudaStream_t st);
-cudaError_t tcp_adjoint(int CB, const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *yt, int src,
-                        const int *item_off, int total_items, int *counter, cudaStream_t st);
+// variant: tiling 0 (B ring 4, phase ring 3) or 1 (B ring 6, phase ring 4)
+cudaError_t tcp_forward(int CB, int variant, const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *x,
+                        int src, const int *item_off, int total_items, int *counter, cudaStream_t st);
+cudaError_t tcp_adjoint(int CB, int variant, const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *yt,
+                        int src, const int *item_off, int total_items, int *counter, cudaStream_t st);
 constexpr size_t kPhaseBlockBytes = 16384;  // 128 rows x 128 B: BF16 hi (32 K slots) | lo (32 K slots)
 
 // Tensor-core forms (op_tc.cu): the forward packs S*x itself; the adjoint packs yt.
@@ -192,10 +197,12 @@ cudaError_t op_adjoint_tc(const OpLayout &L, const float2 *yt, char *ws, cudaStr
 // image vec[src] (forward) or rt (adjoint), then one persistent launch over all work items.
 // item_off: device prefix offsets [nprob + 1]; counter: device int reset by these calls.
 // precision: AEXP_BF16_TC or AEXP_FP16X2_TC.
-cudaError_t batch_forward_tc(int precision, int CB, int LP, const ProbDesc *pd, int nprob, int max_pack_blocks,
-                             int src, const int *item_off, int total_items, int *counter, cudaStream_t st);
-cudaError_t batch_adjoint_tc(int precision, int CB, int LP, const ProbDesc *pd, int nprob, int max_pack_blocks,
-                             int src, const int *item_off, int total_items, int *counter, cudaStream_t st);
+cudaError_t batch_forward_tc(int precision, int CB, int LP, int variant, const ProbDesc *pd, int nprob,
+                             int max_pack_blocks, int src, const int *item_off, int total_items, int *counter,
+                             cudaStream_t st);
+cudaError_t batch_adjoint_tc(int precision, int CB, int LP, int variant, const ProbDesc *pd, int nprob,
+                             int max_pack_blocks, int src, const int *item_off, int total_items, int *counter,
+                             cudaStream_t st);
 int fwd_pack_blocks(int ntiles, int CB);
 int adj_pack_blocks(int ntp, int CB);
 cudaError_t op_forward_reduce_planar_public(const OpLayout &L, char *ws, float2 *y, cudaStream_t st);

@@ -286,10 +286,10 @@ cudaError_t batch_normal_once(const BatchLayout &B, const aexp_recon_opts *o, ch
     const dim3 g_nr(cdiv(B.max_nr, T), n), g_ntp(cdiv(B.max_ntpcb, T), n);
     enum { Z = 2, W = 4 };
     batch_zero_kernel<<<g_nr, T, 0, st>>>(pd, Z);
-    CK(batch_forward_tc(o->precision, B.CB, B.LP, pd, n, B.max_fwd_pack, Z, ifwd, B.items_fwd[n], &bh->counter[0],
+    CK(batch_forward_tc(o->precision, B.CB, B.LP, o->tile_variant, pd, n, B.max_fwd_pack, Z, ifwd, B.items_fwd[n], &bh->counter[0],
                         st));
     batch_fwd_reduce_kernel<<<g_ntp, T, 0, st>>>(pd, 0);
-    CK(batch_adjoint_tc(o->precision, B.CB, B.LP, pd, n, B.max_adj_pack, -1, iadj, B.items_adj[n], &bh->counter[1],
+    CK(batch_adjoint_tc(o->precision, B.CB, B.LP, o->tile_variant, pd, n, B.max_adj_pack, -1, iadj, B.items_adj[n], &bh->counter[1],
                         st));
     batch_adj_reduce_kernel<<<g_nr, T, 0, st>>>(pd, -1, W);
     return cudaGetLastError();
@@ -313,9 +313,9 @@ cudaError_t batch_recon_issue(const aexp_problem *probs, const BatchLayout &B, c
     const dim3 g_nr(cdiv(B.max_nr, T), n), g_ntp(cdiv(B.max_ntpcb, T), n);
     // w = A^H A v for every problem (v in role vr, w in role wr)
     auto normal = [&](int vr, int wr) -> cudaError_t {
-        CK(batch_forward_tc(o->precision, B.CB, B.LP, pd, n, B.max_fwd_pack, vr, ifwd, tot_f, &bh->counter[0], st));
+        CK(batch_forward_tc(o->precision, B.CB, B.LP, o->tile_variant, pd, n, B.max_fwd_pack, vr, ifwd, tot_f, &bh->counter[0], st));
         batch_fwd_reduce_kernel<<<g_ntp, T, 0, st>>>(pd, 0);
-        CK(batch_adjoint_tc(o->precision, B.CB, B.LP, pd, n, B.max_adj_pack, -1, iadj, tot_a, &bh->counter[1], st));
+        CK(batch_adjoint_tc(o->precision, B.CB, B.LP, o->tile_variant, pd, n, B.max_adj_pack, -1, iadj, tot_a, &bh->counter[1], st));
         batch_adj_reduce_kernel<<<g_nr, T, 0, st>>>(pd, -1, wr);
         return cudaGetLastError();
     };
@@ -325,7 +325,7 @@ cudaError_t batch_recon_issue(const aexp_problem *probs, const BatchLayout &B, c
         batch_finalize_kernel<<<cdiv(n, T), T, 0, st>>>(pd, n, o->lipschitz);
     } else {
         // power iteration from A^H y
-        CK(batch_adjoint_tc(o->precision, B.CB, B.LP, pd, n, B.max_adj_pack, YM, iadj, tot_a, &bh->counter[1], st));
+        CK(batch_adjoint_tc(o->precision, B.CB, B.LP, o->tile_variant, pd, n, B.max_adj_pack, YM, iadj, tot_a, &bh->counter[1], st));
         batch_adj_reduce_kernel<<<g_nr, T, 0, st>>>(pd, -1, W);
         batch_dot_norm_kernel<<<n, kRedThreads, 0, st>>>(pd, -1, W);
         batch_scale_kernel<<<g_nr, T, 0, st>>>(pd, W, V);
@@ -344,9 +344,9 @@ cudaError_t batch_recon_issue(const aexp_problem *probs, const BatchLayout &B, c
     int prev = XA, next = XB;
     double t = 1.0;
     for (int k = 0; k < iters; ++k) {
-        CK(batch_forward_tc(o->precision, B.CB, B.LP, pd, n, B.max_fwd_pack, Z, ifwd, tot_f, &bh->counter[0], st));
+        CK(batch_forward_tc(o->precision, B.CB, B.LP, o->tile_variant, pd, n, B.max_fwd_pack, Z, ifwd, tot_f, &bh->counter[0], st));
         batch_fwd_reduce_kernel<<<g_ntp, T, 0, st>>>(pd, 1);
-        CK(batch_adjoint_tc(o->precision, B.CB, B.LP, pd, n, B.max_adj_pack, -1, iadj, tot_a, &bh->counter[1], st));
+        CK(batch_adjoint_tc(o->precision, B.CB, B.LP, o->tile_variant, pd, n, B.max_adj_pack, -1, iadj, tot_a, &bh->counter[1], st));
         batch_adj_reduce_kernel<<<g_nr, T, 0, st>>>(pd, Z, V);
         const double t_next = (1.0 + sqrt(1.0 + 4.0 * t * t)) / 2.0;
         const double beta = (t - 1.0) / t_next;

@@ -58,6 +58,7 @@ struct PrepRecord {
     aexp_problem prob;
     int precision;
     int items_per_sm;  // layout granularity the workspace was prepared with (0 = default)
+    int tile_variant;  // kernel tiling of that layout
 };
 std::mutex g_mu;
 std::unordered_map<const void *, PrepRecord> g_prepared;
@@ -69,16 +70,16 @@ int effective_items(int precision, int items_per_sm) {
     return items_per_sm > 0 ? items_per_sm : default_items_per_sm(precision);
 }
 
-void record_prepared(const void *ws, const aexp_problem *p, int precision, int items_per_sm = 0) {
+void record_prepared(const void *ws, const aexp_problem *p, int precision, int items_per_sm = 0, int variant = 0) {
     std::lock_guard<std::mutex> lk(g_mu);
-    g_prepared[ws] = PrepRecord{*p, precision, effective_items(precision, items_per_sm)};
+    g_prepared[ws] = PrepRecord{*p, precision, effective_items(precision, items_per_sm), variant};
 }
 
-bool is_prepared(const void *ws, const aexp_problem *p, int precision, int items_per_sm = 0) {
+bool is_prepared(const void *ws, const aexp_problem *p, int precision, int items_per_sm = 0, int variant = 0) {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_prepared.find(ws);
     return it != g_prepared.end() && same_problem(it->second.prob, *p) && it->second.precision == precision &&
-           it->second.items_per_sm == effective_items(precision, items_per_sm);
+           it->second.items_per_sm == effective_items(precision, items_per_sm) && it->second.tile_variant == variant;
 }
 
 // One captured cs_recon per workspace, relaunched while every argument is identical.
@@ -133,6 +134,7 @@ int check_opts(const aexp_recon_opts *o) {
     if (o->levels < 1 || o->levels > 12) return AEXP_ERR_INVALID_ARG;
     if (!(o->lipschitz > 0.0) && o->n_power < 1) return AEXP_ERR_INVALID_ARG;
     if (o->items_per_sm < 0 || o->items_per_sm > 256) return AEXP_ERR_INVALID_ARG;
+    if (o->tile_variant < 0 || o->tile_variant >= kTileVariants) return AEXP_ERR_INVALID_ARG;
     if (o->lambda_rule != AEXP_LAMBDA_GIVEN && o->lambda_rule != AEXP_LAMBDA_RAYLEIGH) return AEXP_ERR_INVALID_ARG;
     if (o->lambda_rule == AEXP_LAMBDA_RAYLEIGH && !o->undecimated) return AEXP_ERR_UNSUPPORTED;
     if (!aligned(o->x0, 8) || !aligned(o->power_init, 8) || !aligned(o->lambda_out, 8)) return AEXP_ERR_MISALIGNED;
@@ -248,6 +250,7 @@ void aexp_recon_opts_default(aexp_recon_opts *o) {
     o->lambda_rule = AEXP_LAMBDA_GIVEN;
     o->lambda_out = nullptr;
     o->items_per_sm = 0;
+    o->tile_variant = 0;
 }
 
 int aexp_recon_workspace_size(const aexp_problem *prob, const aexp_recon_opts *opts, size_t *bytes) {
@@ -280,7 +283,7 @@ int cs_recon(const aexp_problem *prob, const void *y, float lambda, int iters, c
         e = recon_issue(prob, R, opts, (const float2 *)y, lambda, iters, (float2 *)x_out,
                         lipschitz_out, w, st);
         if (e != cudaSuccess) return cuda_fail(e);
-        record_prepared(ws, prob, opts->precision, opts->items_per_sm);
+        record_prepared(ws, prob, opts->precision, opts->items_per_sm, opts->tile_variant);
         return AEXP_OK;
     }
 
@@ -320,7 +323,8 @@ int cs_recon(const aexp_problem *prob, const void *y, float lambda, int iters, c
     }
     e = cudaGraphLaunch(ge.exec, st);
     if (e != cudaSuccess) return cuda_fail(e);
-    g_prepared[ws] = PrepRecord{*prob, opts->precision, effective_items(opts->precision, opts->items_per_sm)};
+    g_prepared[ws] = PrepRecord{*prob, opts->precision, effective_items(opts->precision, opts->items_per_sm),
+                                opts->tile_variant};
     return AEXP_OK;
 }
 
@@ -364,7 +368,7 @@ int cgls_recon(const aexp_problem *prob, const void *y, int iters, const aexp_re
         e = launch_captured(ws, key, st, issue);
     }
     if (e != cudaSuccess) return cuda_fail(e);
-    record_prepared(ws, prob, opts->precision, opts->items_per_sm);
+    record_prepared(ws, prob, opts->precision, opts->items_per_sm, opts->tile_variant);
     return AEXP_OK;
 }
 
@@ -493,7 +497,7 @@ static int unroll_common(const aexp_problem *prob, const aexp_recon_opts *opts, 
     if (!aligned(y, 8)) return AEXP_ERR_MISALIGNED;
     rec_layout(prob, opts, R, -1, 1);
     if ((rc = check_ws(ws, ws_bytes, R->bytes))) return rc;
-    if (!is_prepared(ws, prob, opts->precision, opts->items_per_sm)) return AEXP_ERR_NOT_PREPARED;
+    if (!is_prepared(ws, prob, opts->precision, opts->items_per_sm, opts->tile_variant)) return AEXP_ERR_NOT_PREPARED;
     return AEXP_OK;
 }
 

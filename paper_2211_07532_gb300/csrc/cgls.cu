@@ -95,7 +95,7 @@ unsigned grid_for(size_t n) { return (unsigned)((n + 255) / 256); }
 
 int cgls_layout(const aexp_problem *p, const aexp_recon_opts *o, CglsLayout *C) {
     CglsLayout c{};
-    int rc = op_layout(p, o->precision, &c.op, items_target(o->precision, o->items_per_sm));
+    int rc = op_layout(p, o->precision, &c.op, items_target(o->precision, o->items_per_sm), o->tile_variant);
     if (rc) return rc;
     size_t off = c.op.bytes;
     auto take = [&](size_t bytes) {

@@ -12,7 +12,7 @@ int pad_coils(int n) { return n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : n <= 20 ?
 int pad_coils_tc(int n) { return n <= 8 ? 8 : n <= 16 ? 16 : 32; }
 }  // namespace
 
-int op_layout(const aexp_problem *p, int precision, OpLayout *L, int target_items) {
+int op_layout(const aexp_problem *p, int precision, OpLayout *L, int target_items, int variant) {
     if (target_items <= 0) target_items = items_target(precision, 0);
     OpLayout o{};
     o.nx = p->nx;
@@ -26,6 +26,7 @@ int op_layout(const aexp_problem *p, int precision, OpLayout *L, int target_item
     o.LP = pad_terms(o.nterms);
     o.CB = precision == AEXP_FP32 ? pad_coils(o.nc) : pad_coils_tc(o.nc);
     o.precision = precision;
+    o.variant = variant;
     o.ntx = cdiv(o.nx, kTileSide);
     o.nty = cdiv(o.ny, kTileSide);
     o.ntiles = o.ntx * o.nty;
@@ -33,7 +34,8 @@ int op_layout(const aexp_problem *p, int precision, OpLayout *L, int target_item
     o.ntp = cdiv(o.nt, kTPad) * kTPad;
 
     // forward: blocks own 128*mt samples and a contiguous run of tiles
-    o.fwd_mt = fwd_mt_for(o.CB);
+    const bool alt32 = precision == AEXP_FP32 && o.CB == 32 && variant == 1;
+    o.fwd_mt = alt32 ? kFp32AltBlocking : fwd_mt_for(o.CB);
     o.fwd_tblocks = o.ntp / (kFwdThreads * o.fwd_mt);
     {
         int by_sum = cdiv(o.ntiles, 32);                       // <= 32 tiles (2048 voxels) per block
@@ -44,7 +46,7 @@ int op_layout(const aexp_problem *p, int precision, OpLayout *L, int target_item
         o.fwd_splits = cdiv(o.ntiles, o.fwd_tiles_per_split);
     }
     // adjoint: blocks own 2*mr tiles (128*mr voxels) and a contiguous run of samples
-    o.adj_mr = adj_mr_for(o.CB);
+    o.adj_mr = alt32 ? kFp32AltBlocking : adj_mr_for(o.CB);
     o.adj_vblocks = cdiv(o.ntiles, 2 * o.adj_mr);
     {
         int nstage = o.ntp / kAdjStageT;
@@ -131,7 +133,7 @@ int rec_layout(const aexp_problem *p, const aexp_recon_opts *opt, RecLayout *R, 
                int with_grad) {
     RecLayout r{};
     if (target_items < 0) target_items = items_target(opt->precision, opt->items_per_sm);
-    int rc = op_layout(p, opt->precision, &r.op, target_items);
+    int rc = op_layout(p, opt->precision, &r.op, target_items, opt->tile_variant);
     if (rc) return rc;
     rc = wave_layout(p->nx, p->ny, opt->wavelet, opt->levels, &r.wv);
     if (rc) return rc;

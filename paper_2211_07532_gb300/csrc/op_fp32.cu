@@ -380,9 +380,8 @@ __global__ void adj_reduce_kernel(const float2 *part, int splits, int nr_pad, in
 
 // ---- dispatch over the compile-time coil / term paddings ----
 
-template <int CB, int LP>
-cudaError_t launch_fwd(const OpLayout &L, char *ws, cudaStream_t st) {
-    constexpr int MT = fwd_mt_for(CB);
+template <int CB, int LP, int MT>
+cudaError_t launch_fwd_mt(const OpLayout &L, char *ws, cudaStream_t st) {
     constexpr unsigned STAGE = kTileVox * LP * sizeof(float) + kTileVox * CB * sizeof(float2);
     auto kern = fwd_fp32_kernel<CB, LP, MT>;
     {  // always opted in: the static barriers count against the 48 KB default too
@@ -397,9 +396,8 @@ cudaError_t launch_fwd(const OpLayout &L, char *ws, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int CB, int LP>
-cudaError_t launch_adj(const OpLayout &L, const float2 *yt, char *ws, cudaStream_t st) {
-    constexpr int MR = adj_mr_for(CB);
+template <int CB, int LP, int MR>
+cudaError_t launch_adj_mr(const OpLayout &L, const float2 *yt, char *ws, cudaStream_t st) {
     constexpr unsigned STAGE = kAdjStageT * (LP * sizeof(float) + CB * sizeof(float2) + 2 * MR * sizeof(float));
     auto kern = adj_fp32_kernel<CB, LP, MR>;
     {  // always opted in: the static barriers count against the 48 KB default too
@@ -412,6 +410,22 @@ cudaError_t launch_adj(const OpLayout &L, const float2 *yt, char *ws, cudaStream
         (const float2 *)(ws + L.off_S), yt, (float2 *)(ws + L.off_apart), L.ntp, L.ntiles, L.adj_t_per_split,
         &hdr->status);
     return cudaGetLastError();
+}
+
+// The layout's register blocking (fwd_mt / adj_mr): the default of the coil padding, or the
+// alternative tiling at 32 coils.
+template <int CB, int LP>
+cudaError_t launch_fwd(const OpLayout &L, char *ws, cudaStream_t st) {
+    if constexpr (CB == 32 && fwd_mt_for(32) != kFp32AltBlocking)
+        if (L.fwd_mt == kFp32AltBlocking) return launch_fwd_mt<CB, LP, kFp32AltBlocking>(L, ws, st);
+    return launch_fwd_mt<CB, LP, fwd_mt_for(CB)>(L, ws, st);
+}
+
+template <int CB, int LP>
+cudaError_t launch_adj(const OpLayout &L, const float2 *yt, char *ws, cudaStream_t st) {
+    if constexpr (CB == 32 && adj_mr_for(32) != kFp32AltBlocking)
+        if (L.adj_mr == kFp32AltBlocking) return launch_adj_mr<CB, LP, kFp32AltBlocking>(L, yt, ws, st);
+    return launch_adj_mr<CB, LP, adj_mr_for(CB)>(L, yt, ws, st);
 }
 
 #define AEXP_DISPATCH_LP(FN, CBV, ...)                   \

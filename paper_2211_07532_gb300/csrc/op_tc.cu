@@ -746,7 +746,7 @@ cudaError_t op_forward_tc(const OpLayout &L, const float2 *x, char *ws, cudaStre
     WsHeader *hdr = (WsHeader *)(ws + L.off_hdr);
     const ProbDesc *pd = (const ProbDesc *)(ws + L.off_desc);
     if (L.precision == AEXP_BF16_TC)
-        return tcp_forward(L.CB, pd, 1, fwd_pack_blocks(L.ntiles, L.CB), x, 0, &hdr->item_off[0], L.fwd_items,
+        return tcp_forward(L.CB, L.variant, pd, 1, fwd_pack_blocks(L.ntiles, L.CB), x, 0, &hdr->item_off[0], L.fwd_items,
                            &hdr->counter[0], st);
     AEXP_TC_DISPATCH(launch_fwd_tc, pd, 1, fwd_pack_blocks(L.ntiles, L.CB), x, 0, &hdr->item_off[0], L.fwd_items,
                      &hdr->counter[0], st)
@@ -757,25 +757,27 @@ cudaError_t op_adjoint_tc(const OpLayout &L, const float2 *yt, char *ws, cudaStr
     WsHeader *hdr = (WsHeader *)(ws + L.off_hdr);
     const ProbDesc *pd = (const ProbDesc *)(ws + L.off_desc);
     if (L.precision == AEXP_BF16_TC)
-        return tcp_adjoint(L.CB, pd, 1, adj_pack_blocks(L.ntp, L.CB), yt, -1, &hdr->item_off[2], L.adj_items,
+        return tcp_adjoint(L.CB, L.variant, pd, 1, adj_pack_blocks(L.ntp, L.CB), yt, -1, &hdr->item_off[2], L.adj_items,
                            &hdr->counter[1], st);
     AEXP_TC_DISPATCH(launch_adj_tc, pd, 1, adj_pack_blocks(L.ntp, L.CB), yt, -1, &hdr->item_off[2], L.adj_items,
                      &hdr->counter[1], st)
 }
 
-cudaError_t batch_forward_tc(int precision, int CB, int LP, const ProbDesc *pd, int nprob, int max_pack_blocks,
-                             int src, const int *item_off, int total_items, int *counter, cudaStream_t st) {
+cudaError_t batch_forward_tc(int precision, int CB, int LP, int variant, const ProbDesc *pd, int nprob,
+                             int max_pack_blocks, int src, const int *item_off, int total_items, int *counter,
+                             cudaStream_t st) {
     const int CBv = CB, LPv = LP;
     if (precision == AEXP_BF16_TC)
-        return tcp_forward(CB, pd, nprob, max_pack_blocks, nullptr, src, item_off, total_items, counter, st);
+        return tcp_forward(CB, variant, pd, nprob, max_pack_blocks, nullptr, src, item_off, total_items, counter, st);
     AEXP_TC_DISPATCH(launch_fwd_tc, pd, nprob, max_pack_blocks, nullptr, src, item_off, total_items, counter, st)
 }
 
-cudaError_t batch_adjoint_tc(int precision, int CB, int LP, const ProbDesc *pd, int nprob, int max_pack_blocks,
-                             int src, const int *item_off, int total_items, int *counter, cudaStream_t st) {
+cudaError_t batch_adjoint_tc(int precision, int CB, int LP, int variant, const ProbDesc *pd, int nprob,
+                             int max_pack_blocks, int src, const int *item_off, int total_items, int *counter,
+                             cudaStream_t st) {
     const int CBv = CB, LPv = LP;
     if (precision == AEXP_BF16_TC)
-        return tcp_adjoint(CB, pd, nprob, max_pack_blocks, nullptr, src, item_off, total_items, counter, st);
+        return tcp_adjoint(CB, variant, pd, nprob, max_pack_blocks, nullptr, src, item_off, total_items, counter, st);
     AEXP_TC_DISPATCH(launch_adj_tc, pd, nprob, max_pack_blocks, nullptr, src, item_off, total_items, counter, st)
 }
 

@@ -123,26 +123,29 @@ constexpr int kLoadBWarp = kMmaWarp + 1;
 constexpr int kPhaseWarp = kMmaWarp + 2;
 constexpr int kLoadPWarp = kMmaWarp + 3;
 constexpr int kTcpThreads = kTcGen + 128;
-constexpr int kNP = 3;   // ring of per-stage phase operands (hi | lo image, 8 KB)
-constexpr int kNBB = 4;  // ring of per-stage contraction operands + reference phases
+// Ring depths (template parameters NBB, NP of the kernels): per-stage contraction operands +
+// reference phases (NBB) and per-stage phase operands (NP, hi | lo image of 8 KB).  Tiling 0:
+// 4 and 3; tiling 1 (aexp_recon_opts::tile_variant): 6 and 4.
 // A generator group waits only on the stages of its parity, so each B slot and each phase tile
 // must belong to one group: with an odd count a slot would alternate between the groups, a
 // group would skip every other phase of that slot's barrier and its parity test could pass a
-// phase early.  (The MMA thread and the loaders wait on every stage; kNP may be anything.)
-static_assert(kNBB % 2 == 0 && kPhBufs % 2 == 0, "each generator group must own its B slots and phase tiles");
+// phase early.  (The MMA thread and the loaders wait on every stage; NP may be anything.)
+static_assert(kPhBufs % 2 == 0, "each generator group must own its phase tiles");
 
 // Shared-memory plan of both kernels (byte offsets from the 1024-aligned base):
 //   A[2] generated encoding tiles | AP item phase operand (hi | lo) | PH ring | B ring
-template <int N>
+template <int N, int NBB, int NP>
 struct TcpPlan {
+    static_assert(NBB % 2 == 0, "each generator group must own its B slots");
+    static_assert(NBB <= kNBMax && NP <= kNBMax, "ring deeper than the CTA's barriers");
     static constexpr unsigned B_BYTES = N * 256;
     static constexpr unsigned F_BYTES = kRows * 4;  // forward: 128 f0; adjoint: 2 x 64 f0
     static constexpr unsigned BS = (B_BYTES + F_BYTES + 1023u) & ~1023u;  // B ring stride
     static constexpr unsigned PS = kHalfImg;                              // PH ring stride
     static constexpr unsigned OFF_AP = 2 * kA_BYTES;
     static constexpr unsigned OFF_PH = OFF_AP + kApBytes;
-    static constexpr unsigned OFF_B = OFF_PH + kNP * PS;
-    static constexpr unsigned BYTES = OFF_B + kNBB * BS;
+    static constexpr unsigned OFF_B = OFF_PH + NP * PS;
+    static constexpr unsigned BYTES = OFF_B + NBB * BS;
 };
 
 // Contraction of one stage: 8 MMAs of K = 16 (BF16) into columns 0..N-1.
@@ -178,14 +181,14 @@ __device__ __forceinline__ void phase_mma(int ks, uint32_t d, uint64_t a, uint64
 }
 
 // Contraction thread, one item.
-template <int N>
+template <int N, int NBB, int NP>
 __device__ __forceinline__ void tcp_contraction_item(TcShared &sh, uint32_t tmem, unsigned char *base, int gs, int n,
                                                      int *status) {
-    using PL = TcpPlan<N>;
+    using PL = TcpPlan<N, NBB, NP>;
     for (int it = 0; it < n; ++it) {
-        const int g = gs + it, sa = g & 1, sb = g % kNBB;
+        const int g = gs + it, sa = g & 1, sb = g % NBB;
         if (!wait_or_abort(&sh.afull[sa], (g >> 1) & 1, &sh.abort_flag, status)) return;
-        if (!wait_or_abort(&sh.bfull[sb], (g / kNBB) & 1, &sh.abort_flag, status)) return;
+        if (!wait_or_abort(&sh.bfull[sb], (g / NBB) & 1, &sh.abort_flag, status)) return;
         tc::fence_after_sync();
         contraction_mma<N>(tmem, tc::sdesc_k128(smem_u32(base + sa * kA_BYTES)),
                            tc::sdesc_k128(smem_u32(base + PL::OFF_B + sb * PL::BS)), it == 0);
@@ -197,17 +200,17 @@ __device__ __forceinline__ void tcp_contraction_item(TcShared &sh, uint32_t tmem
 
 // Phase thread, one item: the phases of stage g go into tile g % 4 once the generators have
 // read that tile for stage g - 4 and the stage's operand has landed.
-template <int N>
+template <int N, int NBB, int NP>
 __device__ __forceinline__ void tcp_phase_item(TcShared &sh, uint32_t tmem, unsigned char *base, int gs, int n,
                                                int iter, int ks, int *status) {
-    using PL = TcpPlan<N>;
+    using PL = TcpPlan<N, NBB, NP>;
     const uint64_t ad = tc::sdesc_k128(smem_u32(base + PL::OFF_AP));
     if (!wait_or_abort(&sh.apfull, iter & 1, &sh.abort_flag, status)) return;
     for (int it = 0; it < n; ++it) {
-        const int g = gs + it, b = g % kPhBufs, sp = g % kNP;
+        const int g = gs + it, b = g % kPhBufs, sp = g % NP;
         if (g >= kPhBufs && !wait_or_abort(&sh.phfree[b], ((g - kPhBufs) / kPhBufs) & 1, &sh.abort_flag, status))
             return;
-        if (!wait_or_abort(&sh.pfull[sp], (g / kNP) & 1, &sh.abort_flag, status)) return;
+        if (!wait_or_abort(&sh.pfull[sp], (g / NP) & 1, &sh.abort_flag, status)) return;
         tc::fence_after_sync();
         phase_mma(ks, tmem + phase_col(g), ad, tc::sdesc_k128(smem_u32(base + PL::OFF_PH + sp * PL::PS)));
         tc::mma_commit(&sh.phfull[b]);
@@ -288,18 +291,19 @@ __device__ __forceinline__ bool generate_row(TcShared &sh, int g, uint32_t taddr
 
 // Generator waits of stage g before its TMEM read (warp-uniform result): reference phases
 // landed, phase tile ready.  The A buffer is waited for inside generate_row.
+template <int NBB>
 __device__ __forceinline__ bool gen_waits(TcShared &sh, int g, int *status) {
-    bool ok = wait_or_abort(&sh.bfull[g % kNBB], (g / kNBB) & 1, &sh.abort_flag, status);
+    bool ok = wait_or_abort(&sh.bfull[g % NBB], (g / NBB) & 1, &sh.abort_flag, status);
     if (ok) ok = wait_or_abort(&sh.phfull[g % kPhBufs], (g / kPhBufs) & 1, &sh.abort_flag, status);
     return __all_sync(0xffffffffu, ok);
 }
 
 // Forward: item = (problem, block of 128 samples, run of voxel tiles).
-template <int CB>
+template <int CB, int NBB, int NP>
 __global__ void __launch_bounds__(kTcpThreads, 1)
     fwd_tcp_kernel(const ProbDesc *__restrict__ pd, const int *__restrict__ item_off, int nprob, int *counter) {
     constexpr int N = 2 * CB;
-    using PL = TcpPlan<N>;
+    using PL = TcpPlan<N, NBB, NP>;
 
     extern __shared__ unsigned char smem_raw[];
     __shared__ TcShared sh;
@@ -329,11 +333,11 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
         if (warp >= kMmaWarp) {
             const bool lead = (tid & 31) == 0;
             if (warp == kMmaWarp && lead) {
-                tcp_contraction_item<N>(sh, tmem, gbase, gs, ntl, status);
+                tcp_contraction_item<N, NBB, NP>(sh, tmem, gbase, gs, ntl, status);
             } else if (warp == kPhaseWarp && lead) {
-                tcp_phase_item<N>(sh, tmem, gbase, gs, ntl, iter, (P.LP + 15) >> 4, status);
+                tcp_phase_item<N, NBB, NP>(sh, tmem, gbase, gs, ntl, iter, (P.LP + 15) >> 4, status);
             } else if (warp == kLoadBWarp && lead) {
-                ring_load_item(sh.bfree, kNBB, gs, ntl, &sh.abort_flag, status, [&](int it, int sb) {
+                ring_load_item(sh.bfree, NBB, gs, ntl, &sh.abort_flag, status, [&](int it, int sb) {
                     const int tile = tile0 + it;  // packed S x of the tile and its reference phases
                     unsigned char *dst = gbase + PL::OFF_B + sb * PL::BS;
                     mbar_arrive_expect_tx(&sh.bfull[sb], PL::B_BYTES + PL::F_BYTES);
@@ -343,7 +347,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
             } else if (warp == kLoadPWarp && lead) {
                 mbar_arrive_expect_tx(&sh.apfull, kApBytes);
                 bulk_g2s(gbase + PL::OFF_AP, P.kph + (size_t)(tbase / kRows) * kPhaseBlockBytes, kApBytes, &sh.apfull);
-                ring_load_item(sh.pfree, kNP, gs, ntl, &sh.abort_flag, status, [&](int it, int sp) {
+                ring_load_item(sh.pfree, NP, gs, ntl, &sh.abort_flag, status, [&](int it, int sp) {
                     const int tile = tile0 + it;  // the tile's basis offsets, hi | lo
                     const unsigned char *dp =
                         P.dhph + (size_t)(tile >> 1) * kPhaseBlockBytes + (size_t)(tile & 1) * kHalfImg;
@@ -358,9 +362,9 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
             const int ch = (warp >> 2) & 1;
             const int grp = warp >> 3;
             for (int it = 0; it < ntl; ++it) {
-                const int g = gs + it, sa = g & 1, sb = g % kNBB;
+                const int g = gs + it, sa = g & 1, sb = g % NBB;
                 if ((g & 1) != grp) continue;
-                if (!gen_waits(sh, g, status)) break;  // warp-uniform exit
+                if (!gen_waits<NBB>(sh, g, status)) break;  // warp-uniform exit
                 tc::fence_after_sync();
                 if (!generate_row<false>(sh, g,
                                     tmem + ((uint32_t)(32 * (warp & 3)) << 16) + phase_col(g) + (uint32_t)(32 * ch),
@@ -403,12 +407,12 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
 }
 
 // Adjoint: item = (problem, pair of voxel tiles, run of 64-sample stages).
-template <int CB>
+template <int CB, int NBB, int NP>
 __global__ void __launch_bounds__(kTcpThreads, 1)
     adj_tcp_kernel(const ProbDesc *__restrict__ pd, const int *__restrict__ item_off, int nprob, int *counter) {
     constexpr int N = 2 * CB;
     constexpr int TS = kCols;  // samples per stage
-    using PL = TcpPlan<N>;
+    using PL = TcpPlan<N, NBB, NP>;
     constexpr unsigned FT = TS * 4;  // reference phases of one tile for one stage
 
     extern __shared__ unsigned char smem_raw[];
@@ -440,11 +444,11 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
         if (warp >= kMmaWarp) {
             const bool lead = (tid & 31) == 0;
             if (warp == kMmaWarp && lead) {
-                tcp_contraction_item<N>(sh, tmem, gbase, gs, nst, status);
+                tcp_contraction_item<N, NBB, NP>(sh, tmem, gbase, gs, nst, status);
             } else if (warp == kPhaseWarp && lead) {
-                tcp_phase_item<N>(sh, tmem, gbase, gs, nst, iter, (P.LP + 15) >> 4, status);
+                tcp_phase_item<N, NBB, NP>(sh, tmem, gbase, gs, nst, iter, (P.LP + 15) >> 4, status);
             } else if (warp == kLoadBWarp && lead) {
-                ring_load_item(sh.bfree, kNBB, gs, nst, &sh.abort_flag, status, [&](int it, int sb) {
+                ring_load_item(sh.bfree, NBB, gs, nst, &sh.abort_flag, status, [&](int it, int sb) {
                     const size_t ts = (size_t)t0 + (size_t)it * TS;  // packed y and both tiles' f0
                     unsigned char *dst = gbase + PL::OFF_B + sb * PL::BS;
                     mbar_arrive_expect_tx(&sh.bfull[sb], PL::B_BYTES + 2 * FT);
@@ -455,7 +459,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
             } else if (warp == kLoadPWarp && lead) {
                 mbar_arrive_expect_tx(&sh.apfull, kApBytes);
                 bulk_g2s(gbase + PL::OFF_AP, P.dhph + (size_t)vb * kPhaseBlockBytes, kApBytes, &sh.apfull);
-                ring_load_item(sh.pfree, kNP, gs, nst, &sh.abort_flag, status, [&](int it, int sp) {
+                ring_load_item(sh.pfree, NP, gs, nst, &sh.abort_flag, status, [&](int it, int sp) {
                     const size_t ts = (size_t)t0 + (size_t)it * TS;  // the stage's k rows, hi | lo
                     const unsigned char *kp =
                         P.kph + (ts / kRows) * kPhaseBlockBytes + ((ts / TS) & 1) * (size_t)kHalfImg;
@@ -472,9 +476,9 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
             const int ch = (warp >> 2) & 1;
             const int grp = warp >> 3;
             for (int it = 0; it < nst; ++it) {
-                const int g = gs + it, sa = g & 1, sb = g % kNBB;
+                const int g = gs + it, sa = g & 1, sb = g % NBB;
                 if ((g & 1) != grp) continue;
-                if (!gen_waits(sh, g, status)) break;  // warp-uniform exit
+                if (!gen_waits<NBB>(sh, g, status)) break;  // warp-uniform exit
                 tc::fence_after_sync();
                 if (!generate_row<true>(sh, g,
                                    tmem + ((uint32_t)(32 * (warp & 3)) << 16) + phase_col(g) + (uint32_t)(32 * ch),
@@ -534,17 +538,30 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
 }
 
 // ---- launches ----
-template <int CB>
+template <int CB, int NBB, int NP>
 size_t tcp_smem() {
-    return 1024 + TcpPlan<2 * CB>::BYTES;
+    return 1024 + TcpPlan<2 * CB, NBB, NP>::BYTES;
 }
 
-template <int CB>
+template <int CB, int NBB, int NP>
 cudaError_t launch_fwd_tcp(const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *x, int src,
                            const int *item_off, int total_items, int *counter, cudaStream_t st) {
     pack_b_fwd_kernel<CB, false><<<dim3(pack_grid(max_pack_blocks, CB), nprob), 256, 0, st>>>(pd, x, src);
-    auto kern = fwd_tcp_kernel<CB>;
-    const size_t smem = tcp_smem<CB>();
+    auto kern = fwd_tcp_kernel<CB, NBB, NP>;
+    const size_t smem = tcp_smem<CB, NBB, NP>();
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    kern<<<std::min(total_items, num_sms()), kTcpThreads, smem, st>>>(pd, item_off, nprob, counter);
+    return cudaGetLastError();
+}
+
+template <int CB, int NBB, int NP>
+cudaError_t launch_adj_tcp(const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *yt, int src,
+                           const int *item_off, int total_items, int *counter, cudaStream_t st) {
+    pack_y_adj_kernel<CB, false><<<dim3(pack_grid(max_pack_blocks, CB), nprob), 256, 0, st>>>(pd, yt, src);
+    auto kern = adj_tcp_kernel<CB, NBB, NP>;
+    const size_t smem = tcp_smem<CB, NBB, NP>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
@@ -553,16 +570,17 @@ cudaError_t launch_fwd_tcp(const ProbDesc *pd, int nprob, int max_pack_blocks, c
 }
 
 template <int CB>
-cudaError_t launch_adj_tcp(const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *yt, int src,
-                           const int *item_off, int total_items, int *counter, cudaStream_t st) {
-    pack_y_adj_kernel<CB, false><<<dim3(pack_grid(max_pack_blocks, CB), nprob), 256, 0, st>>>(pd, yt, src);
-    auto kern = adj_tcp_kernel<CB>;
-    const size_t smem = tcp_smem<CB>();
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(int), st);
-    if (e != cudaSuccess) return e;
-    kern<<<std::min(total_items, num_sms()), kTcpThreads, smem, st>>>(pd, item_off, nprob, counter);
-    return cudaGetLastError();
+cudaError_t launch_fwd_tcp_variant(int variant, const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *x,
+                                   int src, const int *item_off, int total_items, int *counter, cudaStream_t st) {
+    return variant == 1 ? launch_fwd_tcp<CB, 6, 4>(pd, nprob, max_pack_blocks, x, src, item_off, total_items, counter, st)
+                        : launch_fwd_tcp<CB, 4, 3>(pd, nprob, max_pack_blocks, x, src, item_off, total_items, counter, st);
+}
+
+template <int CB>
+cudaError_t launch_adj_tcp_variant(int variant, const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *yt,
+                                   int src, const int *item_off, int total_items, int *counter, cudaStream_t st) {
+    return variant == 1 ? launch_adj_tcp<CB, 6, 4>(pd, nprob, max_pack_blocks, yt, src, item_off, total_items, counter, st)
+                        : launch_adj_tcp<CB, 4, 3>(pd, nprob, max_pack_blocks, yt, src, item_off, total_items, counter, st);
 }
 
 }  // namespace
@@ -578,21 +596,21 @@ cudaError_t op_prepare_phase_operands(const OpLayout &L, char *ws, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t tcp_forward(int CB, const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *x, int src,
-                        const int *item_off, int total_items, int *counter, cudaStream_t st) {
+cudaError_t tcp_forward(int CB, int variant, const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *x,
+                        int src, const int *item_off, int total_items, int *counter, cudaStream_t st) {
     switch (CB) {
-        case 8: return launch_fwd_tcp<8>(pd, nprob, max_pack_blocks, x, src, item_off, total_items, counter, st);
-        case 16: return launch_fwd_tcp<16>(pd, nprob, max_pack_blocks, x, src, item_off, total_items, counter, st);
-        default: return launch_fwd_tcp<32>(pd, nprob, max_pack_blocks, x, src, item_off, total_items, counter, st);
+        case 8: return launch_fwd_tcp_variant<8>(variant, pd, nprob, max_pack_blocks, x, src, item_off, total_items, counter, st);
+        case 16: return launch_fwd_tcp_variant<16>(variant, pd, nprob, max_pack_blocks, x, src, item_off, total_items, counter, st);
+        default: return launch_fwd_tcp_variant<32>(variant, pd, nprob, max_pack_blocks, x, src, item_off, total_items, counter, st);
     }
 }
 
-cudaError_t tcp_adjoint(int CB, const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *yt, int src,
-                        const int *item_off, int total_items, int *counter, cudaStream_t st) {
+cudaError_t tcp_adjoint(int CB, int variant, const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *yt,
+                        int src, const int *item_off, int total_items, int *counter, cudaStream_t st) {
     switch (CB) {
-        case 8: return launch_adj_tcp<8>(pd, nprob, max_pack_blocks, yt, src, item_off, total_items, counter, st);
-        case 16: return launch_adj_tcp<16>(pd, nprob, max_pack_blocks, yt, src, item_off, total_items, counter, st);
-        default: return launch_adj_tcp<32>(pd, nprob, max_pack_blocks, yt, src, item_off, total_items, counter, st);
+        case 8: return launch_adj_tcp_variant<8>(variant, pd, nprob, max_pack_blocks, yt, src, item_off, total_items, counter, st);
+        case 16: return launch_adj_tcp_variant<16>(variant, pd, nprob, max_pack_blocks, yt, src, item_off, total_items, counter, st);
+        default: return launch_adj_tcp_variant<32>(variant, pd, nprob, max_pack_blocks, yt, src, item_off, total_items, counter, st);
     }
 }
 

@@ -20,7 +20,7 @@ constexpr int kCols = 64;                // voxels (forward) or samples (adjoint
 constexpr int kA_BYTES = kRows * kCols * 2 * 2;  // 128 rows x 128 bf16 = 32 KB
 constexpr float kTwoPi = 6.283185307179586f;
 constexpr int kSpin = 1 << 22;
-constexpr int kNBMax = 4;  // deepest operand ring (slots with their own full / free barriers)
+constexpr int kNBMax = 6;  // deepest operand ring (slots with their own full / free barriers)
 constexpr float kLoScale = 2048.f;           // 2^11: scale of the low parts
 constexpr float kLoInv = 1.f / 2048.f;
 constexpr int kPromote = 8;                  // FP16 hi+lo: stages per accumulator chunk

@@ -138,7 +138,7 @@ def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
 
 def test_items_per_sm_sizes_and_validation(L):
     """The work-item granularity changes only the partial-sum space; the tuner's workspace
-    covers every candidate; out-of-range values are rejected on the host."""
+    covers every candidate (granularity x tiling); out-of-range values are rejected on the host."""
     import paper_2211_07532_gb300 as ax
     p = _fake_problem(nx=200, ny=200, nt=24000, nc=32, nl=16)
     sizes = {}
@@ -154,10 +154,17 @@ def test_items_per_sm_sizes_and_validation(L):
         assert sizes[(prec, 2)] <= sizes[(prec, 8)] <= sizes[(prec, 32)]
         # 0 is the default: 16 per SM for FP32, 8 for the tensor cores
         assert sizes[(prec, 0)] == sizes[(prec, 16 if prec == ax.FP32 else 8)]
-        o.items_per_sm = 0
+        variants = (0, 1) if prec != ax.FP16X2_TC else (0,)   # 32 coils: FP32 and BF16 have two tilings
+        for ips in (2, 4, 8, 16, 32):
+            o.items_per_sm, o.tile_variant = ips, 1
+            n = ctypes.c_size_t()
+            assert L.aexp_recon_workspace_size(ctypes.byref(p), ctypes.byref(o), ctypes.byref(n)) == 0
+            sizes[(prec, ips, 1)] = n.value
+        o.items_per_sm, o.tile_variant = 0, 0
         need = ctypes.c_size_t()
         assert L.aexp_autotune_workspace_size(ctypes.byref(p), 1, ctypes.byref(o), ctypes.byref(need)) == 0
-        assert need.value == max(sizes[(prec, c)] for c in (2, 4, 8, 16, 32))
+        assert need.value == max([sizes[(prec, c)] for c in (2, 4, 8, 16, 32)] +
+                                 [sizes[(prec, c, 1)] for c in (2, 4, 8, 16, 32) if 1 in variants])
     for bad in (-1, 257):
         o.items_per_sm = bad
         assert L.aexp_recon_workspace_size(ctypes.byref(p), ctypes.byref(o), ctypes.byref(n)) == -1
@@ -170,4 +177,9 @@ def test_items_per_sm_sizes_and_validation(L):
     assert L.aexp_autotune_workspace_size(arr, 2, ctypes.byref(o), ctypes.byref(need)) == 0
     # no device call is made for a null workspace
     best = ctypes.c_int()
-    assert L.aexp_autotune(arr, 2, ctypes.byref(o), None, 0, None, ctypes.byref(best), None) == -1
+    variant = ctypes.c_int()
+    assert L.aexp_autotune(arr, 2, ctypes.byref(o), None, 0, None, ctypes.byref(best), ctypes.byref(variant),
+                           None) == -1
+    o.tile_variant = 2   # out of range
+    assert L.aexp_recon_workspace_size(ctypes.byref(p), ctypes.byref(o), ctypes.byref(n)) == -1
+    o.tile_variant = 0

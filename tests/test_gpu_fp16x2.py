@@ -164,7 +164,7 @@ def test_fp16x2_batch_matches_oracle(ax):
     Ls = L.cpu().numpy()
     for q, (p, y, lam) in enumerate(zip(probs, ys, lams)):
         Lo = recon.power_lipschitz(p, oracle.adjoint(p, y), 20)
-        ref = recon.fista(p, y, lam, 8, float(Ls[q]), "db4", 2)
+        ref = recon.fista(p, y, lam, 8, Lo, "db4", 2)  # the oracle's own L_f
         e = rel(xs[q].cpu().numpy(), ref)
         print(f"fp16x2 batch problem {q}: vs oracle {e:.2e}, L_f rel {abs(Ls[q] - Lo) / Lo:.2e}")
         assert abs(Ls[q] - Lo) < TOL * Lo
