@@ -788,7 +788,8 @@ def run_solve_only(args):
 def run_kernel_classes(args):
     """One small invocation of every kernel class outside the operator (a bounded profiling
     target): the orthogonal wavelet levels and FP64 norms of a 2-iteration FISTA on the 200^2
-    slice, the undecimated wavelet and lambda-rule kernels, coil compression 32 -> 20, one
+    slice, the undecimated wavelet and lambda-rule kernels, coil compression 32 -> 20, two CGLS
+    iterations, one
     unrolled-FISTA step and its VJP on the 170^2 / 16-coil slice (k-gradient kernel), and a
     2-iteration batched solve of six ragged problems (persistent batch kernels)."""
     import torch
@@ -811,6 +812,7 @@ def run_kernel_classes(args):
         ax.cs_recon(prob, y, 0.0, 2, wavelet="db4", undecimated=True, lambda_rule=ax.LAMBDA_RAYLEIGH,
                     lambda_out=lam, n_power=2, use_graph=False)
         ax.coil_compress(prob, y, 20)
+        ax.cgls_recon(prob, y, 2)
         q = synth.diff_170()
         pq = ax.Problem.from_arrays(q, device=dev)
         wq = ax.workspace(pq)

@@ -98,7 +98,7 @@ def test_tiling_variant_matches_oracle(ax, precision):
     import oracle
     from oracle import precision as prec_emul
     from oracle import recon
-    p = synth.make_problem(40, 36, nt=1500, nc=32, order=3, dwell=4e-6, turns=6.0, seed=4242)
+    p = synth.make_problem(32, 24, nt=1000, nc=32, order=3, dwell=4e-6, turns=5.0, seed=4242)
     y0 = oracle.forward(p, p["x_gt"])
     y = (y0 + 0.05 * np.sqrt(np.mean(np.abs(y0) ** 2)) * p["noise"]).astype(np.complex64)
     lam = float(np.float32(1e-2 * np.max(np.abs(oracle.adjoint(p, y)))))

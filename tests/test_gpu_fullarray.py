@@ -1,0 +1,102 @@
+"""Whole-array parity of A_exp and A_exp^H at an intermediate size, every form.
+
+94x90 voxels (12x12 tiles of 8, the last row and column partial), 6000 samples (a ragged last
+sample block), 32 coils, 3rd-order field + B0 (17 terms): every output element of the forward
+and the adjoint is compared with the FP64 oracle, at a size where the default launch shape
+splits both reductions (forward: voxel tiles across blocks; adjoint: sample runs across
+blocks) into many partial sums, so a wrong split, edge tile or partial-sum combine shows here
+even where it would carry little energy.
+
+Two measures per output: the relative L2 error (the forms' stated bars) and the largest
+element error over the largest reference magnitude.  For outputs driven by white inputs the
+reference's extreme is ~4-5 rms and so is the error's, so the two ratios agree within a small
+factor; a localised error (one bad tile or sample block) moves the max-abs ratio by orders of
+magnitude while hardly moving the L2 one.  The max-abs bar is 3x the L2 bar.
+
+BF16 in addition, element by element against the oracle's rounding emulation (the same two
+BF16 roundings of Sec. 1's operator written out densely) on a smaller problem: the GPU output
+must sit much closer to the emulation than the emulation sits to the exact operator, because
+the two differ only where an FP32 phase or operand difference flips one BF16 rounding."""
+
+import numpy as np
+import pytest
+
+from paper_2211_07532_gb300 import synth
+from tests._data import rel
+
+pytestmark = pytest.mark.gpu
+L2_BAR = {"FP32": 1e-5, "FP16X2_TC": 1e-5, "BF16_TC": 5e-3}
+MAX_FACTOR = 3.0
+EMUL_RATIO = 0.3     # ||gpu - emul|| / ||emul - exact|| for the BF16 form
+
+
+@pytest.fixture(scope="module")
+def ax():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2211_07532_gb300 import build
+    build.build()
+    import paper_2211_07532_gb300 as ax
+    ax.lib()
+    return ax
+
+
+def maxrel(a, b):
+    a = np.asarray(a, np.complex128).reshape(-1)
+    b = np.asarray(b, np.complex128).reshape(-1)
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+@pytest.fixture(scope="module")
+def case():
+    import oracle
+    p = synth.make_problem(94, 90, nt=6000, nc=32, order=3, dwell=2e-6, turns=12.0, seed=9490)
+    rng = np.random.default_rng(9490)
+    x = synth.random_image(rng, 94 * 90)
+    y = synth.random_kspace(rng, 32, 6000)
+    return p, x, y, oracle.forward(p, x), oracle.adjoint(p, y)
+
+
+def _apply(ax, p, x, y, prec):
+    import torch
+    prob = ax.Problem.from_arrays(p)
+    ws = ax.workspace(prob, prec)
+    ax.prepare(prob, ws, prec)
+    f = ax.a_exp_forward(prob, torch.as_tensor(x, device="cuda"), ws, precision=prec)
+    a = ax.a_exp_adjoint(prob, torch.as_tensor(y, device="cuda"), ws, precision=prec)
+    torch.cuda.synchronize()
+    assert ax.read_status(ws) == 0
+    return f.cpu().numpy(), a.cpu().numpy()
+
+
+@pytest.mark.parametrize("precision", ["FP32", "FP16X2_TC", "BF16_TC"])
+def test_whole_array_matches_oracle(ax, case, precision):
+    p, x, y, fref, aref = case
+    f, a = _apply(ax, p, x, y, getattr(ax, precision))
+    ef, ea = rel(f, fref), rel(a, aref)
+    mf, ma = maxrel(f, fref), maxrel(a, aref)
+    bar = L2_BAR[precision]
+    print(f"{precision}: forward L2 {ef:.2e} max {mf:.2e}; adjoint L2 {ea:.2e} max {ma:.2e} (bar {bar:.0e})")
+    assert ef < bar and ea < bar
+    assert mf < MAX_FACTOR * bar and ma < MAX_FACTOR * bar
+    # every coil row and every voxel is written (no element left at zero by a missed tile)
+    assert np.all(np.abs(f).max(axis=1) > 0) and np.count_nonzero(a) == a.size
+
+
+def test_bf16_elementwise_against_rounding_emulation(ax):
+    import oracle
+    from oracle import precision as emul
+    p = synth.make_problem(40, 36, nt=1500, nc=32, order=3, dwell=4e-6, turns=6.0, seed=4036)
+    rng = np.random.default_rng(4036)
+    x = synth.random_image(rng, 40 * 36)
+    y = synth.random_kspace(rng, 32, 1500)
+    fwd, adj = emul.bf16_operators(p)
+    fe, ae = fwd(x), adj(y)
+    fx, ax_ = oracle.forward(p, x), oracle.adjoint(p, y)
+    f, a = _apply(ax, p, x, y, ax.BF16_TC)
+    rf, ra = rel(f, fe) / rel(fe, fx), rel(a, ae) / rel(ae, ax_)
+    print(f"BF16 vs emulation: forward {rel(f, fe):.2e} (emulation vs exact {rel(fe, fx):.2e}, ratio {rf:.3f}); "
+          f"adjoint {rel(a, ae):.2e} (emulation vs exact {rel(ae, ax_):.2e}, ratio {ra:.3f})")
+    assert rf < EMUL_RATIO and ra < EMUL_RATIO
+    # and element by element: no output is further from the emulation than the rounding scale
+    assert maxrel(f, fe) < MAX_FACTOR * rel(fe, fx) and maxrel(a, ae) < MAX_FACTOR * rel(ae, ax_)
