@@ -11,12 +11,12 @@
 
 #include "aexp_internal.cuh"
 #include "batch_internal.h"
+#include "reduce_f64.cuh"
 
 namespace aexp {
 
 namespace {
 
-constexpr int kRedThreads = 1024;
 // prefix arrays of up to kMaxBatchProblems + 1 entries written through one kernel argument
 struct OffsetsArg {
     int n;
@@ -32,7 +32,7 @@ __device__ __forceinline__ int tile_index(const ProbDesc &P, int r) {
     return ((iy / kTileSide) * P.ntx + ix / kTileSide) * kTileVox + (iy % kTileSide) * kTileSide + ix % kTileSide;
 }
 
-// zero the per-problem header scalars and status
+// zero the per-problem header scalars, status and FP64-reduction ticket
 __global__ void batch_reset_kernel(const ProbDesc *pd, int nprob) {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nprob) return;
@@ -41,6 +41,7 @@ __global__ void batch_reset_kernel(const ProbDesc *pd, int nprob) {
     h->lipschitz = 0.0;
     h->mu = 0.0;
     h->nrm2 = 0.0;
+    h->red_ticket = 0u;
 }
 
 // measured k-space y[c][t] -> sample-major vec[5][t][CB] (zero padded)
@@ -95,42 +96,27 @@ __global__ void batch_adj_reduce_kernel(const ProbDesc *pd, int z_role, int out_
     P.vec[out_role][r] = s;
 }
 
-// FP64 mu = Re <v, w> (when v_role >= 0) and nrm2 = ||w||^2, one block per problem
-__global__ void __launch_bounds__(kRedThreads) batch_dot_norm_kernel(const ProbDesc *pd, int v_role, int w_role) {
-    const ProbDesc &P = pd[blockIdx.x];
-    __shared__ double s_mu[kRedThreads / 32], s_nn[kRedThreads / 32];
+// FP64 mu = Re <v, w> (when v_role >= 0) and nrm2 = ||w||^2 of every problem: blockIdx.y is
+// the problem, its gridDim.x blocks form one deterministic grid reduction over its own
+// partials and ticket (WsHeader of the problem)
+__global__ void __launch_bounds__(kDotThreads) batch_dot_norm_kernel(const ProbDesc *pd, int v_role, int w_role) {
+    const ProbDesc &P = pd[blockIdx.y];
     const float2 *w = P.vec[w_role];
     const float2 *v = v_role >= 0 ? P.vec[v_role] : nullptr;
     double a = 0.0, b = 0.0;
-    for (int i = threadIdx.x; i < P.nr; i += kRedThreads) {
-        float2 wv = w[i];
+    for (int i = blockIdx.x * kDotThreads + threadIdx.x; i < P.nr; i += gridDim.x * kDotThreads) {
+        const float2 wv = w[i];
         if (v) {
-            float2 vv = v[i];
-            a += (double)vv.x * wv.x + (double)vv.y * wv.y;
+            const float2 vv = v[i];
+            a = fma((double)vv.x, (double)wv.x, a);
+            a = fma((double)vv.y, (double)wv.y, a);
         }
-        b += (double)wv.x * wv.x + (double)wv.y * wv.y;
+        b = fma((double)wv.x, (double)wv.x, b);
+        b = fma((double)wv.y, (double)wv.y, b);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-    }
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    if (lane == 0) {
-        s_mu[warp] = a;
-        s_nn[warp] = b;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        a = s_mu[lane];
-        b = s_nn[lane];
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            b += __shfl_xor_sync(0xffffffffu, b, o);
-        }
-        if (lane == 0) {
-            if (v) P.hdr->mu = a;
-            P.hdr->nrm2 = b;
-        }
+    if (grid_sum2(a, b, blockIdx.x, gridDim.x, P.hdr->red_part, &P.hdr->red_ticket)) {
+        if (v) P.hdr->mu = a;
+        P.hdr->nrm2 = b;
     }
 }
 
@@ -311,6 +297,8 @@ cudaError_t batch_recon_issue(const aexp_problem *probs, const BatchLayout &B, c
 
     const int tot_f = B.items_fwd[n], tot_a = B.items_adj[n];
     const dim3 g_nr(cdiv(B.max_nr, T), n), g_ntp(cdiv(B.max_ntpcb, T), n);
+    // FP64 norms: enough blocks per problem to spread the FP64 work, at most ~8 per SM in all
+    const int g_red = std::max(1, std::min(std::min(kRedMaxBlocks, cdiv(B.max_nr, 2 * kDotThreads)), cdiv(8 * num_sms(), n)));
     // w = A^H A v for every problem (v in role vr, w in role wr)
     auto normal = [&](int vr, int wr) -> cudaError_t {
         CK(batch_forward_tc(o->precision, B.CB, B.LP, o->tile_variant, pd, n, B.max_fwd_pack, vr, ifwd, tot_f, &bh->counter[0], st));
@@ -327,11 +315,11 @@ cudaError_t batch_recon_issue(const aexp_problem *probs, const BatchLayout &B, c
         // power iteration from A^H y
         CK(batch_adjoint_tc(o->precision, B.CB, B.LP, o->tile_variant, pd, n, B.max_adj_pack, YM, iadj, tot_a, &bh->counter[1], st));
         batch_adj_reduce_kernel<<<g_nr, T, 0, st>>>(pd, -1, W);
-        batch_dot_norm_kernel<<<n, kRedThreads, 0, st>>>(pd, -1, W);
+        batch_dot_norm_kernel<<<dim3(g_red, n), kDotThreads, 0, st>>>(pd, -1, W);
         batch_scale_kernel<<<g_nr, T, 0, st>>>(pd, W, V);
         for (int i = 0; i < o->n_power; ++i) {
             CK(normal(V, W));
-            batch_dot_norm_kernel<<<n, kRedThreads, 0, st>>>(pd, V, W);
+            batch_dot_norm_kernel<<<dim3(g_red, n), kDotThreads, 0, st>>>(pd, V, W);
             batch_scale_kernel<<<g_nr, T, 0, st>>>(pd, W, V);
         }
         batch_finalize_kernel<<<cdiv(n, T), T, 0, st>>>(pd, n, 0.0);

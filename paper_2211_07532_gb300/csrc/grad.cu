@@ -15,7 +15,10 @@
 // of 8x8 voxel tiles staged by bulk TMA copies, exactly like the forward operator kernel.
 #include <math.h>
 
+#include <algorithm>
+
 #include "aexp_internal.cuh"
+#include "reduce_f64.cuh"
 
 namespace aexp {
 
@@ -203,15 +206,15 @@ __global__ void combine_kernel(int n, float a, const float2 *X, float b, const f
 
 // Soft-threshold VJP on the detail coefficients of a Mallat pyramid (npy x npx, J levels):
 // gw <- (1 - tau/r) gw + (tau/r^3) w Re(conj(w) gw) where |w| > tau, 0 where |w| <= tau;
-// the low-pass block is left as is.  lambar += (1/L) sum -Re(conj(gw) w)/r (FP64, one block).
-__global__ void __launch_bounds__(1024) soft_vjp_kernel(const float2 *w, float2 *gw, int npx, int npy, int levels,
-                                                        float lam, const WsHeader *hdr, double *lambar) {
-    __shared__ double s_red[32];
+// the low-pass block is left as is.  lambar += (1/L) sum -Re(conj(gw) w)/r (FP64, one
+// deterministic grid reduction through the header's partials and ticket).
+__global__ void __launch_bounds__(kDotThreads) soft_vjp_kernel(const float2 *w, float2 *gw, int npx, int npy,
+                                                               int levels, float lam, WsHeader *hdr, double *lambar) {
     const double L = hdr->lipschitz;
     const float tau = (float)((double)lam / L);
     const int lpx = npx >> levels, lpy = npy >> levels;
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < npx * npy; i += blockDim.x) {
+    double acc = 0.0, unused = 0.0;
+    for (int i = blockIdx.x * kDotThreads + threadIdx.x; i < npx * npy; i += gridDim.x * kDotThreads) {
         const int iy = i / npx, ix = i % npx;
         if (iy < lpy && ix < lpx) continue;  // low-pass block: weight 0
         const float2 wv = w[i], g = gw[i];
@@ -227,14 +230,8 @@ __global__ void __launch_bounds__(1024) soft_vjp_kernel(const float2 *w, float2 
         }
         gw[i] = o;
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        acc = threadIdx.x < (blockDim.x >> 5) ? s_red[threadIdx.x] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (threadIdx.x == 0 && lambar) *lambar += acc / L;
-    }
+    if (grid_sum2(acc, unused, blockIdx.x, gridDim.x, hdr->red_part, &hdr->red_ticket) && lambar)
+        *lambar += acc / L;
 }
 
 template <int CB, int LP>
@@ -328,7 +325,12 @@ cudaError_t unroll_step_vjp(const RecLayout &R, const float2 *y, float lam, doub
     // vbar_k = crop W^H S'^T W pad xbar_k, lambar += taubar / L
     CK(wave_forward(R.wv, v, ws + R.off_wave, 0.f, nullptr, 0, st));
     CK(wave_forward(R.wv, xbar, ws + R.off_wave2, 0.f, nullptr, 0, st));
-    soft_vjp_kernel<<<1, 1024, 0, st>>>(pyr_w, pyr_g, R.wv.npx, R.wv.npy, R.wv.levels, lam, hdr, lambar);
+    {
+        const int n = R.wv.npx * R.wv.npy;
+        const int blocks = std::max(1, std::min(kRedMaxBlocks, cdiv(n, 2 * kDotThreads)));
+        soft_vjp_kernel<<<blocks, kDotThreads, 0, st>>>(pyr_w, pyr_g, R.wv.npx, R.wv.npy, R.wv.levels, lam, hdr,
+                                                        lambar);
+    }
     CK(wave_inverse(R.wv, ws + R.off_wave2, vbar, 0, 0.0, nullptr, nullptr, st));
     // u = A vbar; kbar += -(2/L) Re[d/dk <u, A z_k> + d/dk <vbar, A^H r_k>]
     CK(op_apply_forward(L, vbar, ws, st));

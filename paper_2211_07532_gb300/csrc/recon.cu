@@ -8,44 +8,17 @@
 #include <algorithm>
 
 #include "aexp_internal.cuh"
+#include "reduce_f64.cuh"
 
 namespace aexp {
 
 namespace {
 
-constexpr int kDotThreads = 256;
-
-// Block sum of (a, b) in a fixed tree order; the result is valid in thread 0.
-__device__ __forceinline__ void block_sum2(double &a, double &b, double *sa, double *sb) {
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-    }
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    if (lane == 0) {
-        sa[warp] = a;
-        sb[warp] = b;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        a = lane < kDotThreads / 32 ? sa[lane] : 0.0;
-        b = lane < kDotThreads / 32 ? sb[lane] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            b += __shfl_xor_sync(0xffffffffu, b, o);
-        }
-    }
-}
-
-// mu = Re <v, w>, nrm2 = ||w||^2 in FP64 (each product of two floats is exact in FP64).
-// Every block sums a fixed grid-stride set of elements in a fixed tree order and leaves its
-// pair in part[]; the block that takes the last ticket adds the partials in block order.
-// The result depends only on n and the grid, never on which block finishes first.
+// mu = Re <v, w>, nrm2 = ||w||^2 in FP64 (each product of two floats is exact in FP64), one
+// deterministic grid reduction.
 __global__ void __launch_bounds__(kDotThreads) dot_norm_kernel(const float2 *__restrict__ v,
                                                                const float2 *__restrict__ w, int n, double *part,
                                                                unsigned *ticket, double *mu, double *nrm2) {
-    __shared__ double sa[kDotThreads / 32], sb[kDotThreads / 32];
-    __shared__ bool last;
     double a = 0.0, b = 0.0;
     for (int i = blockIdx.x * kDotThreads + threadIdx.x; i < n; i += gridDim.x * kDotThreads) {
         const float2 wv = w[i];
@@ -57,27 +30,9 @@ __global__ void __launch_bounds__(kDotThreads) dot_norm_kernel(const float2 *__r
         b = fma((double)wv.x, (double)wv.x, b);
         b = fma((double)wv.y, (double)wv.y, b);
     }
-    block_sum2(a, b, sa, sb);
-    if (threadIdx.x == 0) {
-        part[2 * blockIdx.x] = a;
-        part[2 * blockIdx.x + 1] = b;
-        __threadfence();
-        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    a = b = 0.0;
-    for (int k = threadIdx.x; k < (int)gridDim.x; k += kDotThreads) {
-        a += __ldcg(part + 2 * k);
-        b += __ldcg(part + 2 * k + 1);
-    }
-    __syncthreads();  // the shared partials of the first block_sum2 are reused
-    block_sum2(a, b, sa, sb);
-    if (threadIdx.x == 0) {
+    if (grid_sum2(a, b, blockIdx.x, gridDim.x, part, ticket)) {
         if (mu) *mu = a;
         *nrm2 = b;
-        *ticket = 0u;  // ready for the next launch (also inside a replayed graph)
     }
 }
 
