@@ -14,9 +14,10 @@
 //
 // Generators then read their row's phase offsets of the stage with one tcgen05.ld (in
 // radians: the k operand carries the factor 2 pi), add 2 pi f0(tile, t) with the tile's
-// tabulated reference phase f0 in [-1/2, 1/2) turn, take one MUFU sincos and store the BF16
-// encoding tile; the contraction with the
-// coil-weighted image (or the k-space data) is a tcgen05 kind::f16 GEMM of BF16 operands.
+// tabulated reference phase f0 in [-1/2, 1/2) turn, take one MUFU sincos and write their row
+// of the BF16 encoding tile into TMEM with one tcgen05.st (no shared-memory stores, no proxy
+// fence); the contraction with the coil-weighted image (or the k-space data) is a tcgen05
+// kind::f16 GEMM with A read from TMEM and B, the packed BF16 operand, from shared memory.
 // The two GEMMs are issued by two threads of their own: the
 // contraction thread issues 8 MMAs per stage once the generators have stored A(g); the
 // phase thread fills four TMEM phase tiles, each as soon as the generators have read it.
@@ -47,12 +48,17 @@ namespace {
 constexpr unsigned kHalfImg = 64 * 128;         // the hi | lo image of 64 rows, 8 KB
 constexpr unsigned kApBytes = kRows * 128;      // item operand: hi | lo image of 128 rows, 16 KB
 constexpr uint32_t kLoBytes = 64;               // the lo parts start 32 slots (64 B) into a row
-// TMEM: the contraction accumulates in columns 0..N-1, phase tile b (of 4) sits at 64 + 64 b
+// TMEM: the contraction accumulates in columns 0..N-1, phase tile b (of 4) sits at 64 + 64 b,
+// the generated encoding tile of A buffer a (of 2: 128 rows x 128 BF16, two per column) at
+// 320 + 64 a
 constexpr uint32_t kPhBase = 64;
 constexpr int kPhBufs = 4;
+constexpr uint32_t kABase = kPhBase + 64 * kPhBufs;
 constexpr uint32_t kTmemCols = 512;
+static_assert(kABase + 2 * 64 <= kTmemCols, "TMEM plan");
 
 __device__ __forceinline__ uint32_t phase_col(int g) { return kPhBase + 64u * (uint32_t)(g % kPhBufs); }
+__device__ __forceinline__ uint32_t a_col(int sa) { return kABase + 64u * (uint32_t)sa; }
 
 // ---- operand preparation ----
 
@@ -132,8 +138,9 @@ constexpr int kTcpThreads = kTcGen + 128;
 // phase early.  (The MMA thread and the loaders wait on every stage; NP may be anything.)
 static_assert(kPhBufs % 2 == 0, "each generator group must own its phase tiles");
 
-// Shared-memory plan of both kernels (byte offsets from the 1024-aligned base):
-//   A[2] generated encoding tiles | AP item phase operand (hi | lo) | PH ring | B ring
+// Shared-memory plan of both kernels (byte offsets from the 1024-aligned base; the generated
+// encoding tiles live in TMEM):
+//   AP item phase operand (hi | lo) | PH ring | B ring
 template <int N, int NBB, int NP>
 struct TcpPlan {
     static_assert(NBB % 2 == 0, "each generator group must own its B slots");
@@ -142,21 +149,21 @@ struct TcpPlan {
     static constexpr unsigned F_BYTES = kRows * 4;  // forward: 128 f0; adjoint: 2 x 64 f0
     static constexpr unsigned BS = (B_BYTES + F_BYTES + 1023u) & ~1023u;  // B ring stride
     static constexpr unsigned PS = kHalfImg;                              // PH ring stride
-    static constexpr unsigned OFF_AP = 2 * kA_BYTES;
+    static constexpr unsigned OFF_AP = 0;
     static constexpr unsigned OFF_PH = OFF_AP + kApBytes;
     static constexpr unsigned OFF_B = OFF_PH + NP * PS;
     static constexpr unsigned BYTES = OFF_B + NBB * BS;
 };
 
-// Contraction of one stage: 8 MMAs of K = 16 (BF16) into columns 0..N-1.
+// Contraction of one stage: 8 MMAs of K = 16 (BF16) into columns 0..N-1, A (the encoding
+// tile) read from TMEM at `ta` (8 columns per K step), B from shared memory.
 template <int N>
-__device__ __forceinline__ void contraction_mma(uint32_t tmem, uint64_t da, uint64_t db, bool first) {
+__device__ __forceinline__ void contraction_mma(uint32_t tmem, uint32_t ta, uint64_t db, bool first) {
     constexpr uint32_t ID = tc::idesc_f16(kRows, N, 1);
 #pragma unroll
     for (int kk = 0; kk < 8; ++kk) {
-        const uint32_t koff = (uint32_t)((kk >> 2) * (kRows * 128) + (kk & 3) * 32);
         const uint32_t kofb = (uint32_t)((kk >> 2) * (N * 128) + (kk & 3) * 32);
-        tc::mma_f16(tmem, tc::sdesc_advance(da, koff), tc::sdesc_advance(db, kofb), ID, !(first && kk == 0));
+        tc::mma_f16_ts(tmem, ta + 8u * (uint32_t)kk, tc::sdesc_advance(db, kofb), ID, !(first && kk == 0));
     }
 }
 
@@ -190,8 +197,8 @@ __device__ __forceinline__ void tcp_contraction_item(TcShared &sh, uint32_t tmem
         if (!wait_or_abort(&sh.afull[sa], (g >> 1) & 1, &sh.abort_flag, status)) return;
         if (!wait_or_abort(&sh.bfull[sb], (g / NBB) & 1, &sh.abort_flag, status)) return;
         tc::fence_after_sync();
-        contraction_mma<N>(tmem, tc::sdesc_k128(smem_u32(base + sa * kA_BYTES)),
-                           tc::sdesc_k128(smem_u32(base + PL::OFF_B + sb * PL::BS)), it == 0);
+        contraction_mma<N>(tmem, tmem + a_col(sa), tc::sdesc_k128(smem_u32(base + PL::OFF_B + sb * PL::BS)),
+                           it == 0);
         tc::mma_commit(&sh.afree[sa]);
         tc::mma_commit(&sh.bfree[sb]);
     }
@@ -237,12 +244,12 @@ __device__ __forceinline__ void tcp_teardown(TcShared &sh, int tid, int warp, in
 // One generator thread's part of a stage (generators work in two groups of 8 warps that take
 // alternate stages; warp w of a group reads TMEM lanes 32 (w & 3) .. + 31 and owns the 32
 // columns 32 (w >> 2) .. + 31): its row's 32 phase offsets (TMEM; the tile is released to the
-// phase thread right after the read) plus the reference phases -> E (or conj E) as BF16 in 8
-// chunks of the A tile.  Forward: one reference phase per row (fsrc[0]); adjoint: one per
-// column (fsrc[0..31]).
+// phase thread right after the read) plus the reference phases -> E (or conj E) as BF16, one
+// (re, im) pair per TMEM column of its row of the A tile at `ta`.  Forward: one reference phase
+// per row (fsrc[0]); adjoint: one per column (fsrc[0..31]).
 template <bool CONJ>
-__device__ __forceinline__ bool generate_row(TcShared &sh, int g, uint32_t taddr, const float *fsrc,
-                                             unsigned char *A, int row, int ch, int *status) {
+__device__ __forceinline__ bool generate_row(TcShared &sh, int g, uint32_t taddr, const float *fsrc, uint32_t ta,
+                                             int *status) {
     float ph[32];
     tc::tmem_ld<32>(taddr, ph);
     tc::tmem_ld_wait();
@@ -280,12 +287,8 @@ __device__ __forceinline__ bool generate_row(TcShared &sh, int g, uint32_t taddr
     bool ok = g < 2 || wait_or_abort(&sh.afree[g & 1], ((g - 2) >> 1) & 1, &sh.abort_flag, status);
     if (!__all_sync(0xffffffffu, ok)) return false;
     tc::fence_after_sync();
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int j = 8 * ch + c;  // chunk of 4 columns: atom j >> 3, swizzle column j & 7
-        *reinterpret_cast<uint4 *>(A + (j >> 3) * (kRows * 128) + tc::swz128(row, j & 7)) =
-            make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
-    }
+    tc::tmem_st32(ta, w);
+    tc::tmem_st_wait();
     return true;
 }
 
@@ -366,12 +369,11 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
                 if ((g & 1) != grp) continue;
                 if (!gen_waits<NBB>(sh, g, status)) break;  // warp-uniform exit
                 tc::fence_after_sync();
-                if (!generate_row<false>(sh, g,
-                                    tmem + ((uint32_t)(32 * (warp & 3)) << 16) + phase_col(g) + (uint32_t)(32 * ch),
+                const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
+                if (!generate_row<false>(sh, g, tmem + lanes + phase_col(g) + (uint32_t)(32 * ch),
                                     reinterpret_cast<const float *>(gbase + PL::OFF_B + sb * PL::BS + PL::B_BYTES) + row,
-                                    gbase + sa * kA_BYTES, row, ch, status))
+                                    tmem + lanes + a_col(sa) + (uint32_t)(32 * ch), status))
                     break;  // warp-uniform exit
-                tc::fence_proxy_async_smem();
                 tc::fence_before_sync();
                 tc::mbar_arrive(&sh.afull[sa]);
             }
@@ -480,13 +482,12 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
                 if ((g & 1) != grp) continue;
                 if (!gen_waits<NBB>(sh, g, status)) break;  // warp-uniform exit
                 tc::fence_after_sync();
-                if (!generate_row<true>(sh, g,
-                                   tmem + ((uint32_t)(32 * (warp & 3)) << 16) + phase_col(g) + (uint32_t)(32 * ch),
+                const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
+                if (!generate_row<true>(sh, g, tmem + lanes + phase_col(g) + (uint32_t)(32 * ch),
                                    reinterpret_cast<const float *>(gbase + PL::OFF_B + sb * PL::BS + PL::B_BYTES + th * FT) +
                                        32 * ch,
-                                   gbase + sa * kA_BYTES, row, ch, status))
+                                   tmem + lanes + a_col(sa) + (uint32_t)(32 * ch), status))
                     break;  // warp-uniform exit
-                tc::fence_proxy_async_smem();
                 tc::fence_before_sync();
                 tc::mbar_arrive(&sh.afull[sa]);
             }
