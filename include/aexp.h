@@ -163,8 +163,10 @@ typedef struct aexp_recon_opts {
                                forward thread and two voxels per adjoint thread at 2 blocks per
                                SM (default: one each at 4 blocks per SM); BF16 form: a 6-deep
                                contraction-operand ring and 4 phase-operand stages (default 4
-                               and 3).  The FP16 hi+lo form has one tiling.  aexp_autotune picks
-                               it; a workspace must be used with the tiling it was prepared for */
+                               and 3); FP16 hi+lo form: the phase sums on the CUDA cores
+                               (default: on the tensor cores, like the BF16 form).  aexp_autotune
+                               picks it; a workspace must be used with the tiling it was prepared
+                               for */
 } aexp_recon_opts;
 
 /* Fill opts with defaults: FP32, Haar, 3 levels, 30 power iterations, estimate L_f,

@@ -49,6 +49,8 @@ struct WsHeader {
     unsigned red_ticket;
     int pad2;
     double red_part[2 * 128];
+    // FP16 hi+lo form: per-term power-of-two scale of the phase-GEMM operands (k_l 2^s_l, dh_l 2^-s_l)
+    float kscale[32];
 };
 constexpr int kRedMaxBlocks = 128;  // blocks of one dot_norm_f64 launch (WsHeader::red_part)
 
@@ -180,13 +182,14 @@ ProbDesc make_op_desc(const OpLayout &L, char *ws);
 cudaError_t write_desc(const ProbDesc &d, ProbDesc *dst, cudaStream_t st);
 int num_sms();
 
-// BF16 form with the phase on the tensor cores (op_tc_phase.cu): operand preparation and the
-// launches (same contract as batch_forward_tc / batch_adjoint_tc).
+// Tensor-core forms with the phase on the tensor cores (op_tc_phase.cu): operand preparation
+// and the launches (same contract as batch_forward_tc / batch_adjoint_tc).  BF16: variant =
+// tiling 0 (B ring 4, phase ring 3) or 1 (B ring 6, phase ring 4); FP16 hi+lo: tiling 0 (the
+// FP16 hi+lo form with CUDA-core phases, op_tc.cu, is its tiling 1).
 cudaError_t op_prepare_phase_operands(const OpLayout &L, char *ws, cudaStream_t st);
-// variant: tiling 0 (B ring 4, phase ring 3) or 1 (B ring 6, phase ring 4)
-cudaError_t tcp_forward(int CB, int variant, const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *x,
+cudaError_t tcp_forward(int precision, int CB, int variant, const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *x,
                         int src, const int *item_off, int total_items, int *counter, cudaStream_t st);
-cudaError_t tcp_adjoint(int CB, int variant, const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *yt,
+cudaError_t tcp_adjoint(int precision, int CB, int variant, const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *yt,
                         int src, const int *item_off, int total_items, int *counter, cudaStream_t st);
 constexpr size_t kPhaseBlockBytes = 16384;  // 128 rows x 128 B: BF16 hi (32 K slots) | lo (32 K slots)
 

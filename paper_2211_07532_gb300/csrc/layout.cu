@@ -96,7 +96,7 @@ int op_layout(const aexp_problem *p, int precision, OpLayout *L, int target_item
     o.off_ypk = take(precision == AEXP_FP32 ? 0 : npk * sizeof(float2) * (size_t)o.ntp * o.CB);
     o.off_desc = take(sizeof(ProbDesc));
     o.off_hp = take(sizeof(float) * (size_t)o.LP * o.nr_pad);
-    const bool tcp = precision == AEXP_BF16_TC;
+    const bool tcp = precision != AEXP_FP32;  // the phase-GEMM operands of both tensor-core forms
     o.off_kph = take(tcp ? (size_t)(o.ntp / 128) * kPhaseBlockBytes : 0);
     o.off_dhph = take(tcp ? (size_t)cdiv(o.ntiles, 2) * kPhaseBlockBytes : 0);
     o.fwd_items = o.fwd_tblocks * o.fwd_splits;

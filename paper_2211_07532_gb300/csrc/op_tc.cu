@@ -587,54 +587,6 @@ __global__ void __launch_bounds__(kHlThreads, 1)
     tc_teardown(sh, warp, TMEM_COLS, last_issued, &pd[0].hdr->status);
 }
 
-// ---- FP16 hi+lo: largest component of the operand to be packed (atomic max on the bit
-// pattern of a non-negative float, which orders like the value) ----
-__global__ void amax_reset_kernel(const ProbDesc *__restrict__ pd, int nprob, int which) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < nprob) pd[q].hdr->amax[which] = 0u;
-}
-
-__device__ __forceinline__ void amax_commit(float m, unsigned *slot) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(slot, __float_as_uint(m));
-}
-
-// max |Re|, |Im| of b_c(v) = S_c(v) x(v); thread = (voxel in tile order, pair of coils)
-template <int CB>
-__global__ void amax_b_kernel(const ProbDesc *__restrict__ pd, const float2 *__restrict__ x, int src) {
-    const ProbDesc &P = pd[blockIdx.y];
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    float m = 0.f;
-    if (i < (size_t)P.ntiles * kTileVox * (CB / 2)) {
-        const float2 *img = x ? x : P.vec[src];
-        const int p = (int)(i / (CB / 2));
-        const int tile = p / kTileVox, v = p % kTileVox;
-        const int ix = (tile % P.ntx) * kTileSide + v % kTileSide, iy = (tile / P.ntx) * kTileSide + v / kTileSide;
-        if (ix < P.nx && iy < P.ny) {
-            const float4 s = reinterpret_cast<const float4 *>(P.Sp)[i];
-            const float2 xv = img[(size_t)iy * P.nx + ix];
-            m = fmaxf(fmaxf(fabsf(s.x * xv.x - s.y * xv.y), fabsf(s.x * xv.y + s.y * xv.x)),
-                      fmaxf(fabsf(s.z * xv.x - s.w * xv.y), fabsf(s.z * xv.y + s.w * xv.x)));
-        }
-    }
-    amax_commit(m, &P.hdr->amax[0]);
-}
-
-// max |Re|, |Im| of the sample-major k-space yt[t][CB] (or vec[src], or rt when src < 0)
-template <int CB>
-__global__ void amax_y_kernel(const ProbDesc *__restrict__ pd, const float2 *__restrict__ yt, int src) {
-    const ProbDesc &P = pd[blockIdx.y];
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    float m = 0.f;
-    if (i < (size_t)P.ntp * (CB / 2)) {
-        const float2 *y = yt ? yt : (src >= 0 ? P.vec[src] : P.rt);
-        const float4 v = reinterpret_cast<const float4 *>(y)[i];
-        m = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
-    }
-    amax_commit(m, &P.hdr->amax[1]);
-}
-
 // Reductions of the planar forward partials [split][t][re(0..C) | im(0..C)].
 __global__ void fwd_reduce_planar_public_kernel(const float *part, int splits, int ntp, int CB, int nt, int nc,
                                                 float2 *y) {
@@ -689,7 +641,7 @@ cudaError_t launch_fwd_tc(const ProbDesc *pd, int nprob, int max_pack_blocks, co
                           const int *item_off, int total_items, int *counter, cudaStream_t st) {
     amax_reset_kernel<<<cdiv(nprob, 256), 256, 0, st>>>(pd, nprob, 0);
     amax_b_kernel<CB><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, x, src);
-    pack_b_fwd_kernel<CB, true><<<dim3(pack_grid(max_pack_blocks, CB), nprob), 256, 0, st>>>(pd, x, src);
+    pack_b_fwd_kernel<CB, kPackHL><<<dim3(pack_grid(max_pack_blocks, CB), nprob), 256, 0, st>>>(pd, x, src);
     auto kern = fwd_tc_kernel<CB, LP>;
     const size_t smem = fwd_tc_smem<CB, LP>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -704,7 +656,7 @@ cudaError_t launch_adj_tc(const ProbDesc *pd, int nprob, int max_pack_blocks, co
                           const int *item_off, int total_items, int *counter, cudaStream_t st) {
     amax_reset_kernel<<<cdiv(nprob, 256), 256, 0, st>>>(pd, nprob, 1);
     amax_y_kernel<CB><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, yt, src);
-    pack_y_adj_kernel<CB, true><<<dim3(pack_grid(max_pack_blocks, CB), nprob), 256, 0, st>>>(pd, yt, src);
+    pack_y_adj_kernel<CB, kPackHL><<<dim3(pack_grid(max_pack_blocks, CB), nprob), 256, 0, st>>>(pd, yt, src);
     auto kern = adj_tc_kernel<CB, LP>;
     const size_t smem = adj_tc_smem<CB, LP>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -745,8 +697,8 @@ cudaError_t op_forward_tc(const OpLayout &L, const float2 *x, char *ws, cudaStre
     const int CBv = L.CB, LPv = L.LP;
     WsHeader *hdr = (WsHeader *)(ws + L.off_hdr);
     const ProbDesc *pd = (const ProbDesc *)(ws + L.off_desc);
-    if (L.precision == AEXP_BF16_TC)
-        return tcp_forward(L.CB, L.variant, pd, 1, fwd_pack_blocks(L.ntiles, L.CB), x, 0, &hdr->item_off[0], L.fwd_items,
+    if (L.precision == AEXP_BF16_TC || L.variant == 0)
+        return tcp_forward(L.precision, L.CB, L.variant, pd, 1, fwd_pack_blocks(L.ntiles, L.CB), x, 0, &hdr->item_off[0], L.fwd_items,
                            &hdr->counter[0], st);
     AEXP_TC_DISPATCH(launch_fwd_tc, pd, 1, fwd_pack_blocks(L.ntiles, L.CB), x, 0, &hdr->item_off[0], L.fwd_items,
                      &hdr->counter[0], st)
@@ -756,8 +708,8 @@ cudaError_t op_adjoint_tc(const OpLayout &L, const float2 *yt, char *ws, cudaStr
     const int CBv = L.CB, LPv = L.LP;
     WsHeader *hdr = (WsHeader *)(ws + L.off_hdr);
     const ProbDesc *pd = (const ProbDesc *)(ws + L.off_desc);
-    if (L.precision == AEXP_BF16_TC)
-        return tcp_adjoint(L.CB, L.variant, pd, 1, adj_pack_blocks(L.ntp, L.CB), yt, -1, &hdr->item_off[2], L.adj_items,
+    if (L.precision == AEXP_BF16_TC || L.variant == 0)
+        return tcp_adjoint(L.precision, L.CB, L.variant, pd, 1, adj_pack_blocks(L.ntp, L.CB), yt, -1, &hdr->item_off[2], L.adj_items,
                            &hdr->counter[1], st);
     AEXP_TC_DISPATCH(launch_adj_tc, pd, 1, adj_pack_blocks(L.ntp, L.CB), yt, -1, &hdr->item_off[2], L.adj_items,
                      &hdr->counter[1], st)
@@ -767,8 +719,8 @@ cudaError_t batch_forward_tc(int precision, int CB, int LP, int variant, const P
                              int max_pack_blocks, int src, const int *item_off, int total_items, int *counter,
                              cudaStream_t st) {
     const int CBv = CB, LPv = LP;
-    if (precision == AEXP_BF16_TC)
-        return tcp_forward(CB, variant, pd, nprob, max_pack_blocks, nullptr, src, item_off, total_items, counter, st);
+    if (precision == AEXP_BF16_TC || variant == 0)
+        return tcp_forward(precision, CB, variant, pd, nprob, max_pack_blocks, nullptr, src, item_off, total_items, counter, st);
     AEXP_TC_DISPATCH(launch_fwd_tc, pd, nprob, max_pack_blocks, nullptr, src, item_off, total_items, counter, st)
 }
 
@@ -776,8 +728,8 @@ cudaError_t batch_adjoint_tc(int precision, int CB, int LP, int variant, const P
                              int max_pack_blocks, int src, const int *item_off, int total_items, int *counter,
                              cudaStream_t st) {
     const int CBv = CB, LPv = LP;
-    if (precision == AEXP_BF16_TC)
-        return tcp_adjoint(CB, variant, pd, nprob, max_pack_blocks, nullptr, src, item_off, total_items, counter, st);
+    if (precision == AEXP_BF16_TC || variant == 0)
+        return tcp_adjoint(precision, CB, variant, pd, nprob, max_pack_blocks, nullptr, src, item_off, total_items, counter, st);
     AEXP_TC_DISPATCH(launch_adj_tc, pd, nprob, max_pack_blocks, nullptr, src, item_off, total_items, counter, st)
 }
 

@@ -167,7 +167,7 @@ cudaError_t op_prepare(const aexp_problem *p, const OpLayout &L, char *ws, cudaS
     size_t n = (size_t)L.nr_pad * L.CB;
     prep_coil_kernel<<<(unsigned)((n + T - 1) / T), T, 0, st>>>((const float2 *)p->S, L.nc, L.nx, L.ny, L.ntx,
                                                                L.nr_pad, L.CB, Sp);
-    if (L.precision == AEXP_BF16_TC) {
+    if (L.precision != AEXP_FP32) {
         cudaError_t e = op_prepare_phase_operands(L, ws, st);
         if (e != cudaSuccess) return e;
     }

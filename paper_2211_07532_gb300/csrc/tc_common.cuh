@@ -44,14 +44,19 @@ __device__ __forceinline__ void split_f16(float a, float b, uint32_t &hi, uint32
 }
 
 // Power-of-two scale 2^e (or 2^-e when `inverse`) that maps a largest component with bit
-// pattern `bits` into [2^13, 2^14); zero (or subnormal) maxima give the largest scale, a
-// non-finite one a small scale (the non-finite values then propagate).
-__device__ __forceinline__ float hl_scale(unsigned bits, bool inverse) {
+// pattern `bits` into [2^top, 2^(top+1)) (top = 13 by default); zero (or subnormal) maxima give
+// the largest scale, a non-finite one a small scale (the non-finite values then propagate).
+__device__ __forceinline__ float hl_scale(unsigned bits, bool inverse, int top = 13) {
     const int ex = (int)((bits >> 23) & 0xffu);
-    int se = 140 - max(ex, 1);  // 13 - (ex - 127)
+    int se = 127 + top - max(ex, 1);  // top - (ex - 127)
     se = max(-126, min(126, se));
     return __int_as_float((127 + (inverse ? -se : se)) << 23);
 }
+// Operand packing of the contraction's B operand: BF16; FP16 hi | lo' (lo' = 2^11 (v - hi));
+// FP16 hi2 | lo' with hi2 = 2^11 hi (the FP16 hi+lo form whose phases come from the tensor
+// cores: one accumulator takes A_hi B_hi2 + A_hi B_lo' + A_lo B_hi2 = 2^11 A B, see op_tc_phase.cu).
+enum PackMode { kPackBF16 = 0, kPackHL = 1, kPackHL2 = 2 };
+constexpr int kHl2Top = 3;  // kPackHL2: the operand is scaled below 2^4, so that 2^11 hi < 2^15
 
 // Bounded wait that also gives up as soon as another thread of the CTA has aborted.
 __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, unsigned parity, volatile int *abort_flag,
@@ -171,19 +176,28 @@ __device__ __forceinline__ void tc_teardown(TcShared &sh, int warp, uint32_t nco
 // problems (grid.y = problem; blocks beyond a problem's extent return at once)
 // ---------------------------------------------------------------------------
 
-// Four (first, second) pairs -> one 16-byte chunk of the B image(s) at `dst` (FP16 hi+lo:
-// hi at dst, lo' one image of `img_bytes` further).
-template <bool HL>
+// Four (first, second) pairs -> one 16-byte chunk of the B image(s) at `dst` in mode MODE
+// (FP16 forms: hi or hi2 at dst, lo' one image of `img_bytes` further).
+template <int MODE>
 __device__ __forceinline__ void store_b_chunk(unsigned char *dst, unsigned img_bytes, const float (&a)[4],
                                               const float (&b)[4]) {
     uint32_t w[4], wl[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        if constexpr (HL) split_f16(a[u], b[u], w[u], wl[u]);
-        else w[u] = pack_bf16(a[u], b[u]);
+        if constexpr (MODE == kPackBF16) {
+            w[u] = pack_bf16(a[u], b[u]);
+        } else {
+            split_f16(a[u], b[u], w[u], wl[u]);
+            if constexpr (MODE == kPackHL2) {  // hi2 = 2^11 hi: exact (a power of two, below 2^15)
+                __half2 h = *reinterpret_cast<const __half2 *>(&w[u]);
+                h = __hmul2(h, __float2half2_rn(kLoScale));
+                w[u] = *reinterpret_cast<const uint32_t *>(&h);
+            }
+        }
     }
     *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
-    if constexpr (HL) *reinterpret_cast<uint4 *>(dst + img_bytes) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+    if constexpr (MODE != kPackBF16)
+        *reinterpret_cast<uint4 *>(dst + img_bytes) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
 }
 
 // Shared staging of one tile (64 voxels) or stage (64 samples) of C coil values, coil-major
@@ -206,15 +220,15 @@ inline int pack_grid(int amax_blocks, int CB) { return amax_blocks * 8 / CB; }
 // tile's coil maps are read coalesced (coils fastest) into shared memory, then every thread
 // writes 16-byte chunks of the swizzled operand rows (a row's chunks across the lanes, so
 // that the global writes are coalesced).
-template <int CB, bool HL>
+template <int CB, int MODE>
 __global__ void __launch_bounds__(256) pack_b_fwd_kernel(const ProbDesc *__restrict__ pd, const float2 *__restrict__ x,
                                                          int src) {
     constexpr int N = 2 * CB;
-    constexpr int NPK = HL ? 2 : 1;
+    constexpr int NPK = MODE != kPackBF16 ? 2 : 1;
     __shared__ float2 sb[CB * kStageRow];
     const ProbDesc &P = pd[blockIdx.y];
     const float2 *img = x ? x : P.vec[src];
-    const float sc = HL ? hl_scale(P.hdr->amax[0], false) : 1.f;
+    const float sc = MODE != kPackBF16 ? hl_scale(P.hdr->amax[0], false, MODE == kPackHL2 ? kHl2Top : 13) : 1.f;
     for (int tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
         const int tx = (tile % P.ntx) * kTileSide, ty = (tile / P.ntx) * kTileSide;
         for (int k = threadIdx.x; k < kTileVox * CB; k += blockDim.x) {
@@ -241,7 +255,7 @@ __global__ void __launch_bounds__(256) pack_b_fwd_kernel(const ProbDesc *__restr
             }
             unsigned char *dst =
                 P.bpk + (size_t)tile * (NPK * N * 256) + (jj >> 3) * (N * 128) + tc::swz128(n, jj & 7);
-            store_b_chunk<HL>(dst, N * 256, a, b);
+            store_b_chunk<MODE>(dst, N * 256, a, b);
         }
         __syncthreads();
     }
@@ -252,16 +266,16 @@ __global__ void __launch_bounds__(256) pack_b_fwd_kernel(const ProbDesc *__restr
 // (2s, 2s+1).  FP16 hi+lo: y is scaled by the power of two fixed by amax[1].  One block per
 // stage (grid-stride): the stage's 64 x C values are contiguous and read coalesced into shared
 // memory, then written as 16-byte chunks of the swizzled operand rows.
-template <int CB, bool HL>
+template <int CB, int MODE>
 __global__ void __launch_bounds__(256) pack_y_adj_kernel(const ProbDesc *__restrict__ pd, const float2 *__restrict__ yt,
                                                          int src) {
     constexpr int N = 2 * CB;
-    constexpr int NPK = HL ? 2 : 1;
+    constexpr int NPK = MODE != kPackBF16 ? 2 : 1;
     __shared__ float2 sy[CB * kStageRow];
     const ProbDesc &P = pd[blockIdx.y];
     const int nstages = P.ntp / kCols;
     const float2 *y = yt ? yt : (src >= 0 ? P.vec[src] : P.rt);
-    const float sc = HL ? hl_scale(P.hdr->amax[1], false) : 1.f;
+    const float sc = MODE != kPackBF16 ? hl_scale(P.hdr->amax[1], false, MODE == kPackHL2 ? kHl2Top : 13) : 1.f;
     for (int st = blockIdx.x; st < nstages; st += gridDim.x) {
         for (int k = threadIdx.x; k < kCols * CB; k += blockDim.x) {
             float2 v = y[(size_t)st * kCols * CB + k];
@@ -281,10 +295,58 @@ __global__ void __launch_bounds__(256) pack_y_adj_kernel(const ProbDesc *__restr
                 b[u] = n < CB ? -v.y : v.x;
             }
             unsigned char *dst = P.ypk + (size_t)st * (NPK * N * 256) + (jj >> 3) * (N * 128) + tc::swz128(n, jj & 7);
-            store_b_chunk<HL>(dst, N * 256, a, b);
+            store_b_chunk<MODE>(dst, N * 256, a, b);
         }
         __syncthreads();
     }
+}
+
+// ---- FP16 hi+lo: largest component of the operand to be packed (atomic max on the bit
+// pattern of a non-negative float, which orders like the value) ----
+__global__ void amax_reset_kernel(const ProbDesc *__restrict__ pd, int nprob, int which) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nprob) pd[q].hdr->amax[which] = 0u;
+}
+
+__device__ __forceinline__ void amax_commit(float m, unsigned *slot) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(slot, __float_as_uint(m));
+}
+
+// max |Re|, |Im| of b_c(v) = S_c(v) x(v); thread = (voxel in tile order, pair of coils)
+template <int CB>
+__global__ void amax_b_kernel(const ProbDesc *__restrict__ pd, const float2 *__restrict__ x, int src) {
+    const ProbDesc &P = pd[blockIdx.y];
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float m = 0.f;
+    if (i < (size_t)P.ntiles * kTileVox * (CB / 2)) {
+        const float2 *img = x ? x : P.vec[src];
+        const int p = (int)(i / (CB / 2));
+        const int tile = p / kTileVox, v = p % kTileVox;
+        const int ix = (tile % P.ntx) * kTileSide + v % kTileSide, iy = (tile / P.ntx) * kTileSide + v / kTileSide;
+        if (ix < P.nx && iy < P.ny) {
+            const float4 s = reinterpret_cast<const float4 *>(P.Sp)[i];
+            const float2 xv = img[(size_t)iy * P.nx + ix];
+            m = fmaxf(fmaxf(fabsf(s.x * xv.x - s.y * xv.y), fabsf(s.x * xv.y + s.y * xv.x)),
+                      fmaxf(fabsf(s.z * xv.x - s.w * xv.y), fabsf(s.z * xv.y + s.w * xv.x)));
+        }
+    }
+    amax_commit(m, &P.hdr->amax[0]);
+}
+
+// max |Re|, |Im| of the sample-major k-space yt[t][CB] (or vec[src], or rt when src < 0)
+template <int CB>
+__global__ void amax_y_kernel(const ProbDesc *__restrict__ pd, const float2 *__restrict__ yt, int src) {
+    const ProbDesc &P = pd[blockIdx.y];
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float m = 0.f;
+    if (i < (size_t)P.ntp * (CB / 2)) {
+        const float2 *y = yt ? yt : (src >= 0 ? P.vec[src] : P.rt);
+        const float4 v = reinterpret_cast<const float4 *>(y)[i];
+        m = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
+    }
+    amax_commit(m, &P.hdr->amax[1]);
 }
 
 }  // namespace

@@ -45,9 +45,10 @@ std::vector<int> tune_key(const aexp_problem *probs, int nprob, int precision) {
     return k;
 }
 
-// the tilings worth timing: the FP32 form has two at 32 coils (padded), BF16 two, FP16 hi+lo one
+// the tilings worth timing: the FP32 form has two at 32 coils (padded), BF16 two (ring depths),
+// FP16 hi+lo two (phases on the tensor cores or on the CUDA cores)
 int tile_variants(const aexp_problem *probs, int precision) {
-    if (precision == AEXP_BF16_TC) return kTileVariants;
+    if (precision != AEXP_FP32) return kTileVariants;
     if (precision == AEXP_FP32) {
         OpLayout L;
         op_layout(probs, precision, &L);
