@@ -198,9 +198,9 @@ __global__ void prep_dhph_kernel(const float *__restrict__ dh, int ntiles, int L
 
 // ---- kernels ----
 
-// Warp roles: 16 generator warps; warp 16 issues the contraction MMAs and owns TMEM; warp 17
-// loads the contraction operands (+ reference phases); warp 18 issues the phase MMAs; warp 19
-// loads the phase operands.  One lane of each non-generator warp works.
+// Warp roles: 16 generator warps; warp 16 issues the contraction MMAs and owns TMEM (the whole
+// warp runs its loop, lane 0 issues); warp 17 loads the contraction operands (+ reference
+// phases); warp 18 issues the phase MMAs; warp 19 loads the phase operands (one lane each).
 constexpr int kMmaWarp = kTcGen / 32;
 constexpr int kLoadBWarp = kMmaWarp + 1;
 constexpr int kPhaseWarp = kMmaWarp + 2;
@@ -286,31 +286,38 @@ __device__ __forceinline__ void phase_mma(int ks, uint32_t d, uint64_t a, uint64
 __device__ __forceinline__ uint32_t set_col(int c) { return 64u * (uint32_t)(c & 1); }
 constexpr int kChunk = 4;  // 96 MMAs per chunk
 
-// Contraction thread, one item.  FP16 hi+lo: `cbase` counts the CTA's chunks before this item;
-// a set is reused for chunk c once the promotion of chunk c - 2 has released it.
+// Contraction warp, one item: the whole warp runs the loop and waits, lane 0 (elected) issues the
+// MMAs and commits.  FP16 hi+lo: `cbase` counts the CTA's chunks before this item; a set is
+// reused for chunk c once the promotion of chunk c - 2 has released it.
 template <int F, int N, int NBB, int NP>
 __device__ __forceinline__ void tcp_contraction_item(TcShared &sh, uint32_t tmem, unsigned char *base, int gs, int n,
                                                      int cbase, int *status) {
     using PL = TcpPlan<F, N, NBB, NP>;
+    const bool leader = tc::elect_lane0();
     for (int it = 0; it < n; ++it) {
         const int g = gs + it, sa = g & 1, sb = g % NBB;
         uint32_t acc = tmem;
         bool first = it == 0;
+        bool ok = true;
         if constexpr (F == 1) {
             const int c = cbase + it / kChunk;
             first = it % kChunk == 0;
-            if (first && c >= 2 && !wait_or_abort(&sh.accfree[c & 1], ((c - 2) >> 1) & 1, &sh.abort_flag, status))
-                return;
+            if (first && c >= 2) ok = wait_or_abort(&sh.accfree[c & 1], ((c - 2) >> 1) & 1, &sh.abort_flag, status);
             acc = tmem + set_col(c);
         }
-        if (!wait_or_abort(&sh.afull[sa], (g >> 1) & 1, &sh.abort_flag, status)) return;
-        if (!wait_or_abort(&sh.bfull[sb], (g / NBB) & 1, &sh.abort_flag, status)) return;
+        if (ok) ok = wait_or_abort(&sh.afull[sa], (g >> 1) & 1, &sh.abort_flag, status);
+        if (ok) ok = wait_or_abort(&sh.bfull[sb], (g / NBB) & 1, &sh.abort_flag, status);
+        if (!__all_sync(0xffffffffu, ok)) return;
         tc::fence_after_sync();
-        contraction_mma<F, N>(acc, tmem + a_col<F>(sa), tc::sdesc_k128(smem_u32(base + PL::OFF_B + sb * PL::BS)), first);
-        tc::mma_commit(&sh.afree[sa]);
-        tc::mma_commit(&sh.bfree[sb]);
+        if (leader) {
+            contraction_mma<F, N>(acc, tmem + a_col<F>(sa), tc::sdesc_k128(smem_u32(base + PL::OFF_B + sb * PL::BS)),
+                                  first);
+            tc::mma_commit(&sh.afree[sa]);
+            tc::mma_commit(&sh.bfree[sb]);
+        }
+        __syncwarp();
     }
-    if (n > 0) tc::mma_commit(&sh.accdone);  // the item's accumulators are final
+    if (n > 0 && leader) tc::mma_commit(&sh.accdone);  // the item's accumulators are final
 }
 
 // Phase thread, one item: the phases of stage g go into tile g % PH_BUFS once the generators
@@ -517,7 +524,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
 
         if (warp >= kMmaWarp) {
             const bool lead = (tid & 31) == 0;
-            if (warp == kMmaWarp && lead) {
+            if (warp == kMmaWarp) {  // the whole warp (see tcp_contraction_item)
                 tcp_contraction_item<F, N, NBB, NP>(sh, tmem, gbase, gs, ntl, cbase, status);
             } else if (warp == kPhaseWarp && lead) {
                 tcp_phase_item<F, N, NBB, NP>(sh, tmem, gbase, gs, ntl, iter, (P.LP + 15) >> 4, status);
@@ -655,7 +662,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
 
         if (warp >= kMmaWarp) {
             const bool lead = (tid & 31) == 0;
-            if (warp == kMmaWarp && lead) {
+            if (warp == kMmaWarp) {  // the whole warp (see tcp_contraction_item)
                 tcp_contraction_item<F, N, NBB, NP>(sh, tmem, gbase, gs, nst, cbase, status);
             } else if (warp == kPhaseWarp && lead) {
                 tcp_phase_item<F, N, NBB, NP>(sh, tmem, gbase, gs, nst, iter, (P.LP + 15) >> 4, status);

@@ -21,6 +21,16 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
+// ---- one issuing lane of a converged warp ----
+// True in lane 0 when elect.sync (full mask, so the whole warp must execute it) elects lane 0.
+// Issuing the MMAs from a warp that runs the loop converged, instead of from one diverged lane,
+// lets the compiler keep the descriptors warp-uniform.
+__device__ __forceinline__ bool elect_lane0() {
+    uint32_t e = 0;
+    asm volatile("{\n\t.reg .pred P;\n\telect.sync _|P, 0xffffffff;\n\tselp.b32 %0, 1, 0, P;\n\t}" : "=r"(e));
+    return e != 0 && (threadIdx.x & 31) == 0;
+}
+
 // ---- ordering between thread barriers and tcgen05 operations ----
 __device__ __forceinline__ void fence_before_sync() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
