@@ -89,11 +89,12 @@ def test_autotune_refuses_capture(ax):
                 ax.autotune(prob, opts, ws=ws)
 
 
-@pytest.mark.parametrize("precision", ["FP32", "BF16_TC"])
+@pytest.mark.parametrize("precision", ["FP32", "BF16_TC", "FP16X2_TC"])
 def test_tiling_variant_matches_oracle(ax, precision):
     """The alternative tiling (FP32 at 32 coils: two samples / voxels per thread; BF16: deeper
-    rings) computes the same reconstruction: FP32 within the FP32 bar, BF16 within 3x the
-    oracle's BF16 rounding emulation, as the default tiling."""
+    rings; FP16 hi+lo: phases on the CUDA cores) computes the same reconstruction: FP32 and FP16
+    hi+lo within the FP32 bar, BF16 within 3x the oracle's BF16 rounding emulation, as the
+    default tiling."""
     import torch
     import oracle
     from oracle import precision as prec_emul
@@ -112,7 +113,7 @@ def test_tiling_variant_matches_oracle(ax, precision):
         torch.cuda.synchronize()
     ref = recon.fista(p, y, lam, 10, Lf, "db4", 2)
     e = rel(x.cpu().numpy(), ref)
-    if precision == "FP32":
+    if precision in ("FP32", "FP16X2_TC"):
         bar = 1e-5
     else:
         bar = 3.0 * rel(recon.fista(p, y, lam, 10, Lf, "db4", 2, ops=prec_emul.bf16_operators(p)), ref)
