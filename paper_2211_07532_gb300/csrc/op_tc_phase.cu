@@ -214,7 +214,8 @@ constexpr int kTcpThreads = kTcGen + 128;
 
 // Shared-memory plan of both kernels (byte offsets from the 1024-aligned base; the generated
 // encoding tiles live in TMEM):
-//   AP item phase operand (hi | lo) | PH ring | B ring
+//   AP item phase operand (hi | lo) | PH ring | B ring | FP16 hi+lo forward: the item's promoted
+//   partial sums (128 rows x N floats, float4 c4 of row r at c4 * 128 + r: conflict-free)
 template <int F, int N, int NBB, int NP>
 struct TcpPlan {
     static_assert(NBB % 2 == 0, "each generator group must own its B slots");
@@ -226,7 +227,9 @@ struct TcpPlan {
     static constexpr unsigned OFF_AP = 0;
     static constexpr unsigned OFF_PH = OFF_AP + kApBytes;
     static constexpr unsigned OFF_B = OFF_PH + NP * PS;
-    static constexpr unsigned BYTES = OFF_B + NBB * BS;
+    static constexpr unsigned OFF_ACC = OFF_B + NBB * BS;
+    static constexpr unsigned ACC_BYTES = F == 1 ? kRows * N * 4 : 0;
+    static constexpr unsigned BYTES = OFF_ACC + ACC_BYTES;
     static_assert(BYTES + 1024 <= 227 * 1024, "shared memory");
 };
 
@@ -428,15 +431,12 @@ __device__ __forceinline__ bool gen_waits(TcShared &sh, int g, int *status) {
     return __all_sync(0xffffffffu, ok);
 }
 
-// FP16 hi+lo promotion, forward: (accumulator set at `ta`) x inv for this warp's 32 rows x N/2
-// columns, stored to (first chunk) or added into the partial sums `dst`.
+// FP16 hi+lo promotion, forward: (accumulator set at `ta`) x inv for this thread's row x N/2
+// columns, stored to (first chunk) or added into the item's partial sums in shared memory
+// (`dst`, this thread's float4 chunks `kRows` apart).
 template <int N>
 __device__ __forceinline__ void fwd_promote1(uint32_t ta, float inv, float4 *dst, bool add) {
     constexpr int CH = N / 2 < 16 ? N / 2 : 16;
-    // the partial sums are fetched before the TMEM reads, so that their latency overlaps
-    float4 q[N / 8];
-#pragma unroll
-    for (int c = 0; c < N / 8; ++c) q[c] = add ? dst[c] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int c0 = 0; c0 < N / 2; c0 += CH) {
         float v[CH];
@@ -445,18 +445,19 @@ __device__ __forceinline__ void fwd_promote1(uint32_t ta, float inv, float4 *dst
         tc::tmem_regs_ready<CH>(v);
 #pragma unroll
         for (int c = 0; c < CH / 4; ++c) {
-            const float4 p = q[c0 / 4 + c];
-            dst[c0 / 4 + c] = make_float4(fmaf(v[4 * c], inv, p.x), fmaf(v[4 * c + 1], inv, p.y),
-                                          fmaf(v[4 * c + 2], inv, p.z), fmaf(v[4 * c + 3], inv, p.w));
+            float4 *q = dst + (size_t)(c0 / 4 + c) * kRows;
+            const float4 p = add ? *q : make_float4(0.f, 0.f, 0.f, 0.f);
+            *q = make_float4(fmaf(v[4 * c], inv, p.x), fmaf(v[4 * c + 1], inv, p.y), fmaf(v[4 * c + 2], inv, p.z),
+                             fmaf(v[4 * c + 3], inv, p.w));
         }
     }
 }
 
 // Adjoint accumulator read-out: xr + i xi += sum_c conj(S_c) u_c over the coils of one
-// accumulator (set) at `ta` for this thread's voxel row (FP16 hi+lo: the scale is applied by
-// the caller once the chunks are summed).
+// accumulator (set) at `ta` for this thread's voxel row, its coil maps as float4 pairs `stride`
+// apart at `s4` (FP16 hi+lo: the scale is applied by the caller once the chunks are summed).
 template <int CB>
-__device__ __forceinline__ void adj_promote1(uint32_t ta, const float4 *s4, float &xr, float &xi) {
+__device__ __forceinline__ void adj_promote1(uint32_t ta, const float4 *s4, int stride, float &xr, float &xi) {
 #pragma unroll 1
     for (int c0 = 0; c0 < CB; c0 += 8) {
         float ur[8], ui[8];
@@ -467,7 +468,7 @@ __device__ __forceinline__ void adj_promote1(uint32_t ta, const float4 *s4, floa
         tc::tmem_regs_ready<8>(ui);
 #pragma unroll
         for (int q4 = 0; q4 < 4; ++q4) {
-            const float4 sv = s4[c0 / 2 + q4];
+            const float4 sv = s4[(size_t)(c0 / 2 + q4) * stride];
             xr = fmaf(sv.x, ur[2 * q4], xr);
             xr = fmaf(sv.y, ui[2 * q4], xr);
             xi = fmaf(sv.x, ui[2 * q4], xi);
@@ -556,6 +557,8 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
             const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
             // epilogue (warps 0-7 = group 0): 32 samples x N/2 columns of the planar partial sums
             float4 *dst = reinterpret_cast<float4 *>(P.fpart + ((size_t)split * ntp + tbase + row) * N + ch * (N / 2));
+            // FP16 hi+lo: this thread's promoted partial sums in shared memory during the item
+            float4 *sacc = reinterpret_cast<float4 *>(gbase + PL::OFF_ACC) + (size_t)ch * (N / 8) * kRows + row;
             float inv = 1.f;
             if constexpr (F == 1) inv = hl_scale(P.hdr->amax[0], true, kHl2Top) * kLoInv;
             int next_promo = 0;  // FP16 hi+lo: next chunk of this item to promote
@@ -577,7 +580,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
                         while (next_promo < (it - 1) / kChunk) {
                             tc::fence_after_sync();
                             fwd_promote1<N>(tmem + lanes + set_col(cbase + next_promo) + (uint32_t)(ch * (N / 2)), inv,
-                                            dst, next_promo > 0);
+                                            sacc, next_promo > 0);
                             release_set(sh, cbase + next_promo);
                             ++next_promo;
                         }
@@ -605,9 +608,11 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
                 } else {
                     if (ntl > 0 && ok) {
                         for (int m = next_promo; m < nch; ++m) {
-                            fwd_promote1<N>(tmem + lanes + set_col(cbase + m) + (uint32_t)(ch * (N / 2)), inv, dst, m > 0);
+                            fwd_promote1<N>(tmem + lanes + set_col(cbase + m) + (uint32_t)(ch * (N / 2)), inv, sacc, m > 0);
                             release_set(sh, cbase + m);
                         }
+#pragma unroll
+                        for (int c = 0; c < N / 8; ++c) dst[c] = sacc[(size_t)c * kRows];
                     } else {
 #pragma unroll
                         for (int c = 0; c < N / 8; ++c) dst[c] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -699,6 +704,19 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
             const int p = vb * kRows + row;
             const bool inside = p < ntiles * kTileVox;
             const float4 *s4 = reinterpret_cast<const float4 *>(P.Sp + (size_t)(inside ? p : 0) * CB);
+            // FP16 hi+lo: the promoting warps 0-3 keep their row's coil maps in shared memory for
+            // the item (read once, not once per promotion)
+            const float4 *sp4 = s4;
+            int sstride = 1;
+            if constexpr (F == 1) {
+                if (warp < 4) {
+                    float4 *ss = reinterpret_cast<float4 *>(gbase + PL::OFF_ACC) + row;
+#pragma unroll
+                    for (int q = 0; q < CB / 2; ++q) ss[(size_t)q * kRows] = s4[q];
+                    sp4 = ss;
+                    sstride = kRows;
+                }
+            }
             float xr = 0.f, xi = 0.f;  // coil-combined partial sum (FP16 hi+lo: promoted chunks)
             int next_promo = 0;
             for (int it = 0; it < nst; ++it) {
@@ -717,7 +735,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
                     if (warp < 4) {  // stages <= it - 2 complete: promote finished chunks
                         while (next_promo < (it - 1) / kChunk) {
                             tc::fence_after_sync();
-                            adj_promote1<CB>(tmem + lanes + set_col(cbase + next_promo), s4, xr, xi);
+                            adj_promote1<CB>(tmem + lanes + set_col(cbase + next_promo), sp4, sstride, xr, xi);
                             release_set(sh, cbase + next_promo);
                             ++next_promo;
                         }
@@ -731,11 +749,11 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
                 tc::fence_after_sync();
                 const bool have = nst > 0 && ok;
                 if constexpr (F == 0) {
-                    if (have) adj_promote1<CB>(tmem + lanes, s4, xr, xi);
+                    if (have) adj_promote1<CB>(tmem + lanes, s4, 1, xr, xi);
                 } else {
                     if (have) {
                         for (int m = next_promo; m < nch; ++m) {
-                            adj_promote1<CB>(tmem + lanes + set_col(cbase + m), s4, xr, xi);
+                            adj_promote1<CB>(tmem + lanes + set_col(cbase + m), sp4, sstride, xr, xi);
                             release_set(sh, cbase + m);
                         }
                         const float inv = hl_scale(P.hdr->amax[1], true, kHl2Top) * kLoInv;
