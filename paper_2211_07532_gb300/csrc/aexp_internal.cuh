@@ -191,6 +191,11 @@ cudaError_t tcp_forward(int precision, int CB, int variant, const ProbDesc *pd, 
                         int src, const int *item_off, int total_items, int *counter, cudaStream_t st);
 cudaError_t tcp_adjoint(int precision, int CB, int variant, const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *yt,
                         int src, const int *item_off, int total_items, int *counter, cudaStream_t st);
+// BF16 form: A^H (A z - ymeas) from the forward partials of A z: the reduction, the residual and
+// the packing in one launch, then the adjoint (ymeas as in reduce_pack_y_kernel).
+cudaError_t tcp_residual_adjoint_bf16(int CB, int variant, const ProbDesc *pd, int nprob, int max_pack_blocks,
+                                      const float2 *ymeas, int ymeas_role, const int *item_off, int total_items,
+                                      int *counter, cudaStream_t st);
 constexpr size_t kPhaseBlockBytes = 16384;  // 128 rows x 128 B: BF16 hi (32 K slots) | lo (32 K slots)
 
 // Tensor-core forms (op_tc.cu): the forward packs S*x itself; the adjoint packs yt.
@@ -218,6 +223,11 @@ cudaError_t op_reduce_forward_public(const OpLayout &L, char *ws, float2 *y, cud
 cudaError_t op_reduce_forward_residual(const OpLayout &L, char *ws, const float2 *ymeas_t, float2 *rt,
                                        cudaStream_t st);
 cudaError_t op_apply_adjoint(const OpLayout &L, const float2 *yt, char *ws, cudaStream_t st);
+// The adjoint applied to the residual of the last forward application, A^H (A z - ymeas_t)
+// (ymeas_t == nullptr: A^H A z), into the adjoint partials; the FP32 residual in rt is written
+// by every form but the BF16 one, which packs the residual directly.
+cudaError_t op_residual_adjoint(const OpLayout &L, char *ws, const float2 *ymeas_t, cudaStream_t st);
+cudaError_t op_residual_adjoint_tc(const OpLayout &L, char *ws, const float2 *ymeas_t, cudaStream_t st);
 
 // Wavelet (wavelet.cu).  tau = lam / L_f with L_f from `lipschitz` (device), or
 // lam itself when lipschitz == nullptr.  threshold == 0 disables shrinkage.

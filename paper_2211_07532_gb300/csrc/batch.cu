@@ -274,9 +274,14 @@ cudaError_t batch_normal_once(const BatchLayout &B, const aexp_recon_opts *o, ch
     batch_zero_kernel<<<g_nr, T, 0, st>>>(pd, Z);
     CK(batch_forward_tc(o->precision, B.CB, B.LP, o->tile_variant, pd, n, B.max_fwd_pack, Z, ifwd, B.items_fwd[n], &bh->counter[0],
                         st));
-    batch_fwd_reduce_kernel<<<g_ntp, T, 0, st>>>(pd, 0);
-    CK(batch_adjoint_tc(o->precision, B.CB, B.LP, o->tile_variant, pd, n, B.max_adj_pack, -1, iadj, B.items_adj[n], &bh->counter[1],
-                        st));
+    if (o->precision == AEXP_BF16_TC) {
+        CK(tcp_residual_adjoint_bf16(B.CB, o->tile_variant, pd, n, B.max_adj_pack, nullptr, -1, iadj, B.items_adj[n],
+                                     &bh->counter[1], st));
+    } else {
+        batch_fwd_reduce_kernel<<<g_ntp, T, 0, st>>>(pd, 0);
+        CK(batch_adjoint_tc(o->precision, B.CB, B.LP, o->tile_variant, pd, n, B.max_adj_pack, -1, iadj, B.items_adj[n],
+                            &bh->counter[1], st));
+    }
     batch_adj_reduce_kernel<<<g_nr, T, 0, st>>>(pd, -1, W);
     return cudaGetLastError();
 }
@@ -299,11 +304,21 @@ cudaError_t batch_recon_issue(const aexp_problem *probs, const BatchLayout &B, c
     const dim3 g_nr(cdiv(B.max_nr, T), n), g_ntp(cdiv(B.max_ntpcb, T), n);
     // FP64 norms: enough blocks per problem to spread the FP64 work, at most ~8 per SM in all
     const int g_red = std::max(1, std::min(std::min(kRedMaxBlocks, cdiv(B.max_nr, 2 * kDotThreads)), cdiv(8 * num_sms(), n)));
+    // adjoint partials of A^H (A z - ymeas) (use_ymeas) or A^H A z, from the forward partials
+    // of A z; the BF16 form packs the residual in the reduction's pass
+    auto residual_adjoint = [&](int use_ymeas) -> cudaError_t {
+        if (o->precision == AEXP_BF16_TC)
+            return tcp_residual_adjoint_bf16(B.CB, o->tile_variant, pd, n, B.max_adj_pack, nullptr, use_ymeas ? 5 : -1,  // vec[5]: ymeas
+                                            
+                                             iadj, tot_a, &bh->counter[1], st);
+        batch_fwd_reduce_kernel<<<g_ntp, T, 0, st>>>(pd, use_ymeas);
+        return batch_adjoint_tc(o->precision, B.CB, B.LP, o->tile_variant, pd, n, B.max_adj_pack, -1, iadj, tot_a,
+                                &bh->counter[1], st);
+    };
     // w = A^H A v for every problem (v in role vr, w in role wr)
     auto normal = [&](int vr, int wr) -> cudaError_t {
         CK(batch_forward_tc(o->precision, B.CB, B.LP, o->tile_variant, pd, n, B.max_fwd_pack, vr, ifwd, tot_f, &bh->counter[0], st));
-        batch_fwd_reduce_kernel<<<g_ntp, T, 0, st>>>(pd, 0);
-        CK(batch_adjoint_tc(o->precision, B.CB, B.LP, o->tile_variant, pd, n, B.max_adj_pack, -1, iadj, tot_a, &bh->counter[1], st));
+        CK(residual_adjoint(0));
         batch_adj_reduce_kernel<<<g_nr, T, 0, st>>>(pd, -1, wr);
         return cudaGetLastError();
     };
@@ -333,8 +348,7 @@ cudaError_t batch_recon_issue(const aexp_problem *probs, const BatchLayout &B, c
     double t = 1.0;
     for (int k = 0; k < iters; ++k) {
         CK(batch_forward_tc(o->precision, B.CB, B.LP, o->tile_variant, pd, n, B.max_fwd_pack, Z, ifwd, tot_f, &bh->counter[0], st));
-        batch_fwd_reduce_kernel<<<g_ntp, T, 0, st>>>(pd, 1);
-        CK(batch_adjoint_tc(o->precision, B.CB, B.LP, o->tile_variant, pd, n, B.max_adj_pack, -1, iadj, tot_a, &bh->counter[1], st));
+        CK(residual_adjoint(1));
         batch_adj_reduce_kernel<<<g_nr, T, 0, st>>>(pd, Z, V);
         const double t_next = (1.0 + sqrt(1.0 + 4.0 * t * t)) / 2.0;
         const double beta = (t - 1.0) / t_next;

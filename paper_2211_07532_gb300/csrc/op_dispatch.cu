@@ -26,4 +26,11 @@ cudaError_t op_apply_adjoint(const OpLayout &L, const float2 *yt, char *ws, cuda
     return L.precision == AEXP_FP32 ? op_adjoint_core(L, yt, ws, st) : op_adjoint_tc(L, yt, ws, st);
 }
 
+cudaError_t op_residual_adjoint(const OpLayout &L, char *ws, const float2 *ymeas_t, cudaStream_t st) {
+    if (L.precision == AEXP_BF16_TC) return op_residual_adjoint_tc(L, ws, ymeas_t, st);
+    float2 *rt = (float2 *)(ws + L.off_yt);
+    cudaError_t e = op_reduce_forward_residual(L, ws, ymeas_t, rt, st);
+    return e == cudaSuccess ? op_apply_adjoint(L, rt, ws, st) : e;
+}
+
 }  // namespace aexp

@@ -715,6 +715,13 @@ cudaError_t op_adjoint_tc(const OpLayout &L, const float2 *yt, char *ws, cudaStr
                      &hdr->counter[1], st)
 }
 
+cudaError_t op_residual_adjoint_tc(const OpLayout &L, char *ws, const float2 *ymeas_t, cudaStream_t st) {
+    WsHeader *hdr = (WsHeader *)(ws + L.off_hdr);
+    const ProbDesc *pd = (const ProbDesc *)(ws + L.off_desc);
+    return tcp_residual_adjoint_bf16(L.CB, L.variant, pd, 1, adj_pack_blocks(L.ntp, L.CB), ymeas_t, -1,
+                                     &hdr->item_off[2], L.adj_items, &hdr->counter[1], st);
+}
+
 cudaError_t batch_forward_tc(int precision, int CB, int LP, int variant, const ProbDesc *pd, int nprob,
                              int max_pack_blocks, int src, const int *item_off, int total_items, int *counter,
                              cudaStream_t st) {

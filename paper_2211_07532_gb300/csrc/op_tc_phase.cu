@@ -797,15 +797,17 @@ cudaError_t launch_fwd_tcp(const ProbDesc *pd, int nprob, int max_pack_blocks, c
     return cudaGetLastError();
 }
 
+// pack = 0: the adjoint operand is already packed (reduce_pack_y_kernel)
 template <int F, int CB, int NBB, int NP>
-cudaError_t launch_adj_tcp(const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *yt, int src,
+cudaError_t launch_adj_tcp(const ProbDesc *pd, int nprob, int max_pack_blocks, const float2 *yt, int src, int pack,
                            const int *item_off, int total_items, int *counter, cudaStream_t st) {
     if constexpr (F == 1) {
         amax_reset_kernel<<<cdiv(nprob, 256), 256, 0, st>>>(pd, nprob, 1);
         amax_y_kernel<CB><<<dim3(max_pack_blocks, nprob), 256, 0, st>>>(pd, yt, src);
     }
-    pack_y_adj_kernel<CB, F == 1 ? kPackHL2 : kPackBF16>
-        <<<dim3(pack_grid(max_pack_blocks, CB), nprob), 256, 0, st>>>(pd, yt, src);
+    if (pack || F == 1)
+        pack_y_adj_kernel<CB, F == 1 ? kPackHL2 : kPackBF16>
+            <<<dim3(pack_grid(max_pack_blocks, CB), nprob), 256, 0, st>>>(pd, yt, src);
     auto kern = adj_tcp_kernel<F, CB, NBB, NP>;
     const size_t smem = tcp_smem<F, CB, NBB, NP>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -828,13 +830,24 @@ cudaError_t launch_fwd_tcp_variant(int form, int variant, const ProbDesc *pd, in
 
 template <int CB>
 cudaError_t launch_adj_tcp_variant(int form, int variant, const ProbDesc *pd, int nprob, int max_pack_blocks,
-                                   const float2 *yt, int src, const int *item_off, int total_items, int *counter,
-                                   cudaStream_t st) {
+                                   const float2 *yt, int src, int pack, const int *item_off, int total_items,
+                                   int *counter, cudaStream_t st) {
     if (form == 1)
-        return launch_adj_tcp<1, CB, 4, 3>(pd, nprob, max_pack_blocks, yt, src, item_off, total_items, counter, st);
+        return launch_adj_tcp<1, CB, 4, 3>(pd, nprob, max_pack_blocks, yt, src, 1, item_off, total_items, counter, st);
     return variant == 1
-               ? launch_adj_tcp<0, CB, 6, 4>(pd, nprob, max_pack_blocks, yt, src, item_off, total_items, counter, st)
-               : launch_adj_tcp<0, CB, 4, 3>(pd, nprob, max_pack_blocks, yt, src, item_off, total_items, counter, st);
+               ? launch_adj_tcp<0, CB, 6, 4>(pd, nprob, max_pack_blocks, yt, src, pack, item_off, total_items, counter, st)
+               : launch_adj_tcp<0, CB, 4, 3>(pd, nprob, max_pack_blocks, yt, src, pack, item_off, total_items, counter, st);
+}
+
+// BF16 form: forward reduction + residual + packing (one launch), then the adjoint kernel.
+template <int CB>
+cudaError_t launch_residual_adj_bf16(int variant, const ProbDesc *pd, int nprob, int max_pack_blocks,
+                                     const float2 *ymeas, int ymeas_role, const int *item_off, int total_items,
+                                     int *counter, cudaStream_t st) {
+    reduce_pack_y_kernel<CB>
+        <<<dim3(pack_grid(max_pack_blocks, CB), nprob), kReducePackThreads, 0, st>>>(pd, ymeas, ymeas_role);
+    return launch_adj_tcp_variant<CB>(0, variant, pd, nprob, max_pack_blocks, nullptr, -1, 0, item_off, total_items,
+                                      counter, st);
 }
 
 }  // namespace
@@ -872,9 +885,19 @@ cudaError_t tcp_adjoint(int precision, int CB, int variant, const ProbDesc *pd, 
                         const float2 *yt, int src, const int *item_off, int total_items, int *counter, cudaStream_t st) {
     const int f = precision == AEXP_FP16X2_TC ? 1 : 0;
     switch (CB) {
-        case 8: return launch_adj_tcp_variant<8>(f, variant, pd, nprob, max_pack_blocks, yt, src, item_off, total_items, counter, st);
-        case 16: return launch_adj_tcp_variant<16>(f, variant, pd, nprob, max_pack_blocks, yt, src, item_off, total_items, counter, st);
-        default: return launch_adj_tcp_variant<32>(f, variant, pd, nprob, max_pack_blocks, yt, src, item_off, total_items, counter, st);
+        case 8: return launch_adj_tcp_variant<8>(f, variant, pd, nprob, max_pack_blocks, yt, src, 1, item_off, total_items, counter, st);
+        case 16: return launch_adj_tcp_variant<16>(f, variant, pd, nprob, max_pack_blocks, yt, src, 1, item_off, total_items, counter, st);
+        default: return launch_adj_tcp_variant<32>(f, variant, pd, nprob, max_pack_blocks, yt, src, 1, item_off, total_items, counter, st);
+    }
+}
+
+cudaError_t tcp_residual_adjoint_bf16(int CB, int variant, const ProbDesc *pd, int nprob, int max_pack_blocks,
+                                      const float2 *ymeas, int ymeas_role, const int *item_off, int total_items,
+                                      int *counter, cudaStream_t st) {
+    switch (CB) {
+        case 8: return launch_residual_adj_bf16<8>(variant, pd, nprob, max_pack_blocks, ymeas, ymeas_role, item_off, total_items, counter, st);
+        case 16: return launch_residual_adj_bf16<16>(variant, pd, nprob, max_pack_blocks, ymeas, ymeas_role, item_off, total_items, counter, st);
+        default: return launch_residual_adj_bf16<32>(variant, pd, nprob, max_pack_blocks, ymeas, ymeas_role, item_off, total_items, counter, st);
     }
 }
 

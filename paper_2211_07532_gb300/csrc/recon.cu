@@ -83,10 +83,8 @@ cudaError_t scale_inv_sqrt(const float2 *w, float2 *v, int n, const double *nrm2
 
 // w = A^H A v (v in natural order); uses the operator workspace only.
 cudaError_t normal_apply(const OpLayout &L, char *ws, const float2 *v, float2 *w, cudaStream_t st) {
-    float2 *rt = (float2 *)(ws + L.off_yt);
     CK(op_apply_forward(L, v, ws, st));
-    CK(op_reduce_forward_residual(L, ws, nullptr, rt, st));
-    CK(op_apply_adjoint(L, rt, ws, st));
+    CK(op_residual_adjoint(L, ws, nullptr, st));
     CK(op_adjoint_reduce(L, ws, w, st));
     return cudaSuccess;
 }
@@ -124,7 +122,6 @@ cudaError_t recon_issue(const aexp_problem *p, const RecLayout &R, const aexp_re
     float2 *v = (float2 *)(ws + R.off_v);
     float2 *w = (float2 *)(ws + R.off_w);
     char *wws = ws + R.off_wave;
-    float2 *rt = (float2 *)(ws + L.off_yt);
     const size_t img_bytes = sizeof(float2) * (size_t)L.nr;
 
     CK(op_prepare(p, L, ws, st));
@@ -165,8 +162,7 @@ cudaError_t recon_issue(const aexp_problem *p, const RecLayout &R, const aexp_re
     for (int k = 0; k < iters; ++k) {
         // v = z - (2/L_f) A^H (A z - y)
         CK(op_apply_forward(L, z, ws, st));
-        CK(op_reduce_forward_residual(L, ws, ymeas, rt, st));
-        CK(op_apply_adjoint(L, rt, ws, st));
+        CK(op_residual_adjoint(L, ws, ymeas, st));
         CK(op_adjoint_reduce_step(L, ws, z, v, st));
         // x_k = crop W^H soft(W pad v, lam / L_f);  z_{k+1} = x_k + beta_k (x_k - x_{k-1})
         double t_next = (1.0 + sqrt(1.0 + 4.0 * t * t)) / 2.0;

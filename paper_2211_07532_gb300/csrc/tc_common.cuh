@@ -213,6 +213,27 @@ __device__ __forceinline__ int stage_slot(int c, int pos) { return c * kStageRow
 // CB / 8 blocks per tile or stage.
 inline int pack_grid(int amax_blocks, int CB) { return amax_blocks * 8 / CB; }
 
+// The swizzled operand rows of one tile or stage from its staged values `sv` (stage_slot
+// layout): rows n < C carry (Re, -Im), rows C + c carry (Im, Re) at K positions (2j, 2j+1),
+// written as 16-byte chunks (a row's chunks across the lanes) at `dst` (the tile's or stage's
+// operand image).  The block's threads share the work; the caller synchronises around it.
+template <int CB, int MODE>
+__device__ __forceinline__ void pack_staged_rows(const float2 *sv, unsigned char *dst) {
+    constexpr int N = 2 * CB;
+    for (int k = threadIdx.x; k < N * 16; k += blockDim.x) {  // (n, chunk of 4 positions)
+        const int jj = k % 16, n = k / 16;
+        const int c = n < CB ? n : n - CB;
+        float a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float2 v = sv[c * kStageRow + u * 16 + jj];  // position 4 jj + u
+            a[u] = n < CB ? v.x : v.y;
+            b[u] = n < CB ? -v.y : v.x;
+        }
+        store_b_chunk<MODE>(dst + (jj >> 3) * (N * 128) + tc::swz128(n, jj & 7), N * 256, a, b);
+    }
+}
+
 // Forward: coil-weighted image b_c(v) = S_c(v) x(v) of every 8x8 tile, rows n < C carry
 // (Re b, -Im b), rows C + c carry (Im b, Re b) at K positions (2v, 2v+1).  The image is
 // `x` when given (single problem) or the descriptor's vec[src].  FP16 hi+lo: b is scaled by
@@ -243,20 +264,7 @@ __global__ void __launch_bounds__(256) pack_b_fwd_kernel(const ProbDesc *__restr
             sb[stage_slot(c, v)] = b;
         }
         __syncthreads();
-        for (int k = threadIdx.x; k < N * 16; k += blockDim.x) {  // (n, chunk of 4 voxels)
-            const int jj = k % 16, n = k / 16;
-            const int c = n < CB ? n : n - CB;
-            float a[4], b[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const float2 v = sb[c * kStageRow + u * 16 + jj];  // voxel 4 jj + u
-                a[u] = n < CB ? v.x : v.y;
-                b[u] = n < CB ? -v.y : v.x;
-            }
-            unsigned char *dst =
-                P.bpk + (size_t)tile * (NPK * N * 256) + (jj >> 3) * (N * 128) + tc::swz128(n, jj & 7);
-            store_b_chunk<MODE>(dst, N * 256, a, b);
-        }
+        pack_staged_rows<CB, MODE>(sb, P.bpk + (size_t)tile * (NPK * N * 256));
         __syncthreads();
     }
 }
@@ -284,19 +292,61 @@ __global__ void __launch_bounds__(256) pack_y_adj_kernel(const ProbDesc *__restr
             sy[stage_slot(k % CB, k / CB)] = v;
         }
         __syncthreads();
-        for (int k = threadIdx.x; k < N * 16; k += blockDim.x) {  // (n, chunk of 4 samples)
-            const int jj = k % 16, n = k / 16;
-            const int c = n < CB ? n : n - CB;
-            float a[4], b[4];
+        pack_staged_rows<CB, MODE>(sy, P.ypk + (size_t)st * (NPK * N * 256));
+        __syncthreads();
+    }
+}
+
+// BF16 form, the forward reduction, the residual and the adjoint's packing in one pass:
+// r[t][c] = sum over splits (in split order) of the planar forward partials, minus the
+// measured ymeas[t][c] when given (`ymeas`, or the descriptor's vec[ymeas_role] when
+// ymeas_role >= 0), zero for padded samples and coils; r is packed as the adjoint's operand
+// (the same values and rounding as the reduction kernel followed by pack_y_adj_kernel, without
+// the FP32 residual round trip).  One block per stage (grid-stride), grid.y = problem; the
+// partials are loaded kRedBatch splits at a time and added in split order.
+constexpr int kReducePackThreads = 512;
+constexpr int kRedBatch = 8;
+template <int CB>
+__global__ void __launch_bounds__(kReducePackThreads) reduce_pack_y_kernel(const ProbDesc *__restrict__ pd,
+                                                            const float2 *__restrict__ ymeas, int ymeas_role) {
+    constexpr int N = 2 * CB;
+    __shared__ float2 sy[CB * kStageRow];
+    const ProbDesc &P = pd[blockIdx.y];
+    const int nstages = P.ntp / kCols;
+    const float2 *ym = ymeas ? ymeas : (ymeas_role >= 0 ? P.vec[ymeas_role] : nullptr);
+    for (int st = blockIdx.x; st < nstages; st += gridDim.x) {
+        for (int k = threadIdx.x; k < kCols * CB; k += blockDim.x) {
+            const int t = st * kCols + k / CB, c = k % CB;
+            float2 s = make_float2(0.f, 0.f);
+            if (t < P.nt && c < P.nc) {
+                const float *col = P.fpart + (size_t)t * N + c;
+                const size_t sstride = (size_t)P.ntp * N;
+                for (int s0 = 0; s0 < P.fwd_splits; s0 += kRedBatch) {
+                    float re[kRedBatch], im[kRedBatch];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const float2 v = sy[c * kStageRow + u * 16 + jj];  // sample 4 jj + u
-                a[u] = n < CB ? v.x : v.y;
-                b[u] = n < CB ? -v.y : v.x;
+                    for (int u = 0; u < kRedBatch; ++u) {
+                        const bool in = s0 + u < P.fwd_splits;
+                        re[u] = in ? col[(size_t)(s0 + u) * sstride] : 0.f;
+                        im[u] = in ? col[(size_t)(s0 + u) * sstride + CB] : 0.f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kRedBatch; ++u) {
+                        if (s0 + u < P.fwd_splits) {
+                            s.x += re[u];
+                            s.y += im[u];
+                        }
+                    }
+                }
+                if (ym) {
+                    const float2 m = ym[(size_t)st * kCols * CB + k];
+                    s.x -= m.x;
+                    s.y -= m.y;
+                }
             }
-            unsigned char *dst = P.ypk + (size_t)st * (NPK * N * 256) + (jj >> 3) * (N * 128) + tc::swz128(n, jj & 7);
-            store_b_chunk<MODE>(dst, N * 256, a, b);
+            sy[stage_slot(c, k / CB)] = s;
         }
+        __syncthreads();
+        pack_staged_rows<CB, kPackBF16>(sy, P.ypk + (size_t)st * (N * 256));
         __syncthreads();
     }
 }

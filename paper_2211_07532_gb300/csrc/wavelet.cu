@@ -276,43 +276,56 @@ __device__ __forceinline__ int wrap(int v, int n) {
 // details shrunk by tau, then synthesis back to the level-1 approximation in A.  The same
 // filters, periodic extension and order (rows before columns; synthesis the transpose) as the
 // per-level kernels.
+// Flat loop over an h x w output grid with the block's threads (index = row * w + col, stride
+// kMidThreads), row and column stepped without a division per iteration.
+template <class Body>
+__device__ __forceinline__ void mid_for(int h, int w, Body body) {
+    const int tid = threadIdx.y * kMidTx + threadIdx.x;
+    const int di = kMidThreads / w, dc = kMidThreads - di * w;
+    int r = tid / w, c = tid - r * w;
+    while (r < h) {
+        body(r, c);
+        r += di;
+        c += dc;
+        if (c >= w) {
+            c -= w;
+            ++r;
+        }
+    }
+}
+
 template <int TAPS>
 __device__ void mid_levels(float2 *A, float2 *B, int m1y, int m1x, int levels, float tau) {
-    const int tx = threadIdx.x, ty = threadIdx.y;
     for (int j = 2; j <= levels; ++j) {
         const int my = m1y >> (j - 2), mx = m1x >> (j - 2);
         const int hy = my / 2, hx = mx / 2;
         // rows (x): B[i][q] = sum_t h[t] A[i][(2q + t) mod mx], B[i][hx + q] the same with g
-        for (int i = ty; i < my; i += kMidTy) {
+        mid_for(my, hx, [&](int i, int q) {
             const float2 *row = A + i * m1x;
-            for (int q = tx; q < hx; q += kMidTx) {
-                float2 lo = make_float2(0.f, 0.f), hi = make_float2(0.f, 0.f);
+            float2 lo = make_float2(0.f, 0.f), hi = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int t = 0; t < TAPS; ++t) {
-                    const float2 v = row[wrap<TAPS>(2 * q + t, mx)];
-                    lo = tmad2(tap_h<TAPS>(t), v, lo);
-                    hi = tmad2(tap_g<TAPS>(t), v, hi);
-                }
-                B[i * m1x + q] = lo;
-                B[i * m1x + hx + q] = hi;
+            for (int t = 0; t < TAPS; ++t) {
+                const float2 v = row[wrap<TAPS>(2 * q + t, mx)];
+                lo = tmad2(tap_h<TAPS>(t), v, lo);
+                hi = tmad2(tap_g<TAPS>(t), v, hi);
             }
-        }
+            B[i * m1x + q] = lo;
+            B[i * m1x + hx + q] = hi;
+        });
         __syncthreads();
         // columns (y): A[o][c] = sum_t h[t] B[(2o + t) mod my][c], A[hy + o][c] the same with g;
         // every quadrant but the top-left (the next level's approximation) is a detail band
-        for (int o = ty; o < hy; o += kMidTy) {
-            for (int c = tx; c < mx; c += kMidTx) {
-                float2 lo = make_float2(0.f, 0.f), hi = make_float2(0.f, 0.f);
+        mid_for(hy, mx, [&](int o, int c) {
+            float2 lo = make_float2(0.f, 0.f), hi = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int t = 0; t < TAPS; ++t) {
-                    const float2 v = B[wrap<TAPS>(2 * o + t, my) * m1x + c];
-                    lo = tmad2(tap_h<TAPS>(t), v, lo);
-                    hi = tmad2(tap_g<TAPS>(t), v, hi);
-                }
-                A[o * m1x + c] = c < hx ? lo : shrink(lo, tau);
-                A[(hy + o) * m1x + c] = shrink(hi, tau);
+            for (int t = 0; t < TAPS; ++t) {
+                const float2 v = B[wrap<TAPS>(2 * o + t, my) * m1x + c];
+                lo = tmad2(tap_h<TAPS>(t), v, lo);
+                hi = tmad2(tap_g<TAPS>(t), v, hi);
             }
-        }
+            A[o * m1x + c] = c < hx ? lo : shrink(lo, tau);
+            A[(hy + o) * m1x + c] = shrink(hi, tau);
+        });
         __syncthreads();
     }
     for (int j = levels; j >= 2; --j) {
@@ -320,39 +333,42 @@ __device__ void mid_levels(float2 *A, float2 *B, int m1y, int m1x, int levels, f
         const int hy = my / 2, hx = mx / 2;
         // columns (y): B[q][c] = sum over t with q - t even of h[t] A[k][c] + g[t] A[hy + k][c],
         // k = (q - t) / 2 mod hy; output rows q = 2a and 2a + 1 take the even and odd taps
-        for (int a = ty; a < hy; a += kMidTy) {
-            for (int c = tx; c < mx; c += kMidTx) {
-                float2 ev = make_float2(0.f, 0.f), od = make_float2(0.f, 0.f);
+        mid_for(hy, mx, [&](int a, int c) {
+            float2 ev = make_float2(0.f, 0.f), od = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int t = 0; t < TAPS; t += 2) {
-                    const int k = wrap<TAPS>(a - t / 2 + hy, hy);  // (2a - t) / 2 mod hy, also (2a + 1 - (t + 1)) / 2
-                    const float2 lo = A[k * m1x + c], hi = A[(hy + k) * m1x + c];
-                    ev = tmad2(tap_h<TAPS>(t), lo, tmad2(tap_g<TAPS>(t), hi, ev));
-                    od = tmad2(tap_h<TAPS>(t + 1), lo, tmad2(tap_g<TAPS>(t + 1), hi, od));
-                }
-                B[2 * a * m1x + c] = ev;
-                B[(2 * a + 1) * m1x + c] = od;
+            for (int t = 0; t < TAPS; t += 2) {
+                const int k = wrap<TAPS>(a - t / 2 + hy, hy);  // (2a - t) / 2 mod hy, also (2a + 1 - (t + 1)) / 2
+                const float2 lo = A[k * m1x + c], hi = A[(hy + k) * m1x + c];
+                ev = tmad2(tap_h<TAPS>(t), lo, tmad2(tap_g<TAPS>(t), hi, ev));
+                od = tmad2(tap_h<TAPS>(t + 1), lo, tmad2(tap_g<TAPS>(t + 1), hi, od));
             }
-        }
+            B[2 * a * m1x + c] = ev;
+            B[(2 * a + 1) * m1x + c] = od;
+        });
         __syncthreads();
         // rows (x): A[r][p] = sum over t with p - t even of h[t] B[r][k] + g[t] B[r][hx + k]
-        for (int r = ty; r < my; r += kMidTy) {
+        mid_for(my, hx, [&](int r, int a) {
             const float2 *row = B + r * m1x;
-            for (int a = tx; a < hx; a += kMidTx) {
-                float2 ev = make_float2(0.f, 0.f), od = make_float2(0.f, 0.f);
+            float2 ev = make_float2(0.f, 0.f), od = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int t = 0; t < TAPS; t += 2) {
-                    const int k = wrap<TAPS>(a - t / 2 + hx, hx);
-                    const float2 lo = row[k], hi = row[hx + k];
-                    ev = tmad2(tap_h<TAPS>(t), lo, tmad2(tap_g<TAPS>(t), hi, ev));
-                    od = tmad2(tap_h<TAPS>(t + 1), lo, tmad2(tap_g<TAPS>(t + 1), hi, od));
-                }
-                A[r * m1x + 2 * a] = ev;
-                A[r * m1x + 2 * a + 1] = od;
+            for (int t = 0; t < TAPS; t += 2) {
+                const int k = wrap<TAPS>(a - t / 2 + hx, hx);
+                const float2 lo = row[k], hi = row[hx + k];
+                ev = tmad2(tap_h<TAPS>(t), lo, tmad2(tap_g<TAPS>(t), hi, ev));
+                od = tmad2(tap_h<TAPS>(t + 1), lo, tmad2(tap_g<TAPS>(t + 1), hi, od));
             }
-        }
+            A[r * m1x + 2 * a] = ev;
+            A[r * m1x + 2 * a + 1] = od;
+        });
         __syncthreads();
     }
+}
+
+// Level-1 approximation (m1y x m1x, m1x even) between global and shared memory, two values per
+// 16-byte access.
+__device__ __forceinline__ void mid_copy(float4 *dst, const float4 *src, int n4) {
+    const int tid = threadIdx.y * kMidTx + threadIdx.x;
+    for (int i = tid; i < n4; i += kMidThreads) dst[i] = src[i];
 }
 
 // One CTA: approx (the level-1 approximation, m1y x m1x in global memory) -> levels 2..levels
@@ -363,11 +379,10 @@ __global__ void __launch_bounds__(kMidThreads)
     extern __shared__ float2 smid[];
     const float tau = block_tau(lam, lipschitz);
     float2 *A = smid, *B = smid + m1y * m1x;
-    const int tid = threadIdx.y * kMidTx + threadIdx.x;
-    for (int i = tid; i < m1y * m1x; i += kMidThreads) A[i] = approx[i];
+    mid_copy(reinterpret_cast<float4 *>(A), reinterpret_cast<const float4 *>(approx), m1y * m1x / 2);
     __syncthreads();
     mid_levels<TAPS>(A, B, m1y, m1x, levels, tau);
-    for (int i = tid; i < m1y * m1x; i += kMidThreads) approx[i] = A[i];
+    mid_copy(reinterpret_cast<float4 *>(approx), reinterpret_cast<const float4 *>(A), m1y * m1x / 2);
 }
 
 // The same per problem of a batch (grid.x = problem).
@@ -379,11 +394,10 @@ __global__ void __launch_bounds__(kMidThreads) batch_dwt_mid_kernel(const ProbDe
     const int m1y = P.npy / 2, m1x = P.npx / 2;
     float2 *approx = (float2 *)(P.wws + P.off_approx[1]);
     float2 *A = smid, *B = smid + m1y * m1x;
-    const int tid = threadIdx.y * kMidTx + threadIdx.x;
-    for (int i = tid; i < m1y * m1x; i += kMidThreads) A[i] = approx[i];
+    mid_copy(reinterpret_cast<float4 *>(A), reinterpret_cast<const float4 *>(approx), m1y * m1x / 2);
     __syncthreads();
     mid_levels<TAPS>(A, B, m1y, m1x, P.levels, tau);
-    for (int i = tid; i < m1y * m1x; i += kMidThreads) approx[i] = A[i];
+    mid_copy(reinterpret_cast<float4 *>(approx), reinterpret_cast<const float4 *>(A), m1y * m1x / 2);
 }
 
 template <int TAPS>
