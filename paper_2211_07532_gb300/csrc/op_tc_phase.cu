@@ -323,23 +323,35 @@ __device__ __forceinline__ void tcp_contraction_item(TcShared &sh, uint32_t tmem
     if (n > 0 && leader) tc::mma_commit(&sh.accdone);  // the item's accumulators are final
 }
 
-// Phase thread, one item: the phases of stage g go into tile g % PH_BUFS once the generators
-// have read that tile for stage g - PH_BUFS and the stage's operand has landed.
-template <int F, int N, int NBB, int NP>
+// Phase role, one item: the phases of stage g go into tile g % PH_BUFS once the generators
+// have read that tile for stage g - PH_BUFS and the stage's operand has landed.  WARP = false:
+// lane 0 of the phase warp alone; WARP = true: the whole warp waits and lane 0 (elected) issues,
+// which issues faster but lets the phases run up to PH_BUFS stages ahead of the contractions
+// (measured: the BF16 adjoint 0.645 -> 0.600 ms, the BF16 forward and both FP16 hi+lo kernels
+// slower).  The MMAs and their order are the same either way.
+template <int F, int N, int NBB, int NP, bool WARP>
 __device__ __forceinline__ void tcp_phase_item(TcShared &sh, uint32_t tmem, unsigned char *base, int gs, int n,
                                                int iter, int ks, int *status) {
     using PL = TcpPlan<F, N, NBB, NP>;
     constexpr int PB = Form<F>::PH_BUFS;
     const uint64_t ad = tc::sdesc_k128(smem_u32(base + PL::OFF_AP));
-    if (!wait_or_abort(&sh.apfull, iter & 1, &sh.abort_flag, status)) return;
+    const bool leader = WARP ? tc::elect_lane0() : true;
+    bool ok = wait_or_abort(&sh.apfull, iter & 1, &sh.abort_flag, status);
+    if (WARP) ok = __all_sync(0xffffffffu, ok);
+    if (!ok) return;
     for (int it = 0; it < n; ++it) {
         const int g = gs + it, b = g % PB, sp = g % NP;
-        if (g >= PB && !wait_or_abort(&sh.phfree[b], ((g - PB) / PB) & 1, &sh.abort_flag, status)) return;
-        if (!wait_or_abort(&sh.pfull[sp], (g / NP) & 1, &sh.abort_flag, status)) return;
+        ok = g < PB || wait_or_abort(&sh.phfree[b], ((g - PB) / PB) & 1, &sh.abort_flag, status);
+        if (ok) ok = wait_or_abort(&sh.pfull[sp], (g / NP) & 1, &sh.abort_flag, status);
+        if (WARP) ok = __all_sync(0xffffffffu, ok);
+        if (!ok) return;
         tc::fence_after_sync();
-        phase_mma<F>(ks, tmem + phase_col<F>(g), ad, tc::sdesc_k128(smem_u32(base + PL::OFF_PH + sp * PL::PS)));
-        tc::mma_commit(&sh.phfull[b]);
-        tc::mma_commit(&sh.pfree[sp]);
+        if (leader) {
+            phase_mma<F>(ks, tmem + phase_col<F>(g), ad, tc::sdesc_k128(smem_u32(base + PL::OFF_PH + sp * PL::PS)));
+            tc::mma_commit(&sh.phfull[b]);
+            tc::mma_commit(&sh.pfree[sp]);
+        }
+        if (WARP) __syncwarp();
     }
 }
 
@@ -528,7 +540,7 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
             if (warp == kMmaWarp) {  // the whole warp (see tcp_contraction_item)
                 tcp_contraction_item<F, N, NBB, NP>(sh, tmem, gbase, gs, ntl, cbase, status);
             } else if (warp == kPhaseWarp && lead) {
-                tcp_phase_item<F, N, NBB, NP>(sh, tmem, gbase, gs, ntl, iter, (P.LP + 15) >> 4, status);
+                tcp_phase_item<F, N, NBB, NP, false>(sh, tmem, gbase, gs, ntl, iter, (P.LP + 15) >> 4, status);
             } else if (warp == kLoadBWarp && lead) {
                 ring_load_item(sh.bfree, NBB, gs, ntl, &sh.abort_flag, status, [&](int it, int sb) {
                     const int tile = tile0 + it;  // packed S x of the tile and its reference phases
@@ -669,8 +681,8 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
             const bool lead = (tid & 31) == 0;
             if (warp == kMmaWarp) {  // the whole warp (see tcp_contraction_item)
                 tcp_contraction_item<F, N, NBB, NP>(sh, tmem, gbase, gs, nst, cbase, status);
-            } else if (warp == kPhaseWarp && lead) {
-                tcp_phase_item<F, N, NBB, NP>(sh, tmem, gbase, gs, nst, iter, (P.LP + 15) >> 4, status);
+            } else if (warp == kPhaseWarp && (F == 0 || lead)) {  // BF16: the converged warp
+                tcp_phase_item<F, N, NBB, NP, F == 0>(sh, tmem, gbase, gs, nst, iter, (P.LP + 15) >> 4, status);
             } else if (warp == kLoadBWarp && lead) {
                 ring_load_item(sh.bfree, NBB, gs, nst, &sh.abort_flag, status, [&](int it, int sb) {
                     const size_t ts = (size_t)t0 + (size_t)it * TS;  // packed y and both tiles' f0
