@@ -15,6 +15,10 @@
 // of analysis, threshold and synthesis there, so a prox step is three launches instead of 2J
 // (each level launch is latency bound at these sizes, ~8-11 us whatever its grid).  Images whose
 // level-1 approximation does not fit (over 12800 coefficients) take one launch per level.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
 #include "aexp_internal.cuh"
 #include "wavelet_taps.cuh"
 
@@ -400,6 +404,158 @@ __global__ void __launch_bounds__(kMidThreads) batch_dwt_mid_kernel(const ProbDe
     mid_copy(reinterpret_cast<float4 *>(approx), reinterpret_cast<const float4 *>(A), m1y * m1x / 2);
 }
 
+// ---- levels 2..J of the prox step in one cluster of kMidCluster CTAs ----
+// Each CTA owns a band of output rows per level, o in [rank hy / NC, (rank + 1) hy / NC), the
+// same band for the synthesis.  Two full-size arrays X, Y alternate between levels: level j
+// reads its input approximation from one and writes its outputs (the next approximation and its
+// thresholded details) into the other, in every CTA of the cluster (distributed shared memory),
+// so that each CTA holds a full copy of every level's coefficients and no level overwrites
+// what another CTA may still be reading; a per-CTA scratch B holds only the filtered rows the
+// band needs.  Per output the arithmetic and its order are those of mid_levels.
+constexpr int kMidCluster = 8;
+
+// Rows of B: the most any level's band needs (its 2 nb rows plus the filter's TAPS - 2 halo).
+inline int mid_cluster_brows(int m1y, int taps) {
+    const int hy = m1y / 2;
+    return std::min(m1y, 2 * ((hy + kMidCluster - 1) / kMidCluster) + taps - 2);
+}
+// dynamic shared memory a cluster CTA may take (227 KB less the static s_tau, rounded down)
+constexpr size_t kMidClusterSmemMax = 227 * 1024 - 256;
+inline size_t mid_cluster_smem(int m1y, int m1x, int taps) {
+    return sizeof(float2) * ((size_t)2 * m1y * m1x + (size_t)mid_cluster_brows(m1y, taps) * m1x);
+}
+
+template <int TAPS>
+__device__ void mid_levels_cluster(float2 *__restrict__ approx, float2 *sm, int m1y, int m1x, int levels, float tau) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int n1 = m1y * m1x;
+    float2 *X = sm, *Y = sm + n1, *B = sm + 2 * n1;
+    // every CTA's copy of `arr` at flat index i gets v
+    auto put_all = [&](float2 *arr, int i, float2 v) {
+#pragma unroll
+        for (int r = 0; r < kMidCluster; ++r) cl.map_shared_rank(arr, r)[i] = v;
+    };
+    {   // level 2 reads rows (2 o0 + i) mod m1y, i < L, of the level-1 approximation
+        const int hy = m1y / 2, o0 = rank * hy / kMidCluster, nb = (rank + 1) * hy / kMidCluster - o0;
+        const int L = min(m1y, 2 * nb + TAPS - 2);
+        if (nb > 0)
+            mid_for(L, m1x / 2, [&](int i, int q) {
+                const int r = (2 * o0 + i) % m1y;
+                reinterpret_cast<float4 *>(X + r * m1x)[q] = reinterpret_cast<const float4 *>(approx + r * m1x)[q];
+            });
+    }
+    __syncthreads();
+    float2 *P = X, *Q = Y;
+    for (int j = 2; j <= levels; ++j) {
+        const int my = m1y >> (j - 2), mx = m1x >> (j - 2);
+        const int hy = my / 2, hx = mx / 2;
+        const int o0 = rank * hy / kMidCluster, nb = (rank + 1) * hy / kMidCluster - o0;
+        const int L = min(my, 2 * nb + TAPS - 2);
+        // rows (x): B[i] = the filtered row (2 o0 + i) mod my of P
+        if (nb > 0)
+            mid_for(L, hx, [&](int i, int q) {
+                const float2 *row = P + ((2 * o0 + i) % my) * m1x;
+                float2 lo = make_float2(0.f, 0.f), hi = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int t = 0; t < TAPS; ++t) {
+                    const float2 v = row[wrap<TAPS>(2 * q + t, mx)];
+                    lo = tmad2(tap_h<TAPS>(t), v, lo);
+                    hi = tmad2(tap_g<TAPS>(t), v, hi);
+                }
+                B[i * m1x + q] = lo;
+                B[i * m1x + hx + q] = hi;
+            });
+        __syncthreads();
+        // columns (y) of the band, into Q in every CTA
+        if (nb > 0)
+            mid_for(nb, mx, [&](int oi, int c) {
+                const int o = o0 + oi;
+                float2 lo = make_float2(0.f, 0.f), hi = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int t = 0; t < TAPS; ++t) {
+                    const float2 v = B[wrap<TAPS>(2 * oi + t, L) * m1x + c];
+                    lo = tmad2(tap_h<TAPS>(t), v, lo);
+                    hi = tmad2(tap_g<TAPS>(t), v, hi);
+                }
+                put_all(Q, o * m1x + c, c < hx ? lo : shrink(lo, tau));
+                put_all(Q, (hy + o) * m1x + c, shrink(hi, tau));
+            });
+        cl.sync();
+        float2 *tmp = P;
+        P = Q;
+        Q = tmp;
+    }
+    for (int j = levels; j >= 2; --j) {
+        const int my = m1y >> (j - 2), mx = m1x >> (j - 2);
+        const int hy = my / 2, hx = mx / 2;
+        const int a0 = rank * hy / kMidCluster, nb = (rank + 1) * hy / kMidCluster - a0;
+        // level j's details and the approximation of level j + 1 sit in the array level j wrote
+        // (Y for even j); its output, the approximation of level j, goes where level j - 1's
+        // synthesis reads it (the other array), or to `approx` for j = 2
+        const float2 *Qj = (j & 1) ? X : Y;
+        float2 *Out = (j & 1) ? Y : X;
+        // columns (y): B rows 2 (a - a0) and 2 (a - a0) + 1
+        if (nb > 0)
+            mid_for(nb, mx, [&](int ai, int c) {
+                const int a = a0 + ai;
+                float2 ev = make_float2(0.f, 0.f), od = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int t = 0; t < TAPS; t += 2) {
+                    const int k = wrap<TAPS>(a - t / 2 + hy, hy);
+                    const float2 lo = Qj[k * m1x + c], hi = Qj[(hy + k) * m1x + c];
+                    ev = tmad2(tap_h<TAPS>(t), lo, tmad2(tap_g<TAPS>(t), hi, ev));
+                    od = tmad2(tap_h<TAPS>(t + 1), lo, tmad2(tap_g<TAPS>(t + 1), hi, od));
+                }
+                B[2 * ai * m1x + c] = ev;
+                B[(2 * ai + 1) * m1x + c] = od;
+            });
+        __syncthreads();
+        // rows (x): output rows 2 a0 + i, i < 2 nb
+        if (nb > 0)
+            mid_for(2 * nb, hx, [&](int i, int a) {
+                const float2 *row = B + i * m1x;
+                float2 ev = make_float2(0.f, 0.f), od = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int t = 0; t < TAPS; t += 2) {
+                    const int k = wrap<TAPS>(a - t / 2 + hx, hx);
+                    const float2 lo = row[k], hi = row[hx + k];
+                    ev = tmad2(tap_h<TAPS>(t), lo, tmad2(tap_g<TAPS>(t), hi, ev));
+                    od = tmad2(tap_h<TAPS>(t + 1), lo, tmad2(tap_g<TAPS>(t + 1), hi, od));
+                }
+                const int r = 2 * a0 + i;
+                if (j > 2) {
+                    put_all(Out, r * m1x + 2 * a, ev);
+                    put_all(Out, r * m1x + 2 * a + 1, od);
+                } else {
+                    reinterpret_cast<float4 *>(approx + r * m1x)[a] = make_float4(ev.x, ev.y, od.x, od.y);
+                }
+            });
+        if (j > 2) cl.sync();
+    }
+}
+
+template <int TAPS>
+__global__ void __cluster_dims__(kMidCluster, 1, 1) __launch_bounds__(kMidThreads)
+    dwt_mid_cluster_kernel(float2 *__restrict__ approx, int m1y, int m1x, int levels, float lam,
+                           const double *lipschitz) {
+    extern __shared__ float4 smc4[];
+    const float tau = block_tau(lam, lipschitz);
+    mid_levels_cluster<TAPS>(approx, reinterpret_cast<float2 *>(smc4), m1y, m1x, levels, tau);
+}
+
+// The same per problem of a batch (cluster = problem blockIdx.y).
+template <int TAPS>
+__global__ void __cluster_dims__(kMidCluster, 1, 1) __launch_bounds__(kMidThreads)
+    batch_dwt_mid_cluster_kernel(const ProbDesc *__restrict__ pd) {
+    extern __shared__ float4 smc4[];
+    const ProbDesc &P = pd[blockIdx.y];
+    const float tau = block_tau(P.lam, &P.hdr->lipschitz);
+    mid_levels_cluster<TAPS>((float2 *)(P.wws + P.off_approx[1]), reinterpret_cast<float2 *>(smc4), P.npy / 2,
+                             P.npx / 2, P.levels, tau);
+}
+
 template <int TAPS>
 cudaError_t run_forward(const WaveLayout &W, const float2 *img, char *wws, float lam, const double *lipschitz,
                         int threshold, cudaStream_t st) {
@@ -508,11 +664,19 @@ cudaError_t run_prox(const WaveLayout &W, const float2 *img, char *wws, float la
         dwt_fwd_level<TAPS><<<grid, 256, 0, st>>>(img, W.nx, W.ny, W.nx, W.npy, W.npx, ll1, m1x, pyr, W.npx, lam,
                                                  lipschitz, 1);
     }
-    const size_t smem = 2 * sizeof(float2) * (size_t)m1y * m1x;
-    auto kern = dwt_mid_kernel<TAPS>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<1, dim3(kMidTx, kMidTy), smem, st>>>(ll1, m1y, m1x, W.levels, lam, lipschitz);
+    const size_t csmem = mid_cluster_smem(m1y, m1x, TAPS);
+    if (csmem <= kMidClusterSmemMax) {
+        auto kern = dwt_mid_cluster_kernel<TAPS>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
+        if (e != cudaSuccess) return e;
+        kern<<<kMidCluster, dim3(kMidTx, kMidTy), csmem, st>>>(ll1, m1y, m1x, W.levels, lam, lipschitz);
+    } else {
+        const size_t smem = 2 * sizeof(float2) * (size_t)m1y * m1x;
+        auto kern = dwt_mid_kernel<TAPS>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<1, dim3(kMidTx, kMidTy), smem, st>>>(ll1, m1y, m1x, W.levels, lam, lipschitz);
+    }
     {
         dim3 grid(cdiv(W.npx, OBI), cdiv(W.npy, OBI));
         dwt_inv_level<TAPS><<<grid, 256, 0, st>>>(ll1, m1x, pyr, W.npx, W.npy, W.npx, out, W.nx, W.ny, W.nx, momentum,
@@ -528,11 +692,19 @@ cudaError_t run_batch_prox(const ProbDesc *pd, int nprob, int levels, int max_np
         dim3 grid(cdiv(max_npx / 2, OB), cdiv(max_npy / 2, OB), nprob);
         batch_dwt_fwd_level<TAPS><<<grid, 256, 0, st>>>(pd, 1, img_role, 1);
     }
-    const size_t smem = 2 * sizeof(float2) * (size_t)(max_npy / 2) * (max_npx / 2);
-    auto kern = batch_dwt_mid_kernel<TAPS>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<nprob, dim3(kMidTx, kMidTy), smem, st>>>(pd);
+    const size_t csmem = mid_cluster_smem(max_npy / 2, max_npx / 2, TAPS);
+    if (csmem <= kMidClusterSmemMax) {
+        auto kern = batch_dwt_mid_cluster_kernel<TAPS>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
+        if (e != cudaSuccess) return e;
+        kern<<<dim3(kMidCluster, nprob), dim3(kMidTx, kMidTy), csmem, st>>>(pd);
+    } else {
+        const size_t smem = 2 * sizeof(float2) * (size_t)(max_npy / 2) * (max_npx / 2);
+        auto kern = batch_dwt_mid_kernel<TAPS>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<nprob, dim3(kMidTx, kMidTy), smem, st>>>(pd);
+    }
     {
         dim3 grid(cdiv(max_npx, OBI), cdiv(max_npy, OBI), nprob);
         batch_dwt_inv_level<TAPS><<<grid, 256, 0, st>>>(pd, 1, out_role, momentum, (float)beta, xold_role, z_role);
