@@ -13,8 +13,12 @@ from tests._data import rel
 pytestmark = pytest.mark.gpu
 TOL = 2e-6
 
+# The prox step's levels 2..J run in one cluster of CTAs where its shared memory plan fits (the
+# square cases), in one CTA for wide strips whose band scratch does not fit beside two copies of
+# the level-1 approximation (db4 32 x 1600), and one launch per level beyond that (256 x 240).
 CASES = [("haar", 64, 64, 3), ("db4", 200, 200, 4), ("db4", 13, 11, 2), ("haar", 11, 13, 1),
-         ("db4", 170, 170, 4), ("haar", 1, 1, 1), ("db4", 16, 16, 4)]
+         ("db4", 170, 170, 4), ("haar", 1, 1, 1), ("db4", 16, 16, 4), ("db4", 32, 1600, 4),
+         ("haar", 32, 1600, 4), ("db4", 256, 240, 3)]
 
 
 @pytest.fixture(scope="module")
