@@ -61,6 +61,8 @@ _OPTS = ctypes.POINTER(CReconOpts)
 SIGNATURES = [
     ("aexp_workspace_size", _I, [_PROB, _I, ctypes.POINTER(_SZ)]),
     ("aexp_prepare", _I, [_PROB, _I, _P, _SZ, _P]),
+    ("aexp_workspace_size_tiled", _I, [_PROB, _I, _I, _I, ctypes.POINTER(_SZ)]),
+    ("aexp_prepare_tiled", _I, [_PROB, _I, _I, _I, _P, _SZ, _P]),
     ("a_exp_forward", _I, [_PROB, _I, _P, _P, _P, _SZ, _P]),
     ("a_exp_adjoint", _I, [_PROB, _I, _P, _P, _P, _SZ, _P]),
     ("aexp_recon_opts_default", None, [_OPTS]),
@@ -186,9 +188,13 @@ class Problem:
         return self.S.device
 
 
-def workspace_size(prob: Problem, precision: int = FP32) -> int:
+def workspace_size(prob: Problem, precision: int = FP32, items_per_sm: int = 0, tile_variant: int = 0) -> int:
     n = ctypes.c_size_t()
-    _check(lib().aexp_workspace_size(prob.c, precision, ctypes.byref(n)), "aexp_workspace_size")
+    if items_per_sm or tile_variant:
+        _check(lib().aexp_workspace_size_tiled(prob.c, precision, items_per_sm, tile_variant, ctypes.byref(n)),
+               "aexp_workspace_size_tiled")
+    else:
+        _check(lib().aexp_workspace_size(prob.c, precision, ctypes.byref(n)), "aexp_workspace_size")
     return n.value
 
 
@@ -200,12 +206,18 @@ def _alloc(nbytes: int, device):
     return ws
 
 
-def workspace(prob: Problem, precision: int = FP32):
-    return _alloc(workspace_size(prob, precision), prob.device)
+def workspace(prob: Problem, precision: int = FP32, items_per_sm: int = 0, tile_variant: int = 0):
+    return _alloc(workspace_size(prob, precision, items_per_sm, tile_variant), prob.device)
 
 
-def prepare(prob: Problem, ws, precision: int = FP32, stream=None):
-    _check(lib().aexp_prepare(prob.c, precision, _ptr(ws), ws.numel(), _stream(stream)), "aexp_prepare")
+def prepare(prob: Problem, ws, precision: int = FP32, stream=None, items_per_sm: int = 0, tile_variant: int = 0):
+    """Prepare ws for the operator calls; a nonzero items_per_sm / tile_variant selects that
+    launch shape (aexp_prepare_tiled), which the operator calls on ws then use."""
+    if items_per_sm or tile_variant:
+        _check(lib().aexp_prepare_tiled(prob.c, precision, items_per_sm, tile_variant, _ptr(ws), ws.numel(),
+                                        _stream(stream)), "aexp_prepare_tiled")
+    else:
+        _check(lib().aexp_prepare(prob.c, precision, _ptr(ws), ws.numel(), _stream(stream)), "aexp_prepare")
 
 
 def a_exp_forward(prob: Problem, x, ws, y=None, precision: int = FP32, stream=None):

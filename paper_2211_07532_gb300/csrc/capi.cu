@@ -75,6 +75,16 @@ void record_prepared(const void *ws, const aexp_problem *p, int precision, int i
     g_prepared[ws] = PrepRecord{*p, precision, effective_items(precision, items_per_sm), variant};
 }
 
+// The layout granularity and tiling `ws` was last prepared with for (p, precision), if any.
+bool prepared_tiling(const void *ws, const aexp_problem *p, int precision, int *items_per_sm, int *variant) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_prepared.find(ws);
+    if (it == g_prepared.end() || !same_problem(it->second.prob, *p) || it->second.precision != precision) return false;
+    *items_per_sm = it->second.items_per_sm;
+    *variant = it->second.tile_variant;
+    return true;
+}
+
 bool is_prepared(const void *ws, const aexp_problem *p, int precision, int items_per_sm = 0, int variant = 0) {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_prepared.find(ws);
@@ -126,6 +136,12 @@ cudaError_t launch_captured(const void *ws, const std::vector<unsigned char> &ke
     return cudaGraphLaunch(ge.exec, st);
 }
 
+int check_tiling(int precision, int items_per_sm, int tile_variant) {
+    if (items_per_sm < 0 || items_per_sm > 256) return AEXP_ERR_INVALID_ARG;
+    if (tile_variant < 0 || tile_variant >= tile_variant_limit(precision)) return AEXP_ERR_INVALID_ARG;
+    return AEXP_OK;
+}
+
 int check_opts(const aexp_recon_opts *o) {
     if (!o) return AEXP_ERR_INVALID_ARG;
     int rc = check_precision(o->precision);
@@ -133,8 +149,7 @@ int check_opts(const aexp_recon_opts *o) {
     if (o->wavelet != AEXP_WAVELET_HAAR && o->wavelet != AEXP_WAVELET_DB4) return AEXP_ERR_INVALID_ARG;
     if (o->levels < 1 || o->levels > 12) return AEXP_ERR_INVALID_ARG;
     if (!(o->lipschitz > 0.0) && o->n_power < 1) return AEXP_ERR_INVALID_ARG;
-    if (o->items_per_sm < 0 || o->items_per_sm > 256) return AEXP_ERR_INVALID_ARG;
-    if (o->tile_variant < 0 || o->tile_variant >= kTileVariants) return AEXP_ERR_INVALID_ARG;
+    if ((rc = check_tiling(o->precision, o->items_per_sm, o->tile_variant))) return rc;
     if (o->lambda_rule != AEXP_LAMBDA_GIVEN && o->lambda_rule != AEXP_LAMBDA_RAYLEIGH) return AEXP_ERR_INVALID_ARG;
     if (o->lambda_rule == AEXP_LAMBDA_RAYLEIGH && !o->undecimated) return AEXP_ERR_UNSUPPORTED;
     if (!aligned(o->x0, 8) || !aligned(o->power_init, 8) || !aligned(o->lambda_out, 8)) return AEXP_ERR_MISALIGNED;
@@ -183,17 +198,36 @@ int aexp_workspace_size(const aexp_problem *prob, int precision, size_t *bytes) 
 }
 
 int aexp_prepare(const aexp_problem *prob, int precision, void *ws, size_t ws_bytes, void *stream) {
+    return aexp_prepare_tiled(prob, precision, 0, 0, ws, ws_bytes, stream);
+}
+
+int aexp_workspace_size_tiled(const aexp_problem *prob, int precision, int items_per_sm, int tile_variant,
+                              size_t *bytes) {
     int rc = check_problem(prob);
     if (rc) return rc;
     if ((rc = check_precision(precision))) return rc;
+    if ((rc = check_tiling(precision, items_per_sm, tile_variant))) return rc;
+    if (!bytes) return AEXP_ERR_INVALID_ARG;
     OpLayout L;
-    op_layout(prob, precision, &L);
+    op_layout(prob, precision, &L, items_target(precision, items_per_sm), tile_variant);
+    *bytes = L.bytes;
+    return AEXP_OK;
+}
+
+int aexp_prepare_tiled(const aexp_problem *prob, int precision, int items_per_sm, int tile_variant, void *ws,
+                       size_t ws_bytes, void *stream) {
+    int rc = check_problem(prob);
+    if (rc) return rc;
+    if ((rc = check_precision(precision))) return rc;
+    if ((rc = check_tiling(precision, items_per_sm, tile_variant))) return rc;
+    OpLayout L;
+    op_layout(prob, precision, &L, items_target(precision, items_per_sm), tile_variant);
     if ((rc = check_ws(ws, ws_bytes, L.bytes))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync((char *)ws + L.off_hdr, 0, sizeof(WsHeader), st);
     if (e == cudaSuccess) e = op_prepare(prob, L, (char *)ws, st);
     if (e != cudaSuccess) return cuda_fail(e);
-    record_prepared(ws, prob, precision);
+    record_prepared(ws, prob, precision, items_per_sm, tile_variant);
     return AEXP_OK;
 }
 
@@ -204,10 +238,12 @@ int a_exp_forward(const aexp_problem *prob, int precision, const void *x, void *
     if ((rc = check_precision(precision))) return rc;
     if (!x || !y) return AEXP_ERR_INVALID_ARG;
     if (!aligned(x, 8) || !aligned(y, 8)) return AEXP_ERR_MISALIGNED;
+    int items = 0, variant = 0;
+    const bool prepared = prepared_tiling(ws, prob, precision, &items, &variant);
     OpLayout L;
-    op_layout(prob, precision, &L);
+    op_layout(prob, precision, &L, items_target(precision, items), variant);
     if ((rc = check_ws(ws, ws_bytes, L.bytes))) return rc;
-    if (!is_prepared(ws, prob, precision)) return AEXP_ERR_NOT_PREPARED;
+    if (!prepared) return AEXP_ERR_NOT_PREPARED;
     cudaStream_t st = (cudaStream_t)stream;
     char *w = (char *)ws;
     cudaError_t e = op_apply_forward(L, (const float2 *)x, w, st);
@@ -222,10 +258,12 @@ int a_exp_adjoint(const aexp_problem *prob, int precision, const void *y, void *
     if ((rc = check_precision(precision))) return rc;
     if (!x || !y) return AEXP_ERR_INVALID_ARG;
     if (!aligned(x, 8) || !aligned(y, 8)) return AEXP_ERR_MISALIGNED;
+    int items = 0, variant = 0;
+    const bool prepared = prepared_tiling(ws, prob, precision, &items, &variant);
     OpLayout L;
-    op_layout(prob, precision, &L);
+    op_layout(prob, precision, &L, items_target(precision, items), variant);
     if ((rc = check_ws(ws, ws_bytes, L.bytes))) return rc;
-    if (!is_prepared(ws, prob, precision)) return AEXP_ERR_NOT_PREPARED;
+    if (!prepared) return AEXP_ERR_NOT_PREPARED;
     cudaStream_t st = (cudaStream_t)stream;
     char *w = (char *)ws;
     float2 *yt = (float2 *)(w + L.off_yt);

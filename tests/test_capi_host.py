@@ -154,17 +154,32 @@ def test_items_per_sm_sizes_and_validation(L):
         assert sizes[(prec, 2)] <= sizes[(prec, 8)] <= sizes[(prec, 32)]
         # 0 is the default: 16 per SM for FP32, 8 for the tensor cores
         assert sizes[(prec, 0)] == sizes[(prec, 16 if prec == ax.FP32 else 8)]
-        variants = (0, 1) if prec != ax.FP16X2_TC else (0,)   # 32 coils: FP32 and BF16 have two tilings
-        for ips in (2, 4, 8, 16, 32):
-            o.items_per_sm, o.tile_variant = ips, 1
-            n = ctypes.c_size_t()
-            assert L.aexp_recon_workspace_size(ctypes.byref(p), ctypes.byref(o), ctypes.byref(n)) == 0
-            sizes[(prec, ips, 1)] = n.value
+        # 32 coils: FP32 has three tilings, the tensor-core forms two
+        variants = (1, 2) if prec == ax.FP32 else (1,)
+        for v in variants:
+            for ips in (2, 4, 8, 16, 32):
+                o.items_per_sm, o.tile_variant = ips, v
+                n = ctypes.c_size_t()
+                assert L.aexp_recon_workspace_size(ctypes.byref(p), ctypes.byref(o), ctypes.byref(n)) == 0
+                sizes[(prec, ips, v)] = n.value
         o.items_per_sm, o.tile_variant = 0, 0
         need = ctypes.c_size_t()
         assert L.aexp_autotune_workspace_size(ctypes.byref(p), 1, ctypes.byref(o), ctypes.byref(need)) == 0
         assert need.value == max([sizes[(prec, c)] for c in (2, 4, 8, 16, 32)] +
-                                 [sizes[(prec, c, 1)] for c in (2, 4, 8, 16, 32) if 1 in variants])
+                                 [sizes[(prec, c, v)] for c in (2, 4, 8, 16, 32) for v in variants])
+        # the operator-only workspace of a chosen launch shape; (0, 0) is aexp_workspace_size's
+        w0, wt = ctypes.c_size_t(), ctypes.c_size_t()
+        assert L.aexp_workspace_size(ctypes.byref(p), prec, ctypes.byref(w0)) == 0
+        assert L.aexp_workspace_size_tiled(ctypes.byref(p), prec, 0, 0, ctypes.byref(wt)) == 0
+        assert wt.value == w0.value
+        for v in variants:
+            assert L.aexp_workspace_size_tiled(ctypes.byref(p), prec, 8, v, ctypes.byref(wt)) == 0
+        top = 3 if prec == ax.FP32 else 2
+        assert L.aexp_workspace_size_tiled(ctypes.byref(p), prec, 0, top, ctypes.byref(wt)) == -1
+        assert L.aexp_workspace_size_tiled(ctypes.byref(p), prec, 257, 0, ctypes.byref(wt)) == -1
+        assert L.aexp_prepare_tiled(ctypes.byref(p), prec, 0, top, None, 0, None) == -1
+    # FP32 three-multiplication tiling: b carries three floats per voxel and coil instead of two
+    assert sizes[(ax.FP32, 16, 2)] >= sizes[(ax.FP32, 16)] + 4 * 32 * 200 * 200
     for bad in (-1, 257):
         o.items_per_sm = bad
         assert L.aexp_recon_workspace_size(ctypes.byref(p), ctypes.byref(o), ctypes.byref(n)) == -1
@@ -180,6 +195,8 @@ def test_items_per_sm_sizes_and_validation(L):
     variant = ctypes.c_int()
     assert L.aexp_autotune(arr, 2, ctypes.byref(o), None, 0, None, ctypes.byref(best), ctypes.byref(variant),
                            None) == -1
-    o.tile_variant = 2   # out of range
+    o.tile_variant = 2   # out of range for the tensor-core forms
     assert L.aexp_recon_workspace_size(ctypes.byref(p), ctypes.byref(o), ctypes.byref(n)) == -1
-    o.tile_variant = 0
+    o.precision, o.tile_variant = ax.FP32, 3
+    assert L.aexp_recon_workspace_size(ctypes.byref(p), ctypes.byref(o), ctypes.byref(n)) == -1
+    o.precision, o.tile_variant = ax.BF16_TC, 0

@@ -57,11 +57,11 @@ def case():
     return p, x, y, oracle.forward(p, x), oracle.adjoint(p, y)
 
 
-def _apply(ax, p, x, y, prec):
+def _apply(ax, p, x, y, prec, tile_variant=0):
     import torch
     prob = ax.Problem.from_arrays(p)
-    ws = ax.workspace(prob, prec)
-    ax.prepare(prob, ws, prec)
+    ws = ax.workspace(prob, prec, tile_variant=tile_variant)
+    ax.prepare(prob, ws, prec, tile_variant=tile_variant)
     f = ax.a_exp_forward(prob, torch.as_tensor(x, device="cuda"), ws, precision=prec)
     a = ax.a_exp_adjoint(prob, torch.as_tensor(y, device="cuda"), ws, precision=prec)
     torch.cuda.synchronize()
@@ -69,14 +69,16 @@ def _apply(ax, p, x, y, prec):
     return f.cpu().numpy(), a.cpu().numpy()
 
 
-@pytest.mark.parametrize("precision", ["FP32", "FP16X2_TC", "BF16_TC"])
-def test_whole_array_matches_oracle(ax, case, precision):
+@pytest.mark.parametrize("precision,tiling", [("FP32", 0), ("FP32", 2), ("FP16X2_TC", 0), ("BF16_TC", 0)])
+def test_whole_array_matches_oracle(ax, case, precision, tiling):
+    """FP32 tiling 2: each complex multiply-accumulate as three real products."""
     p, x, y, fref, aref = case
-    f, a = _apply(ax, p, x, y, getattr(ax, precision))
+    f, a = _apply(ax, p, x, y, getattr(ax, precision), tiling)
     ef, ea = rel(f, fref), rel(a, aref)
     mf, ma = maxrel(f, fref), maxrel(a, aref)
     bar = L2_BAR[precision]
-    print(f"{precision}: forward L2 {ef:.2e} max {mf:.2e}; adjoint L2 {ea:.2e} max {ma:.2e} (bar {bar:.0e})")
+    print(f"{precision} tiling {tiling}: forward L2 {ef:.2e} max {mf:.2e}; adjoint L2 {ea:.2e} max {ma:.2e} "
+          f"(bar {bar:.0e})")
     assert ef < bar and ea < bar
     assert mf < MAX_FACTOR * bar and ma < MAX_FACTOR * bar
     # every coil row and every voxel is written (no element left at zero by a missed tile)
