@@ -333,11 +333,6 @@ def _run_ours(args, rank, world, local, dev):
     nterms = p["nl"] + 1
     flops_per_launch = nr * nt * (8.0 * nc + 2.0 * nterms + 4.0)   # contraction + phase FMAs + reduction
     achieved = flops_per_launch / (kern[dom] / 1e3) / 1e12
-    # the FP32 tiling 2 executes 3 FMAs per complex multiply-accumulate (Gauss) plus one add per
-    # pair, so its executed flops sit below the algorithmic count
-    three_mult = args.form == "fp32" and opts.tile_variant == 2 and nc > 20
-    executed = nr * nt * ((6.0 if three_mult else 8.0) * nc + 2.0 * nterms + (6.0 if three_mult else 4.0))
-    executed_tflops = executed / (kern[dom] / 1e3) / 1e12
     sm_mhz_peak = measured_peaks().get("sm_max_mhz", 2070.0)
     peak = fp32_alu_peak_tflops(sm_mhz_peak)
     traffic = None
@@ -551,11 +546,8 @@ def _run_ours(args, rank, world, local, dev):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": dom,
                          "kernel_ms": kern[dom],
-                         "executed_frac": executed_tflops / peak,
-                         "complex_mac": "3 FMAs (Gauss three-product form)" if three_mult else "4 FMAs",
                          "peak_basis": f"FP32 FMA pipe 152 SM x 128 lanes x 2 flop at {sm_mhz_peak:.0f} MHz "
-                                       "(sm_max_mhz of MEASURED_PEAKS.json); achieved counts 8 flops per "
-                                       "complex multiply-accumulate, executed_frac the flops the kernel issues"},
+                                       "(sm_max_mhz of MEASURED_PEAKS.json)"},
             "kernels_ms": kern,
             "comparison": comparison,
             "ls_baseline_cgls20": ls_baseline,
@@ -578,7 +570,6 @@ def _run_ours(args, rank, world, local, dev):
                           "op_ms": round(c["roofline"]["kernel_ms"], 3) if "roofline" in c else None}
         out["tc_summary"] = {"fp32_s_per_slice": round(ms_per_step / 1e3, 4), "fp32_nrmse": round(nrmse, 4),
                              "fp32_fma_frac": round(achieved / peak, 3),
-                             "fp32_executed_frac": round(executed_tflops / peak, 3),
                              "fp32_tile_variant": opts.tile_variant, **summary}
         if ragged:
             out["ragged_summary"] = {"problems": ragged["config"]["problems"], "s_per_batch": round(ragged["ms_per_step"] / 1e3, 2),

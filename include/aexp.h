@@ -170,18 +170,15 @@ typedef struct aexp_recon_opts {
                                launch holds about 152 x items_per_sm blocks or persistent
                                work items (shared among the problems of a batch); 0 = the
                                default (FP32 16, tensor cores 8); aexp_autotune picks one */
-    int tile_variant;       /* kernel tiling of the operator launches, 0 = the default.
-                               FP32 form at more than 20 coils (at fewer, 1 and 2 act as 0):
-                               1 = two samples per forward thread and two voxels per adjoint
+    int tile_variant;       /* kernel tiling of the operator launches, 0 = the default, 1 = the
+                               alternative.  FP32 form at more than 20 coils (at fewer, 1 acts
+                               as 0): two samples per forward thread and two voxels per adjoint
                                thread at 2 blocks per SM (default: one each at 4 blocks per
-                               SM); 2 = each complex multiply-accumulate as three real FMAs
-                               into three sums per coil (Gauss's three-product identity), one
-                               sample / voxel per thread at 3 blocks per SM.  BF16 form: 1 = a
-                               6-deep contraction-operand ring and 4 phase-operand stages
-                               (default 4 and 3).  FP16 hi+lo form: 1 = the phase sums on the
-                               CUDA cores (default: on the tensor cores, like the BF16 form).
-                               aexp_autotune picks it; a workspace must be used with the tiling
-                               it was prepared for */
+                               SM).  BF16 form: a 6-deep contraction-operand ring and 4
+                               phase-operand stages (default 4 and 3).  FP16 hi+lo form: the
+                               phase sums on the CUDA cores (default: on the tensor cores, like
+                               the BF16 form).  aexp_autotune picks it; a workspace must be used
+                               with the tiling it was prepared for */
 } aexp_recon_opts;
 
 /* Fill opts with defaults: FP32, Haar, 3 levels, 30 power iterations, estimate L_f,
@@ -258,8 +255,7 @@ AEXP_API int aexp_power_lipschitz(const aexp_problem *prob, int precision, const
  * Autotuning of the operator's launch shape (no counterpart in the paper; it serves the
  * ragged many-problem workload of Sec. 2.2.1's protocol grid).  Candidates: the work-item
  * granularity items_per_sm in {2, 4, 8, 16, 32} times the kernel tilings of the precision
- * (tile_variant 0, 1 and 2 for the FP32 form at more than 20 coils, 0 and 1 for the tensor-core
- * forms, see aexp_recon_opts).  For each candidate
+ * (tile_variant 0 and 1 where the form has two, see aexp_recon_opts).  For each candidate
  * the call lays out the workspace, prepares the problem(s) and times one A^H A application
  * with CUDA events, after one warm-up, 5 times (3 for a batch): of `probs[0]` alone when
  * nprob == 1 (the cs_recon layout, any precision), of the whole batch when nprob > 1 (the

@@ -136,16 +136,7 @@ constexpr int fwd_mt_for(int CB) { return CB >= 32 ? AEXP_FWD_MT32 : CB >= 16 ? 
 constexpr int adj_mr_for(int CB) { return CB >= 32 ? AEXP_ADJ_MR32 : CB >= 16 ? 2 : CB >= 8 ? 2 : 4; }
 // tiling variant 1 of the FP32 form at 32 coils: two samples / voxels per thread, 2 blocks per SM
 constexpr int kFp32AltBlocking = 2;
-// tiling variant 2 of the FP32 form at 32 coils: the complex products as three real products
-// (one sample / voxel per thread, 3 blocks per SM)
-constexpr int kFp32ThreeMult = 2;
-// tilings a precision accepts (aexp_recon_opts::tile_variant < this)
-inline int tile_variant_limit(int precision) { return precision == AEXP_FP32 ? 3 : 2; }
-// FP32 form laid out for the three-multiplication kernels (tiling 2 at 32 coils): b carries
-// three floats per voxel and coil instead of two
-inline bool fp32_3m(const OpLayout &L) {
-    return L.precision == AEXP_FP32 && L.CB == 32 && L.variant == kFp32ThreeMult;
-}
+constexpr int kTileVariants = 2;
 
 inline size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
 inline int cdiv(int a, int b) { return (a + b - 1) / b; }

@@ -136,9 +136,9 @@ cudaError_t launch_captured(const void *ws, const std::vector<unsigned char> &ke
     return cudaGraphLaunch(ge.exec, st);
 }
 
-int check_tiling(int precision, int items_per_sm, int tile_variant) {
+int check_tiling(int items_per_sm, int tile_variant) {
     if (items_per_sm < 0 || items_per_sm > 256) return AEXP_ERR_INVALID_ARG;
-    if (tile_variant < 0 || tile_variant >= tile_variant_limit(precision)) return AEXP_ERR_INVALID_ARG;
+    if (tile_variant < 0 || tile_variant >= kTileVariants) return AEXP_ERR_INVALID_ARG;
     return AEXP_OK;
 }
 
@@ -149,7 +149,7 @@ int check_opts(const aexp_recon_opts *o) {
     if (o->wavelet != AEXP_WAVELET_HAAR && o->wavelet != AEXP_WAVELET_DB4) return AEXP_ERR_INVALID_ARG;
     if (o->levels < 1 || o->levels > 12) return AEXP_ERR_INVALID_ARG;
     if (!(o->lipschitz > 0.0) && o->n_power < 1) return AEXP_ERR_INVALID_ARG;
-    if ((rc = check_tiling(o->precision, o->items_per_sm, o->tile_variant))) return rc;
+    if ((rc = check_tiling(o->items_per_sm, o->tile_variant))) return rc;
     if (o->lambda_rule != AEXP_LAMBDA_GIVEN && o->lambda_rule != AEXP_LAMBDA_RAYLEIGH) return AEXP_ERR_INVALID_ARG;
     if (o->lambda_rule == AEXP_LAMBDA_RAYLEIGH && !o->undecimated) return AEXP_ERR_UNSUPPORTED;
     if (!aligned(o->x0, 8) || !aligned(o->power_init, 8) || !aligned(o->lambda_out, 8)) return AEXP_ERR_MISALIGNED;
@@ -206,7 +206,7 @@ int aexp_workspace_size_tiled(const aexp_problem *prob, int precision, int items
     int rc = check_problem(prob);
     if (rc) return rc;
     if ((rc = check_precision(precision))) return rc;
-    if ((rc = check_tiling(precision, items_per_sm, tile_variant))) return rc;
+    if ((rc = check_tiling(items_per_sm, tile_variant))) return rc;
     if (!bytes) return AEXP_ERR_INVALID_ARG;
     OpLayout L;
     op_layout(prob, precision, &L, items_target(precision, items_per_sm), tile_variant);
@@ -219,7 +219,7 @@ int aexp_prepare_tiled(const aexp_problem *prob, int precision, int items_per_sm
     int rc = check_problem(prob);
     if (rc) return rc;
     if ((rc = check_precision(precision))) return rc;
-    if ((rc = check_tiling(precision, items_per_sm, tile_variant))) return rc;
+    if ((rc = check_tiling(items_per_sm, tile_variant))) return rc;
     OpLayout L;
     op_layout(prob, precision, &L, items_target(precision, items_per_sm), tile_variant);
     if ((rc = check_ws(ws, ws_bytes, L.bytes))) return rc;

@@ -35,8 +35,7 @@ int op_layout(const aexp_problem *p, int precision, OpLayout *L, int target_item
 
     // forward: blocks own 128*mt samples and a contiguous run of tiles
     const bool alt32 = precision == AEXP_FP32 && o.CB == 32 && variant == 1;
-    const bool three_mult = fp32_3m(o);  // one sample / voxel per thread
-    o.fwd_mt = alt32 ? kFp32AltBlocking : three_mult ? 1 : fwd_mt_for(o.CB);
+    o.fwd_mt = alt32 ? kFp32AltBlocking : fwd_mt_for(o.CB);
     o.fwd_tblocks = o.ntp / (kFwdThreads * o.fwd_mt);
     {
         int by_sum = cdiv(o.ntiles, 32);                       // <= 32 tiles (2048 voxels) per block
@@ -47,7 +46,7 @@ int op_layout(const aexp_problem *p, int precision, OpLayout *L, int target_item
         o.fwd_splits = cdiv(o.ntiles, o.fwd_tiles_per_split);
     }
     // adjoint: blocks own 2*mr tiles (128*mr voxels) and a contiguous run of samples
-    o.adj_mr = alt32 ? kFp32AltBlocking : three_mult ? 1 : adj_mr_for(o.CB);
+    o.adj_mr = alt32 ? kFp32AltBlocking : adj_mr_for(o.CB);
     o.adj_vblocks = cdiv(o.ntiles, 2 * o.adj_mr);
     {
         int nstage = o.ntp / kAdjStageT;
@@ -88,11 +87,9 @@ int op_layout(const aexp_problem *p, int precision, OpLayout *L, int target_item
     o.off_dh = take(sizeof(float) * o.LP * o.nr_pad);
     o.off_f0 = take(sizeof(float) * (size_t)o.ntiles * o.ntp);
     o.off_S = take(sizeof(float2) * (size_t)o.CB * o.nr_pad);
-    // FP32: b = S x in tile order (three-multiplication tiling: three floats per coil);
-    // tensor-core forms: the packed B operand (FP16 hi+lo: two images)
+    // FP32: b = S x in tile order; tensor-core forms: the packed B operand (FP16 hi+lo: two images)
     const size_t npk = precision == AEXP_FP16X2_TC ? 2 : 1;
-    o.off_b = take(three_mult ? 3 * sizeof(float) * (size_t)o.CB * o.nr_pad
-                              : npk * sizeof(float2) * (size_t)o.CB * o.nr_pad);
+    o.off_b = take(npk * sizeof(float2) * (size_t)o.CB * o.nr_pad);
     o.off_fpart = take(sizeof(float2) * (size_t)o.fwd_splits * o.ntp * o.CB);
     o.off_yt = take(sizeof(float2) * (size_t)o.ntp * o.CB);
     o.off_apart = take(sizeof(float2) * (size_t)o.adj_splits * o.nr_pad);

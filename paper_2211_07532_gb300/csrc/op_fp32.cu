@@ -321,261 +321,6 @@ __global__ void __launch_bounds__(kAdjThreads, MR == 1 ? 4 : 2)
     }
 }
 
-// ---- three-multiplication form of the complex products (tiling 2 at 32 coils) ----
-//
-// Gauss's identity for a complex product, (a + ib)(x + iy) = [x(a + b) - b(x + y)] +
-// i[x(a + b) + a(y - x)], needs three real products, one of them shared by the real and the
-// imaginary part.  Summed over voxels (forward) or samples (adjoint) the three products go to
-// three accumulators per coil and are combined once, after the whole run:
-//   forward, E = c - i s, b = S_c x:   A1 = sum br (c - s),  A2 = sum c (bi - br),
-//                                      A3 = sum s (br + bi),  y = (A1 + A3) + i (A1 + A2);
-//   adjoint, conj(E) = c + i s, y:     U1 = sum yr (c + s),  U2 = sum c (yi - yr),
-//                                      U3 = sum s (yr + yi),  u = (U1 - U3) + i (U1 + U2).
-// c -/+ s is formed once per pair for all coils, and the coil-side combinations once per voxel
-// (coil weighting) or per staged sample, so each pair and coil costs 3 FMAs instead of 4.  The
-// coil-side values of a voxel or sample: CB/2 float4 (re 2q, re 2q+1, im-re 2q, im-re 2q+1) for
-// the coil pairs q, then CB/4 float4 (re+im of coils 4u .. 4u+3).  96 accumulator registers
-// per thread leave room for 3 blocks (12 warps) per SM.
-constexpr int k3mBlocksPerSM = 3;
-
-template <int CB, int LP>
-__global__ void __launch_bounds__(kFwdThreads, k3mBlocksPerSM)
-    fwd_fp32_3m_kernel(const float *__restrict__ khi_l, const float *__restrict__ f0, const float *__restrict__ dh,
-                       const float4 *__restrict__ b, float2 *__restrict__ part, int ntp, int ntiles,
-                       int tiles_per_split, int *status) {
-    constexpr int NQ = CB / 2, NU = CB / 4, NV = NQ + NU;  // float4 per voxel
-    constexpr int kVoxUnroll = LP == 12 || LP == 32 ? 1 : 2;  // the unrolling that spills fewest registers
-    constexpr unsigned DH_BYTES = kTileVox * LP * sizeof(float);
-    constexpr unsigned B_BYTES = kTileVox * NV * sizeof(float4);
-    constexpr unsigned STAGE = DH_BYTES + B_BYTES;
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint64_t bar[2];
-
-    const int tid = threadIdx.x;
-    const int split = blockIdx.y;
-    const int tile0 = split * tiles_per_split;
-    const int ntl = min(ntiles, tile0 + tiles_per_split) - tile0;
-    const int t = blockIdx.x * kFwdThreads + tid;
-
-    float2 kh[LP / 2];  // (even term, odd term)
-#pragma unroll
-    for (int l = 0; l < LP / 2; ++l)
-        kh[l] = make_float2(khi_l[(size_t)(2 * l) * ntp + t], khi_l[(size_t)(2 * l + 1) * ntp + t]);
-
-    float2 a1[NQ], a2[NQ], a3[NQ];  // coils (2q, 2q+1)
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) a1[q] = a2[q] = a3[q] = make_float2(0.f, 0.f);
-
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-
-    auto issue = [&](int i) {
-        int buf = i & 1;
-        unsigned char *dst = smem + buf * STAGE;
-        size_t tile = (size_t)(tile0 + i);
-        mbar_arrive_expect_tx(&bar[buf], STAGE);
-        bulk_g2s(dst, dh + tile * kTileVox * LP, DH_BYTES, &bar[buf]);
-        bulk_g2s(dst + DH_BYTES, b + tile * kTileVox * NV, B_BYTES, &bar[buf]);
-    };
-    if (tid == 0) {
-        if (ntl > 0) issue(0);
-        if (ntl > 1) issue(1);
-    }
-
-    for (int i = 0; i < ntl; ++i) {
-        const int buf = i & 1;
-        bool ok = mbar_wait_bounded(&bar[buf], (i >> 1) & 1, status);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0)
-                for (int k = i; k < min(ntl, i + 2); ++k) mbar_wait_bounded(&bar[k & 1], (k >> 1) & 1, status);
-            __syncthreads();
-            return;
-        }
-        const float4 *sdh = reinterpret_cast<const float4 *>(smem + buf * STAGE);
-        const float4 *sb = reinterpret_cast<const float4 *>(smem + buf * STAGE + DH_BYTES);
-        const float f = f0[(size_t)(tile0 + i) * ntp + t];
-
-#pragma unroll kVoxUnroll
-        for (int v = 0; v < kTileVox; ++v) {
-            float2 p = make_float2(f, 0.f);
-#pragma unroll
-            for (int q = 0; q < LP / 4; ++q) {
-                float4 w = sdh[v * (LP / 4) + q];
-                p = ffma2(kh[2 * q], make_float2(w.x, w.y), p);
-                p = ffma2(kh[2 * q + 1], make_float2(w.z, w.w), p);
-            }
-            float c, s;
-            turns_sincos(p.x + p.y, s, c);
-            const float2 cms = dup2(c - s), cc = dup2(c), ss = dup2(s);
-            const float4 *bv = sb + v * NV;
-#pragma unroll
-            for (int u = 0; u < NU; ++u) {
-                const float4 sum = bv[NQ + u];  // br + bi of coils 4u .. 4u+3
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int q = 2 * u + h;
-                    const float4 bb = bv[q];   // (br 2q, br 2q+1, bi-br 2q, bi-br 2q+1)
-                    a1[q] = ffma2(cms, make_float2(bb.x, bb.y), a1[q]);
-                    a2[q] = ffma2(cc, make_float2(bb.z, bb.w), a2[q]);
-                    a3[q] = ffma2(ss, h ? make_float2(sum.z, sum.w) : make_float2(sum.x, sum.y), a3[q]);
-                }
-            }
-        }
-        __syncthreads();
-        if (tid == 0 && i + 2 < ntl) issue(i + 2);
-    }
-
-    float4 *dst = reinterpret_cast<float4 *>(part + ((size_t)split * ntp + t) * CB);
-#pragma unroll
-    for (int q = 0; q < NQ; ++q)
-        dst[q] = make_float4(a1[q].x + a3[q].x, a1[q].x + a2[q].x, a1[q].y + a3[q].y, a1[q].y + a2[q].y);
-}
-
-template <int CB, int LP>
-__global__ void __launch_bounds__(kAdjThreads, k3mBlocksPerSM)
-    adj_fp32_3m_kernel(const float *__restrict__ khi_t, const float *__restrict__ f0, const float *__restrict__ dh,
-                       const float2 *__restrict__ Sp, const float2 *__restrict__ yt, float2 *__restrict__ part,
-                       int ntp, int ntiles, int t_per_split, int *status) {
-    constexpr int TS = kAdjStageT;
-    constexpr int NT = 2;  // tiles per block (one voxel per thread)
-    constexpr int NQ = CB / 2, NU = CB / 4, NV = NQ + NU;
-    constexpr unsigned K_BYTES = TS * LP * sizeof(float);
-    constexpr unsigned Y_BYTES = TS * CB * sizeof(float2);
-    constexpr unsigned F_BYTES = TS * sizeof(float);
-    constexpr unsigned STAGE = K_BYTES + Y_BYTES + NT * F_BYTES;
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint64_t bar[2];
-    // after the two bulk-copy buffers: the staged samples' coil-side values (3M layout)
-    float4 *sye = reinterpret_cast<float4 *>(smem + 2 * STAGE);
-
-    const int tid = threadIdx.x;
-    const int split = blockIdx.y;
-    const int tile_base = NT * blockIdx.x;
-    const int t0 = split * t_per_split;
-    const int nst = (min(ntp, t0 + t_per_split) - t0) / TS;
-
-    const int pv = blockIdx.x * kAdjThreads + tid;
-    const bool valid = pv / kTileVox < ntiles;
-    float2 d[LP / 2];
-    {
-        const float4 *src = reinterpret_cast<const float4 *>(dh + (size_t)(valid ? pv : 0) * LP);
-#pragma unroll
-        for (int q = 0; q < LP / 4; ++q) {
-            float4 w = src[q];
-            d[2 * q] = valid ? make_float2(w.x, w.y) : make_float2(0.f, 0.f);
-            d[2 * q + 1] = valid ? make_float2(w.z, w.w) : make_float2(0.f, 0.f);
-        }
-    }
-    float2 u1[NQ], u2[NQ], u3[NQ];  // coils (2q, 2q+1)
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) u1[q] = u2[q] = u3[q] = make_float2(0.f, 0.f);
-
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-
-    auto issue = [&](int i) {
-        int buf = i & 1;
-        unsigned char *dst = smem + buf * STAGE;
-        size_t ts = (size_t)t0 + (size_t)i * TS;
-        mbar_arrive_expect_tx(&bar[buf], STAGE);
-        bulk_g2s(dst, khi_t + ts * LP, K_BYTES, &bar[buf]);
-        bulk_g2s(dst + K_BYTES, yt + ts * CB, Y_BYTES, &bar[buf]);
-        for (int q = 0; q < NT; ++q) {
-            int tile = min(tile_base + q, ntiles - 1);  // past the end: a valid row, results discarded
-            bulk_g2s(dst + K_BYTES + Y_BYTES + q * F_BYTES, f0 + (size_t)tile * ntp + ts, F_BYTES, &bar[buf]);
-        }
-    };
-    if (tid == 0) {
-        if (nst > 0) issue(0);
-        if (nst > 1) issue(1);
-    }
-
-    for (int i = 0; i < nst; ++i) {
-        const int buf = i & 1;
-        bool ok = mbar_wait_bounded(&bar[buf], (i >> 1) & 1, status);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0)
-                for (int k = i; k < min(nst, i + 2); ++k) mbar_wait_bounded(&bar[k & 1], (k >> 1) & 1, status);
-            __syncthreads();
-            return;
-        }
-        const float4 *sk = reinterpret_cast<const float4 *>(smem + buf * STAGE);
-        const float4 *sy = reinterpret_cast<const float4 *>(smem + buf * STAGE + K_BYTES);
-        const float *sf = reinterpret_cast<const float *>(smem + buf * STAGE + K_BYTES + Y_BYTES);
-        // staged y (re c, im c, re c+1, im c+1) -> the 3M coil-side values of each sample
-        for (int k = tid; k < TS * NQ; k += kAdjThreads) {
-            const int s = k / NQ, q = k % NQ;
-            const float4 w = sy[k];
-            sye[s * NV + q] = make_float4(w.x, w.z, w.y - w.x, w.w - w.z);
-            reinterpret_cast<float2 *>(sye + s * NV + NQ)[q] = make_float2(w.x + w.y, w.z + w.w);
-        }
-        __syncthreads();
-
-        // phase + sincos of sample s for this thread's voxel (two pairs of chains)
-        auto encode = [&](int s, float &cs, float &sn) {
-            float2 p = make_float2(sf[(tid / kTileVox) * TS + s], 0.f), pb = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int q = 0; q < LP / 4; ++q) {
-                float4 kk = sk[s * (LP / 4) + q];
-                p = ffma2(make_float2(kk.x, kk.y), d[2 * q], p);
-                pb = ffma2(make_float2(kk.z, kk.w), d[2 * q + 1], pb);
-            }
-            turns_sincos((p.x + p.y) + (pb.x + pb.y), sn, cs);
-        };
-        float cnx, snx;
-        encode(0, cnx, snx);
-#pragma unroll 1
-        for (int s = 0; s < TS; ++s) {
-            const float cs = cnx, sn = snx;
-            if (s + 1 < TS) encode(s + 1, cnx, snx);
-            const float2 cps = dup2(cs + sn), cc = dup2(cs), ss = dup2(sn);
-            const float4 *ys = sye + s * NV;
-#pragma unroll
-            for (int u = 0; u < NU; ++u) {
-                const float4 sum = ys[NQ + u];  // yr + yi of coils 4u .. 4u+3
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int q = 2 * u + h;
-                    const float4 yy = ys[q];   // (yr 2q, yr 2q+1, yi-yr 2q, yi-yr 2q+1)
-                    u1[q] = ffma2(cps, make_float2(yy.x, yy.y), u1[q]);
-                    u2[q] = ffma2(cc, make_float2(yy.z, yy.w), u2[q]);
-                    u3[q] = ffma2(ss, h ? make_float2(sum.z, sum.w) : make_float2(sum.x, sum.y), u3[q]);
-                }
-            }
-        }
-        __syncthreads();  // sye and this buffer are rewritten by the next stage / copy
-        if (tid == 0 && i + 2 < nst) issue(i + 2);
-    }
-
-    if (!valid) return;
-    const float4 *s4 = reinterpret_cast<const float4 *>(Sp + (size_t)pv * CB);
-    float xr = 0.f, xi = 0.f;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const float4 sv = s4[q];
-        const float2 ure = make_float2(u1[q].x - u3[q].x, u1[q].y - u3[q].y);
-        const float2 uim = make_float2(u1[q].x + u2[q].x, u1[q].y + u2[q].y);
-        // conj(S) * u
-        xr = fmaf(sv.x, ure.x, xr);
-        xr = fmaf(sv.y, uim.x, xr);
-        xi = fmaf(sv.x, uim.x, xi);
-        xi = fmaf(-sv.y, ure.x, xi);
-        xr = fmaf(sv.z, ure.y, xr);
-        xr = fmaf(sv.w, uim.y, xr);
-        xi = fmaf(sv.z, uim.y, xi);
-        xi = fmaf(-sv.w, ure.y, xi);
-    }
-    part[(size_t)split * (size_t)(ntiles * kTileVox) + pv] = make_float2(xr, xi);
-}
-
 // ---- reductions of the partial sums (fixed order => deterministic) ----
 
 __global__ void fwd_reduce_public_kernel(const float2 *part, int splits, int ntp, int CB, int nt, int nc, float2 *y) {
@@ -667,54 +412,19 @@ cudaError_t launch_adj_mr(const OpLayout &L, const float2 *yt, char *ws, cudaStr
     return cudaGetLastError();
 }
 
-template <int CB, int LP>
-cudaError_t launch_fwd_3m(const OpLayout &L, char *ws, cudaStream_t st) {
-    constexpr unsigned STAGE = kTileVox * LP * sizeof(float) + kTileVox * CB * 3 * sizeof(float);
-    auto kern = fwd_fp32_3m_kernel<CB, LP>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * STAGE);
-    if (e != cudaSuccess) return e;
-    WsHeader *hdr = (WsHeader *)(ws + L.off_hdr);
-    kern<<<dim3(L.fwd_tblocks, L.fwd_splits), kFwdThreads, 2 * STAGE, st>>>(
-        (const float *)(ws + L.off_khi_l), (const float *)(ws + L.off_f0), (const float *)(ws + L.off_dh),
-        (const float4 *)(ws + L.off_b), (float2 *)(ws + L.off_fpart), L.ntp, L.ntiles, L.fwd_tiles_per_split,
-        &hdr->status);
-    return cudaGetLastError();
-}
-
-template <int CB, int LP>
-cudaError_t launch_adj_3m(const OpLayout &L, const float2 *yt, char *ws, cudaStream_t st) {
-    constexpr unsigned STAGE = kAdjStageT * (LP * sizeof(float) + CB * sizeof(float2) + 2 * sizeof(float));
-    constexpr unsigned SMEM = 2 * STAGE + kAdjStageT * CB * 3 * sizeof(float);
-    auto kern = adj_fp32_3m_kernel<CB, LP>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-    if (e != cudaSuccess) return e;
-    WsHeader *hdr = (WsHeader *)(ws + L.off_hdr);
-    kern<<<dim3(L.adj_vblocks, L.adj_splits), kAdjThreads, SMEM, st>>>(
-        (const float *)(ws + L.off_khi_t), (const float *)(ws + L.off_f0), (const float *)(ws + L.off_dh),
-        (const float2 *)(ws + L.off_S), yt, (float2 *)(ws + L.off_apart), L.ntp, L.ntiles, L.adj_t_per_split,
-        &hdr->status);
-    return cudaGetLastError();
-}
-
-// The layout's kernel tiling: the default register blocking of the coil padding, or at 32
-// coils the alternatives (two samples / voxels per thread; the three-multiplication form).
+// The layout's register blocking (fwd_mt / adj_mr): the default of the coil padding, or the
+// alternative tiling at 32 coils.
 template <int CB, int LP>
 cudaError_t launch_fwd(const OpLayout &L, char *ws, cudaStream_t st) {
-    if constexpr (CB == 32) {
-        if (fp32_3m(L)) return launch_fwd_3m<CB, LP>(L, ws, st);
-        if constexpr (fwd_mt_for(32) != kFp32AltBlocking)
-            if (L.fwd_mt == kFp32AltBlocking) return launch_fwd_mt<CB, LP, kFp32AltBlocking>(L, ws, st);
-    }
+    if constexpr (CB == 32 && fwd_mt_for(32) != kFp32AltBlocking)
+        if (L.fwd_mt == kFp32AltBlocking) return launch_fwd_mt<CB, LP, kFp32AltBlocking>(L, ws, st);
     return launch_fwd_mt<CB, LP, fwd_mt_for(CB)>(L, ws, st);
 }
 
 template <int CB, int LP>
 cudaError_t launch_adj(const OpLayout &L, const float2 *yt, char *ws, cudaStream_t st) {
-    if constexpr (CB == 32) {
-        if (fp32_3m(L)) return launch_adj_3m<CB, LP>(L, yt, ws, st);
-        if constexpr (adj_mr_for(32) != kFp32AltBlocking)
-            if (L.adj_mr == kFp32AltBlocking) return launch_adj_mr<CB, LP, kFp32AltBlocking>(L, yt, ws, st);
-    }
+    if constexpr (CB == 32 && adj_mr_for(32) != kFp32AltBlocking)
+        if (L.adj_mr == kFp32AltBlocking) return launch_adj_mr<CB, LP, kFp32AltBlocking>(L, yt, ws, st);
     return launch_adj_mr<CB, LP, adj_mr_for(CB)>(L, yt, ws, st);
 }
 

@@ -133,28 +133,6 @@ __global__ void coil_weight_kernel(const float2 *Sp, const float2 *x, int nx, in
     dst[2] = out.y;
 }
 
-// The three-multiplication tiling's b: per voxel p, float4 (re c, re c+1, im-re c, im-re c+1)
-// for the coil pairs c = 2q, then float4 (re+im of coils 4u .. 4u+3); 3 * CB floats per voxel.
-__global__ void coil_weight_3m_kernel(const float2 *Sp, const float2 *x, int nx, int ny, int ntx, int nr_pad, int CB,
-                                      float *b) {
-    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (size_t)nr_pad * CB) return;
-    int p = (int)(i / CB), c = (int)(i % CB);
-    int tile = p / kTileVox, v = p % kTileVox;
-    int ix = (tile % ntx) * kTileSide + v % kTileSide, iy = (tile / ntx) * kTileSide + v / kTileSide;
-    float2 out = make_float2(0.f, 0.f);
-    if (ix < nx && iy < ny) {
-        float2 s = Sp[i];
-        float2 xv = x[(size_t)iy * nx + ix];
-        out.x = s.x * xv.x - s.y * xv.y;
-        out.y = s.x * xv.y + s.y * xv.x;
-    }
-    float *dst = b + (size_t)p * CB * 3;
-    dst[(c >> 1) * 4 + (c & 1)] = out.x;
-    dst[(c >> 1) * 4 + 2 + (c & 1)] = out.y - out.x;
-    dst[2 * CB + c] = out.x + out.y;
-}
-
 __global__ void set_items_kernel(WsHeader *hdr, int fwd_items, int adj_items) {
     hdr->item_off[0] = 0;
     hdr->item_off[1] = fwd_items;
@@ -205,11 +183,6 @@ cudaError_t op_prepare(const aexp_problem *p, const OpLayout &L, char *ws, cudaS
 cudaError_t op_coil_weight(const OpLayout &L, const float2 *x, char *ws, cudaStream_t st) {
     size_t n = (size_t)L.nr_pad * L.CB;
     const int T = 256;
-    if (fp32_3m(L)) {
-        coil_weight_3m_kernel<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(
-            (const float2 *)(ws + L.off_S), x, L.nx, L.ny, L.ntx, L.nr_pad, L.CB, (float *)(ws + L.off_b));
-        return cudaGetLastError();
-    }
     coil_weight_kernel<<<(unsigned)((n + T - 1) / T), T, 0, st>>>((const float2 *)(ws + L.off_S), x, L.nx, L.ny,
                                                                  L.ntx, L.nr_pad, L.CB, (float *)(ws + L.off_b));
     return cudaGetLastError();

@@ -45,14 +45,16 @@ std::vector<int> tune_key(const aexp_problem *probs, int nprob, int precision) {
     return k;
 }
 
-// the tilings worth timing: the FP32 form has three at 32 coils (padded: one or two samples /
-// voxels per thread, three-multiplication products), BF16 two (ring depths), FP16 hi+lo two
-// (phases on the tensor cores or on the CUDA cores)
+// the tilings worth timing: the FP32 form has two at 32 coils (padded), BF16 two (ring depths),
+// FP16 hi+lo two (phases on the tensor cores or on the CUDA cores)
 int tile_variants(const aexp_problem *probs, int precision) {
-    if (precision != AEXP_FP32) return tile_variant_limit(precision);
-    OpLayout L;
-    op_layout(probs, precision, &L);
-    return L.CB == 32 ? tile_variant_limit(precision) : 1;
+    if (precision != AEXP_FP32) return kTileVariants;
+    if (precision == AEXP_FP32) {
+        OpLayout L;
+        op_layout(probs, precision, &L);
+        return L.CB == 32 ? kTileVariants : 1;
+    }
+    return 1;
 }
 
 #define TK(x)                                      \

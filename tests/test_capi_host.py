@@ -154,8 +154,7 @@ def test_items_per_sm_sizes_and_validation(L):
         assert sizes[(prec, 2)] <= sizes[(prec, 8)] <= sizes[(prec, 32)]
         # 0 is the default: 16 per SM for FP32, 8 for the tensor cores
         assert sizes[(prec, 0)] == sizes[(prec, 16 if prec == ax.FP32 else 8)]
-        # 32 coils: FP32 has three tilings, the tensor-core forms two
-        variants = (1, 2) if prec == ax.FP32 else (1,)
+        variants = (1,)   # 32 coils: every form has two tilings
         for v in variants:
             for ips in (2, 4, 8, 16, 32):
                 o.items_per_sm, o.tile_variant = ips, v
@@ -174,12 +173,10 @@ def test_items_per_sm_sizes_and_validation(L):
         assert wt.value == w0.value
         for v in variants:
             assert L.aexp_workspace_size_tiled(ctypes.byref(p), prec, 8, v, ctypes.byref(wt)) == 0
-        top = 3 if prec == ax.FP32 else 2
+        top = 2
         assert L.aexp_workspace_size_tiled(ctypes.byref(p), prec, 0, top, ctypes.byref(wt)) == -1
         assert L.aexp_workspace_size_tiled(ctypes.byref(p), prec, 257, 0, ctypes.byref(wt)) == -1
         assert L.aexp_prepare_tiled(ctypes.byref(p), prec, 0, top, None, 0, None) == -1
-    # FP32 three-multiplication tiling: b carries three floats per voxel and coil instead of two
-    assert sizes[(ax.FP32, 16, 2)] >= sizes[(ax.FP32, 16)] + 4 * 32 * 200 * 200
     for bad in (-1, 257):
         o.items_per_sm = bad
         assert L.aexp_recon_workspace_size(ctypes.byref(p), ctypes.byref(o), ctypes.byref(n)) == -1
@@ -195,8 +192,6 @@ def test_items_per_sm_sizes_and_validation(L):
     variant = ctypes.c_int()
     assert L.aexp_autotune(arr, 2, ctypes.byref(o), None, 0, None, ctypes.byref(best), ctypes.byref(variant),
                            None) == -1
-    o.tile_variant = 2   # out of range for the tensor-core forms
+    o.tile_variant = 2   # out of range
     assert L.aexp_recon_workspace_size(ctypes.byref(p), ctypes.byref(o), ctypes.byref(n)) == -1
-    o.precision, o.tile_variant = ax.FP32, 3
-    assert L.aexp_recon_workspace_size(ctypes.byref(p), ctypes.byref(o), ctypes.byref(n)) == -1
-    o.precision, o.tile_variant = ax.BF16_TC, 0
+    o.tile_variant = 0

@@ -34,7 +34,7 @@ def test_autotune_single_problem(ax, precision):
     opts = ax.recon_opts(precision=prec, wavelet="haar", levels=3)
     best, variant, ms = ax.autotune(prob, opts)
     print(f"{precision}: items_per_sm {best}, tiling {variant}, {ms:.3f} ms per A^H A")
-    assert best in CANDIDATES and variant in ((0, 1, 2) if precision == "FP32" else (0, 1)) and ms > 0
+    assert best in CANDIDATES and variant in (0, 1) and ms > 0
     assert ax.autotune(prob, opts)[:2] == (best, variant)  # remembered for the shape
     Lf = recon.power_lipschitz(p, oracle.adjoint(p, y), 30)
     side = torch.cuda.Stream()
@@ -89,12 +89,12 @@ def test_autotune_refuses_capture(ax):
                 ax.autotune(prob, opts, ws=ws)
 
 
-@pytest.mark.parametrize("precision,tiling", [("FP32", 1), ("FP32", 2), ("BF16_TC", 1), ("FP16X2_TC", 1)])
-def test_tiling_variant_matches_oracle(ax, precision, tiling):
-    """The alternative tilings (FP32 at 32 coils: two samples / voxels per thread, or the complex
-    products as three real products; BF16: deeper rings; FP16 hi+lo: phases on the CUDA cores)
-    compute the same reconstruction: FP32 and FP16 hi+lo within the FP32 bar, BF16 within 3x
-    the oracle's BF16 rounding emulation, as the default tiling."""
+@pytest.mark.parametrize("precision", ["FP32", "BF16_TC", "FP16X2_TC"])
+def test_tiling_variant_matches_oracle(ax, precision):
+    """The alternative tiling (FP32 at 32 coils: two samples / voxels per thread; BF16: deeper
+    rings; FP16 hi+lo: phases on the CUDA cores) computes the same reconstruction: FP32 and FP16
+    hi+lo within the FP32 bar, BF16 within 3x the oracle's BF16 rounding emulation, as the
+    default tiling."""
     import torch
     import oracle
     from oracle import precision as prec_emul
@@ -109,7 +109,7 @@ def test_tiling_variant_matches_oracle(ax, precision, tiling):
     side = torch.cuda.Stream()
     with torch.cuda.stream(side):
         x, _ = ax.cs_recon(prob, torch.as_tensor(y, device="cuda"), lam, 10, precision=prec, wavelet="db4",
-                           levels=2, lipschitz=Lf, tile_variant=tiling)
+                           levels=2, lipschitz=Lf, tile_variant=1)
         torch.cuda.synchronize()
     ref = recon.fista(p, y, lam, 10, Lf, "db4", 2)
     e = rel(x.cpu().numpy(), ref)
@@ -117,5 +117,5 @@ def test_tiling_variant_matches_oracle(ax, precision, tiling):
         bar = 1e-5
     else:
         bar = 3.0 * rel(recon.fista(p, y, lam, 10, Lf, "db4", 2, ops=prec_emul.bf16_operators(p)), ref)
-    print(f"{precision} tiling {tiling}: image rel {e:.2e} (bar {bar:.2e})")
+    print(f"{precision} tiling 1: image rel {e:.2e} (bar {bar:.2e})")
     assert e < bar

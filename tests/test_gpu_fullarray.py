@@ -69,9 +69,10 @@ def _apply(ax, p, x, y, prec, tile_variant=0):
     return f.cpu().numpy(), a.cpu().numpy()
 
 
-@pytest.mark.parametrize("precision,tiling", [("FP32", 0), ("FP32", 2), ("FP16X2_TC", 0), ("BF16_TC", 0)])
+@pytest.mark.parametrize("precision,tiling", [(f, t) for f in ("FP32", "FP16X2_TC", "BF16_TC") for t in (0, 1)])
 def test_whole_array_matches_oracle(ax, case, precision, tiling):
-    """FP32 tiling 2: each complex multiply-accumulate as three real products."""
+    """Both tilings of every form (aexp_prepare_tiled): FP32 one or two samples / voxels per
+    thread, BF16 ring depths 4 / 3 or 6 / 4, FP16 hi+lo phases on the tensor or CUDA cores."""
     p, x, y, fref, aref = case
     f, a = _apply(ax, p, x, y, getattr(ax, precision), tiling)
     ef, ea = rel(f, fref), rel(a, aref)
