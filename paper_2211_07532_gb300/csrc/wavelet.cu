@@ -429,6 +429,9 @@ template <int TAPS>
 __device__ void mid_levels_cluster(float2 *__restrict__ approx, float2 *sm, int m1y, int m1x, int levels, float tau) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
+    // no CTA may write into another's shared memory before that CTA has started: arrive here,
+    // wait before the first distributed-shared-memory store
+    auto started = cl.barrier_arrive();
     const int rank = (int)cl.block_rank();
     const int n1 = m1y * m1x;
     float2 *X = sm, *Y = sm + n1, *B = sm + 2 * n1;
@@ -447,6 +450,7 @@ __device__ void mid_levels_cluster(float2 *__restrict__ approx, float2 *sm, int 
             });
     }
     __syncthreads();
+    cl.barrier_wait(std::move(started));
     float2 *P = X, *Q = Y;
     for (int j = 2; j <= levels; ++j) {
         const int my = m1y >> (j - 2), mx = m1x >> (j - 2);
