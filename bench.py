@@ -138,16 +138,27 @@ def sfu_peak_gops(sm_mhz: float) -> float:
     return 152 * 16 * sm_mhz * 1e6 / 1e9
 
 
-def launches_per_recon(levels: int, iters: int, n_power: int, form: str = "fp32") -> int:
-    """Kernel launches issued by cs_recon (mirrors the host sequence in recon.cu)."""
-    # one application: FP32 forward = coil weight + contraction + reduce, adjoint = contraction
-    # + reduce; tensor-core forms pack + persistent contraction + reduce each way, the FP16
-    # hi+lo form two more (max reset + max reduction) per packing
-    fwd, adj = {"fp32": (3, 2), "bf16": (3, 3), "fp16x2": (5, 5)}[form]
-    # coef, tiles, phases, coils; y transpose; descriptor + items; BF16: the two phase-GEMM operands
-    prep = 4 + 1 + {"fp32": 0, "bf16": 4, "fp16x2": 2}[form]
-    power = adj + 2 + n_power * (fwd + adj + 2) + 1  # A^H y; norm + scale; per iteration A^H A + dot + scale; finalize
-    fista = iters * (fwd + adj + 2 * levels)          # A^H (A z - y) + J analysis + J synthesis levels
+def launches_per_recon(levels: int, iters: int, n_power: int, form: str = "fp32", nx: int = 200,
+                       ny: int = 200) -> int:
+    """Kernel launches issued by cs_recon (mirrors the host sequence in recon.cu; checked against
+    the ncu launch lists of one solve in each form)."""
+    # one A^H A (power iteration or FISTA gradient step): FP32 coil weighting, contraction,
+    # reduction with the residual, contraction, reduction with the gradient step; BF16 packing,
+    # persistent contraction, fused reduction + residual + packing, persistent contraction,
+    # reduction; FP16 hi+lo in addition a max reset and a max reduction per packing and a
+    # separate packing of the residual
+    aha = {"fp32": 5, "bf16": 5, "fp16x2": 10}[form]
+    ahy = {"fp32": 2, "bf16": 3, "fp16x2": 5}[form]          # A^H y: the power iteration's start
+    # coefficients, tiles, reference phases, coils (+ BF16: phase-GEMM operands, descriptor,
+    # items; + FP16 hi+lo: the per-term scaling), then the transpose of y
+    prep = {"fp32": 4, "bf16": 8, "fp16x2": 9}[form] + 1
+    # wavelet prox step: level 1 each way plus levels 2..J in one launch where the level-1
+    # approximation fits the middle-level kernel's shared memory, else one launch per level each way
+    q = 1 << levels
+    npx, npy = -(-nx // q) * q, -(-ny // q) * q
+    prox = 3 if levels >= 2 and (npx // 2) * (npy // 2) <= 12800 else 2 * levels
+    power = ahy + 2 + n_power * (aha + 2) + 1            # A^H y; norm + scale; per iteration A^H A + norm + scale; finalize
+    fista = iters * (aha + prox)
     return prep + power + fista
 
 
@@ -544,7 +555,7 @@ def _run_ours(args, rank, world, local, dev):
             "device_status": status,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(y.numel() * 8),
                     "d2h_bytes_per_step": int(nr * 8), "s_per_slice": e2e_total / len(e2e_ms) / 1e3},
-            "gpu_launches": launches_per_recon(levels, iters, n_power, args.form) * args.steps,
+            "gpu_launches": launches_per_recon(levels, iters, n_power, args.form, p["nx"], p["ny"]) * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": dom,
                          "kernel_ms": kern[dom],

@@ -73,3 +73,17 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
         steps, warmup, ref_seconds = 1, 0, 0.01
     assert bench.run_reference(Args()) is None
     assert capsys.readouterr().out == ""
+
+
+def test_launch_count_matches_the_measured_launch_lists():
+    """`gpu_launches` counts the kernels of one solve; the counts per form are those of the ncu
+    launch lists of one 200^2 / J = 4 / 30 power + 50 FISTA solve (profiles/launches_slice200_*.md,
+    without the simulation's forward): FP32 620, BF16 625, FP16 hi+lo 1028."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.launches_per_recon(4, 50, 30, "fp32", 200, 200) == 620
+    assert bench.launches_per_recon(4, 50, 30, "bf16", 200, 200) == 625
+    assert bench.launches_per_recon(4, 50, 30, "fp16x2", 200, 200) == 1028
+    # images whose level-1 approximation exceeds the middle-level kernel: one launch per level each way
+    assert (bench.launches_per_recon(4, 50, 30, "fp32", 512, 512)
+            - bench.launches_per_recon(4, 50, 30, "fp32", 200, 200)) == 50 * (8 - 3)
