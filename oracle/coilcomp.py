@@ -2,8 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-Sec. 2.2.1 compresses the 32 receive channels to 20 virtual coils "to improve reconstruction
-speed" and Sec. 2.2.2 studies 8, 16 and 32 virtual coils; the method is not stated.  Reading:
+Sec. 2.2.1 reduces the 32 receive channels to 20 virtual coils so that the reconstruction runs
+faster, and Sec. 2.2.2 studies 8, 16 and 32 virtual coils; the method is not stated.  Reading:
 principal components of the measured data, the same matrix applied to data and coil maps:
     C = y y^H  (nc x nc, y: [nc][nt]),  C = U diag(e) U^H with e descending,
     every column u_k scaled by conj(u_ak*) / |u_ak*| where a* = argmax_a |u_ak| (lowest a on a
